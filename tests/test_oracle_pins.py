@@ -1,0 +1,206 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something
+other than itself (a closed form, an identity of analysis, a library routine
+on a special case, or an invariant), so that a dropped term, a wrong sign or
+index, or a transposed operand fails one of them."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import alg1, eigen, graph
+from paper_2007_05239_gb300 import workloads
+
+
+# ------------------------------------------------------------------ graph
+def test_two_points_closed_form():
+    # W = [[0, w], [w, 0]], w = exp(-r^2/sigma^2); L_sym = [[1,-1],[-1,1]].
+    r, sigma = 0.3, 0.2
+    X = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    w = math.exp(-r * r / sigma ** 2)
+    out = graph.W_apply(X, sigma, np.array([2.0, -3.0]))
+    assert np.allclose(out, [-3.0 * w, 2.0 * w], rtol=1e-15, atol=0)
+    L = graph.L_sym_dense(X, sigma)
+    assert np.allclose(L, [[1, -1], [-1, 1]], atol=1e-15)
+
+
+def test_regular_tetrahedron_closed_form():
+    # All pair distances equal (2 sqrt 2): W = w (11^T - I), deg = 3w,
+    # spectrum of L_sym = {0, 4/3, 4/3, 4/3}.
+    X = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+    sigma = 2.5
+    w = math.exp(-8.0 / sigma ** 2)
+    assert np.allclose(graph.degrees(X, sigma), 3 * w, rtol=1e-15)
+    lam, _ = eigen.lsym_eigs(X, sigma, 4)
+    assert np.allclose(lam, [0, 4 / 3, 4 / 3, 4 / 3], atol=1e-14)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_lattice_degree_poisson_summation(d):
+    # Centre of the lattice h*Z^d truncated to |k| <= M: by Poisson summation
+    # sum_{k in Z^d} exp(-|k h|^2/sigma^2) = (sigma sqrt(pi)/h)^d (1 + 2 sum_l e^{-pi^2 sigma^2 l^2/h^2})^d.
+    h, sigma, M = 1.0, 2.0, 10
+    g = np.arange(-M, M + 1, dtype=float) * h
+    X = np.stack(np.meshgrid(*([g] * d), indexing="ij"), axis=-1).reshape(-1, d)
+    centre = int(np.argmin((X ** 2).sum(axis=1)))
+    q = math.exp(-(math.pi * sigma / h) ** 2)
+    theta = (sigma * math.sqrt(math.pi) / h) * (1 + 2 * sum(q ** (l * l) for l in range(1, 5)))
+    expect = theta ** d - 1.0          # minus the excluded self term K(0) = 1
+    got = graph.degrees(X, sigma, rows=np.array([centre]))[0]
+    assert abs(got - expect) <= 1e-9 * expect
+
+
+def test_sigma_infinity_limit():
+    # W -> 11^T - I: A = W/(n-1) has eigenvalues 1 (once) and -1/(n-1).
+    X = workloads.uniform_cube(40, 2, seed=7)
+    n = X.shape[0]
+    L = graph.L_sym_dense(X, 1e7)
+    lam = np.linalg.eigvalsh(np.eye(n) - L)
+    assert abs(lam[-1] - 1.0) < 1e-10
+    assert np.allclose(lam[:-1], -1.0 / (n - 1), atol=1e-10)
+
+
+def test_normalised_operator_invariants():
+    X = workloads.uniform_cube(300, 3, seed=5)
+    sigma = 0.1
+    deg = graph.degrees(X, sigma)
+    s = np.sqrt(deg)
+    # A D^{1/2} 1 = D^{-1/2} W 1 = D^{1/2} 1
+    assert np.allclose(graph.A_apply(X, sigma, s, deg), s, rtol=1e-12)
+    L = graph.L_sym_dense(X, sigma)
+    assert abs(np.trace(L) - X.shape[0]) < 1e-10          # trace A = 0
+    # dense W against the C direct sum on a random vector
+    v = np.random.default_rng(0).standard_normal(300)
+    assert np.allclose(graph.weight_matrix(X, sigma) @ v, graph.W_apply(X, sigma, v), rtol=1e-12, atol=1e-12)
+
+
+def test_spectrum_bounds_and_null_vector():
+    X = workloads.uniform_cube(200, 3, seed=3)
+    sigma = 0.1
+    lam, Phi = eigen.lsym_eigs(X, sigma, 200)
+    assert lam.min() > -1e-12 and lam.max() < 2 + 1e-12
+    assert abs(lam[0]) < 1e-12
+    assert abs(lam.sum() - 200) < 1e-9
+    v0 = np.sqrt(graph.degrees(X, sigma))
+    v0 /= np.linalg.norm(v0)
+    assert abs(abs(Phi[:, 0] @ v0) - 1) < 1e-10
+
+
+def test_jacobi_matches_lapack():
+    X = workloads.uniform_cube(60, 3, seed=11)
+    L = graph.L_sym_dense(X, 0.12)
+    lj, Vj = eigen.jacobi_eigh(L)
+    le, Ve = np.linalg.eigh(L)
+    assert np.allclose(lj, le, atol=1e-12)
+    # eigenvector check through residuals (independent of sign/order ties)
+    assert np.abs(L @ Vj - Vj * lj[None, :]).max() < 1e-11
+    # closed 2x2 case
+    lam, _ = eigen.jacobi_eigh(np.array([[2.0, 1.0], [1.0, 2.0]]))
+    assert np.allclose(lam, [1.0, 3.0], atol=1e-15)
+
+
+def test_power_mean_identical_layers():
+    # T identical layers: L_{p,delta} = L_sym + delta I for every p; p=1 gives L_sym.
+    X = workloads.uniform_cube(80, 2, seed=4)
+    lam, _ = eigen.lsym_eigs(X, 0.15, 6)
+    lp, _ = eigen.Lp_eigs([X, X, X], [0.15] * 3, -1.0, 6)
+    assert np.allclose(lp, lam + math.log(2.0), atol=1e-10)
+    l1, _ = eigen.L1_eigs([X, X], [0.15] * 2, 6)
+    assert np.allclose(l1, lam, atol=1e-12)
+
+
+def test_power_mean_two_commuting_layers():
+    # Any connected 2-node graph has L_sym = [[1,-1],[-1,1]] with spectrum {0, 2},
+    # whatever its weight; so two such layers give L_{-1,delta} = L_sym + delta I
+    # with eigenvalues {delta, 2 + delta}, delta = log 2.
+    X = np.array([[0.0], [0.3]])
+    lp, _ = eigen.Lp_eigs([X, X * 2], [0.2, 0.5], -1.0, 2)
+    assert np.allclose(lp, [math.log(2), 2 + math.log(2)], atol=1e-12)
+
+
+# ------------------------------------------------------------------ Alg. 1
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_bhat_box_matches_poisson(d):
+    # Samples of exp(-y^2/s^2) on the period cube: b_l = prod_a sum_r c(l_a + rN)
+    # with c(x) = s sqrt(pi) exp(-pi^2 s^2 x^2) (Fourier transform of the
+    # Gaussian, aliased by sampling), up to the wrap term exp(-1/(4 s^2)).
+    s, N = 0.07, 16
+    b = alg1.bhat(s, N, d)
+    l = np.arange(-N // 2, N // 2)
+    c1 = sum(s * math.sqrt(math.pi) * np.exp(-(math.pi * s * (l + r * N)) ** 2) for r in range(-3, 4))
+    expect = c1
+    for _ in range(d - 1):
+        expect = np.multiply.outer(expect, c1)
+    assert np.abs(b - expect).max() < 1e-14
+
+
+def test_adjoint_ndft_on_grid_is_fft():
+    # Nodes on the equispaced grid k/N: step 1 of Alg. 1 is a plain DFT.
+    N = 8
+    k = np.arange(-N // 2, N // 2)
+    Xs = (np.stack(np.meshgrid(k, k, indexing="ij"), -1).reshape(-1, 2)) / N
+    v = np.random.default_rng(1).standard_normal(Xs.shape[0])
+    got = alg1.adjoint_ndft(Xs, v, N)
+    V = v.reshape(N, N)
+    F = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(V)))
+    assert np.allclose(got, F, atol=1e-12)
+    # and step 3 is the inverse DFT times N^d
+    back = alg1.ndft(Xs, F, N).reshape(N, N)
+    assert np.allclose(back, N * N * V, atol=1e-9)
+
+
+def _tail_bound(s, N, d):
+    """Bound on max |K_RF - K| over the domain for the box reading:
+    per dimension twice the Fourier tail beyond N/2 plus the wrap term, times d."""
+    tail = 2 * sum(s * math.sqrt(math.pi) * math.exp(-(math.pi * s * l) ** 2) for l in range(N // 2, N // 2 + 200))
+    wrap = 2 * math.exp(-0.25 / s ** 2)
+    return 3 * d * (2 * tail + wrap)
+
+
+@pytest.mark.parametrize("d,N", [(1, 32), (2, 24), (3, 16)])
+def test_alg1_against_direct_sum(d, N):
+    X = workloads.uniform_cube(400, d, seed=21)
+    sigma = 0.12
+    Xs, ss, _, _ = alg1.scale_to_domain(X, sigma, eps_B=0.0, eps_wrap=1e-12)
+    assert np.abs(Xs).max() <= 0.25 + 1e-15
+    v = np.random.default_rng(2).uniform(0, 1, X.shape[0])
+    b = alg1.bhat(ss, N, d)
+    got = alg1.fastsum_W(Xs, v, b)
+    ref = graph.W_apply(X, sigma, v)
+    bound = _tail_bound(ss, N, d) * np.abs(v).sum()
+    err = np.abs(got - ref).max()
+    assert err <= bound
+    # a coarser bandwidth must be visibly worse (the comparison has teeth)
+    b2 = alg1.bhat(ss, N // 2, d)
+    err2 = np.abs(alg1.fastsum_W(Xs, v, b2) - ref).max()
+    assert err2 > 10 * err
+
+
+def test_regulariser_matching_conditions():
+    sigma, eps_B, p = 0.3, 1.0 / 16, 4
+    rI = 0.5 - eps_B
+    q = alg1.regulariser_poly(sigma, eps_B, p)
+    P = np.polynomial.Polynomial(q)
+    dK = alg1._gauss_derivs(rI, sigma, p)
+    # derivatives k at t=0 equal eps^k K^{(k)}(r_I) (finite differences of the
+    # closed-form Gaussian as an independent check of _gauss_derivs)
+    hstep = 1e-4
+    fd1 = (math.exp(-(rI + hstep) ** 2 / sigma ** 2) - math.exp(-(rI - hstep) ** 2 / sigma ** 2)) / (2 * hstep)
+    assert abs(fd1 - dK[1]) < 1e-7
+    for k in range(p):
+        assert abs(P.deriv(k)(0.0) - dK[k] * eps_B ** k) < 1e-12 * max(1.0, abs(dK[k]))
+    assert abs(P(1.0) - math.exp(-0.25 / sigma ** 2)) < 1e-14
+    for k in range(1, p):
+        assert abs(P.deriv(k)(1.0)) < 1e-9
+    # inside the ball K_R is the Gaussian
+    r = np.linspace(0, rI, 7)
+    assert np.allclose(alg1.K_R(r, sigma, eps_B, p), np.exp(-r ** 2 / sigma ** 2), rtol=1e-15)
+
+
+def test_ball_domain_scaling():
+    X = workloads.uniform_cube(500, 3, seed=8)
+    Xs, ss, c, s = alg1.scale_to_domain(X, 0.1, eps_B=1.0 / 16)
+    assert np.sqrt((Xs ** 2).sum(1)).max() <= 0.25 - 1.0 / 32 + 1e-15
+    assert abs(ss - 0.1 * s) < 1e-16
+    # pairwise distances stay below 1/2 - eps_B
+    D = np.sqrt(((Xs[:, None] - Xs[None]) ** 2).sum(-1))
+    assert D.max() <= 0.5 - 1.0 / 16 + 1e-14
