@@ -1,0 +1,197 @@
+/*
+ * ml_fastsum.h - C ABI of the GB300 multilayer Gaussian-graph fast summation
+ * and Lanczos eigensolver.
+ *
+ * What is computed (Bergermann, Stoll, Volkmer, "Semi-supervised learning for
+ * aggregated multilayer graphs using diffuse interface methods and fast
+ * matrix vector products"):
+ *   - per layer t, the fully connected graph on n points x_i in R^{d_t},
+ *     d_t in {1,2,3}, with weights W_ij = exp(-||x_i - x_j||^2 / sigma_t^2),
+ *     i != j, and zero diagonal (Sec. 2, Sec. 4);
+ *   - the product W_t v by NFFT-based fast summation (Alg. 1), using
+ *     W = W~ - K(0) I with K(0) = 1 (Sec. 4);
+ *   - degrees D_t = diag(W_t 1) and the normalised operator
+ *     D_t^{-1/2} W_t D_t^{-1/2} = I - L_sym^(t) (Sec. 2);
+ *   - the multilayer operator I - L_1 = (1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2}
+ *     (Eq. I-L_1) and the shifted power mean L_{p,delta}^p (Eq.
+ *     L_p_delta_power_p, delta = log(1+|p|) for p < 0);
+ *   - the k smallest eigenpairs of L_1 or L_{p,delta} by the Lanczos method
+ *     (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - Pointers are plain addresses; the caller owns every buffer it passes.
+ *     "device" means memory of the current CUDA device; "host or device"
+ *     arguments are detected with cudaPointerGetAttributes and staged
+ *     through plan-owned device buffers when they live on the host.
+ *   - Matrices of n points / n-vectors are row-major and point-major:
+ *     element (i, c) of an n x b block is at [i*b + c].
+ *   - All layers passed together must share n and the node order.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it unless stated otherwise.
+ *   - No exception crosses the ABI.  On failure the call returns a non-zero
+ *     ml_status and ml_last_error() describes the cause (thread-local).
+ *   - The library never falls back to the CPU: without a usable GPU every
+ *     call returns ML_ERR_CUDA.
+ */
+#ifndef ML_FASTSUM_H
+#define ML_FASTSUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ml_plan_s *ml_plan_t; /* opaque, library-owned */
+
+typedef enum {
+    ML_OK = 0,
+    ML_ERR_ARG = 1,        /* invalid argument (null pointer, size, mode...) */
+    ML_ERR_CUDA = 2,       /* a CUDA call failed, or no usable GPU */
+    ML_ERR_OOM = 3,        /* device allocation failed */
+    ML_ERR_DOMAIN = 4,     /* the requested accuracy needs a grid beyond the limits */
+    ML_ERR_DEGREE = 5,     /* a degree D_i is not positive/finite: D^{-1/2} undefined */
+    ML_ERR_BREAKDOWN = 6,  /* Lanczos could not extend the Krylov basis */
+    ML_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up */
+    ML_WARN_NOT_CONVERGED = 8 /* Lanczos stopped at maxit with nconv < k */
+} ml_status;
+
+typedef enum {
+    ML_F32 = 0, /* window weights, spreading, grid transforms, interpolation in FP32 */
+    ML_F64 = 1  /* the same steps in FP64 */
+} ml_prec;
+/* In both precisions the degree normalisation, the multilayer accumulation,
+ * the output vectors and every Lanczos quantity are FP64. */
+
+/* apply modes */
+#define ML_RAW_W 0        /* Y = (1/T) sum_t W_t X                          */
+#define ML_NORMALIZED_A 1 /* Y = (1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2} X    */
+#define ML_DEGREE 2       /* Y = (1/T) sum_t D_t  (X unused, b must be 1)   */
+#define ML_PER_LAYER 16   /* flag: X, Y hold T blocks of n x b; block t of Y
+                             gets layer t's operator applied to block t of X
+                             (no 1/T, no sum) */
+
+/* Plan parameters chosen (or accepted) for one layer; see ml_plan_get_info. */
+typedef struct {
+    int64_t n;
+    int d;
+    int N;              /* bandwidth of K_RF, I_N = {-N/2..N/2-1}^d (Eq. K_RF)  */
+    int m;              /* window half-width in grid cells (2m taps per dim)    */
+    int n_os;           /* oversampled grid size per dim (torus of n_os cells)  */
+    int L[3];           /* active grid extent per dim (cells that can be nonzero) */
+    int bin;            /* spreading tile (bin) edge in cells                   */
+    int nbins;          /* bins over the active grid                            */
+    int nsub;           /* subproblems (point chunks of one bin)                */
+    int prec;           /* ml_prec                                              */
+    int domain;         /* 0 = box (periodised Gaussian), 1 = ball (eps_B > 0)  */
+    int p_reg;          /* regularisation degree (ball domain)                  */
+    double eps_B;       /* regularisation length (ball domain)                  */
+    double sigma;       /* kernel width in input units                          */
+    double sigma_s;     /* kernel width after scaling into the Alg. 1 domain    */
+    double scale;       /* x' = scale * (x - center)                            */
+    double center[3];
+    double target_rel_err;
+    double deg_min, deg_max; /* range of the computed degrees                    */
+    int64_t device_bytes;    /* device memory owned by the plan                  */
+} ml_plan_info;
+
+/*
+ * ml_fastsum_plan - set up one layer's fast summation (Alg. 1 input, Sec. 4)
+ * and compute its degrees (Sec. 2).
+ *
+ *   out            receives the plan handle (caller destroys it).
+ *   points         device, n x d row-major FP64, read during the call only.
+ *   n, d           n >= 2, d in {1,2,3}.
+ *   sigma          Gaussian width > 0 in the units of `points`.
+ *   N              bandwidth (even, 4..512), or 0 to choose from target_rel_err.
+ *   m              window half-width (2..8), or 0 to choose from target_rel_err.
+ *   eps_B, p_reg   eps_B = 0: box domain (periodised Gaussian, no regulariser);
+ *                  0 < eps_B < 1/2: ball domain with the regularised kernel
+ *                  K_R of degree 2*p_reg-1 on (1/2-eps_B, 1/2], p_reg in 1..8.
+ *   prec           ML_F32 or ML_F64.
+ *   target_rel_err accuracy the automatic choices aim at (<= 0: 1e-4 for
+ *                  ML_F32, 1e-6 for ML_F64).
+ *   stream         cudaStream_t used for the set-up kernels.
+ * The call synchronises `stream` (it reads bounding boxes and bin counts back
+ * to the host).  Errors: ML_ERR_ARG, ML_ERR_DOMAIN (grid beyond limits),
+ * ML_ERR_DEGREE (a degree <= 0 or non-finite), ML_ERR_OOM, ML_ERR_CUDA.
+ */
+ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
+                          int N, int m, double eps_B, int p_reg, ml_prec prec,
+                          double target_rel_err, void *stream);
+
+/*
+ * ml_fastsum_apply - Y = multilayer operator applied to X (Alg. 1 per layer,
+ * then the D^{-1/2} scaling and the 1/T sum of Eq. I-L_1).
+ *
+ *   layers, T   T >= 1 plans sharing n.
+ *   X           host or device, n x b FP64 (T blocks with ML_PER_LAYER);
+ *               ignored for ML_DEGREE.
+ *   b           vectors per block, 1..64.
+ *   Y           host or device, n x b FP64 (T blocks with ML_PER_LAYER),
+ *               overwritten.  Must not overlap X.
+ *   mode        ML_RAW_W, ML_NORMALIZED_A or ML_DEGREE, optionally | ML_PER_LAYER.
+ * Asynchronous on `stream` for device X and Y; with host X or Y the call
+ * copies through plan-owned buffers and synchronises `stream`.  Two calls
+ * that use the same plan must not run concurrently (they share its
+ * workspace).  Errors: ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA.
+ */
+ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int b, double *Y,
+                           int mode, void *stream);
+
+/*
+ * ml_lanczos_eigs - the k smallest eigenpairs of the power mean Laplacian of
+ * the T layers by thick-restart Lanczos with full reorthogonalisation (Sec. 3).
+ *
+ *   p == 1   eigenpairs of L_1: the k largest theta of I - L_1 (Eq. I-L_1),
+ *            lambda = 1 - theta.
+ *   p == -1  eigenpairs of L_{-1,delta}, delta = log 2: the k largest mu of
+ *            L_{-1,delta}^{-1} = (1/T) sum_t (L_sym^(t) + delta I)^{-1}
+ *            (Eq. L_p_delta_power_p), each term applied by an inner conjugate
+ *            gradient solve driven by the fast summation; lambda = 1/mu.
+ *   tol      relative residual ||A phi - theta phi|| <= tol * |theta_max|
+ *            (<= 0: 1e-10).
+ *   maxit    limit on outer operator applications (<= 0: 2000).
+ *   block    1 (single-vector Lanczos); reserved for block variants.
+ *   seed     seed of the start vector (SplitMix64 counter stream).
+ *   evals    host, k FP64: ascending eigenvalues lambda of L_1 / L_{p,delta}.
+ *   evecs    host or device, n x k FP64, column-major (column j contiguous),
+ *            unit 2-norm, sign fixed so the largest-magnitude entry is
+ *            positive; may be NULL.
+ *   nconv    host, number of converged pairs (may be NULL).
+ * Synchronises `stream`.  Returns ML_WARN_NOT_CONVERGED when maxit is reached
+ * with fewer than k converged pairs (evals/evecs then hold the best Ritz
+ * pairs); ML_ERR_ARG for k < 1, k > n/2, p not in {1, -1}.
+ */
+ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, double tol, int maxit,
+                          int block, uint64_t seed, double *evals, double *evecs, int *nconv,
+                          void *stream);
+
+/* Copy the plan's parameters into *info (host).  Never fails on a valid plan. */
+ml_status ml_plan_get_info(ml_plan_t plan, ml_plan_info *info);
+
+/*
+ * ml_plan_copy_table - copy one of the plan's host-side FP64 tables (for
+ * tests and inspection):
+ *   which = 0: b_l for l = 0..N/2 in every dim, (N/2+1)^d values, dim 0 fastest
+ *              (the Fourier coefficients of K_RF, Eq. K_RF; b_l is even in each l_a)
+ *   which = 1: the window's Fourier coefficients phi_hat(k), k = 0..N/2
+ *   which = 2: the degrees D_i in input order (n values)
+ * `out` is host memory of `count` doubles; count must be at least the size.
+ */
+ml_status ml_plan_copy_table(ml_plan_t plan, int which, double *out, int64_t count);
+
+/* Release the plan and all device memory it owns.  NULL is accepted. */
+ml_status ml_plan_destroy(ml_plan_t plan);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *ml_last_error(void);
+
+/* Library version string. */
+const char *ml_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ML_FASTSUM_H */

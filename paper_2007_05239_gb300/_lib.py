@@ -1,0 +1,198 @@
+"""Thin Python binding of the C ABI in include/ml_fastsum.h.
+
+Argument marshalling only: every step of the fast summation and of the
+eigensolver runs in the CUDA library libmlfastsum.so.  There is no CPU
+fallback; without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmlfastsum.so")
+
+ML_OK, ML_ERR_ARG, ML_ERR_CUDA, ML_ERR_OOM, ML_ERR_DOMAIN, ML_ERR_DEGREE, ML_ERR_BREAKDOWN, \
+    ML_ERR_TIMEOUT, ML_WARN_NOT_CONVERGED = range(9)
+STATUS_NAMES = ["ML_OK", "ML_ERR_ARG", "ML_ERR_CUDA", "ML_ERR_OOM", "ML_ERR_DOMAIN", "ML_ERR_DEGREE",
+                "ML_ERR_BREAKDOWN", "ML_ERR_TIMEOUT", "ML_WARN_NOT_CONVERGED"]
+ML_F32, ML_F64 = 0, 1
+ML_RAW_W, ML_NORMALIZED_A, ML_DEGREE, ML_PER_LAYER = 0, 1, 2, 16
+MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
+
+# every symbol the header declares
+EXPORTS = ["ml_fastsum_plan", "ml_fastsum_apply", "ml_lanczos_eigs", "ml_plan_get_info",
+           "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version"]
+
+
+class MLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int), ("N", ctypes.c_int), ("m", ctypes.c_int),
+                ("n_os", ctypes.c_int), ("L", ctypes.c_int * 3), ("bin", ctypes.c_int), ("nbins", ctypes.c_int),
+                ("nsub", ctypes.c_int), ("prec", ctypes.c_int), ("domain", ctypes.c_int), ("p_reg", ctypes.c_int),
+                ("eps_B", ctypes.c_double), ("sigma", ctypes.c_double), ("sigma_s", ctypes.c_double),
+                ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("target_rel_err", ctypes.c_double),
+                ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+_LIB = None
+
+
+def load():
+    """Load libmlfastsum.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_2007_05239_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.ml_fastsum_plan.restype = ctypes.c_int
+    lib.ml_fastsum_plan.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, P]
+    lib.ml_fastsum_apply.restype = ctypes.c_int
+    lib.ml_fastsum_apply.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P]
+    lib.ml_lanczos_eigs.restype = ctypes.c_int
+    lib.ml_lanczos_eigs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P, P, P]
+    lib.ml_plan_get_info.restype = ctypes.c_int
+    lib.ml_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.ml_plan_copy_table.restype = ctypes.c_int
+    lib.ml_plan_copy_table.argtypes = [P, ctypes.c_int, P, ctypes.c_int64]
+    lib.ml_plan_destroy.restype = ctypes.c_int
+    lib.ml_plan_destroy.argtypes = [P]
+    lib.ml_last_error.restype = ctypes.c_char_p
+    lib.ml_last_error.argtypes = []
+    lib.ml_version.restype = ctypes.c_char_p
+    lib.ml_version.argtypes = []
+    _LIB = lib
+    return lib
+
+
+def _check(st):
+    if st == ML_OK:
+        return st
+    msg = load().ml_last_error().decode()
+    if st == ML_WARN_NOT_CONVERGED:
+        warnings.warn(f"ML_WARN_NOT_CONVERGED: {msg}")
+        return st
+    raise MLError(st, msg)
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (contiguous float64)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("numpy arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """One layer's plan (owns library memory until destroy())."""
+
+    def __init__(self, handle, n, d):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+        self.d = d
+
+    @property
+    def info(self):
+        inf = PlanInfo()
+        _check(load().ml_plan_get_info(self.handle, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def table(self, which):
+        inf = self.info
+        H = inf["N"] // 2 + 1
+        size = {0: H ** inf["d"], 1: H, 2: inf["n"]}[which]
+        out = np.empty(size, dtype=np.float64)
+        _check(load().ml_plan_copy_table(self.handle, which, out.ctypes.data, size))
+        return out
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            load().ml_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ml_fastsum_plan(points, sigma, N=0, m=0, eps_B=0.0, p_reg=0, prec="f64", target_rel_err=0.0, stream=None):
+    """Plan one layer.  `points`: CUDA float64 tensor (n, d)."""
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    h = ctypes.c_void_p()
+    pr = {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec)
+    _check(lib.ml_fastsum_plan(ctypes.byref(h), _ptr(points), n, d, float(sigma), int(N), int(m), float(eps_B),
+                               int(p_reg), pr, float(target_rel_err), _stream(stream)))
+    return Plan(h.value, n, d)
+
+
+def _handles(layers):
+    arr = (ctypes.c_void_p * len(layers))(*[p.handle.value for p in layers])
+    return arr
+
+
+def ml_fastsum_apply(layers, X, Y, mode="normalized", per_layer=False, stream=None):
+    """Y <- operator(X).  X, Y: float64 torch tensors (CUDA or CPU) or numpy arrays, shape (n, b)
+    or (T, n, b) with per_layer.  Y is overwritten."""
+    lib = load()
+    md = MODES[mode] if isinstance(mode, str) else int(mode)
+    if per_layer:
+        md |= ML_PER_LAYER
+    b = 1 if len(Y.shape) == (2 if per_layer else 1) else int(Y.shape[-1])
+    arr = _handles(layers)
+    _check(lib.ml_fastsum_apply(arr, len(layers), _ptr(X), b, _ptr(Y), md, _stream(stream)))
+    return Y
+
+
+def ml_lanczos_eigs(layers, k, p=1.0, tol=0.0, maxit=0, seed=0, evecs=None, stream=None, block=1):
+    """k smallest eigenpairs of L_1 (p=1) or L_{-1,delta} (p=-1).
+
+    evecs: None, or a float64 buffer with n*k elements (CUDA or CPU) that
+    receives the eigenvectors column-major.  Returns (evals, nconv, status)."""
+    lib = load()
+    ev = np.empty(k, dtype=np.float64)
+    nconv = ctypes.c_int(0)
+    arr = _handles(layers)
+    st = lib.ml_lanczos_eigs(arr, len(layers), int(k), float(p), float(tol), int(maxit), int(block),
+                             ctypes.c_uint64(seed), ev.ctypes.data, _ptr(evecs), ctypes.byref(nconv),
+                             _stream(stream))
+    _check(st)
+    return ev, nconv.value, st
+
+
+def version():
+    return load().ml_version().decode()

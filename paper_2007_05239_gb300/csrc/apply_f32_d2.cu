@@ -1,0 +1,9 @@
+// F32 form of one layer's fast summation for d = 2 (kernels in kernels.cuh).
+#include "launch.cuh"
+
+namespace ml {
+ml_status run_layer_f32_d2(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    return run_layer_d<float, 2>(p, v, o, st);
+}
+}  // namespace ml

@@ -1,0 +1,9 @@
+// F64 form of one layer's fast summation for d = 1 (kernels in kernels.cuh).
+#include "launch.cuh"
+
+namespace ml {
+ml_status run_layer_f64_d1(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    return run_layer_d<double, 1>(p, v, o, st);
+}
+}  // namespace ml

@@ -1,0 +1,154 @@
+// ml_fastsum_apply: the multilayer operator of Eq. I-L_1 (or the raw W, or
+// the degrees) applied to a block of vectors, one layer after another on the
+// caller's stream so that the FP64 output accumulates in a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "ml_internal.h"
+
+namespace ml {
+
+#define ML_DECL_LAYER(P, D) \
+    ml_status run_layer_##P##_d##D(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+ML_DECL_LAYER(f32, 1)
+ML_DECL_LAYER(f32, 2)
+ML_DECL_LAYER(f32, 3)
+ML_DECL_LAYER(f64, 1)
+ML_DECL_LAYER(f64, 2)
+ML_DECL_LAYER(f64, 3)
+
+ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
+    ML_TRY(ensure_workspace(p, v.nv));
+    if (p->prec == ML_F32) {
+        switch (p->d) {
+        case 1: return run_layer_f32_d1(p, v, o, st);
+        case 2: return run_layer_f32_d2(p, v, o, st);
+        default: return run_layer_f32_d3(p, v, o, st);
+        }
+    }
+    switch (p->d) {
+    case 1: return run_layer_f64_d1(p, v, o, st);
+    case 2: return run_layer_f64_d2(p, v, o, st);
+    default: return run_layer_f64_d3(p, v, o, st);
+    }
+}
+
+// vectors in the next pass: 8 or 4 when the plan's tile holds them and the
+// window is small (M <= 4), else 1
+int pass_width(const ml_plan_s *p, int remaining)
+{
+    if (p->m <= 4) {
+        if (remaining >= 8 && p->vp >= 8) return 8;
+        if (remaining >= 4 && p->vp >= 4) return 4;
+    }
+    return 1;
+}
+
+// Y[perm[i]] = (accumulate ? Y : 0) + alpha * deg[i]
+__global__ void k_degree_out(const double *__restrict__ deg, const int *__restrict__ perm, int64_t n, double alpha,
+                             int accumulate, double *Y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double *y = Y + perm[i];
+        *y = (accumulate ? *y : 0.0) + alpha * deg[i];
+    }
+}
+
+static bool is_device_ptr(const void *ptr)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unregistered pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Apply on device buffers (no staging).
+ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, double *Y, int mode,
+                       cudaStream_t st)
+{
+    const int64_t n = layers[0]->n;
+    const bool per_layer = (mode & ML_PER_LAYER) != 0;
+    const int base = mode & ~ML_PER_LAYER;
+    if (base == ML_DEGREE) {
+        if (b != 1) return fail(ML_ERR_ARG, "ML_DEGREE needs b = 1");
+        for (int t = 0; t < T; ++t) {
+            double *Yt = per_layer ? Y + (int64_t)t * n : Y;
+            const double alpha = per_layer ? 1.0 : 1.0 / T;
+            const int acc = (!per_layer && t > 0) ? 1 : 0;
+            const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+            k_degree_out<<<blocks, 256, 0, st>>>(layers[t]->deg.as<double>(), layers[t]->perm.as<int>(), n, alpha,
+                                                 acc, Yt);
+            ML_CUDA(cudaGetLastError());
+        }
+        return ML_OK;
+    }
+    for (int t = 0; t < T; ++t) {
+        ml_plan_s *p = layers[t];
+        const double *Xt = per_layer ? X + (int64_t)t * n * b : X;
+        double *Yt = per_layer ? Y + (int64_t)t * n * b : Y;
+        for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+            nv = pass_width(p, b - c0);
+            ApplyVec v{Xt + c0, b, Yt + c0, b, nv};
+            ApplyOpts o;
+            o.normalized = base == ML_NORMALIZED_A;
+            o.accumulate = !per_layer && t > 0;
+            o.alpha = per_layer ? 1.0 : 1.0 / T;
+            ML_TRY(apply_layer(p, v, o, st));
+        }
+    }
+    return ML_OK;
+}
+
+}  // namespace ml
+
+extern "C" ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int b, double *Y, int mode,
+                                      void *stream)
+{
+    using namespace ml;
+    if (!layers || T < 1) return fail(ML_ERR_ARG, "layers is null or T < 1");
+    for (int t = 0; t < T; ++t)
+        if (!layers[t]) return fail(ML_ERR_ARG, "layer " + std::to_string(t) + " is null");
+    const int64_t n = layers[0]->n;
+    for (int t = 1; t < T; ++t)
+        if (layers[t]->n != n) return fail(ML_ERR_ARG, "layers do not share n");
+    if (b < 1 || b > 64) return fail(ML_ERR_ARG, "b must be in [1, 64]");
+    const int base = mode & ~ML_PER_LAYER;
+    if ((mode & ~(ML_PER_LAYER | 3)) != 0 || base > ML_DEGREE) return fail(ML_ERR_ARG, "unknown mode");
+    if (!Y) return fail(ML_ERR_ARG, "Y is null");
+    if (base != ML_DEGREE && !X) return fail(ML_ERR_ARG, "X is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool per_layer = (mode & ML_PER_LAYER) != 0;
+    const int64_t elems = n * b * (per_layer ? T : 1);
+    const bool x_dev = base == ML_DEGREE || is_device_ptr(X);
+    const bool y_dev = is_device_ptr(Y);
+    {
+        // the output buffer must not overlap the input
+        const char *xb = (const char *)X, *yb = (const char *)Y;
+        const size_t bytes = (size_t)elems * sizeof(double);
+        if (X && xb < yb + bytes && yb < xb + bytes) return fail(ML_ERR_ARG, "X and Y overlap");
+    }
+    ml_plan_s *p0 = layers[0];
+    const double *Xd = X;
+    double *Yd = Y;
+    if (!x_dev) {
+        ML_TRY(p0->stage_x.ensure((size_t)elems * sizeof(double)));
+        ML_CUDA(cudaMemcpyAsync(p0->stage_x.p, X, (size_t)elems * sizeof(double), cudaMemcpyHostToDevice, st));
+        Xd = p0->stage_x.as<double>();
+    }
+    if (!y_dev) {
+        ML_TRY(p0->stage_y.ensure((size_t)elems * sizeof(double)));
+        Yd = p0->stage_y.as<double>();
+    }
+    ML_TRY(apply_device(layers, T, Xd, b, Yd, mode, st));
+    if (!y_dev) {
+        ML_CUDA(cudaMemcpyAsync(Y, Yd, (size_t)elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (!x_dev || !y_dev) ML_CUDA(cudaStreamSynchronize(st));
+    return ML_OK;
+}

@@ -1,0 +1,292 @@
+// Host-side FP64 tables of the plan: window Fourier coefficients, kernel
+// Fourier coefficients b_l (Eq. K_RF and the footnote to Sec. 4), the
+// regulariser of the ball domain, the coefficient-slot multiplier and the
+// real trigonometric transform matrices; plus a small dense symmetric
+// eigensolver for the Lanczos projection.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ml_internal.h"
+
+namespace ml {
+
+static const double kPi = 3.14159265358979323846;
+
+// I_0(x) = sum_k (x/2)^{2k} / (k!)^2 (Abramowitz & Stegun 9.6.12); all terms
+// are positive, so the partial sums converge monotonically in FP64.
+double bessel_i0(double x)
+{
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// The Kaiser-Bessel pair used by the NFFT (window phi with shape
+// b = pi (2 - 1/sigma_os)):  phi(x) = (1/pi) sinh(b sqrt(m^2 - n^2 x^2)) /
+// sqrt(m^2 - n^2 x^2) on |x| <= m/n, with Fourier transform
+// phi_hat(k) = (1/n) I_0(m sqrt(b^2 - (2 pi k / n)^2)) for |k| <= n(1 - 1/(2 sigma_os)).
+// The device evaluates the normalised window phi_n = pi m / sinh(b m) * phi
+// (phi_n(0) = 1), so its coefficients carry the same factor.
+void window_fourier(int n_os, int m, double b, int kmax, std::vector<double> &out)
+{
+    out.assign(kmax + 1, 0.0);
+    const double c = kPi * m / std::sinh(b * m);
+    for (int k = 0; k <= kmax; ++k) {
+        const double w = 2.0 * kPi * k / n_os;
+        const double arg = b * b - w * w;
+        out[k] = arg > 0 ? c * bessel_i0(m * std::sqrt(arg)) / n_os : 0.0;
+    }
+}
+
+// Physicists' Hermite recursion for the derivatives of exp(-r^2/s^2):
+// d^k/dr^k = (-1)^k s^{-k} H_k(r/s) exp(-(r/s)^2).
+static void gauss_derivs(double r, double s, int p, std::vector<double> &dk)
+{
+    const double z = r / s;
+    std::vector<double> H(p + 1);
+    H[0] = 1.0;
+    if (p >= 1) H[1] = 2.0 * z;
+    for (int k = 1; k < p; ++k) H[k + 1] = 2.0 * z * H[k] - 2.0 * k * H[k - 1];
+    const double e = std::exp(-z * z);
+    dk.assign(p, 0.0);
+    for (int k = 0; k < p; ++k) dk[k] = ((k & 1) ? -1.0 : 1.0) * std::pow(s, -k) * H[k] * e;
+}
+
+// Solve A x = rhs (n x n, row-major) by Gaussian elimination with partial pivoting.
+static bool solve_dense(int n, std::vector<double> A, std::vector<double> &x)
+{
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * (n + 1) + c]) > std::fabs(A[piv * (n + 1) + c])) piv = r;
+        if (A[piv * (n + 1) + c] == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j <= n; ++j) std::swap(A[c * (n + 1) + j], A[piv * (n + 1) + j]);
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r * (n + 1) + c] / A[c * (n + 1) + c];
+            for (int j = c; j <= n; ++j) A[r * (n + 1) + j] -= f * A[c * (n + 1) + j];
+        }
+    }
+    x.assign(n, 0.0);
+    for (int r = n - 1; r >= 0; --r) {
+        double s = A[r * (n + 1) + n];
+        for (int j = r + 1; j < n; ++j) s -= A[r * (n + 1) + j] * x[j];
+        x[r] = s / A[r * (n + 1) + r];
+    }
+    return true;
+}
+
+// Regulariser of the ball domain: on t = (r - r_I)/eps_B in [0, 1], a
+// polynomial of degree 2p-1 whose derivatives 0..p-1 at t = 0 equal those of
+// the Gaussian at r_I = 1/2 - eps_B (chain rule factor eps_B^k), whose value
+// at t = 1 is K(1/2) and whose derivatives 1..p-1 vanish at t = 1.
+bool regulariser_coeffs(double s, double eps_B, int p, std::vector<double> &q)
+{
+    const int n = 2 * p;
+    const double rI = 0.5 - eps_B;
+    std::vector<double> dK;
+    gauss_derivs(rI, s, p, dK);
+    std::vector<double> A((size_t)n * (n + 1), 0.0);
+    for (int k = 0; k < p; ++k) {
+        for (int j = k; j < n; ++j) {
+            double f = 1.0;  // j!/(j-k)!
+            for (int i = 0; i < k; ++i) f *= (double)(j - i);
+            A[k * (n + 1) + j] = (j == k) ? f : 0.0;        // at t = 0 only t^k survives
+            A[(p + k) * (n + 1) + j] = f;                    // at t = 1
+        }
+        A[k * (n + 1) + n] = dK[k] * std::pow(eps_B, k);
+        A[(p + k) * (n + 1) + n] = (k == 0) ? std::exp(-0.25 / (s * s)) : 0.0;
+    }
+    return solve_dense(n, A, q);
+}
+
+static double kernel_regularised(double r, double s, double eps_B, const std::vector<double> &q)
+{
+    if (eps_B <= 0 || r <= 0.5 - eps_B) return std::exp(-r * r / (s * s));
+    double t = (r - (0.5 - eps_B)) / eps_B;
+    if (t > 1.0) t = 1.0;
+    double v = 0.0;
+    for (int j = (int)q.size() - 1; j >= 0; --j) v = v * t + q[j];
+    return v;
+}
+
+// b_l = N^{-d} sum_{k in I_N} K_R(k/N) exp(-2 pi i l.k/N).  K_R is even in each
+// coordinate, so b_l is real, even in each l_a, and equals the cosine sum;
+// only l_a = 0..N/2 are stored (dim 0 fastest).
+void kernel_fourier(double s, int N, int d, double eps_B, int p_reg, std::vector<double> &bhat)
+{
+    const int H = N / 2 + 1;
+    std::vector<double> C((size_t)H * N);  // C[l][k + N/2] = cos(2 pi l k / N)
+    for (int l = 0; l < H; ++l)
+        for (int k = -N / 2; k < N / 2; ++k)
+            C[(size_t)l * N + (k + N / 2)] = std::cos(2.0 * kPi * (double)l * (double)k / N);
+    if (eps_B <= 0) {
+        // the box-domain kernel is the Gaussian on the period cube: separable
+        std::vector<double> b1(H, 0.0);
+        for (int l = 0; l < H; ++l) {
+            double acc = 0.0;
+            for (int k = -N / 2; k < N / 2; ++k) {
+                const double y = (double)k / N;
+                acc += std::exp(-y * y / (s * s)) * C[(size_t)l * N + (k + N / 2)];
+            }
+            b1[l] = acc / N;
+        }
+        size_t tot = 1;
+        for (int a = 0; a < d; ++a) tot *= H;
+        bhat.assign(tot, 1.0);
+        for (size_t idx = 0; idx < tot; ++idx) {
+            size_t r = idx;
+            double v = 1.0;
+            for (int a = 0; a < d; ++a) {
+                v *= b1[r % H];
+                r /= H;
+            }
+            bhat[idx] = v;
+        }
+        return;
+    }
+    std::vector<double> q;
+    regulariser_coeffs(s, eps_B, p_reg, q);
+    // samples on the full grid, then cosine sums one axis at a time
+    std::vector<size_t> ext(3, 1);
+    for (int a = 0; a < d; ++a) ext[a] = N;
+    std::vector<double> cur(ext[0] * ext[1] * ext[2]);
+    for (size_t z = 0; z < ext[2]; ++z)
+        for (size_t y = 0; y < ext[1]; ++y)
+            for (size_t x = 0; x < ext[0]; ++x) {
+                double r2 = 0.0;
+                const size_t id[3] = {x, y, z};
+                for (int a = 0; a < d; ++a) {
+                    const double t = ((double)id[a] - N / 2) / N;
+                    r2 += t * t;
+                }
+                cur[(z * ext[1] + y) * ext[0] + x] = kernel_regularised(std::sqrt(r2), s, eps_B, q);
+            }
+    for (int a = 0; a < d; ++a) {
+        std::vector<size_t> next = ext;
+        next[a] = H;
+        std::vector<double> out(next[0] * next[1] * next[2], 0.0);
+        size_t stride = 1;
+        for (int b2 = 0; b2 < a; ++b2) stride *= next[b2];
+        const size_t inner = stride;
+        size_t outer = 1;
+        for (int b2 = a + 1; b2 < 3; ++b2) outer *= ext[b2];
+        for (size_t o = 0; o < outer; ++o)
+            for (size_t l = 0; l < (size_t)H; ++l)
+                for (size_t i = 0; i < inner; ++i) {
+                    double acc = 0.0;
+                    for (size_t k = 0; k < (size_t)N; ++k)
+                        acc += C[l * N + k] * cur[(o * ext[a] + k) * inner + i];
+                    out[(o * H + l) * inner + i] = acc / N;
+                }
+        cur.swap(out);
+        ext = next;
+    }
+    bhat.swap(cur);
+}
+
+// Multiplier over coefficient slots.  Per dim, slot s <= N/2 is the cosine of
+// frequency s, slot N/2 + j (j = 1..N/2) the sine of frequency j.  The
+// convolution kernel of the grid step has Fourier weights
+//   w_l = b_l / (n_os^{2d} prod_a phi_hat(l_a)^2)
+// on the symmetric set {-N/2..N/2}^d with half weight on each edge frequency
+// (the real part of Alg. 1's sum over I_N); folding the pairs +-l gives the
+// per-dim factor c(0) = 1, c(j) = 2 for 0 < j < N/2, c(N/2) = 1.
+void slot_multiplier(int N, int d, int n_os, const std::vector<double> &bhat,
+                     const std::vector<double> &phihat, std::vector<double> &mult)
+{
+    const int K = N + 1, H = N / 2 + 1;
+    size_t tot = 1;
+    for (int a = 0; a < d; ++a) tot *= K;
+    mult.assign(tot, 0.0);
+    const double scale = std::pow((double)n_os, -2.0 * d);
+    for (size_t idx = 0; idx < tot; ++idx) {
+        size_t r = idx, bidx = 0, bstride = 1;
+        double f = scale;
+        for (int a = 0; a < d; ++a) {
+            const int slot = (int)(r % K);
+            r /= K;
+            const int kap = slot <= N / 2 ? slot : slot - N / 2;
+            const double c = (kap == 0 || kap == N / 2) ? 1.0 : 2.0;
+            f *= c / (phihat[kap] * phihat[kap]);
+            bidx += (size_t)kap * bstride;
+            bstride *= H;
+        }
+        mult[idx] = f * bhat[bidx];
+    }
+}
+
+void trig_matrix(int N, int n_os, int s0, int L, std::vector<double> &M)
+{
+    const int K = N + 1;
+    M.assign((size_t)K * L, 0.0);
+    for (int slot = 0; slot < K; ++slot) {
+        const bool is_sin = slot > N / 2;
+        const int kap = is_sin ? slot - N / 2 : slot;
+        for (int j = 0; j < L; ++j) {
+            // reduce kap*(j+s0) mod n_os exactly before scaling to radians
+            const long long t = ((long long)kap * (long long)(j + s0)) % n_os;
+            const double ang = 2.0 * kPi * (double)t / n_os;
+            M[(size_t)slot * L + j] = is_sin ? std::sin(ang) : std::cos(ang);
+        }
+    }
+}
+
+// Cyclic Jacobi rotations for a small symmetric matrix.
+void sym_eig(int n, std::vector<double> &a, std::vector<double> &evals, std::vector<double> &evecs)
+{
+    std::vector<double> v((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double x = a[(size_t)i * n + j];
+                tot += x * x;
+                if (i != j) off += x * x;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+                const double tau = (aqq - app) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = c * akp - s * akq;
+                    a[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = c * apk - s * aqk;
+                    a[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+                    v[(size_t)k * n + p] = c * vkp - s * vkq;
+                    v[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return a[(size_t)x * n + x] < a[(size_t)y * n + y]; });
+    evals.assign(n, 0.0);
+    evecs.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        evals[j] = a[(size_t)order[j] * n + order[j]];
+        for (int k = 0; k < n; ++k) evecs[(size_t)k * n + j] = v[(size_t)k * n + order[j]];
+    }
+}
+
+}  // namespace ml

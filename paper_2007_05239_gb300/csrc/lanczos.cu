@@ -1,0 +1,486 @@
+// ml_lanczos_eigs: k smallest eigenpairs of L_1 (Eq. I-L_1) or L_{-1,delta}
+// (Eq. L_p_delta_power_p) by the Lanczos method (Sec. 3).
+//
+// Thick-restart Lanczos (Wu & Simon) on the symmetric operator
+//   p =  1: Op = I - L_1 = (1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2}
+//   p = -1: Op = L_{-1,delta}^{-1} = (1/T) sum_t (L_sym^(t) + delta I)^{-1}
+// for its k largest eigenvalues.  The Krylov basis Q (n x (ncv+1), column
+// major, FP64) lives on the device; every new vector is orthogonalised
+// against all columns twice (classical Gram-Schmidt, CGS2) with
+// deterministic block reductions.  The projected (ncv x ncv) matrix and its
+// eigendecomposition are on the host in FP64.  For p = -1 each term
+// (L_sym^(t) + delta I)^{-1} x is a conjugate-gradient solve whose matvec is
+// the fast summation of layer t (the polynomial Krylov approach of Sec. 3
+// specialised to the inverse, an SPD solve with condition <= (2+delta)/delta).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ml_internal.h"
+
+namespace ml {
+
+ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, double *Y, int mode, cudaStream_t st);
+
+constexpr int kDotThreads = 256;
+
+// partial dot products of columns c0.. of Q (column stride n) with x
+__global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
+                                                      const double *__restrict__ x, double *part)
+{
+    __shared__ double red[kDotThreads / 32][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < ncol; c0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+        for (int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; r < n; r += (int64_t)gridDim.x * kDotThreads) {
+            const double xr = x[r];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + k < ncol) acc[k] = fma(Q[(int64_t)(c0 + k) * ldq + r], xr, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < ncol) {
+            double s = 0.0;
+            for (int w = 0; w < kDotThreads / 32; ++w) s += red[w][threadIdx.x];
+            part[(int64_t)blockIdx.x * ncol + c0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// out[c] = sum over blocks of part[b][c] (fixed order)
+__global__ void k_reduce_cols(const double *__restrict__ part, int nblk, int ncol, double *out)
+{
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ncol + c];
+        out[c] = s;
+    }
+}
+
+// x -= Q[:, 0:ncol] h
+__global__ void k_update(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol, const double *__restrict__ h,
+                         double *x)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < ncol; ++c) s = fma(Q[(int64_t)c * ldq + r], h[c], s);
+        x[r] -= s;
+    }
+}
+
+// y = a * x
+__global__ void k_scale(const double *__restrict__ x, double a, int64_t n, double *y)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        y[r] = a * x[r];
+}
+
+// y += a * x
+__global__ void k_axpy(double a, const double *__restrict__ x, int64_t n, double *y)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        y[r] = fma(a, x[r], y[r]);
+}
+
+// p = r + beta p
+__global__ void k_xpby(const double *__restrict__ r, double beta, int64_t n, double *p)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) of a counter, mapped to (-1, 1)
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+__global__ void k_random(uint64_t seed, int64_t n, double *x)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        x[r] = splitmix_uniform(seed, (uint64_t)r);
+}
+
+// out[:, i] = Q[:, 0:ncv] S[:, i] for i < kk  (S is ncv x kk, column-major)
+__global__ void k_combine(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv, const double *__restrict__ S,
+                          int kk, double *out, int64_t ldo)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        for (int i0 = 0; i0 < kk; i0 += 8) {
+            double acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+            for (int c = 0; c < ncv; ++c) {
+                const double q = Q[(int64_t)c * ldq + r];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (i0 + k < kk) acc[k] = fma(q, S[(int64_t)(i0 + k) * ncv + c], acc[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (i0 + k < kk) out[(int64_t)(i0 + k) * ldo + r] = acc[k];
+        }
+    }
+}
+
+// per-block (max |x|, signed value at the first maximum) of each column
+__global__ void k_colmax(const double *__restrict__ V, int64_t ldv, int64_t n, int k, double *part)
+{
+    __shared__ double sa[256], sv[256];
+    __shared__ long long si[256];
+    for (int c = 0; c < k; ++c) {
+        double ba = -1.0, bv = 0.0;
+        long long bi = LLONG_MAX;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+            const double v = V[(int64_t)c * ldv + r];
+            const double a = fabs(v);
+            if (a > ba) {
+                ba = a;
+                bv = v;
+                bi = r;
+            }
+        }
+        sa[threadIdx.x] = ba;
+        sv[threadIdx.x] = bv;
+        si[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) {
+                const int o = threadIdx.x + s;
+                if (sa[o] > sa[threadIdx.x] || (sa[o] == sa[threadIdx.x] && si[o] < si[threadIdx.x])) {
+                    sa[threadIdx.x] = sa[o];
+                    sv[threadIdx.x] = sv[o];
+                    si[threadIdx.x] = si[o];
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            part[((int64_t)blockIdx.x * k + c) * 3 + 0] = sa[0];
+            part[((int64_t)blockIdx.x * k + c) * 3 + 1] = sv[0];
+            part[((int64_t)blockIdx.x * k + c) * 3 + 2] = (double)si[0];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_scale_cols(double *V, int64_t ldv, int64_t n, int k, const double *__restrict__ f)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < k; ++c) V[(int64_t)c * ldv + r] *= f[c];
+}
+
+static int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+struct Workspace {
+    cudaStream_t st = nullptr;
+    int64_t n = 0;
+    int nblk = 1;
+    DevBuf part, hdev, scal;
+
+    ml_status init(int64_t n_, int maxcol, cudaStream_t s)
+    {
+        n = n_;
+        st = s;
+        nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 456));
+        ML_TRY(part.ensure((size_t)nblk * std::max(maxcol, 1) * sizeof(double)));
+        ML_TRY(hdev.ensure((size_t)(2 * maxcol + 8) * sizeof(double)));
+        ML_TRY(scal.ensure(64 * sizeof(double)));
+        return ML_OK;
+    }
+    // out (device, ncol) = Q[:, 0:ncol]^T x
+    ml_status dots(const double *Q, int64_t ldq, int ncol, const double *x, double *out)
+    {
+        k_dots<<<nblk, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
+        k_reduce_cols<<<1, 128, 0, st>>>(part.as<double>(), nblk, ncol, out);
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+    ml_status dot_host(const double *a, const double *b, double *out)
+    {
+        ML_TRY(dots(a, n, 1, b, scal.as<double>()));
+        ML_CUDA(cudaMemcpyAsync(out, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaStreamSynchronize(st));
+        return ML_OK;
+    }
+    // x <- x - Q h twice (CGS2); hsum_host (ncol) receives h1 + h2, beta the norm of x after
+    ml_status orthogonalize(const double *Q, int64_t ldq, int ncol, double *x, std::vector<double> &hsum,
+                            double *beta)
+    {
+        double *h1 = hdev.as<double>(), *h2 = h1 + ncol, *nrm = h2 + ncol;
+        if (ncol > 0) {
+            ML_TRY(dots(Q, ldq, ncol, x, h1));
+            k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h1, x);
+            ML_TRY(dots(Q, ldq, ncol, x, h2));
+            k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h2, x);
+        }
+        ML_TRY(dots(x, n, 1, x, nrm));
+        std::vector<double> hh(2 * ncol + 1);
+        ML_CUDA(cudaMemcpyAsync(hh.data(), h1, (2 * ncol + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaStreamSynchronize(st));
+        hsum.assign(ncol, 0.0);
+        for (int c = 0; c < ncol; ++c) hsum[c] = hh[c] + hh[ncol + c];
+        *beta = std::sqrt(std::max(hh[2 * ncol], 0.0));
+        return ML_OK;
+    }
+};
+
+// y = (1/T) sum_t (L_sym^(t) + delta I)^{-1} x by CG per layer
+struct InverseOp {
+    ml_plan_s *const *layers;
+    int T;
+    double delta;
+    int64_t n;
+    Workspace *ws;
+    DevBuf r, p, ap, y;
+    int inner_max = 200;
+    double inner_tol = 1e-12;
+    long long inner_iters = 0;
+
+    ml_status init()
+    {
+        ML_TRY(r.ensure(n * 8));
+        ML_TRY(p.ensure(n * 8));
+        ML_TRY(ap.ensure(n * 8));
+        ML_TRY(y.ensure(n * 8));
+        return ML_OK;
+    }
+    // ap = (L_sym + delta I) v = (1 + delta) v - A v
+    ml_status shifted(ml_plan_s *L, const double *v, double *out, cudaStream_t st)
+    {
+        ApplyVec av{v, 1, out, 1, 1};
+        ApplyOpts o;
+        o.normalized = true;
+        o.alpha = -1.0;
+        o.shift = 1.0 + delta;
+        return apply_layer(L, av, o, st);
+    }
+    ml_status apply(const double *x, double *out, cudaStream_t st)
+    {
+        const int nb = vec_blocks(n);
+        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
+        double bb;
+        ML_TRY(ws->dot_host(x, x, &bb));
+        const double bnorm = std::sqrt(bb);
+        for (int t = 0; t < T; ++t) {
+            // x0 = 0: r = x, p = x
+            ML_CUDA(cudaMemcpyAsync(r.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
+            ML_CUDA(cudaMemcpyAsync(p.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
+            ML_CUDA(cudaMemsetAsync(y.p, 0, n * 8, st));
+            double rr = bb;
+            for (int it = 0; it < inner_max && std::sqrt(rr) > inner_tol * bnorm; ++it) {
+                ML_TRY(shifted(layers[t], p.as<double>(), ap.as<double>(), st));
+                double pap;
+                ML_TRY(ws->dot_host(p.as<double>(), ap.as<double>(), &pap));
+                if (!(pap > 0)) return fail(ML_ERR_BREAKDOWN, "CG: operator not positive definite (p^T A p <= 0)");
+                const double alpha = rr / pap;
+                k_axpy<<<nb, 256, 0, st>>>(alpha, p.as<double>(), n, y.as<double>());
+                k_axpy<<<nb, 256, 0, st>>>(-alpha, ap.as<double>(), n, r.as<double>());
+                double rr2;
+                ML_TRY(ws->dot_host(r.as<double>(), r.as<double>(), &rr2));
+                k_xpby<<<nb, 256, 0, st>>>(r.as<double>(), rr2 / rr, n, p.as<double>());
+                rr = rr2;
+                ++inner_iters;
+            }
+            k_axpy<<<nb, 256, 0, st>>>(1.0 / T, y.as<double>(), n, out);
+            ML_CUDA(cudaGetLastError());
+        }
+        return ML_OK;
+    }
+};
+
+static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw, double tol, int maxit,
+                              uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
+{
+    const int64_t n = layers[0]->n;
+    const int ncv = (int)std::min<int64_t>(std::max(2 * k + 1, 20), n - 1);
+    const int kkeep = std::min(ncv - 2, std::max(k + 1, (ncv + k) / 2));
+    Workspace ws;
+    ML_TRY(ws.init(n, ncv + 1, st));
+    DevBuf Qb, Qtmp, wv, Sd;
+    ML_TRY(Qb.ensure((size_t)n * (ncv + 1) * 8));
+    ML_TRY(Qtmp.ensure((size_t)n * (ncv + 1) * 8));
+    ML_TRY(wv.ensure((size_t)n * 8));
+    ML_TRY(Sd.ensure((size_t)ncv * ncv * 8));
+    double *Q = Qb.as<double>(), *w = wv.as<double>();
+    InverseOp inv{layers, T, std::log(2.0), n, &ws};
+    if (pw < 0) ML_TRY(inv.init());
+    auto op = [&](const double *x, double *y) -> ml_status {
+        if (pw > 0) return apply_device(layers, T, x, 1, y, ML_NORMALIZED_A, st);
+        return inv.apply(x, y, st);
+    };
+    const int nb = vec_blocks(n);
+    // start vector
+    k_random<<<nb, 256, 0, st>>>(seed, n, Q);
+    std::vector<double> h;
+    double beta = 0;
+    ML_TRY(ws.orthogonalize(Q, n, 0, Q, h, &beta));
+    if (!(beta > 0)) return fail(ML_ERR_BREAKDOWN, "zero start vector");
+    k_scale<<<nb, 256, 0, st>>>(Q, 1.0 / beta, n, Q);
+
+    std::vector<double> Tm((size_t)ncv * ncv, 0.0);
+    std::vector<double> theta, S;
+    int kk = 0;         // kept Ritz vectors at the front of Q
+    int matvecs = 0;
+    int nconv = 0;
+    double beta_last = 0.0;
+    uint64_t restart_seed = seed ^ 0xA5A5A5A5DEADBEEFULL;
+    while (true) {
+        for (int j = kk; j < ncv; ++j) {
+            ML_TRY(op(Q + (int64_t)j * n, w));
+            ++matvecs;
+            ML_TRY(ws.orthogonalize(Q, n, j + 1, w, h, &beta));
+            for (int i = 0; i <= j; ++i) {
+                if (i < kk && j >= kk && j != kk) continue;  // keep the arrow structure exact
+                Tm[(size_t)i * ncv + j] = h[i];
+                Tm[(size_t)j * ncv + i] = h[i];
+            }
+            double tnorm = 0.0;
+            for (int i = 0; i <= j; ++i) tnorm = std::max(tnorm, std::fabs(Tm[(size_t)i * ncv + i]));
+            if (beta <= 1e-14 * std::max(tnorm, 1e-300) * std::sqrt((double)n)) {
+                // invariant subspace found: continue with a fresh random direction
+                k_random<<<nb, 256, 0, st>>>(restart_seed++, n, w);
+                std::vector<double> hh;
+                double b2;
+                ML_TRY(ws.orthogonalize(Q, n, j + 1, w, hh, &b2));
+                if (!(b2 > 0)) return fail(ML_ERR_BREAKDOWN, "Lanczos breakdown: no new direction");
+                beta = 0.0;
+                k_scale<<<nb, 256, 0, st>>>(w, 1.0 / b2, n, Q + (int64_t)(j + 1) * n);
+            } else {
+                k_scale<<<nb, 256, 0, st>>>(w, 1.0 / beta, n, Q + (int64_t)(j + 1) * n);
+            }
+            ML_CUDA(cudaGetLastError());
+            beta_last = beta;
+        }
+        // Rayleigh-Ritz on the projected matrix
+        std::vector<double> a = Tm;
+        sym_eig(ncv, a, theta, S);
+        double tmax = 0.0;
+        for (double t : theta) tmax = std::max(tmax, std::fabs(t));
+        nconv = 0;
+        for (int i = ncv - 1; i >= ncv - k; --i) {
+            const double res = std::fabs(beta_last * S[(size_t)(ncv - 1) * ncv + i]);
+            if (res <= tol * std::max(tmax, 1e-300)) ++nconv;
+            else break;
+        }
+        const bool done = nconv >= k || matvecs >= maxit;
+        const int keep = done ? k : kkeep;
+        // Ritz vectors of the largest `keep` values -> front of Qtmp
+        std::vector<double> Sk((size_t)ncv * keep);
+        for (int i = 0; i < keep; ++i) {
+            const int col = ncv - 1 - i;  // descending theta
+            for (int c = 0; c < ncv; ++c) Sk[(size_t)i * ncv + c] = S[(size_t)c * ncv + col];
+        }
+        ML_CUDA(cudaMemcpyAsync(Sd.p, Sk.data(), Sk.size() * 8, cudaMemcpyHostToDevice, st));
+        k_combine<<<nb, 256, 0, st>>>(Q, n, n, ncv, Sd.as<double>(), keep, Qtmp.as<double>(), n);
+        ML_CUDA(cudaGetLastError());
+        if (done) {
+            for (int i = 0; i < k; ++i) {
+                const double th = theta[ncv - 1 - i];
+                evals[i] = pw > 0 ? 1.0 - th : 1.0 / th;
+            }
+            // ascending eigenvalues of the Laplacian: p = 1 maps descending theta to
+            // ascending 1 - theta already; p = -1 maps descending mu to ascending 1/mu.
+            if (evecs_dev) {
+                ML_CUDA(cudaMemcpyAsync(evecs_dev, Qtmp.p, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, st));
+                // sign: largest-magnitude entry positive
+                const int cb = std::min(nb, 256);
+                DevBuf part;
+                ML_TRY(part.ensure((size_t)cb * k * 3 * 8));
+                k_colmax<<<cb, 256, 0, st>>>(evecs_dev, n, n, k, part.as<double>());
+                std::vector<double> hp((size_t)cb * k * 3);
+                ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, st));
+                ML_CUDA(cudaStreamSynchronize(st));
+                std::vector<double> f(k, 1.0);
+                for (int c = 0; c < k; ++c) {
+                    double ba = -1, bv = 0, bi = 1e300;
+                    for (int b = 0; b < cb; ++b) {
+                        const double *e = &hp[((size_t)b * k + c) * 3];
+                        if (e[0] > ba || (e[0] == ba && e[2] < bi)) {
+                            ba = e[0];
+                            bv = e[1];
+                            bi = e[2];
+                        }
+                    }
+                    f[c] = bv < 0 ? -1.0 : 1.0;
+                }
+                ML_CUDA(cudaMemcpyAsync(Sd.p, f.data(), k * 8, cudaMemcpyHostToDevice, st));
+                k_scale_cols<<<nb, 256, 0, st>>>(evecs_dev, n, n, k, Sd.as<double>());
+                ML_CUDA(cudaGetLastError());
+            }
+            ML_CUDA(cudaStreamSynchronize(st));
+            if (nconv_out) *nconv_out = std::min(nconv, k);
+            return nconv >= k ? ML_OK : ML_WARN_NOT_CONVERGED;
+        }
+        // thick restart: Q[:, 0:kk] = Ritz vectors, Q[:, kk] = last residual direction
+        kk = keep;
+        ML_CUDA(cudaMemcpyAsync(Q + (int64_t)kk * n, Q + (int64_t)ncv * n, n * 8, cudaMemcpyDeviceToDevice, st));
+        ML_CUDA(cudaMemcpyAsync(Q, Qtmp.p, (size_t)n * kk * 8, cudaMemcpyDeviceToDevice, st));
+        std::fill(Tm.begin(), Tm.end(), 0.0);
+        for (int i = 0; i < kk; ++i) {
+            const int col = ncv - 1 - i;
+            Tm[(size_t)i * ncv + i] = theta[col];
+            const double coup = beta_last * S[(size_t)(ncv - 1) * ncv + col];
+            Tm[(size_t)i * ncv + kk] = coup;
+            Tm[(size_t)kk * ncv + i] = coup;
+        }
+    }
+}
+
+}  // namespace ml
+
+extern "C" ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, double tol, int maxit,
+                                     int block, uint64_t seed, double *evals, double *evecs, int *nconv,
+                                     void *stream)
+{
+    using namespace ml;
+    if (!layers || T < 1) return fail(ML_ERR_ARG, "layers is null or T < 1");
+    for (int t = 0; t < T; ++t)
+        if (!layers[t]) return fail(ML_ERR_ARG, "null layer");
+    const int64_t n = layers[0]->n;
+    for (int t = 1; t < T; ++t)
+        if (layers[t]->n != n) return fail(ML_ERR_ARG, "layers do not share n");
+    if (k < 1 || k > n / 2) return fail(ML_ERR_ARG, "k must be in [1, n/2]");
+    if (p != 1.0 && p != -1.0) return fail(ML_ERR_ARG, "p must be 1 or -1");
+    if (block > 1) return fail(ML_ERR_ARG, "block Lanczos is not available (block must be 1)");
+    if (!evals) return fail(ML_ERR_ARG, "evals is null");
+    if (tol <= 0) tol = 1e-10;
+    if (maxit <= 0) maxit = 2000;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *evd = nullptr;
+    DevBuf stage;
+    bool host_out = false;
+    if (evecs) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, evecs) == cudaSuccess &&
+            (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+            evd = evecs;
+        } else {
+            cudaGetLastError();
+            ML_TRY(stage.ensure((size_t)n * k * 8));
+            evd = stage.as<double>();
+            host_out = true;
+        }
+    }
+    ml_status s = lanczos_impl(layers, T, k, p, tol, maxit, seed, evals, evd, nconv, st);
+    if ((s == ML_OK || s == ML_WARN_NOT_CONVERGED) && host_out) {
+        ML_CUDA(cudaMemcpy(evecs, evd, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+    }
+    return s;
+}

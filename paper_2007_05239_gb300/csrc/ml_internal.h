@@ -1,0 +1,158 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/ml_fastsum.h"
+
+namespace ml {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+ml_status fail(ml_status st, const std::string &msg);
+ml_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define ML_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return ::ml::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define ML_TRY(expr)                             \
+    do {                                         \
+        ml_status s_ = (expr);                   \
+        if (s_ != ML_OK) return s_;              \
+    } while (0)
+
+// --------------------------------------------------------- limits / sizes
+constexpr int kMaxVec = 8;       // vectors per spreading/interpolation pass
+constexpr int kMaxM = 8;         // window half-width limit
+constexpr int kMaxN = 512;       // bandwidth limit
+constexpr int kSubPoints = 1024; // points per subproblem (bounds per-cell counts)
+
+// ------------------------------------------------------------ device buffer
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ml_status ensure(size_t nbytes);   // grow (contents not kept)
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------------ plan
+struct GridGeom {
+    int d = 1;
+    int m = 2;          // half-width: taps f0 .. f0+2m-1 per dim
+    int B = 8;          // bin edge (cells)
+    int Pt = 0;         // padded tile edge = B + 2m - 1
+    int L[3] = {1, 1, 1};
+    int nb[3] = {1, 1, 1};
+    int R = 1;          // neighbour bins reaching into a bin per dim = ceil((2m-1)/B)
+    int K = 0;          // coefficient slots per dim = N + 1
+    int64_t cells() const { return (int64_t)L[0] * L[1] * L[2]; }
+    int64_t nbins() const { return (int64_t)nb[0] * nb[1] * nb[2]; }
+    int64_t tile_cells() const {
+        int64_t t = 1;
+        for (int a = 0; a < d; ++a) t *= Pt;
+        return t;
+    }
+};
+
+struct ml_plan_impl;
+
+}  // namespace ml
+
+struct ml_plan_s {
+    // parameters
+    int64_t n = 0;
+    int d = 0;
+    int N = 0;
+    int m = 0;
+    int n_os = 0;
+    ml_prec prec = ML_F64;
+    int domain = 0;
+    int p_reg = 0;
+    double eps_B = 0;
+    double sigma = 0, sigma_s = 0, scale = 0;
+    double center[3] = {0, 0, 0};
+    double target = 0;
+    double kb_shape = 0;   // b = pi (2 - 1/sigma_os)
+    double kb_norm = 0;    // m / (1 - exp(-2 b m)) * exp(-b m): phi_n(t) = norm * 2 sinh(b s)/s
+    int s0[3] = {0, 0, 0}; // torus index of active-grid cell 0 per dim
+    ml::GridGeom g;
+    int vp = 1;            // vectors per pass
+    int nsub = 0;
+    double deg_min = 0, deg_max = 0;
+
+    // host tables (FP64)
+    std::vector<double> bhat;    // (N/2+1)^d
+    std::vector<double> phihat;  // N/2+1
+    std::vector<double> mult;    // K^d over coefficient slots
+
+    // device data (sorted order unless noted)
+    ml::DevBuf perm;      // int32 n: sorted position -> input index
+    ml::DevBuf coords;    // T n*d local grid coordinates
+    ml::DevBuf deg;       // double n: degrees
+    ml::DevBuf dinv;      // double n: D^{-1/2}
+    ml::DevBuf sub_bin, sub_start, sub_count;  // int32 nsub
+    ml::DevBuf bin_sub;   // int32 nbins+1: first subproblem of each bin
+    ml::DevBuf trig_f[3]; // T K x L_a  (forward, cos rows then sin rows)
+    ml::DevBuf trig_b[3]; // T L_a x K  (backward = transpose)
+    ml::DevBuf mult_d;    // T K^d
+
+    // workspace
+    ml::DevBuf scratch;   // spreading tiles: nsub * Pt^d * vp (T)
+    ml::DevBuf work[2];   // transform ping-pong buffers
+    ml::DevBuf stage_x, stage_y;  // staging for host X / Y
+    ml::DevBuf status;    // int flags written by device code
+    int64_t device_bytes() const;
+};
+
+namespace ml {
+
+// --------------------------------------------------------- host math (FP64)
+double bessel_i0(double x);
+// Fourier coefficients phi_hat_n(k), k = 0..kmax, of the normalised window
+// phi_n(t) = sinh(b sqrt(m^2 - t^2)) / sqrt(m^2 - t^2) / (sinh(b m)/m).
+void window_fourier(int n_os, int m, double b, int kmax, std::vector<double> &out);
+// b_l, l = 0..N/2 per dim, for the box domain (separable) or the ball domain.
+void kernel_fourier(double sigma_s, int N, int d, double eps_B, int p_reg, std::vector<double> &bhat);
+// the two-point Taylor regulariser's monomial coefficients in t = (r - r_I)/eps_B
+bool regulariser_coeffs(double sigma_s, double eps_B, int p, std::vector<double> &q);
+// multiplier over coefficient slots
+void slot_multiplier(int N, int d, int n_os, const std::vector<double> &bhat,
+                     const std::vector<double> &phihat, std::vector<double> &mult);
+// forward trig matrix K x L for one dim (cos rows 0..N/2, sin rows 1..N/2)
+void trig_matrix(int N, int n_os, int s0, int L, std::vector<double> &M);
+// symmetric eigen-decomposition of a small dense matrix (cyclic Jacobi);
+// a is n x n row-major (destroyed), evals ascending, evecs column j = vector j
+void sym_eig(int n, std::vector<double> &a, std::vector<double> &evals, std::vector<double> &evecs);
+
+// ------------------------------------------------------------- launchers
+struct ApplyVec {      // one pass over up to kMaxVec vectors
+    const double *X;   // input block base (point-major, row stride ldx), or null (ones)
+    int ldx;
+    double *Y;         // output base (row stride ldy)
+    int ldy;
+    int nv;            // vectors in this pass
+};
+
+// layer apply: y (+)= alpha * post(D^{-1/2}) * (W~ u - u),  u = pre(D^{-1/2}) * x
+struct ApplyOpts {
+    bool normalized = false;   // pre- and post-scale by D^{-1/2}
+    bool accumulate = false;   // Y += instead of Y =
+    bool sorted_out = false;   // write Y in sorted order, no post-scale (degree set-up)
+    double alpha = 1.0;
+    double shift = 0.0;        // adds shift * x (input order) to the output: used for L_sym + delta I
+    double self = 1.0;         // K(0): subtracted self term coefficient
+};
+
+ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+ml_status ensure_workspace(ml_plan_s *p, int nv);
+
+}  // namespace ml

@@ -1,0 +1,734 @@
+// ml_fastsum_plan and friends: one layer's set-up for Alg. 1 (Sec. 4) and its
+// degrees (Sec. 2).  Device work: bounding box, grid coordinates, a stable
+// LSD radix sort of the points by spreading bin, bin counts; host work (FP64):
+// domain scaling, parameter choice, Fourier tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ml_internal.h"
+
+namespace ml {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+ml_status fail(ml_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+ml_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
+{
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
+             cudaGetErrorString(e), what, file, line);
+    g_err = buf;
+    return e == cudaErrorMemoryAllocation ? ML_ERR_OOM : ML_ERR_CUDA;
+}
+
+ml_status DevBuf::ensure(size_t nbytes)
+{
+    if (nbytes <= bytes && p) return ML_OK;
+    release();
+    if (nbytes == 0) return ML_OK;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+    bytes = nbytes;
+    return ML_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+// ------------------------------------------------------------- reductions
+__global__ void k_bbox(const double *__restrict__ X, int64_t n, int d, double *part)
+{
+    // part[block][2*a] = min, part[block][2*a+1] = max
+    __shared__ double smin[3][256], smax[3][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < d; ++a) {
+            const double x = X[i * d + a];
+            lo[a] = fmin(lo[a], x);
+            hi[a] = fmax(hi[a], x);
+        }
+    for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = lo[a];
+        smax[a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + s]);
+                smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            part[blockIdx.x * 6 + 2 * a] = smin[a][0];
+            part[blockIdx.x * 6 + 2 * a + 1] = smax[a][0];
+        }
+}
+
+// max_i ||x_i - c||^2 per block
+__global__ void k_maxrad(const double *__restrict__ X, int64_t n, int d, double c0, double c1, double c2, double *part)
+{
+    __shared__ double s[256];
+    const double c[3] = {c0, c1, c2};
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double r2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+            const double t = X[i * d + a] - c[a];
+            r2 += t * t;
+        }
+        m = fmax(m, r2);
+    }
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+struct TorusMap {
+    double c[3];
+    double s;      // scale into the Alg. 1 domain
+    int n_os, m, d;
+};
+
+// U_a = n_os (s (x_a - c_a) + 1/2): torus grid coordinate; F_a = floor(U_a) - m + 1
+// is the first tap.  Per-block min/max of F_a.
+__global__ void k_first_tap_range(const double *__restrict__ X, int64_t n, TorusMap tm, long long *part)
+{
+    __shared__ long long smin[3][256], smax[3][256];
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < tm.d; ++a) {
+            const double U = tm.n_os * (tm.s * (X[i * tm.d + a] - tm.c[a]) + 0.5);
+            const long long F = (long long)floor(U) - tm.m + 1;
+            lo[a] = min(lo[a], F);
+            hi[a] = max(hi[a], F);
+        }
+    for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = lo[a];
+        smax[a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][threadIdx.x] = min(smin[a][threadIdx.x], smin[a][threadIdx.x + k]);
+                smax[a][threadIdx.x] = max(smax[a][threadIdx.x], smax[a][threadIdx.x + k]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            part[blockIdx.x * 6 + 2 * a] = smin[a][0];
+            part[blockIdx.x * 6 + 2 * a + 1] = smax[a][0];
+        }
+}
+
+// local coordinate relative to the point's bin origin, and the bin key
+struct KeyArgs {
+    TorusMap tm;
+    int s0[3];
+    int B;
+    int nb0, nb1;
+};
+
+__global__ void k_keys(const double *__restrict__ X, int64_t n, KeyArgs ka, double *urel, uint32_t *keys, int *idx)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int bcoord[3] = {0, 0, 0};
+        for (int a = 0; a < ka.tm.d; ++a) {
+            const double U = ka.tm.n_os * (ka.tm.s * (X[i * ka.tm.d + a] - ka.tm.c[a]) + 0.5);
+            const double u = U - ka.s0[a];                        // local active-grid coordinate
+            const long long f0 = (long long)floor(u) - ka.tm.m + 1; // >= 0 by construction of s0
+            const int b = (int)(f0 / ka.B);
+            bcoord[a] = b;
+            urel[i * ka.tm.d + a] = u - (double)b * ka.B;
+        }
+        keys[i] = (uint32_t)((bcoord[2] * ka.nb1 + bcoord[1]) * ka.nb0 + bcoord[0]);
+        idx[i] = (int)i;
+    }
+}
+
+template <typename T>
+__global__ void k_gather_coords(const double *__restrict__ urel, const int *__restrict__ perm, int64_t n, int d, T *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = perm[i];
+        for (int a = 0; a < d; ++a) out[i * d + a] = (T)urel[src * d + a];
+    }
+}
+
+__global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, int *counts)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&counts[keys[i]], 1);
+}
+
+// ------------------------------------------------------------ radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_TILE = 4096;
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                        uint32_t *hist, int nblk)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int e = threadIdx.x; e < RS_TILE; e += RS_THREADS) {
+        const int64_t i = base + e;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of `total` entries in place, one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *a, int64_t total)
+{
+    __shared__ uint32_t sums[1024];
+    const int64_t chunk = (total + 1023) / 1024;
+    const int64_t lo = threadIdx.x * chunk, hi = min(total, lo + chunk);
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += a[i];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < 1024; ++t) {
+            const uint32_t v = sums[t];
+            sums[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    uint32_t run = sums[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: items of a block are ranked in input order, 256 per round;
+// within a round the rank of an item among equal digits is (count in earlier
+// warps) + (count in earlier lanes), the latter from __match_any_sync.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+                                                           uint32_t *kout, int *vout, int64_t n, int shift,
+                                                           const uint32_t *__restrict__ scanned, int nblk)
+{
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    base[tid] = scanned[(int64_t)tid * nblk + blockIdx.x];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < RS_TILE / RS_THREADS; ++r) {
+        const int64_t item = (int64_t)blockIdx.x * RS_TILE + (int64_t)r * RS_THREADS + tid;
+        const bool valid = item < n;
+        const uint32_t key = valid ? kin[item] : 0u;
+        const uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
+        for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const unsigned mask = __match_any_sync(0xffffffffu, digit);
+        const uint32_t lrank = __popc(mask & lt_mask);
+        if (valid && lrank == 0) wcnt[warp][digit] = __popc(mask);
+        __syncthreads();
+        uint32_t run = 0;
+        for (int w = 0; w < RS_THREADS / 32; ++w) {
+            const uint32_t t = wcnt[w][tid];
+            wcnt[w][tid] = run;
+            run += t;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = base[digit] + wcnt[warp][digit] + lrank;
+            kout[pos] = key;
+            vout[pos] = vin[item];
+        }
+        __syncthreads();
+        base[tid] += run;
+        __syncthreads();
+    }
+}
+
+static ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int64_t n, int bits,
+                            cudaStream_t st, int **result_vals)
+{
+    const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+    DevBuf hist;
+    ML_TRY(hist.ensure((size_t)256 * nblk * sizeof(uint32_t)));
+    uint32_t *ka = keys, *kb = keys2;
+    int *va = vals, *vb = vals2;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist.as<uint32_t>(), nblk);
+        k_rs_scan<<<1, 1024, 0, st>>>(hist.as<uint32_t>(), (int64_t)256 * nblk);
+        k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist.as<uint32_t>(), nblk);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    ML_CUDA(cudaGetLastError());
+    ML_CUDA(cudaStreamSynchronize(st));
+    hist.release();
+    *result_vals = va;
+    return ML_OK;
+}
+
+__global__ void k_copy_int(const int *src, int *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// D^{-1/2} and a validity flag (degree not positive or not finite)
+__global__ void k_dinv(const double *__restrict__ deg, int64_t n, double *dinv, int *bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = deg[i];
+        if (!(v > 0.0) || !isfinite(v)) {
+            atomicExch(bad, 1);
+            dinv[i] = 0.0;
+        } else {
+            dinv[i] = 1.0 / sqrt(v);
+        }
+    }
+}
+
+static int grid_for(int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+// ---------------------------------------------------------- parameters
+static int auto_m(double target)
+{
+    if (target >= 1e-3) return 2;
+    if (target >= 1e-5) return 3;
+    if (target >= 1e-7) return 4;
+    if (target >= 1e-9) return 5;
+    if (target >= 1e-11) return 6;
+    if (target >= 1e-13) return 7;
+    return 8;
+}
+
+static int auto_N(double sigma_s, double target)
+{
+    const double half = std::sqrt(std::log(10.0 / target)) / (M_PI * sigma_s);
+    int N = 2 * (int)std::ceil(half);
+    return std::max(N, 8);
+}
+
+// spreading bin edge: the largest B whose padded tile (B + 2m)^d of doubles
+// stays within 48 KB per vector
+static int choose_bin(int d, int m)
+{
+    const int budget = 48 * 1024 / 8;
+    int Pt = 1;
+    while (true) {
+        int64_t v = 1;
+        for (int a = 0; a < d; ++a) v *= (Pt + 1);
+        if (v > budget) break;
+        ++Pt;
+        if (Pt >= 1024) break;
+    }
+    int B = Pt - 2 * m;
+    if (d == 1) B = std::min(B, 512);
+    return std::max(B, 1);
+}
+
+template <typename T>
+static ml_status upload(DevBuf &buf, const std::vector<double> &src)
+{
+    std::vector<T> tmp(src.begin(), src.end());
+    ML_TRY(buf.ensure(tmp.size() * sizeof(T)));
+    ML_CUDA(cudaMemcpy(buf.p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ML_OK;
+}
+
+ml_status ensure_workspace(ml_plan_s *p, int nv)
+{
+    const size_t ts = p->prec == ML_F32 ? 4 : 8;
+    const GridGeom &g = p->g;
+    ML_TRY(p->scratch.ensure((size_t)p->nsub * g.tile_cells() * nv * ts));
+    // transform stages: extents go from L to K one dim at a time and back
+    int64_t mx = 1;
+    for (int stage = 0; stage <= p->d; ++stage) {
+        int64_t v = 1;
+        for (int a = 0; a < p->d; ++a) v *= (a < stage ? g.K : g.L[a]);
+        mx = std::max(mx, v);
+    }
+    ML_TRY(p->work[0].ensure((size_t)mx * nv * ts));
+    ML_TRY(p->work[1].ensure((size_t)mx * nv * ts));
+    ML_TRY(p->status.ensure(64));
+    return ML_OK;
+}
+
+static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
+{
+    const int64_t n = p->n;
+    const int d = p->d;
+    // ---- bounding box
+    const int nblk = grid_for(n);
+    DevBuf part;
+    ML_TRY(part.ensure((size_t)nblk * 6 * sizeof(double)));
+    k_bbox<<<nblk, 256, 0, st>>>(points, n, d, part.as<double>());
+    ML_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)nblk * 6);
+    ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+        for (int b = 0; b < nblk; ++b) {
+            lo[a] = std::min(lo[a], hp[b * 6 + 2 * a]);
+            hi[a] = std::max(hi[a], hp[b * 6 + 2 * a + 1]);
+        }
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) return fail(ML_ERR_ARG, "points contain non-finite values");
+        p->center[a] = 0.5 * (lo[a] + hi[a]);
+    }
+    // ---- domain scaling (isotropic, exact for W)
+    if (p->eps_B > 0) {
+        k_maxrad<<<nblk, 256, 0, st>>>(points, n, d, p->center[0], p->center[1], p->center[2], part.as<double>());
+        ML_CUDA(cudaGetLastError());
+        ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaStreamSynchronize(st));
+        double r2 = 0.0;
+        for (int b = 0; b < nblk; ++b) r2 = std::max(r2, hp[b]);
+        double rmax = std::sqrt(r2);
+        if (!(rmax > 0)) rmax = p->sigma;
+        p->scale = (0.25 - 0.5 * p->eps_B) / rmax;
+        p->domain = 1;
+    } else {
+        double h = 0.0;
+        for (int a = 0; a < d; ++a) h = std::max(h, 0.5 * (hi[a] - lo[a]));
+        if (!(h > 0)) h = p->sigma;
+        const double eps_wrap = 0.1 * p->target;
+        const double aa = std::min(0.25, 1.0 / (2.0 + (p->sigma / h) * std::sqrt(std::log(2.0 * d / eps_wrap))));
+        p->scale = aa / h;
+        p->domain = 0;
+    }
+    p->sigma_s = p->scale * p->sigma;
+    // ---- parameters
+    if (p->N == 0) p->N = auto_N(p->sigma_s, p->target);
+    if (p->m == 0) p->m = auto_m(p->target);
+    if (p->N > kMaxN)
+        return fail(ML_ERR_DOMAIN, "bandwidth N=" + std::to_string(p->N) + " needed for the target exceeds the limit");
+    p->n_os = 2 * p->N;
+    const double sig_os = (double)p->n_os / p->N;
+    p->kb_shape = M_PI * (2.0 - 1.0 / sig_os);
+    {
+        const double b = p->kb_shape, m = p->m;
+        p->kb_norm = m * std::exp(-b * m) / (1.0 - std::exp(-2.0 * b * m));
+    }
+    // ---- active grid
+    TorusMap tm;
+    for (int a = 0; a < 3; ++a) tm.c[a] = p->center[a];
+    tm.s = p->scale;
+    tm.n_os = p->n_os;
+    tm.m = p->m;
+    tm.d = d;
+    DevBuf lpart;
+    ML_TRY(lpart.ensure((size_t)nblk * 6 * sizeof(long long)));
+    k_first_tap_range<<<nblk, 256, 0, st>>>(points, n, tm, lpart.as<long long>());
+    ML_CUDA(cudaGetLastError());
+    std::vector<long long> lp((size_t)nblk * 6);
+    ML_CUDA(cudaMemcpyAsync(lp.data(), lpart.p, lp.size() * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    GridGeom &g = p->g;
+    g.d = d;
+    g.m = p->m;
+    g.K = p->N + 1;
+    for (int a = 0; a < 3; ++a) {
+        g.L[a] = 1;
+        g.nb[a] = 1;
+    }
+    for (int a = 0; a < d; ++a) {
+        long long fmin = LLONG_MAX, fmax = LLONG_MIN;
+        for (int b = 0; b < nblk; ++b) {
+            fmin = std::min(fmin, lp[b * 6 + 2 * a]);
+            fmax = std::max(fmax, lp[b * 6 + 2 * a + 1]);
+        }
+        p->s0[a] = (int)fmin;
+        // +1: an FP32 coordinate just below an integer may round up, moving
+        // its first tap one cell to the right
+        g.L[a] = (int)(fmax - fmin) + 2 * p->m + 1;
+    }
+    g.B = choose_bin(d, p->m);
+    g.Pt = g.B + 2 * p->m;              // first tap offset in [0, B], 2m taps
+    g.R = 1 + (2 * p->m - 1) / g.B;     // bins below that reach into a bin
+    for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
+    {
+        const size_t ts = p->prec == ML_F32 ? 4 : 8;
+        const int64_t tc = g.tile_cells();
+        p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * (int64_t)ts)));
+    }
+    // ---- keys, sort
+    DevBuf urel, keys, keys2, idx, idx2;
+    ML_TRY(urel.ensure((size_t)n * d * sizeof(double)));
+    ML_TRY(keys.ensure((size_t)n * 4));
+    ML_TRY(keys2.ensure((size_t)n * 4));
+    ML_TRY(idx.ensure((size_t)n * 4));
+    ML_TRY(idx2.ensure((size_t)n * 4));
+    KeyArgs ka;
+    ka.tm = tm;
+    for (int a = 0; a < 3; ++a) ka.s0[a] = p->s0[a];
+    ka.B = g.B;
+    ka.nb0 = g.nb[0];
+    ka.nb1 = g.nb[1];
+    k_keys<<<grid_for(n), 256, 0, st>>>(points, n, ka, urel.as<double>(), keys.as<uint32_t>(), idx.as<int>());
+    ML_CUDA(cudaGetLastError());
+    const int64_t nbins = g.nbins();
+    int bits = 0;
+    while ((1LL << bits) < nbins) ++bits;
+    int *sorted_idx = nullptr;
+    ML_TRY(radix_sort(keys.as<uint32_t>(), idx.as<int>(), keys2.as<uint32_t>(), idx2.as<int>(), n, bits, st,
+                      &sorted_idx));
+    // the sorted keys sit in the buffer paired with sorted_idx
+    const uint32_t *sorted_keys = (sorted_idx == idx.as<int>()) ? keys.as<uint32_t>() : keys2.as<uint32_t>();
+    ML_TRY(p->perm.ensure((size_t)n * 4));
+    k_copy_int<<<grid_for(n), 256, 0, st>>>(sorted_idx, p->perm.as<int>(), n);
+    const size_t ts = p->prec == ML_F32 ? 4 : 8;
+    ML_TRY(p->coords.ensure((size_t)n * d * ts));
+    if (p->prec == ML_F32)
+        k_gather_coords<float><<<grid_for(n), 256, 0, st>>>(urel.as<double>(), p->perm.as<int>(), n, d, p->coords.as<float>());
+    else
+        k_gather_coords<double><<<grid_for(n), 256, 0, st>>>(urel.as<double>(), p->perm.as<int>(), n, d, p->coords.as<double>());
+    ML_CUDA(cudaGetLastError());
+    // ---- bins -> subproblems
+    DevBuf counts;
+    ML_TRY(counts.ensure((size_t)nbins * 4));
+    ML_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)nbins * 4, st));
+    k_bin_count<<<grid_for(n), 256, 0, st>>>(sorted_keys, n, counts.as<int>());
+    ML_CUDA(cudaGetLastError());
+    std::vector<int> hc(nbins);
+    ML_CUDA(cudaMemcpyAsync(hc.data(), counts.p, (size_t)nbins * 4, cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> sb, ss, sc, bs(nbins + 1);
+    int64_t pos = 0;
+    for (int64_t b = 0; b < nbins; ++b) {
+        bs[b] = (int)sb.size();
+        const int c = hc[b];
+        if (c > 0) {
+            const int parts = (c + kSubPoints - 1) / kSubPoints;
+            for (int q = 0; q < parts; ++q) {
+                const int lo_i = (int)((int64_t)c * q / parts), hi_i = (int)((int64_t)c * (q + 1) / parts);
+                sb.push_back((int)b);
+                ss.push_back((int)(pos + lo_i));
+                sc.push_back(hi_i - lo_i);
+            }
+        }
+        pos += c;
+    }
+    bs[nbins] = (int)sb.size();
+    p->nsub = (int)sb.size();
+    ML_TRY(p->sub_bin.ensure(sb.size() * 4));
+    ML_TRY(p->sub_start.ensure(sb.size() * 4));
+    ML_TRY(p->sub_count.ensure(sb.size() * 4));
+    ML_TRY(p->bin_sub.ensure(bs.size() * 4));
+    ML_CUDA(cudaMemcpy(p->sub_bin.p, sb.data(), sb.size() * 4, cudaMemcpyHostToDevice));
+    ML_CUDA(cudaMemcpy(p->sub_start.p, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice));
+    ML_CUDA(cudaMemcpy(p->sub_count.p, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice));
+    ML_CUDA(cudaMemcpy(p->bin_sub.p, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice));
+    urel.release();
+    keys.release();
+    keys2.release();
+    idx.release();
+    idx2.release();
+    // ---- Fourier tables (host FP64) -> device
+    window_fourier(p->n_os, p->m, p->kb_shape, p->N / 2, p->phihat);
+    kernel_fourier(p->sigma_s, p->N, d, p->eps_B, p->p_reg, p->bhat);
+    slot_multiplier(p->N, d, p->n_os, p->bhat, p->phihat, p->mult);
+    for (int a = 0; a < d; ++a) {
+        std::vector<double> M, Mt;
+        trig_matrix(p->N, p->n_os, p->s0[a], g.L[a], M);
+        Mt.assign(M.size(), 0.0);
+        for (int s = 0; s < g.K; ++s)
+            for (int j = 0; j < g.L[a]; ++j) Mt[(size_t)j * g.K + s] = M[(size_t)s * g.L[a] + j];
+        if (p->prec == ML_F32) {
+            ML_TRY(upload<float>(p->trig_f[a], M));
+            ML_TRY(upload<float>(p->trig_b[a], Mt));
+        } else {
+            ML_TRY(upload<double>(p->trig_f[a], M));
+            ML_TRY(upload<double>(p->trig_b[a], Mt));
+        }
+    }
+    if (p->prec == ML_F32) ML_TRY(upload<float>(p->mult_d, p->mult));
+    else ML_TRY(upload<double>(p->mult_d, p->mult));
+    // ---- degrees D = W~ 1 - K(0) (sorted order), D^{-1/2}
+    ML_TRY(ensure_workspace(p, 1));
+    ML_TRY(p->deg.ensure((size_t)n * 8));
+    ML_TRY(p->dinv.ensure((size_t)n * 8));
+    ApplyVec v{nullptr, 1, p->deg.as<double>(), 1, 1};
+    ApplyOpts o;
+    o.sorted_out = true;
+    ML_TRY(apply_layer(p, v, o, st));
+    ML_CUDA(cudaMemsetAsync(p->status.p, 0, 4, st));
+    k_dinv<<<grid_for(n), 256, 0, st>>>(p->deg.as<double>(), n, p->dinv.as<double>(), p->status.as<int>());
+    ML_CUDA(cudaGetLastError());
+    int bad = 0;
+    ML_CUDA(cudaMemcpyAsync(&bad, p->status.p, 4, cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    {
+        std::vector<double> hd(n);
+        ML_CUDA(cudaMemcpy(hd.data(), p->deg.p, n * 8, cudaMemcpyDeviceToHost));
+        p->deg_min = *std::min_element(hd.begin(), hd.end());
+        p->deg_max = *std::max_element(hd.begin(), hd.end());
+    }
+    if (bad) return fail(ML_ERR_DEGREE, "a degree D_i is not positive: D^{-1/2} is undefined (isolated point or too coarse an approximation)");
+    return ML_OK;
+}
+
+}  // namespace ml
+
+int64_t ml_plan_s::device_bytes() const
+{
+    int64_t t = 0;
+    const ml::DevBuf *bufs[] = {&perm, &coords, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub,
+                                &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
+                                &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status};
+    for (auto *b : bufs) t += (int64_t)b->bytes;
+    return t;
+}
+
+static void release_all(ml_plan_s *p)
+{
+    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
+                          &p->bin_sub, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
+                          &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
+                          &p->stage_y, &p->status};
+    for (auto *b : bufs) b->release();
+}
+
+extern "C" {
+
+const char *ml_last_error(void) { return ml::g_err.c_str(); }
+
+const char *ml_version(void) { return "ml_fastsum 0.1 (sm_103a)"; }
+
+ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int m,
+                          double eps_B, int p_reg, ml_prec prec, double target_rel_err, void *stream)
+{
+    using namespace ml;
+    if (!out) return fail(ML_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!points) return fail(ML_ERR_ARG, "points is null");
+    if (n < 2 || n > (int64_t)INT32_MAX - 1) return fail(ML_ERR_ARG, "n must be in [2, 2^31-2]");
+    if (d < 1 || d > 3) return fail(ML_ERR_ARG, "d must be 1, 2 or 3");
+    if (!(sigma > 0) || !std::isfinite(sigma)) return fail(ML_ERR_ARG, "sigma must be positive and finite");
+    if (N != 0 && (N < 4 || N > kMaxN || (N & 1))) return fail(ML_ERR_ARG, "N must be 0 or even in [4, 512]");
+    if (m != 0 && (m < 2 || m > kMaxM)) return fail(ML_ERR_ARG, "m must be 0 or in [2, 8]");
+    if (!(eps_B >= 0 && eps_B < 0.5)) return fail(ML_ERR_ARG, "eps_B must be in [0, 1/2)");
+    if (eps_B > 0 && (p_reg < 1 || p_reg > 8)) return fail(ML_ERR_ARG, "p_reg must be in [1, 8] when eps_B > 0");
+    if (prec != ML_F32 && prec != ML_F64) return fail(ML_ERR_ARG, "prec must be ML_F32 or ML_F64");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+    ml_plan_s *p = new (std::nothrow) ml_plan_s;
+    if (!p) return fail(ML_ERR_OOM, "host allocation failed");
+    p->n = n;
+    p->d = d;
+    p->sigma = sigma;
+    p->N = N;
+    p->m = m;
+    p->eps_B = eps_B;
+    p->p_reg = eps_B > 0 ? p_reg : 0;
+    p->prec = prec;
+    p->target = target_rel_err > 0 ? target_rel_err : (prec == ML_F32 ? 1e-4 : 1e-6);
+    ml_status st = plan_impl(p, points, (cudaStream_t)stream);
+    if (st != ML_OK) {
+        release_all(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return ML_OK;
+}
+
+ml_status ml_plan_destroy(ml_plan_t plan)
+{
+    if (!plan) return ML_OK;
+    release_all(plan);
+    delete plan;
+    return ML_OK;
+}
+
+ml_status ml_plan_get_info(ml_plan_t p, ml_plan_info *info)
+{
+    if (!p || !info) return ml::fail(ML_ERR_ARG, "null plan or info");
+    std::memset(info, 0, sizeof(*info));
+    info->n = p->n;
+    info->d = p->d;
+    info->N = p->N;
+    info->m = p->m;
+    info->n_os = p->n_os;
+    for (int a = 0; a < 3; ++a) {
+        info->L[a] = p->g.L[a];
+        info->center[a] = p->center[a];
+    }
+    info->bin = p->g.B;
+    info->nbins = (int)p->g.nbins();
+    info->nsub = p->nsub;
+    info->prec = p->prec;
+    info->domain = p->domain;
+    info->p_reg = p->p_reg;
+    info->eps_B = p->eps_B;
+    info->sigma = p->sigma;
+    info->sigma_s = p->sigma_s;
+    info->scale = p->scale;
+    info->target_rel_err = p->target;
+    info->deg_min = p->deg_min;
+    info->deg_max = p->deg_max;
+    info->device_bytes = p->device_bytes();
+    return ML_OK;
+}
+
+ml_status ml_plan_copy_table(ml_plan_t p, int which, double *out, int64_t count)
+{
+    if (!p || !out) return ml::fail(ML_ERR_ARG, "null plan or output");
+    if (which == 0 || which == 1) {
+        const std::vector<double> &t = which == 0 ? p->bhat : p->phihat;
+        if (count < (int64_t)t.size()) return ml::fail(ML_ERR_ARG, "count too small");
+        std::memcpy(out, t.data(), t.size() * sizeof(double));
+        return ML_OK;
+    }
+    if (which == 2) {
+        if (count < p->n) return ml::fail(ML_ERR_ARG, "count too small");
+        std::vector<double> deg(p->n);
+        std::vector<int> perm(p->n);
+        ML_CUDA(cudaDeviceSynchronize());
+        ML_CUDA(cudaMemcpy(deg.data(), p->deg.p, p->n * 8, cudaMemcpyDeviceToHost));
+        ML_CUDA(cudaMemcpy(perm.data(), p->perm.p, p->n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < p->n; ++i) out[perm[i]] = deg[i];
+        return ML_OK;
+    }
+    return ml::fail(ML_ERR_ARG, "unknown table");
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+"""GPU parity of the Lanczos eigensolver (Sec. 3) against dense eigensolves of
+the oracle: eigenvalues within 1e-8, eigenvector (or, inside clusters of
+near-degenerate eigenvalues, subspace) angles within 1e-6."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import eigen, graph
+from paper_2007_05239_gb300 import _lib as ml
+from paper_2007_05239_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def check_pairs(lam, V, lam_ref, V_ref, k, tol_val=1e-8, tol_ang=1e-6):
+    assert np.abs(lam - lam_ref).max() <= tol_val, (lam, lam_ref)
+    groups = eigen.eigen_groups(lam_ref, rel_gap=1e-6)
+    for g in groups:
+        if max(g) >= k:
+            continue
+        ang = eigen.subspace_angle(V[:, g], V_ref[:, g])
+        assert ang <= tol_ang, (g, ang)
+
+
+def test_single_layer_n2000_d3_k10():
+    # the small FP64 workload: n = 2000 uniform in [-1/4,1/4]^3, sigma = 0.1
+    X = workloads.uniform_cube(2000, 3, seed=1)
+    sigma, k = 0.1, 10
+    plan = ml.ml_fastsum_plan(dev(X), sigma, prec="f64", target_rel_err=1e-12)
+    V = torch.empty(k * 2000, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs([plan], k, p=1.0, tol=1e-11, seed=3, evecs=V)
+    assert st == ml.ML_OK and nconv == k
+    V = V.cpu().numpy().reshape(k, 2000).T
+    lam_ref, V_ref = eigen.lsym_eigs(X, sigma, k + 3)
+    check_pairs(lam, V, lam_ref[:k], V_ref[:, :k], k)
+    assert abs(lam[0]) <= 1e-9
+    v0 = np.sqrt(graph.degrees(X, sigma))
+    assert abs(abs(V[:, 0] @ v0) / np.linalg.norm(v0) - 1) <= 1e-9
+
+
+def test_multilayer_p1():
+    n = 1500
+    layers = [workloads.uniform_cube(n, 3, seed=100), workloads.uniform_cube(n, 2, seed=101)]
+    sig = [0.1, 0.08]
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    k = 8
+    V = np.empty(k * n)
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=1.0, tol=1e-11, seed=5, evecs=V)   # host output
+    assert st == ml.ML_OK
+    lam_ref, V_ref = eigen.L1_eigs(layers, sig, k + 3)
+    check_pairs(lam, V.reshape(k, n).T, lam_ref[:k], V_ref[:, :k], k)
+
+
+def test_power_mean_p_minus_one():
+    n = 800
+    layers = [workloads.uniform_cube(n, 3, seed=110), workloads.uniform_cube(n, 2, seed=111)]
+    sig = [0.1, 0.1]
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    k = 6
+    V = torch.empty(k * n, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=-1.0, tol=1e-10, seed=7, evecs=V)
+    assert st == ml.ML_OK
+    lam_ref, V_ref = eigen.Lp_eigs(layers, sig, -1.0, k + 3)
+    check_pairs(lam, V.cpu().numpy().reshape(k, n).T, lam_ref[:k], V_ref[:, :k], k, tol_val=1e-8, tol_ang=1e-6)
+    # the smallest eigenvalue of L_{-1,delta} sits at delta when every layer has lambda_0 = 0
+    assert abs(lam[0] - math.log(2.0)) <= 1e-8
+
+
+def test_argument_errors():
+    X = workloads.uniform_cube(100, 3, seed=120)
+    plan = ml.ml_fastsum_plan(dev(X), 0.1, prec="f64")
+    for bad in (dict(k=0), dict(k=51), dict(k=3, p=2.0)):
+        with pytest.raises(ml.MLError):
+            ml.ml_lanczos_eigs([plan], **bad)
