@@ -21,9 +21,11 @@ Readings of what the paper leaves open (listed in the design doc as well):
     pair distance is <= 1/2 - eps_B where K_R = K.
   - eps_B = 0 ("box"): s = a / h with h the largest bounding-box half-extent
     and a = min(1/4, 1 / (2 + (sigma/h) sqrt(ln(2d/eps_wrap)))), which keeps
-    the periodisation error 2d exp(-(1-2a)^2/sigma'^2) below eps_wrap; K_R is
-    the plain Gaussian restricted to the period cube [-1/2, 1/2)^d.
-* Regulariser (reading 2).  For eps_B > 0, K_R(r) = K(r) for
+    the periodisation error 2d exp(-(1-2a)^2/sigma'^2) below eps_wrap.
+* Regulariser (reading 2).  K_R is the smooth 1-periodic regularised kernel
+  of the footnote to Sec. 4.  For eps_B = 0 it is the 1-periodisation of the
+  Gaussian, K_R(y) = sum_{r in Z^d} K(y + r), which equals K up to the wrap
+  error above for every difference of two nodes.  For eps_B > 0, K_R(r) = K(r) for
   r <= r_I = 1/2 - eps_B; on (r_I, 1/2] it is the two-point Taylor polynomial
   of degree 2p-1 matching K's derivatives 0..p-1 at r_I, with value K(1/2)
   and vanishing derivatives 1..p-1 at r = 1/2; beyond 1/2 (cube corners) it
@@ -100,7 +102,9 @@ def regulariser_poly(sigma, eps_B, p):
 
 
 def K_R(r, sigma, eps_B=0.0, p=0):
-    """Regularised radial kernel (reading 2); the plain Gaussian when eps_B = 0."""
+    """Regularised radial kernel of the ball domain (reading 2); the plain
+    Gaussian when eps_B = 0 (the box domain samples its periodisation instead,
+    see kernel_samples)."""
     r = np.asarray(r, dtype=np.float64)
     K = np.exp(-(r * r) / (sigma * sigma))
     if eps_B <= 0:
@@ -112,16 +116,34 @@ def K_R(r, sigma, eps_B=0.0, p=0):
     return np.where(r <= rI, K, P)
 
 
+def periodised_gaussian_1d(y, sigma, images=None):
+    """sum_{r in Z} exp(-(y + r)^2 / sigma^2), truncated where the terms vanish."""
+    y = np.asarray(y, dtype=np.float64)
+    R = images if images is not None else 2 + int(math.ceil(8.0 * sigma))
+    return sum(np.exp(-((y + r) ** 2) / (sigma * sigma)) for r in range(-R, R + 1))
+
+
 # ------------------------------------------------------- Fourier coefficients
+def kernel_samples(sigma_s, N, d, eps_B=0.0, p=0):
+    """K_R on the grid k/N, k in I_N^d (reading 2), shape (N,)*d indexed by k + N/2."""
+    k = np.arange(-N // 2, N // 2) / N
+    if eps_B <= 0:
+        g1 = periodised_gaussian_1d(k, sigma_s)
+        out = g1
+        for _ in range(d - 1):
+            out = np.multiply.outer(out, g1)
+        return out
+    grids = np.meshgrid(*([k] * d), indexing="ij")
+    r = np.sqrt(sum(g * g for g in grids))
+    return K_R(r, sigma_s, eps_B, p)
+
+
 def bhat(sigma_s, N, d, eps_B=0.0, p=0):
     """b_l, l in I_N^d, from N^d samples of K_R on k/N and a d-dim FFT.
 
     Returned as a real array of shape (N,)*d indexed by l + N/2 on every axis.
     """
-    k = np.arange(-N // 2, N // 2) / N
-    grids = np.meshgrid(*([k] * d), indexing="ij")
-    r = np.sqrt(sum(g * g for g in grids))
-    samples = K_R(r, sigma_s, eps_B, p)
+    samples = kernel_samples(sigma_s, N, d, eps_B, p)
     # FFT wants index 0 at k = 0: shift, transform, shift back to l + N/2 order.
     F = np.fft.fftn(np.fft.ifftshift(samples)) / float(N) ** d
     return np.real(np.fft.fftshift(F))

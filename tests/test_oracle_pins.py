@@ -120,10 +120,11 @@ def test_power_mean_two_commuting_layers():
 # ------------------------------------------------------------------ Alg. 1
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_bhat_box_matches_poisson(d):
-    # Samples of exp(-y^2/s^2) on the period cube: b_l = prod_a sum_r c(l_a + rN)
-    # with c(x) = s sqrt(pi) exp(-pi^2 s^2 x^2) (Fourier transform of the
-    # Gaussian, aliased by sampling), up to the wrap term exp(-1/(4 s^2)).
-    s, N = 0.07, 16
+    # Samples of the 1-periodised Gaussian: by Poisson summation its Fourier
+    # coefficients are c(j) = s sqrt(pi) exp(-pi^2 s^2 j^2), and sampling on
+    # k/N aliases them: b_l = prod_a sum_r c(l_a + rN) exactly.  A wide s
+    # makes the periodisation matter.
+    s, N = 0.3, 16
     b = alg1.bhat(s, N, d)
     l = np.arange(-N // 2, N // 2)
     c1 = sum(s * math.sqrt(math.pi) * np.exp(-(math.pi * s * (l + r * N)) ** 2) for r in range(-3, 4))
@@ -148,11 +149,12 @@ def test_adjoint_ndft_on_grid_is_fft():
     assert np.allclose(back, N * N * V, atol=1e-9)
 
 
-def _tail_bound(s, N, d):
-    """Bound on max |K_RF - K| over the domain for the box reading:
-    per dimension twice the Fourier tail beyond N/2 plus the wrap term, times d."""
+def _tail_bound(s, N, d, a=0.25):
+    """Bound on max |K_RF - K| over differences of nodes in [-a, a]^d for the
+    box reading: per dimension twice the Fourier tail beyond N/2 (truncation
+    plus aliasing) and the wrap term 2 exp(-(1-2a)^2/s^2), times 3d."""
     tail = 2 * sum(s * math.sqrt(math.pi) * math.exp(-(math.pi * s * l) ** 2) for l in range(N // 2, N // 2 + 200))
-    wrap = 2 * math.exp(-0.25 / s ** 2)
+    wrap = 2 * math.exp(-((1 - 2 * a) ** 2) / s ** 2)
     return 3 * d * (2 * tail + wrap)
 
 
@@ -166,7 +168,7 @@ def test_alg1_against_direct_sum(d, N):
     b = alg1.bhat(ss, N, d)
     got = alg1.fastsum_W(Xs, v, b)
     ref = graph.W_apply(X, sigma, v)
-    bound = _tail_bound(ss, N, d) * np.abs(v).sum()
+    bound = _tail_bound(ss, N, d, a=np.abs(Xs).max()) * np.abs(v).sum()
     err = np.abs(got - ref).max()
     assert err <= bound
     # a coarser bandwidth must be visibly worse (the comparison has teeth)
@@ -194,6 +196,17 @@ def test_regulariser_matching_conditions():
     # inside the ball K_R is the Gaussian
     r = np.linspace(0, rI, 7)
     assert np.allclose(alg1.K_R(r, sigma, eps_B, p), np.exp(-r ** 2 / sigma ** 2), rtol=1e-15)
+
+
+def test_box_reading_wide_kernel_two_points():
+    # Two points with a kernel much wider than their distance: the box scaling
+    # shrinks the cloud so that the periodised kernel's wrap stays below
+    # 1e-8; Alg. 1 then reproduces the closed form W = [[0, w], [w, 0]].
+    X = np.array([[0.0, 0.0, 0.0], [0.05, 0.0, 0.0]])
+    Xs, ss, _, _ = alg1.scale_to_domain(X, 0.1, 0.0, 1e-8)
+    w = math.exp(-0.25)
+    y = alg1.fastsum_W(Xs, np.array([2.0, -3.0]), alg1.bhat(ss, 16, 3))
+    assert np.abs(y - [-3 * w, 2 * w]).max() <= 1e-7
 
 
 def test_ball_domain_scaling():
