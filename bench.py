@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the multilayer Gaussian-graph fast summation + Lanczos hot path.
+
+One step = one pass of the whole hot path over the workload: plan every
+layer (domain scaling, parameter choice, sort, Fourier tables, degrees) and
+compute the k smallest eigenpairs of the power mean Laplacian with the
+Lanczos method, every operator application going through the NFFT-based
+fast summation.  The headline value is the fast-summation throughput of that
+step in points x vectors per second (n x layer-vector applications / step
+time), the metric's unit; the step time itself is the k-eigenpair Lanczos
+time (plan included), reported as lanczos_s.
+
+Default workload: the image-like multilayer graph, n = 1,000,000 pixels,
+3 layers of d = 3 (RGB; x, y, texture; box-filtered RGB), sigma = 0.2, FP64
+form at 1e-6 relative error, k = 20 eigenpairs of L_{-1,delta} (p = -1).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload NAME] [--prec f32|f64] [--p 1|-1] [--k K]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload on its own GPU (the path has no exchange step); the value is the
+sum over ranks and the time the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# ------------------------------------------------------------- workloads
+WORKLOADS = {
+    "image_voronoi_n1e6_T3": dict(desc="1000x1000 image, 8 Voronoi colour regions + N(0,0.02) noise; layers RGB, "
+                                       "(x,y,texture), 3x3 box-filtered RGB", n=1_000_000, T=3, d=3, sigma=0.2,
+                                  prec="f64", target=1e-6, k=20, p=-1.0),
+    "gmm_n250k_T52_d2": dict(desc="250k samples of a 12-component GMM in R^104, 52 layers of 2 features", n=250_000,
+                             T=52, d=2, sigma="half_range", prec="f32", target=1e-4, k=10, p=1.0),
+    "image_discs_n1e7_T2": dict(desc="4000x2500 image, 5 uniform-colour discs + noise; layers RGB, (x,y,texture)",
+                                n=10_000_000, T=2, d=3, sigma=0.15, prec="f32", target=1e-4, k=10, p=1.0),
+    "single_n2000_d3": dict(desc="n=2000 uniform in [-1/4,1/4]^3", n=2000, T=1, d=3, sigma=0.1, prec="f64",
+                            target=1e-12, k=10, p=1.0),
+}
+
+
+def make_layers(name):
+    from paper_2007_05239_gb300 import workloads as wl
+    spec = WORKLOADS[name]
+    if name == "image_voronoi_n1e6_T3":
+        layers = wl.image_voronoi_layers(1000, 1000, 8, 0.02, seed=2)
+    elif name == "gmm_n250k_T52_d2":
+        layers, _ = wl.gmm_band_layers(250_000, 104, 12, seed=3)
+    elif name == "image_discs_n1e7_T2":
+        layers = wl.image_discs_layers(2500, 4000, 5, 0.02, seed=4)
+    else:
+        layers = [wl.uniform_cube(2000, 3, seed=1)]
+    if spec["sigma"] == "half_range":
+        sig = [0.5 * float((L.max(0) - L.min(0)).max()) for L in layers]
+    else:
+        sig = [float(spec["sigma"])] * len(layers)
+    return layers, sig
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- peaks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# 152 SMs x 2070 MHz: FP64 4 flop/clk/SM (2 DFMA), FP32 256 flop/clk/SM (128 FFMA)
+ALU_PEAK_TFLOPS = {"f64": 152 * 2.070e9 * 4 / 1e12, "f32": 152 * 2.070e9 * 256 / 1e12}
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle (direct FP64 sums) timed on the host cores, as it stands."""
+    if rank != 0:
+        return 0
+    from oracle import graph
+    spec = WORKLOADS[args.workload]
+    layers, sig = make_layers(args.workload)
+    n, T = layers[0].shape[0], len(layers)
+    rng = np.random.default_rng(0)
+    v = rng.uniform(0, 1, n)
+
+    def step(rows):
+        for t in range(T):
+            graph.W_apply(layers[t], sig[t], v, rows=rows)
+
+    # size the per-step row sample to ~4 s
+    r0 = np.sort(rng.choice(n, size=min(n, 16), replace=False))
+    t0 = time.perf_counter()
+    step(r0)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    R = int(min(n, max(16, 16 * 4.0 / dt)))
+    rows = np.sort(rng.choice(n, size=R, replace=False))
+    for _ in range(args.warmup):
+        step(rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(rows)
+    el = time.perf_counter() - t0
+    val = R * T * args.steps / el / 1e9
+    cores = graph.num_threads()
+    line = {
+        "impl": "reference", "metric": metric_name(spec), "value": val, "unit": "Gpts·vec/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, spec, n, T),
+        "cpu_baseline": {"value": val, "unit": "Gpts·vec/s", "cores": cores, "kind": "oracle",
+                         "sample": f"direct FP64 sum (W v) on {R} sampled rows of each of the {T} layers per step"},
+        "e2e": {"value": val, "unit": "Gpts·vec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def metric_name(spec):
+    tol = "1e-6" if spec["prec"] == "f64" else "1e-4"
+    return (f"fast-summation Gpts·vec/s ({spec['prec'].upper()} form, <= {tol} rel err vs FP64) inside the "
+            f"k={spec['k']} Lanczos step (p={int(spec['p'])})")
+
+
+def config_dict(args, spec, n, T):
+    return {"workload": args.workload, "desc": spec["desc"], "n": n, "layers": T, "d": spec["d"],
+            "sigma": spec["sigma"], "prec": spec["prec"], "target_rel_err": spec["target"], "k": spec["k"],
+            "p": spec["p"], "l2": "inputs exceed L2 (per-layer point data and the Krylov basis are > 129 MB)",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+# ------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="image_voronoi_n1e6_T3", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["f32", "f64"])
+    ap.add_argument("--p", type=float, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    spec = dict(WORKLOADS[args.workload])
+    if args.prec:
+        spec["prec"] = args.prec
+        spec["target"] = 1e-6 if args.prec == "f64" else 1e-4
+    if args.p is not None:
+        spec["p"] = args.p
+    if args.k is not None:
+        spec["k"] = args.k
+    WORKLOADS[args.workload] = spec
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2007_05239_gb300 import _lib as ml
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    layers, sig = make_layers(args.workload)
+    n, T = layers[0].shape[0], len(layers)
+    dev_layers = [torch.as_tensor(L, device="cuda") for L in layers]
+    k, p, prec, target = spec["k"], spec["p"], spec["prec"], spec["target"]
+
+    def step(dl, evecs):
+        plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dl, sig)]
+        lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=p, tol=1e-8, seed=1, evecs=evecs)
+        applied = sum(pl.info["applied_vectors"] for pl in plans) * n
+        ms = [pl.info["m"] for pl in plans]
+        for pl in plans:
+            pl.destroy()
+        return lam, nconv, applied, ms
+
+    evecs = torch.empty(n * k, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        step(dev_layers, evecs)
+    torch.cuda.synchronize()
+    barrier()
+
+    # ---- timed region (device-resident inputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ml.ml_profile_reset()
+    ml.ml_profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    applied = 0
+    for _ in range(args.steps):
+        lam, nconv, a, msz = step(dev_layers, evecs)
+        applied += a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ml.ml_profile_enable(False)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof = ml.ml_profile_read()
+    t_max = ms_total
+    tot_applied = applied
+    if world > 1:
+        tt = torch.tensor([ms_total, float(applied)], dtype=torch.float64, device="cuda")
+        t_all = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(t_all, tt)
+        t_max = max(float(x[0]) for x in t_all)
+        tot_applied = sum(float(x[1]) for x in t_all)
+    value = tot_applied / (t_max / 1e3) / 1e9
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # ---- roofline of the dominant kernel family
+    d = spec["d"]
+    m = msz[0]
+    taps = (2 * m) ** d
+    fam = max(("spread", "interp"), key=lambda f: prof.get(f, (0, 0.0))[1])
+    fam_launches, fam_ms = prof.get(fam, (0, 0.0))
+    flops = applied * 2.0 * taps                  # one multiply-add per tap and point-vector
+    achieved = flops / (fam_ms / 1e3) / 1e12 if fam_ms > 0 else 0.0
+    peak = ALU_PEAK_TFLOPS[prec]
+    roofline = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"nominal {prec.upper()} ALU rate: 152 SMs x 2070 MHz x "
+                               f"{4 if prec == 'f64' else 256} flop/clk/SM",
+                "work": f"2 flop per tap, (2m)^d = {taps} taps per point-vector, m = {m}",
+                "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()}}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    host_layers = [torch.as_tensor(L).pin_memory() for L in layers]
+    host_evecs = torch.empty(n * k, dtype=torch.float64).pin_memory()
+    h2d = sum(L.numel() * 8 for L in host_layers)
+    d2h = n * k * 8 + k * 8
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    applied_e2e = 0
+    for _ in range(args.steps):
+        dl = [x.to("cuda", non_blocking=True) for x in host_layers]
+        lam_e, _, a, _ = step(dl, host_evecs)
+        applied_e2e += a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_val = applied_e2e / (e2e_ms / 1e3) / 1e9
+    if world > 1:
+        tt = torch.tensor([e2e_ms, float(applied_e2e)], dtype=torch.float64, device="cuda")
+        t_all = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(t_all, tt)
+        e2e_val = sum(float(x[1]) for x in t_all) / (max(float(x[0]) for x in t_all) / 1e3) / 1e9
+
+    line = {
+        "metric": metric_name(spec), "value": value, "unit": "Gpts·vec/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic", "config": config_dict(args, spec, n, T),
+        "lanczos_s": t_max / args.steps / 1e3, "eigenvalues": [float(x) for x in lam[:min(5, k)]],
+        "nconv": int(nconv), "gpu_launches": launches,
+        "e2e": {"value": e2e_val, "unit": "Gpts·vec/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline, "clocks": clk,
+    }
+
+    # ---- CPU baseline (oracle on the host cores) and sampled accuracy, rank 0 at N = 1
+    if rank == 0 and world == 1 and not args.no_baseline:
+        line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch):
+    """Time the oracle's direct FP64 sum of (1/T) sum_t W_t v on a bounded row
+    sample (~12 s), and compare the GPU's FP64/FP32-form result on the same rows."""
+    from oracle import graph
+    n, T = layers[0].shape[0], len(layers)
+    rng = np.random.default_rng(123)
+    v = rng.uniform(0, 1, n)
+    r0 = np.sort(rng.choice(n, size=min(n, 8), replace=False))
+    t0 = time.perf_counter()
+    for t in range(T):
+        graph.W_apply(layers[t], sig[t], v, rows=r0)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    R = int(min(n, max(32, 8 * 12.0 / dt)))
+    rows = np.sort(rng.choice(n, size=R, replace=False))
+    t0 = time.perf_counter()
+    ref = sum(graph.W_apply(layers[t], sig[t], v, rows=rows) for t in range(T)) / T
+    el = time.perf_counter() - t0
+    plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dev_layers, sig)]
+    Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+    ml.ml_fastsum_apply(plans, torch.as_tensor(v[:, None].copy(), device="cuda"), Y, mode="raw")
+    got = Y.cpu().numpy()[rows, 0]
+    for pl in plans:
+        pl.destroy()
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    base = {"value": R * T / el / 1e9, "unit": "Gpts·vec/s", "cores": graph.num_threads(), "kind": "oracle",
+            "sample": f"direct FP64 sum of (1/T) sum_t W_t v on {R} sampled rows x {T} layers ({el:.1f} s)"}
+    return base, {"E2": err, "rows": R, "vector": "uniform [0,1]", "operator": "(1/T) sum_t W_t"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

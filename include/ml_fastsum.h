@@ -93,6 +93,8 @@ typedef struct {
     double target_rel_err;
     double deg_min, deg_max; /* range of the computed degrees                    */
     int64_t device_bytes;    /* device memory owned by the plan                  */
+    int64_t applied_vectors; /* vectors pushed through this layer's fast summation
+                                since the plan was made (work counter)          */
 } ml_plan_info;
 
 /*
@@ -180,6 +182,24 @@ ml_status ml_plan_get_info(ml_plan_t plan, ml_plan_info *info);
  * `out` is host memory of `count` doubles; count must be at least the size.
  */
 ml_status ml_plan_copy_table(ml_plan_t plan, int which, double *out, int64_t count);
+
+/*
+ * Kernel timing (tracing; the paper has no counterpart).  While enabled, every
+ * library kernel launch is bracketed by two CUDA events recorded on the
+ * stream it is launched on; ml_profile_read synchronises those events and
+ * returns, per kernel family ("spread", "fold", "axis", "mult", "interp",
+ * "dots", "update", ...), the number of launches and the summed device time.
+ *   ml_profile_enable(1/0)   switch recording on/off (off by default)
+ *   ml_profile_reset()       drop all records
+ *   ml_profile_read(i, name, launches, ms): entry i (0-based) of the table;
+ *            returns ML_ERR_ARG when i is past the end.  `name` receives a
+ *            pointer to a static string owned by the library.
+ * Recording costs two event records per launch; it is meant for measurement
+ * runs, not for production.
+ */
+ml_status ml_profile_enable(int on);
+ml_status ml_profile_reset(void);
+ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *ms);
 
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 ml_status ml_plan_destroy(ml_plan_t plan);

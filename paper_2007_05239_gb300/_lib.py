@@ -25,7 +25,8 @@ MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
 EXPORTS = ["ml_fastsum_plan", "ml_fastsum_apply", "ml_lanczos_eigs", "ml_plan_get_info",
-           "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version"]
+           "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
+           "ml_profile_reset", "ml_profile_read"]
 
 
 class MLError(RuntimeError):
@@ -40,7 +41,8 @@ class PlanInfo(ctypes.Structure):
                 ("nsub", ctypes.c_int), ("prec", ctypes.c_int), ("domain", ctypes.c_int), ("p_reg", ctypes.c_int),
                 ("eps_B", ctypes.c_double), ("sigma", ctypes.c_double), ("sigma_s", ctypes.c_double),
                 ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("target_rel_err", ctypes.c_double),
-                ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("applied_vectors", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -81,6 +83,13 @@ def load():
     lib.ml_last_error.argtypes = []
     lib.ml_version.restype = ctypes.c_char_p
     lib.ml_version.argtypes = []
+    lib.ml_profile_enable.restype = ctypes.c_int
+    lib.ml_profile_enable.argtypes = [ctypes.c_int]
+    lib.ml_profile_reset.restype = ctypes.c_int
+    lib.ml_profile_reset.argtypes = []
+    lib.ml_profile_read.restype = ctypes.c_int
+    lib.ml_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_double)]
     _LIB = lib
     return lib
 
@@ -192,6 +201,27 @@ def ml_lanczos_eigs(layers, k, p=1.0, tol=0.0, maxit=0, seed=0, evecs=None, stre
                              _stream(stream))
     _check(st)
     return ev, nconv.value, st
+
+
+def ml_profile_enable(on=True):
+    _check(load().ml_profile_enable(1 if on else 0))
+
+
+def ml_profile_reset():
+    _check(load().ml_profile_reset())
+
+
+def ml_profile_read():
+    """{kernel family: (launches, total ms)} recorded since the last reset."""
+    lib = load()
+    out, i = {}, 0
+    name = ctypes.c_char_p()
+    launches = ctypes.c_int64()
+    ms = ctypes.c_double()
+    while lib.ml_profile_read(i, ctypes.byref(name), ctypes.byref(launches), ctypes.byref(ms)) == ML_OK:
+        out[name.value.decode()] = (launches.value, ms.value)
+        i += 1
+    return out
 
 
 def version():

@@ -23,6 +23,7 @@ ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaS
 {
     if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
     ML_TRY(ensure_workspace(p, v.nv));
+    p->applied += v.nv;
     if (p->prec == ML_F32) {
         switch (p->d) {
         case 1: return run_layer_f32_d1(p, v, o, st);
@@ -82,6 +83,7 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             const double alpha = per_layer ? 1.0 : 1.0 / T;
             const int acc = (!per_layer && t > 0) ? 1 : 0;
             const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+            ProfScope pr("degree_out", st);
             k_degree_out<<<blocks, 256, 0, st>>>(layers[t]->deg.as<double>(), layers[t]->perm.as<int>(), n, alpha,
                                                  acc, Yt);
             ML_CUDA(cudaGetLastError());

@@ -127,13 +127,17 @@ void kernel_fourier(double s, int N, int d, double eps_B, int p_reg, std::vector
         for (int k = -N / 2; k < N / 2; ++k)
             C[(size_t)l * N + (k + N / 2)] = std::cos(2.0 * kPi * (double)l * (double)k / N);
     if (eps_B <= 0) {
-        // the box-domain kernel is the Gaussian on the period cube: separable
+        // box domain: K_R is the 1-periodisation of the Gaussian,
+        // sum_r exp(-|y + r|^2/s^2), a product of 1-d periodic factors
+        const int R = 2 + (int)std::ceil(8.0 * s);
         std::vector<double> b1(H, 0.0);
         for (int l = 0; l < H; ++l) {
             double acc = 0.0;
             for (int k = -N / 2; k < N / 2; ++k) {
                 const double y = (double)k / N;
-                acc += std::exp(-y * y / (s * s)) * C[(size_t)l * N + (k + N / 2)];
+                double kp = 0.0;
+                for (int r = -R; r <= R; ++r) kp += std::exp(-(y + r) * (y + r) / (s * s));
+                acc += kp * C[(size_t)l * N + (k + N / 2)];
             }
             b1[l] = acc / N;
         }

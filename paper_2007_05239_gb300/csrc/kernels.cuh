@@ -69,6 +69,7 @@ struct SpreadArgs {
     const int *sub_bin, *sub_start, *sub_count;
     const int *perm;
     const void *coords;      // T [n][D]
+    const double *wts;       // FP64 form: window weights [n][D][2M]
     const double *dinv;      // null: no pre-scaling
     const double *X;         // null: all-ones input
     int ldx;
@@ -93,6 +94,7 @@ struct InterpArgs {
     const int *sub_bin, *sub_start, *sub_count;
     const int *perm;
     const void *coords;
+    const double *wts;       // FP64 form: window weights [n][D][2M]
     const double *dinv;      // pre/post scale (normalized) or null
     const double *X;         // input (for the self term and the shift), null = ones
     int ldx;
@@ -148,10 +150,14 @@ __device__ __forceinline__ float fixed_scale(float sum_abs, float max_abs)
 }
 
 // ==================================================================== spread
-// FP32 form: weights and taps in FP32; each tile cell accumulates integers
-// (fixed point, per-subproblem power-of-two scale) with 32-bit shared-memory
-// atomics, which are exact and order-independent.  The tile is written to
-// the subproblem's scratch slot as FP32.
+// Shared-memory tiles are vector-major: tile[c * tc + cell], so that the NV
+// values of one tap fall in different banks.
+
+// FP32 form: one thread per point.  Weights and taps in FP32; each tile cell
+// accumulates integers (fixed point, per-subproblem power-of-two scale) with
+// 32-bit shared-memory atomics, which are exact and order-independent.  Each
+// lane walks its (qz, qy) rows starting at a lane-dependent offset, so lanes
+// whose points share a cell (clustered data) hit different addresses.
 template <int D, int M, int NV>
 __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
 {
@@ -160,10 +166,9 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
     __shared__ float s_part[2][NV][8];
     __shared__ float s_scale[NV];
     const int sub = blockIdx.x;
-    const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
-    constexpr int nv = NV;
+    const int start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int tc = tile_cells<D>(a.Pt);
-    for (int e = threadIdx.x; e < tc * nv; e += blockDim.x) tile[e] = 0;
+    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) tile[e] = 0;
 
     // per-vector sum and max of |u| over this subproblem's points
     float lsum[NV], lmax[NV];
@@ -182,25 +187,28 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
-        const float s = warp_sum(lsum[c]), mx = warp_max(lmax[c]);
+        const float sm = warp_sum(lsum[c]), mx = warp_max(lmax[c]);
         if (lane == 0) {
-            s_part[0][c][warp] = s;
+            s_part[0][c][warp] = sm;
             s_part[1][c][warp] = mx;
         }
     }
     __syncthreads();
-    if (threadIdx.x < nv) {
-        float s = 0.0f, mx = 0.0f;
+    if (threadIdx.x < NV) {
+        float sm = 0.0f, mx = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            s += s_part[0][threadIdx.x][w];
+            sm += s_part[0][threadIdx.x][w];
             mx = fmaxf(mx, s_part[1][threadIdx.x][w]);
         }
-        s_scale[threadIdx.x] = fixed_scale(s, mx);
+        s_scale[threadIdx.x] = fixed_scale(sm, mx);
     }
     __syncthreads();
 
-    (void)bin;
+    constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+    const int ry = (D == 2) ? lane % ny : (D == 3 ? (lane / nz) % ny : 0);
+    const int rz = (D == 3) ? lane % nz : 0;
     const float *coords = static_cast<const float *>(a.coords);
+    const int Pt = a.Pt;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
         const int orig = a.perm[i];
         const double ds = a.dinv ? a.dinv[i] : 1.0;
@@ -213,71 +221,117 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
         o[0] = window_row<M>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
         if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
         if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
-        const int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
 #pragma unroll 1
-        for (int qz = 0; qz < nz; ++qz) {
+        for (int qz0 = 0; qz0 < nz; ++qz0) {
+            int qz = qz0 + rz;
+            if (qz >= nz) qz -= nz;
 #pragma unroll 1
-            for (int qy = 0; qy < ny; ++qy) {
+            for (int qy0 = 0; qy0 < ny; ++qy0) {
+                int qy = qy0 + ry;
+                if (qy >= ny) qy -= ny;
                 const float wyz = (D >= 3 ? wz[qz] : 1.0f) * (D >= 2 ? wy[qy] : 1.0f);
-                int *row = tile + (((o[2] + qz) * a.Pt + o[1] + qy) * a.Pt + o[0]) * nv;
+                int *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
 #pragma unroll
                 for (int qx = 0; qx < 2 * M; ++qx) {
                     const float wt = wyz * wx[qx];
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) atomicAdd(row + qx * nv + c, fixed_round(u[c] * wt));
+                    for (int c = 0; c < NV; ++c) atomicAdd(row + c * tc + qx, fixed_round(u[c] * wt));
                 }
             }
         }
     }
     __syncthreads();
-    float *out = static_cast<float *>(a.scratch) + (int64_t)sub * tc * nv;
-    for (int e = threadIdx.x; e < tc * nv; e += blockDim.x) out[e] = (float)tile[e] / s_scale[e % nv];
+    float *out = static_cast<float *>(a.scratch) + (int64_t)sub * tc * NV;
+    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
+        const int c = e % NV, cell = e / NV;
+        out[e] = (float)tile[c * tc + cell] / s_scale[c];
+    }
 }
 
-// FP64 form: weights, taps and the tile in FP64 (shared-memory FP64 atomics).
+// A weight of the point held by the warp: lane l holds weights l and 32 + l
+// of the point's D x 2M row-major table (w0, w1); fetch entry k.
+__device__ __forceinline__ double warp_weight(double w0, double w1, int k)
+{
+    const double x = __shfl_sync(0xffffffffu, w0, k & 31);
+    const double y = __shfl_sync(0xffffffffu, w1, k & 31);
+    return k < 32 ? x : y;
+}
+
+constexpr int kF64Warps = 4;
+
+// FP64 form: one warp per point, each warp with a private tile, so no
+// atomics are needed.  Lane items are (qx, qy) pairs; each item walks qz and
+// adds u wx wy wz with one DFMA per tap.  The point's weights were computed
+// once at plan time (FP64, table wts[n][D][2M]).  At the end the warps'
+// tiles are summed in a fixed order.
 template <int D, int M, int NV>
-__global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
+__global__ void __launch_bounds__(32 * kF64Warps) k_spread_f64(const SpreadArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *tile = reinterpret_cast<double *>(smem_raw);
+    double *tiles = reinterpret_cast<double *>(smem_raw);
     const int sub = blockIdx.x;
-    const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
-    constexpr int nv = NV;
+    const int start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int tc = tile_cells<D>(a.Pt);
-    for (int e = threadIdx.x; e < tc * nv; e += blockDim.x) tile[e] = 0.0;
+    const int Pt = a.Pt;
+    for (int e = threadIdx.x; e < kF64Warps * tc * NV; e += blockDim.x) tiles[e] = 0.0;
     __syncthreads();
-    (void)bin;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *tile = tiles + (int64_t)warp * tc * NV;
+    constexpr int W = 2 * M;
+    constexpr int NW = D * W;                       // weights per point
+    constexpr int ITEMS = (D >= 2) ? W * W : W;     // (qx, qy) pairs or qx
+    constexpr int SLOTS = (ITEMS + 31) / 32;
+    constexpr int nz = (D >= 3) ? W : 1;
     const double *coords = static_cast<const double *>(a.coords);
-    for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
-        const int orig = a.perm[i];
-        const double ds = a.dinv ? a.dinv[i] : 1.0;
+    for (int j = start + warp; j < start + cnt; j += kF64Warps) {
+        const double w0 = lane < NW ? a.wts[(int64_t)j * NW + lane] : 0.0;
+        const double w1 = (NW > 32 && lane + 32 < NW) ? a.wts[(int64_t)j * NW + 32 + lane] : 0.0;
+        const int orig = a.perm[j];
+        const double ds = a.dinv ? a.dinv[j] : 1.0;
         double u[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) u[c] = (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds;
-        double wx[2 * M], wy[2 * M], wz[2 * M];
         int o[3] = {0, 0, 0};
-        o[0] = window_row<M>(coords[(int64_t)i * D], a.m2d, a.bd, a.normd, wx);
-        if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2d, a.bd, a.normd, wy);
-        if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2d, a.bd, a.normd, wz);
-        const int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) o[dd] = (int)floor(coords[(int64_t)j * D + dd]) - M + 1;
+        double uw[SLOTS][NV];
+        int base[SLOTS];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            const int p = lane + 32 * s;
+            const bool valid = p < ITEMS;
+            const int qx = valid ? p % W : 0;
+            const int qy = (D >= 2 && valid) ? p / W : 0;
+            const double wxy = warp_weight(w0, w1, qx) * (D >= 2 ? warp_weight(w0, w1, W + qy) : 1.0);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) uw[s][c] = valid ? u[c] * wxy : 0.0;
+            base[s] = (o[2] * Pt + o[1] + qy) * Pt + o[0] + qx;
+        }
 #pragma unroll 1
         for (int qz = 0; qz < nz; ++qz) {
-#pragma unroll 1
-            for (int qy = 0; qy < ny; ++qy) {
-                const double wyz = (D >= 3 ? wz[qz] : 1.0) * (D >= 2 ? wy[qy] : 1.0);
-                double *row = tile + (((o[2] + qz) * a.Pt + o[1] + qy) * a.Pt + o[0]) * nv;
+            const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz) : 1.0;
+            const int zoff = qz * Pt * Pt;
 #pragma unroll
-                for (int qx = 0; qx < 2 * M; ++qx) {
-                    const double wt = wyz * wx[qx];
+            for (int s = 0; s < SLOTS; ++s) {
+                if (lane + 32 * s < ITEMS) {
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) atomicAdd(row + qx * nv + c, u[c] * wt);
+                    for (int c = 0; c < NV; ++c) {
+                        double *cell = tile + c * tc + base[s] + zoff;
+                        *cell = fma(uw[s][c], wzq, *cell);
+                    }
                 }
             }
         }
     }
     __syncthreads();
-    double *out = static_cast<double *>(a.scratch) + (int64_t)sub * tc * nv;
-    for (int e = threadIdx.x; e < tc * nv; e += blockDim.x) out[e] = tile[e];
+    double *out = static_cast<double *>(a.scratch) + (int64_t)sub * tc * NV;
+    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
+        const int c = e % NV, cell = e / NV;
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < kF64Warps; ++w) acc += tiles[(int64_t)w * tc * NV + c * tc + cell];
+        out[e] = acc;
+    }
 }
 
 // ==================================================================== fold
@@ -402,90 +456,161 @@ __global__ void k_mult(T *coef, const T *__restrict__ mult, int64_t slots, int n
 
 // ==================================================================== interp
 // One CTA per subproblem: the bin's padded tile of the convolved grid is
-// loaded into shared memory, each point sums its (2M)^D taps, and the FP64
-// epilogue forms  alpha * D^{-1/2} * (sum - K(0) u) (+ shift * x)  in input
-// order (or the raw sum minus the self term in sorted order for degrees).
-template <typename T, int D, int M, int NV>
-__global__ void __launch_bounds__(256) k_interp(const InterpArgs a)
+// loaded into shared memory (vector-major), each point sums its (2M)^D taps,
+// and the FP64 epilogue forms  alpha * D^{-1/2} * (sum - K(0) u) (+ shift * x)
+// in input order (or the raw sum minus the self term in sorted order, for
+// the degrees).
+template <typename T, int NV>
+__device__ __forceinline__ void load_interp_tile(const InterpArgs &a, int D, const int bc[3], int tc, T *tile)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);
-    const int sub = blockIdx.x;
-    const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
-    constexpr int nv = NV;
-    const int Pt = a.Pt;
-    const int tc = tile_cells<D>(Pt);
-    int bc[3];
-    bin_coords<D>(bin, a.nb0, a.nb1, bc);
     const T *grid = static_cast<const T *>(a.grid);
-    for (int e = threadIdx.x; e < tc * nv; e += blockDim.x) {
-        const int c = e % nv;
-        const int cell = e / nv;
+    const int Pt = a.Pt;
+    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
+        const int c = e % NV;
+        const int cell = e / NV;
         const int lx = cell % Pt;
         const int ly = (D >= 2) ? (cell / Pt) % Pt : 0;
         const int lz = (D >= 3) ? cell / (Pt * Pt) : 0;
         const int gx = bc[0] * a.B + lx, gy = bc[1] * a.B + ly, gz = bc[2] * a.B + lz;
         T v = 0;
-        if (gx < a.L0 && gy < a.L1 && gz < a.L2) v = grid[((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * nv + c];
-        tile[e] = v;
+        if (gx < a.L0 && gy < a.L1 && gz < a.L2) v = grid[((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * NV + c];
+        tile[c * tc + cell] = v;
     }
+}
+
+__device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int c, double acc)
+{
+    const int orig = a.perm[i];
+    const double ds = a.dinv ? a.dinv[i] : 1.0;
+    const double x = a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0;
+    const double r = acc - a.self * (x * ds);
+    if (a.sorted_out) {
+        a.Y[(int64_t)i * a.ldy + c] = r;
+    } else {
+        double outv = a.alpha * ds * r + a.shift * x;
+        double *yp = a.Y + (int64_t)orig * a.ldy + c;
+        if (a.accumulate) outv += *yp;
+        *yp = outv;
+    }
+}
+
+// FP32 form: one thread per point.
+template <int D, int M, int NV>
+__global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);
+    const int sub = blockIdx.x;
+    const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
+    const int Pt = a.Pt;
+    const int tc = tile_cells<D>(Pt);
+    int bc[3];
+    bin_coords<D>(bin, a.nb0, a.nb1, bc);
+    load_interp_tile<float, NV>(a, D, bc, tc, tile);
     __syncthreads();
-    const T *coords = static_cast<const T *>(a.coords);
+    const float *coords = static_cast<const float *>(a.coords);
+    constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
-        T wx[2 * M], wy[2 * M], wz[2 * M];
+        float wx[2 * M], wy[2 * M], wz[2 * M];
         int o[3] = {0, 0, 0};
-        if (sizeof(T) == 4) {
-            o[0] = window_row<M>((float)coords[(int64_t)i * D], a.m2f, a.bf, a.normf, (float *)wx);
-            if (D >= 2) o[1] = window_row<M>((float)coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, (float *)wy);
-            if (D >= 3) o[2] = window_row<M>((float)coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, (float *)wz);
-        } else {
-            o[0] = window_row<M>((double)coords[(int64_t)i * D], a.m2d, a.bd, a.normd, (double *)wx);
-            if (D >= 2) o[1] = window_row<M>((double)coords[(int64_t)i * D + 1], a.m2d, a.bd, a.normd, (double *)wy);
-            if (D >= 3) o[2] = window_row<M>((double)coords[(int64_t)i * D + 2], a.m2d, a.bd, a.normd, (double *)wz);
-        }
-        T acc[NV];
+        o[0] = window_row<M>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
+        if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
+        if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        float acc[NV];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) acc[c] = 0;
-        const int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+        for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
 #pragma unroll 1
         for (int qz = 0; qz < nz; ++qz) {
-            T pz[NV];
+            float pz[NV];
 #pragma unroll
-            for (int c = 0; c < NV; ++c) pz[c] = 0;
+            for (int c = 0; c < NV; ++c) pz[c] = 0.0f;
 #pragma unroll 1
             for (int qy = 0; qy < ny; ++qy) {
-                const T *row = tile + (((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0]) * nv;
-                T r[NV];
+                const float *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
+                float r[NV];
 #pragma unroll
-                for (int c = 0; c < NV; ++c) r[c] = 0;
+                for (int c = 0; c < NV; ++c) r[c] = 0.0f;
 #pragma unroll
                 for (int qx = 0; qx < 2 * M; ++qx)
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) r[c] += wx[qx] * row[qx * nv + c];
-                const T wyq = (D >= 2) ? wy[qy] : (T)1;
+                    for (int c = 0; c < NV; ++c) r[c] = fmaf(wx[qx], row[c * tc + qx], r[c]);
+                const float wyq = (D >= 2) ? wy[qy] : 1.0f;
 #pragma unroll
-                for (int c = 0; c < NV; ++c) pz[c] += wyq * r[c];
+                for (int c = 0; c < NV; ++c) pz[c] = fmaf(wyq, r[c], pz[c]);
             }
-            const T wzq = (D >= 3) ? wz[qz] : (T)1;
+            const float wzq = (D >= 3) ? wz[qz] : 1.0f;
 #pragma unroll
-            for (int c = 0; c < NV; ++c) acc[c] += wzq * pz[c];
+            for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
         }
-        const int orig = a.perm[i];
-        const double ds = a.dinv ? a.dinv[i] : 1.0;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) interp_epilogue(a, i, c, (double)acc[c]);
+    }
+}
+
+// FP64 form: one warp per point with the precomputed FP64 weights; lanes
+// take (qx, qy) items, walk qz with one DFMA per tap, then the warp sums.
+template <int D, int M, int NV>
+__global__ void __launch_bounds__(32 * kF64Warps) k_interp_f64(const InterpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *tile = reinterpret_cast<double *>(smem_raw);
+    const int sub = blockIdx.x;
+    const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
+    const int Pt = a.Pt;
+    const int tc = tile_cells<D>(Pt);
+    int bc[3];
+    bin_coords<D>(bin, a.nb0, a.nb1, bc);
+    load_interp_tile<double, NV>(a, D, bc, tc, tile);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int W = 2 * M;
+    constexpr int NW = D * W;
+    constexpr int ITEMS = (D >= 2) ? W * W : W;
+    constexpr int SLOTS = (ITEMS + 31) / 32;
+    constexpr int nz = (D >= 3) ? W : 1;
+    const double *coords = static_cast<const double *>(a.coords);
+    for (int j = start + warp; j < start + cnt; j += kF64Warps) {
+        const double w0 = lane < NW ? a.wts[(int64_t)j * NW + lane] : 0.0;
+        const double w1 = (NW > 32 && lane + 32 < NW) ? a.wts[(int64_t)j * NW + 32 + lane] : 0.0;
+        int o[3] = {0, 0, 0};
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) o[dd] = (int)floor(coords[(int64_t)j * D + dd]) - M + 1;
+        double wxy[SLOTS];
+        int base[SLOTS];
+        double acc[SLOTS][NV];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            const int p = lane + 32 * s;
+            const bool valid = p < ITEMS;
+            const int qx = valid ? p % W : 0;
+            const int qy = (D >= 2 && valid) ? p / W : 0;
+            const double v = warp_weight(w0, w1, qx) * (D >= 2 ? warp_weight(w0, w1, W + qy) : 1.0);
+            wxy[s] = valid ? v : 0.0;
+            base[s] = (o[2] * Pt + o[1] + qy) * Pt + o[0] + qx;
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc[s][c] = 0.0;
+        }
+#pragma unroll 1
+        for (int qz = 0; qz < nz; ++qz) {
+            const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz) : 1.0;
+            const int zoff = qz * Pt * Pt;
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+                for (int c = 0; c < NV; ++c) acc[s][c] = fma(wzq, tile[c * tc + base[s] + zoff], acc[s][c]);
+        }
+        double part[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-            const double x = a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0;
-            const double u = x * ds;
-            const double r = (double)acc[c] - a.self * u;
-            if (a.sorted_out) {
-                a.Y[(int64_t)i * a.ldy + c] = r;
-            } else {
-                double outv = a.alpha * ds * r + a.shift * x;
-                double *yp = a.Y + (int64_t)orig * a.ldy + c;
-                if (a.accumulate) outv += *yp;
-                *yp = outv;
-            }
+            double v = 0.0;
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) v = fma(wxy[s], acc[s][c], v);
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            part[c] = v;
         }
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+            if (lane == c) interp_epilogue(a, j, c, part[c]);
     }
 }
 

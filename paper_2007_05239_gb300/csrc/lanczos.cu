@@ -207,8 +207,14 @@ struct Workspace {
     // out (device, ncol) = Q[:, 0:ncol]^T x
     ml_status dots(const double *Q, int64_t ldq, int ncol, const double *x, double *out)
     {
-        k_dots<<<nblk, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
-        k_reduce_cols<<<1, 128, 0, st>>>(part.as<double>(), nblk, ncol, out);
+        {
+            ProfScope pr("dots", st);
+            k_dots<<<nblk, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
+        }
+        {
+            ProfScope pr("dots_reduce", st);
+            k_reduce_cols<<<1, 128, 0, st>>>(part.as<double>(), nblk, ncol, out);
+        }
         ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
@@ -226,9 +232,15 @@ struct Workspace {
         double *h1 = hdev.as<double>(), *h2 = h1 + ncol, *nrm = h2 + ncol;
         if (ncol > 0) {
             ML_TRY(dots(Q, ldq, ncol, x, h1));
-            k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h1, x);
+            {
+                ProfScope pr("update", st);
+                k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h1, x);
+            }
             ML_TRY(dots(Q, ldq, ncol, x, h2));
-            k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h2, x);
+            {
+                ProfScope pr("update", st);
+                k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h2, x);
+            }
         }
         ML_TRY(dots(x, n, 1, x, nrm));
         std::vector<double> hh(2 * ncol + 1);
@@ -290,15 +302,23 @@ struct InverseOp {
                 ML_TRY(ws->dot_host(p.as<double>(), ap.as<double>(), &pap));
                 if (!(pap > 0)) return fail(ML_ERR_BREAKDOWN, "CG: operator not positive definite (p^T A p <= 0)");
                 const double alpha = rr / pap;
+                { ProfScope pr_("vector", st);
                 k_axpy<<<nb, 256, 0, st>>>(alpha, p.as<double>(), n, y.as<double>());
+                }
+                { ProfScope pr_("vector", st);
                 k_axpy<<<nb, 256, 0, st>>>(-alpha, ap.as<double>(), n, r.as<double>());
+                }
                 double rr2;
                 ML_TRY(ws->dot_host(r.as<double>(), r.as<double>(), &rr2));
+                { ProfScope pr_("vector", st);
                 k_xpby<<<nb, 256, 0, st>>>(r.as<double>(), rr2 / rr, n, p.as<double>());
+                }
                 rr = rr2;
                 ++inner_iters;
             }
+            { ProfScope pr_("vector", st);
             k_axpy<<<nb, 256, 0, st>>>(1.0 / T, y.as<double>(), n, out);
+            }
             ML_CUDA(cudaGetLastError());
         }
         return ML_OK;
@@ -327,12 +347,16 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
     };
     const int nb = vec_blocks(n);
     // start vector
+    { ProfScope pr_("vector", st);
     k_random<<<nb, 256, 0, st>>>(seed, n, Q);
+    }
     std::vector<double> h;
     double beta = 0;
     ML_TRY(ws.orthogonalize(Q, n, 0, Q, h, &beta));
     if (!(beta > 0)) return fail(ML_ERR_BREAKDOWN, "zero start vector");
+    { ProfScope pr_("vector", st);
     k_scale<<<nb, 256, 0, st>>>(Q, 1.0 / beta, n, Q);
+    }
 
     std::vector<double> Tm((size_t)ncv * ncv, 0.0);
     std::vector<double> theta, S;
@@ -355,15 +379,21 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
             for (int i = 0; i <= j; ++i) tnorm = std::max(tnorm, std::fabs(Tm[(size_t)i * ncv + i]));
             if (beta <= 1e-14 * std::max(tnorm, 1e-300) * std::sqrt((double)n)) {
                 // invariant subspace found: continue with a fresh random direction
+                { ProfScope pr_("vector", st);
                 k_random<<<nb, 256, 0, st>>>(restart_seed++, n, w);
+                }
                 std::vector<double> hh;
                 double b2;
                 ML_TRY(ws.orthogonalize(Q, n, j + 1, w, hh, &b2));
                 if (!(b2 > 0)) return fail(ML_ERR_BREAKDOWN, "Lanczos breakdown: no new direction");
                 beta = 0.0;
+                { ProfScope pr_("vector", st);
                 k_scale<<<nb, 256, 0, st>>>(w, 1.0 / b2, n, Q + (int64_t)(j + 1) * n);
+                }
             } else {
+                { ProfScope pr_("vector", st);
                 k_scale<<<nb, 256, 0, st>>>(w, 1.0 / beta, n, Q + (int64_t)(j + 1) * n);
+                }
             }
             ML_CUDA(cudaGetLastError());
             beta_last = beta;
@@ -388,7 +418,10 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
             for (int c = 0; c < ncv; ++c) Sk[(size_t)i * ncv + c] = S[(size_t)c * ncv + col];
         }
         ML_CUDA(cudaMemcpyAsync(Sd.p, Sk.data(), Sk.size() * 8, cudaMemcpyHostToDevice, st));
-        k_combine<<<nb, 256, 0, st>>>(Q, n, n, ncv, Sd.as<double>(), keep, Qtmp.as<double>(), n);
+        {
+            ProfScope pr("ritz", st);
+            k_combine<<<nb, 256, 0, st>>>(Q, n, n, ncv, Sd.as<double>(), keep, Qtmp.as<double>(), n);
+        }
         ML_CUDA(cudaGetLastError());
         if (done) {
             for (int i = 0; i < k; ++i) {
@@ -403,7 +436,9 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
                 const int cb = std::min(nb, 256);
                 DevBuf part;
                 ML_TRY(part.ensure((size_t)cb * k * 3 * 8));
+                { ProfScope pr_("vector", st);
                 k_colmax<<<cb, 256, 0, st>>>(evecs_dev, n, n, k, part.as<double>());
+                }
                 std::vector<double> hp((size_t)cb * k * 3);
                 ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, st));
                 ML_CUDA(cudaStreamSynchronize(st));
@@ -421,7 +456,9 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
                     f[c] = bv < 0 ? -1.0 : 1.0;
                 }
                 ML_CUDA(cudaMemcpyAsync(Sd.p, f.data(), k * 8, cudaMemcpyHostToDevice, st));
+                { ProfScope pr_("vector", st);
                 k_scale_cols<<<nb, 256, 0, st>>>(evecs_dev, n, n, k, Sd.as<double>());
+                }
                 ML_CUDA(cudaGetLastError());
             }
             ML_CUDA(cudaStreamSynchronize(st));

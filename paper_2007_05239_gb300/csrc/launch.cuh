@@ -34,6 +34,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.sub_count = p->sub_count.as<int>();
     sa.perm = p->perm.as<int>();
     sa.coords = p->coords.p;
+    sa.wts = p->wts.as<double>();
     sa.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
     sa.X = v.X;
     sa.ldx = v.ldx;
@@ -50,14 +51,15 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.normf = (float)sa.normd;
     sa.scratch = p->scratch.p;
     if (p->nsub > 0) {
+        ProfScope pr("spread", st);
         if (f32) {
             const size_t smem = (size_t)tc * nv * sizeof(int);
             ML_TRY(set_smem(k_spread_f32<D, M, NV>, smem));
             k_spread_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
-            const size_t smem = (size_t)tc * nv * sizeof(double);
+            const size_t smem = (size_t)tc * nv * sizeof(double) * kF64Warps;
             ML_TRY(set_smem(k_spread_f64<D, M, NV>, smem));
-            k_spread_f64<D, M, NV><<<p->nsub, 256, smem, st>>>(sa);
+            k_spread_f64<D, M, NV><<<p->nsub, 32 * kF64Warps, smem, st>>>(sa);
         }
         ML_CUDA(cudaGetLastError());
     }
@@ -76,7 +78,10 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     fa.L0 = g.L[0];
     fa.L1 = g.L[1];
     fa.L2 = g.L[2];
-    k_fold<T, D><<<(int)g.nbins(), 256, 0, st>>>(fa);
+    {
+        ProfScope pr("fold", st);
+        k_fold<T, D><<<(int)g.nbins(), 256, 0, st>>>(fa);
+    }
     ML_CUDA(cudaGetLastError());
     // ---- transforms
     T *bufs[2] = {p->work[0].as<T>(), p->work[1].as<T>()};
@@ -87,6 +92,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         for (int b = a + 1; b < D; ++b) A *= g.L[b];
         const int64_t C = Kpow * nv;
         dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.K + 31) / 32));
+        ProfScope pr("axis", st);
         k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_f[a].as<T>(), (int)A, g.L[a], g.K, (int)C);
         cur ^= 1;
         Kpow *= g.K;
@@ -95,6 +101,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     {
         const int64_t slots = Kpow;
         const int blocks = (int)std::min<int64_t>((slots * nv + 255) / 256, 4096);
+        ProfScope pr("mult", st);
         k_mult<T><<<blocks, 256, 0, st>>>(bufs[cur], p->mult_d.as<T>(), slots, nv);
     }
     for (int a = D - 1; a >= 0; --a) {
@@ -103,6 +110,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         for (int b = a + 1; b < D; ++b) A *= g.L[b];
         const int64_t C = Kpow * nv;
         dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.L[a] + 31) / 32));
+        ProfScope pr("axis", st);
         k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_b[a].as<T>(), (int)A, g.K, g.L[a], (int)C);
         cur ^= 1;
     }
@@ -114,6 +122,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.sub_count = sa.sub_count;
     ia.perm = sa.perm;
     ia.coords = sa.coords;
+    ia.wts = sa.wts;
     ia.dinv = sa.dinv;
     ia.X = v.X;
     ia.ldx = v.ldx;
@@ -142,8 +151,14 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.sorted_out = o.sorted_out;
     if (p->nsub > 0) {
         const size_t smem = (size_t)tc * nv * sizeof(T);
-        ML_TRY(set_smem(k_interp<T, D, M, NV>, smem));
-        k_interp<T, D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
+        ProfScope pr("interp", st);
+        if (f32) {
+            ML_TRY(set_smem(k_interp_f32<D, M, NV>, smem));
+            k_interp_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
+        } else {
+            ML_TRY(set_smem(k_interp_f64<D, M, NV>, smem));
+            k_interp_f64<D, M, NV><<<p->nsub, 32 * kF64Warps, smem, st>>>(ia);
+        }
         ML_CUDA(cudaGetLastError());
     }
     return ML_OK;

@@ -88,6 +88,7 @@ struct ml_plan_s {
     int vp = 1;            // vectors per pass
     int nsub = 0;
     double deg_min = 0, deg_max = 0;
+    int64_t applied = 0;   // vectors pushed through apply_layer
 
     // host tables (FP64)
     std::vector<double> bhat;    // (N/2+1)^d
@@ -97,6 +98,7 @@ struct ml_plan_s {
     // device data (sorted order unless noted)
     ml::DevBuf perm;      // int32 n: sorted position -> input index
     ml::DevBuf coords;    // T n*d local grid coordinates
+    ml::DevBuf wts;       // FP64 form: double n*d*2m window weights
     ml::DevBuf deg;       // double n: degrees
     ml::DevBuf dinv;      // double n: D^{-1/2}
     ml::DevBuf sub_bin, sub_start, sub_count;  // int32 nsub
@@ -153,6 +155,24 @@ struct ApplyOpts {
 };
 
 ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+
+// ---------------------------------------------------------------- tracing
+bool profiling();
+// Records a CUDA event on `st` now and another when it goes out of scope,
+// filed under `name`, while profiling is enabled; otherwise does nothing.
+class ProfScope {
+public:
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+private:
+    const char *name_;
+    cudaStream_t st_;
+    void *a_ = nullptr;
+    bool active_ = false;
+};
 ml_status ensure_workspace(ml_plan_s *p, int nv);
 
 }  // namespace ml

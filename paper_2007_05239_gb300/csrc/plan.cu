@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "kernels.cuh"
 #include "ml_internal.h"
 
 namespace ml {
@@ -190,6 +191,22 @@ __global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, int *c
         atomicAdd(&counts[keys[i]], 1);
 }
 
+// FP64 window weights of every point (plan time): wts[i][a][q] = phi_n(frac(u_a) + M - 1 - q)
+__global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n, int d, int m, double m2, double b,
+                                   double norm2, double *wts)
+{
+    const int W = 2 * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d * W;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e % W);
+        const int64_t ia = e / W;   // point * d + dim
+        const double x = coords[ia];
+        const double fr = x - floor(x);
+        wts[e] = kb_weight(fr + (double)(m - 1 - q), m2, b, norm2);
+    }
+}
+
+
 // ------------------------------------------------------------ radix sort
 constexpr int RS_THREADS = 256;
 constexpr int RS_TILE = 4096;
@@ -286,9 +303,15 @@ static ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *val
     uint32_t *ka = keys, *kb = keys2;
     int *va = vals, *vb = vals2;
     for (int shift = 0; shift < bits; shift += 8) {
+        { ProfScope pr_("plan", st);
         k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist.as<uint32_t>(), nblk);
+        }
+        { ProfScope pr_("plan", st);
         k_rs_scan<<<1, 1024, 0, st>>>(hist.as<uint32_t>(), (int64_t)256 * nblk);
+        }
+        { ProfScope pr_("plan", st);
         k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist.as<uint32_t>(), nblk);
+        }
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -397,7 +420,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     const int nblk = grid_for(n);
     DevBuf part;
     ML_TRY(part.ensure((size_t)nblk * 6 * sizeof(double)));
+    { ProfScope pr_("plan", st);
     k_bbox<<<nblk, 256, 0, st>>>(points, n, d, part.as<double>());
+    }
     ML_CUDA(cudaGetLastError());
     std::vector<double> hp((size_t)nblk * 6);
     ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -415,7 +440,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     }
     // ---- domain scaling (isotropic, exact for W)
     if (p->eps_B > 0) {
+        { ProfScope pr_("plan", st);
         k_maxrad<<<nblk, 256, 0, st>>>(points, n, d, p->center[0], p->center[1], p->center[2], part.as<double>());
+        }
         ML_CUDA(cudaGetLastError());
         ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
         ML_CUDA(cudaStreamSynchronize(st));
@@ -456,7 +483,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     tm.d = d;
     DevBuf lpart;
     ML_TRY(lpart.ensure((size_t)nblk * 6 * sizeof(long long)));
+    { ProfScope pr_("plan", st);
     k_first_tap_range<<<nblk, 256, 0, st>>>(points, n, tm, lpart.as<long long>());
+    }
     ML_CUDA(cudaGetLastError());
     std::vector<long long> lp((size_t)nblk * 6);
     ML_CUDA(cudaMemcpyAsync(lp.data(), lpart.p, lp.size() * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -485,9 +514,10 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     g.R = 1 + (2 * p->m - 1) / g.B;     // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
     {
-        const size_t ts = p->prec == ML_F32 ? 4 : 8;
+        // FP32: one shared tile per CTA; FP64: one tile per warp
         const int64_t tc = g.tile_cells();
-        p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * (int64_t)ts)));
+        const int64_t per_vec = p->prec == ML_F32 ? tc * 4 : tc * 8 * kF64Warps;
+        p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / per_vec));
     }
     // ---- keys, sort
     DevBuf urel, keys, keys2, idx, idx2;
@@ -502,7 +532,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ka.B = g.B;
     ka.nb0 = g.nb[0];
     ka.nb1 = g.nb[1];
+    { ProfScope pr_("plan", st);
     k_keys<<<grid_for(n), 256, 0, st>>>(points, n, ka, urel.as<double>(), keys.as<uint32_t>(), idx.as<int>());
+    }
     ML_CUDA(cudaGetLastError());
     const int64_t nbins = g.nbins();
     int bits = 0;
@@ -513,19 +545,35 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     // the sorted keys sit in the buffer paired with sorted_idx
     const uint32_t *sorted_keys = (sorted_idx == idx.as<int>()) ? keys.as<uint32_t>() : keys2.as<uint32_t>();
     ML_TRY(p->perm.ensure((size_t)n * 4));
+    { ProfScope pr_("plan", st);
     k_copy_int<<<grid_for(n), 256, 0, st>>>(sorted_idx, p->perm.as<int>(), n);
+    }
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     ML_TRY(p->coords.ensure((size_t)n * d * ts));
     if (p->prec == ML_F32)
+        { ProfScope pr_("plan", st);
         k_gather_coords<float><<<grid_for(n), 256, 0, st>>>(urel.as<double>(), p->perm.as<int>(), n, d, p->coords.as<float>());
+        }
     else
+        { ProfScope pr_("plan", st);
         k_gather_coords<double><<<grid_for(n), 256, 0, st>>>(urel.as<double>(), p->perm.as<int>(), n, d, p->coords.as<double>());
+        }
     ML_CUDA(cudaGetLastError());
+    if (p->prec == ML_F64) {
+        // FP64 window weights, once per plan
+        ML_TRY(p->wts.ensure((size_t)n * d * 2 * p->m * sizeof(double)));
+        ProfScope pr_("plan", st);
+        k_window_table_f64<<<grid_for(n * d * 2 * p->m), 256, 0, st>>>(
+            p->coords.as<double>(), n, d, p->m, (double)p->m * p->m, p->kb_shape, p->kb_norm, p->wts.as<double>());
+        ML_CUDA(cudaGetLastError());
+    }
     // ---- bins -> subproblems
     DevBuf counts;
     ML_TRY(counts.ensure((size_t)nbins * 4));
     ML_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)nbins * 4, st));
+    { ProfScope pr_("plan", st);
     k_bin_count<<<grid_for(n), 256, 0, st>>>(sorted_keys, n, counts.as<int>());
+    }
     ML_CUDA(cudaGetLastError());
     std::vector<int> hc(nbins);
     ML_CUDA(cudaMemcpyAsync(hc.data(), counts.p, (size_t)nbins * 4, cudaMemcpyDeviceToHost, st));
@@ -590,7 +638,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     o.sorted_out = true;
     ML_TRY(apply_layer(p, v, o, st));
     ML_CUDA(cudaMemsetAsync(p->status.p, 0, 4, st));
+    { ProfScope pr_("plan", st);
     k_dinv<<<grid_for(n), 256, 0, st>>>(p->deg.as<double>(), n, p->dinv.as<double>(), p->status.as<int>());
+    }
     ML_CUDA(cudaGetLastError());
     int bad = 0;
     ML_CUDA(cudaMemcpyAsync(&bad, p->status.p, 4, cudaMemcpyDeviceToHost, st));
@@ -610,7 +660,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
 int64_t ml_plan_s::device_bytes() const
 {
     int64_t t = 0;
-    const ml::DevBuf *bufs[] = {&perm, &coords, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub,
+    const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
                                 &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status};
     for (auto *b : bufs) t += (int64_t)b->bytes;
@@ -619,7 +669,7 @@ int64_t ml_plan_s::device_bytes() const
 
 static void release_all(ml_plan_s *p)
 {
-    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
+    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
                           &p->stage_y, &p->status};
@@ -706,6 +756,7 @@ ml_status ml_plan_get_info(ml_plan_t p, ml_plan_info *info)
     info->deg_min = p->deg_min;
     info->deg_max = p->deg_max;
     info->device_bytes = p->device_bytes();
+    info->applied_vectors = p->applied;
     return ML_OK;
 }
 
