@@ -142,6 +142,42 @@ ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int 
                            int mode, void *stream);
 
 /*
+ * ml_fastsum_apply_noalloc - ml_fastsum_apply without any device allocation.
+ * (Not from the paper: the paper has no counterpart; it is a deployment aid.)
+ *
+ * Who needs it: callers that must not call cudaMalloc/cudaFree during the
+ * matrix-vector product, e.g. code that runs under a memory allocator which
+ * owns the whole device (a framework's caching allocator), real-time or
+ * latency-bound loops where an allocation stalls or synchronises the device,
+ * and embedded/safety builds where allocation after start-up is forbidden.
+ * ml_fastsum_apply may grow the plan's workspace (and, for host X/Y, its
+ * staging buffers) with cudaMalloc; this entry point never does.
+ *
+ * How: all scratch of the call - the spreading tiles of every subproblem and
+ * the two grid-transform buffers - is taken from one file-scope device array
+ * of 32 MiB (every GPU that loads the library holds it until the process
+ * exits).  The plans' own data were allocated by ml_fastsum_plan.
+ *
+ * Arguments and results are those of ml_fastsum_apply, except:
+ *   - X and Y must be device memory (host buffers would need staging copies);
+ *     ML_ERR_ARG otherwise.
+ *   - ML_ERR_ARG, with the required size in ml_last_error(), when the layers'
+ *     scratch (tiles + two transform buffers at the widest vector pass)
+ *     exceeds 32 MiB.
+ *   - kernel timing (ml_profile_enable) is not recorded for these calls.
+ * Set-up: the first call on each device looks the array's device address up
+ * with cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.
+ * Sharing: every call uses the same array and leaves its contents behind; the
+ * kernels overwrite every scratch value before reading it, so nothing needs
+ * clearing, but calls whose executions overlap on the GPU (other streams,
+ * other threads) race on the array and must be serialised by the caller.
+ * ML_DEGREE reads stored degrees and uses no scratch.
+ */
+ml_status ml_fastsum_apply_noalloc(const ml_plan_t *layers, int T, const double *X, int b, double *Y,
+                                   int mode, void *stream);
+
+/*
  * ml_lanczos_eigs - the k smallest eigenpairs of the power mean Laplacian of
  * the T layers by thick-restart Lanczos with full reorthogonalisation (Sec. 3).
  *

@@ -24,7 +24,7 @@ ML_RAW_W, ML_NORMALIZED_A, ML_DEGREE, ML_PER_LAYER = 0, 1, 2, 16
 MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
-EXPORTS = ["ml_fastsum_plan", "ml_fastsum_apply", "ml_lanczos_eigs", "ml_plan_get_info",
+EXPORTS = ["ml_fastsum_plan", "ml_fastsum_apply", "ml_fastsum_apply_noalloc", "ml_lanczos_eigs", "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read"]
 
@@ -70,6 +70,8 @@ def load():
                                     ctypes.c_double, P]
     lib.ml_fastsum_apply.restype = ctypes.c_int
     lib.ml_fastsum_apply.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P]
+    lib.ml_fastsum_apply_noalloc.restype = ctypes.c_int
+    lib.ml_fastsum_apply_noalloc.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P]
     lib.ml_lanczos_eigs.restype = ctypes.c_int
     lib.ml_lanczos_eigs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P, P, P]
@@ -184,6 +186,18 @@ def ml_fastsum_apply(layers, X, Y, mode="normalized", per_layer=False, stream=No
     b = 1 if len(Y.shape) == (2 if per_layer else 1) else int(Y.shape[-1])
     arr = _handles(layers)
     _check(lib.ml_fastsum_apply(arr, len(layers), _ptr(X), b, _ptr(Y), md, _stream(stream)))
+    return Y
+
+
+def ml_fastsum_apply_noalloc(layers, X, Y, mode="normalized", per_layer=False, stream=None):
+    """As ml_fastsum_apply, without device allocation (static scratch; device X and Y only)."""
+    lib = load()
+    md = MODES[mode] if isinstance(mode, str) else int(mode)
+    if per_layer:
+        md |= ML_PER_LAYER
+    b = 1 if len(Y.shape) == (2 if per_layer else 1) else int(Y.shape[-1])
+    arr = _handles(layers)
+    _check(lib.ml_fastsum_apply_noalloc(arr, len(layers), _ptr(X), b, _ptr(Y), md, _stream(stream)))
     return Y
 
 

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlfastsum.so")
 SOURCES = ["apply_f32_d3.cu", "apply_f64_d3.cu", "apply_f32_d2.cu", "apply_f64_d2.cu", "apply_f32_d1.cu",
-           "apply_f64_d1.cu", "plan.cu", "apply_host.cu", "lanczos.cu", "profile.cu", "host_math.cpp"]
+           "apply_f64_d1.cu", "plan.cu", "apply_host.cu", "lanczos.cu", "profile.cu", "noalloc.cu",
+           "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

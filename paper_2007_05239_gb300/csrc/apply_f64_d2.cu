@@ -2,8 +2,9 @@
 #include "launch.cuh"
 
 namespace ml {
-ml_status run_layer_f64_d2(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+ml_status run_layer_f64_d2(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
+                           cudaStream_t st)
 {
-    return run_layer_d<double, 2>(p, v, o, st);
+    return run_layer_d<double, 2>(p, v, o, w, st);
 }
 }  // namespace ml

@@ -10,8 +10,9 @@
 
 namespace ml {
 
-#define ML_DECL_LAYER(P, D) \
-    ml_status run_layer_##P##_d##D(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+#define ML_DECL_LAYER(P, D)                                                                                 \
+    ml_status run_layer_##P##_d##D(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, \
+                                   cudaStream_t st);
 ML_DECL_LAYER(f32, 1)
 ML_DECL_LAYER(f32, 2)
 ML_DECL_LAYER(f32, 3)
@@ -19,23 +20,30 @@ ML_DECL_LAYER(f64, 1)
 ML_DECL_LAYER(f64, 2)
 ML_DECL_LAYER(f64, 3)
 
+ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st)
+{
+    if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
+    p->applied += v.nv;
+    if (p->prec == ML_F32) {
+        switch (p->d) {
+        case 1: return run_layer_f32_d1(p, v, o, w, st);
+        case 2: return run_layer_f32_d2(p, v, o, w, st);
+        default: return run_layer_f32_d3(p, v, o, w, st);
+        }
+    }
+    switch (p->d) {
+    case 1: return run_layer_f64_d1(p, v, o, w, st);
+    case 2: return run_layer_f64_d2(p, v, o, w, st);
+    default: return run_layer_f64_d3(p, v, o, w, st);
+    }
+}
+
 ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
 {
     if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
     ML_TRY(ensure_workspace(p, v.nv));
-    p->applied += v.nv;
-    if (p->prec == ML_F32) {
-        switch (p->d) {
-        case 1: return run_layer_f32_d1(p, v, o, st);
-        case 2: return run_layer_f32_d2(p, v, o, st);
-        default: return run_layer_f32_d3(p, v, o, st);
-        }
-    }
-    switch (p->d) {
-    case 1: return run_layer_f64_d1(p, v, o, st);
-    case 2: return run_layer_f64_d2(p, v, o, st);
-    default: return run_layer_f64_d3(p, v, o, st);
-    }
+    const LayerWork w{p->scratch.p, p->work[0].p, p->work[1].p};
+    return run_layer_ws(p, v, o, w, st);
 }
 
 // vectors in the next pass: 8 or 4 when the plan's tile holds them and the

@@ -21,7 +21,8 @@ static ml_status set_smem(K kernel, size_t bytes)
 }
 
 template <typename T, int D, int M, int NV>
-static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
+                              cudaStream_t st)
 {
     const GridGeom &g = p->g;
     const int nv = v.nv;
@@ -49,7 +50,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.m2f = (float)sa.m2d;
     sa.bf = (float)sa.bd;
     sa.normf = (float)sa.normd;
-    sa.scratch = p->scratch.p;
+    sa.scratch = w.scratch;
     if (p->nsub > 0) {
         ProfScope pr("spread", st);
         if (f32) {
@@ -66,8 +67,8 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     // ---- fold into the active grid (work[0])
     FoldArgs fa;
     fa.bin_sub = p->bin_sub.as<int>();
-    fa.scratch = p->scratch.p;
-    fa.grid = p->work[0].p;
+    fa.scratch = w.scratch;
+    fa.grid = w.work0;
     fa.nv = nv;
     fa.B = g.B;
     fa.Pt = g.Pt;
@@ -84,7 +85,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     }
     ML_CUDA(cudaGetLastError());
     // ---- transforms
-    T *bufs[2] = {p->work[0].as<T>(), p->work[1].as<T>()};
+    T *bufs[2] = {static_cast<T *>(w.work0), static_cast<T *>(w.work1)};
     int cur = 0;
     int64_t Kpow = 1;  // K^a
     for (int a = 0; a < D; ++a) {
@@ -167,27 +168,29 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
 // Vector passes use NV = 1, 4 or 8 vectors; the wide passes exist for the
 // small windows (M <= 4) where they matter for throughput.
 template <typename T, int D, int M>
-static ml_status run_layer_dmv(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+static ml_status run_layer_dmv(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
+                               cudaStream_t st)
 {
     if constexpr (M <= 4) {
-        if (v.nv == 8) return run_layer_dm<T, D, M, 8>(p, v, o, st);
-        if (v.nv == 4) return run_layer_dm<T, D, M, 4>(p, v, o, st);
+        if (v.nv == 8) return run_layer_dm<T, D, M, 8>(p, v, o, w, st);
+        if (v.nv == 4) return run_layer_dm<T, D, M, 4>(p, v, o, w, st);
     }
-    if (v.nv == 1) return run_layer_dm<T, D, M, 1>(p, v, o, st);
+    if (v.nv == 1) return run_layer_dm<T, D, M, 1>(p, v, o, w, st);
     return fail(ML_ERR_ARG, "unsupported vectors per pass");
 }
 
 template <typename T, int D>
-static ml_status run_layer_d(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+static ml_status run_layer_d(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
+                             cudaStream_t st)
 {
     switch (p->m) {
-    case 2: return run_layer_dmv<T, D, 2>(p, v, o, st);
-    case 3: return run_layer_dmv<T, D, 3>(p, v, o, st);
-    case 4: return run_layer_dmv<T, D, 4>(p, v, o, st);
-    case 5: return run_layer_dmv<T, D, 5>(p, v, o, st);
-    case 6: return run_layer_dmv<T, D, 6>(p, v, o, st);
-    case 7: return run_layer_dmv<T, D, 7>(p, v, o, st);
-    case 8: return run_layer_dmv<T, D, 8>(p, v, o, st);
+    case 2: return run_layer_dmv<T, D, 2>(p, v, o, w, st);
+    case 3: return run_layer_dmv<T, D, 3>(p, v, o, w, st);
+    case 4: return run_layer_dmv<T, D, 4>(p, v, o, w, st);
+    case 5: return run_layer_dmv<T, D, 5>(p, v, o, w, st);
+    case 6: return run_layer_dmv<T, D, 6>(p, v, o, w, st);
+    case 7: return run_layer_dmv<T, D, 7>(p, v, o, w, st);
+    case 8: return run_layer_dmv<T, D, 8>(p, v, o, w, st);
     default: return fail(ML_ERR_ARG, "window half-width out of range");
     }
 }

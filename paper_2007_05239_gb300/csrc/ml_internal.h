@@ -158,6 +158,16 @@ ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaS
 
 // ---------------------------------------------------------------- tracing
 bool profiling();
+// Switches kernel timing off on this thread for its lifetime (timing creates
+// CUDA events, which callers that must not allocate cannot accept).
+class NoProfileScope {
+public:
+    NoProfileScope();
+    ~NoProfileScope();
+
+private:
+    bool prev_;
+};
 // Records a CUDA event on `st` now and another when it goes out of scope,
 // filed under `name`, while profiling is enabled; otherwise does nothing.
 class ProfScope {
@@ -174,5 +184,19 @@ private:
     bool active_ = false;
 };
 ml_status ensure_workspace(ml_plan_s *p, int nv);
+
+// Device workspace of one layer pass: the spreading tiles and the two
+// transform buffers.
+struct LayerWork {
+    void *scratch;
+    void *work0;
+    void *work1;
+};
+// bytes of the tile scratch and of each transform buffer for nv vectors
+void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work);
+// run one layer pass on the given workspace (no allocation)
+ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st);
+// vectors in the next pass for `remaining` vectors
+int pass_width(const ml_plan_s *p, int remaining);
 
 }  // namespace ml

@@ -394,11 +394,11 @@ static ml_status upload(DevBuf &buf, const std::vector<double> &src)
     return ML_OK;
 }
 
-ml_status ensure_workspace(ml_plan_s *p, int nv)
+void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work)
 {
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     const GridGeom &g = p->g;
-    ML_TRY(p->scratch.ensure((size_t)p->nsub * g.tile_cells() * nv * ts));
+    *scratch = (size_t)p->nsub * g.tile_cells() * nv * ts;
     // transform stages: extents go from L to K one dim at a time and back
     int64_t mx = 1;
     for (int stage = 0; stage <= p->d; ++stage) {
@@ -406,8 +406,16 @@ ml_status ensure_workspace(ml_plan_s *p, int nv)
         for (int a = 0; a < p->d; ++a) v *= (a < stage ? g.K : g.L[a]);
         mx = std::max(mx, v);
     }
-    ML_TRY(p->work[0].ensure((size_t)mx * nv * ts));
-    ML_TRY(p->work[1].ensure((size_t)mx * nv * ts));
+    *work = (size_t)mx * nv * ts;
+}
+
+ml_status ensure_workspace(ml_plan_s *p, int nv)
+{
+    size_t sb = 0, wb = 0;
+    workspace_bytes(p, nv, &sb, &wb);
+    ML_TRY(p->scratch.ensure(sb));
+    ML_TRY(p->work[0].ensure(wb));
+    ML_TRY(p->work[1].ensure(wb));
     ML_TRY(p->status.ensure(64));
     return ML_OK;
 }

@@ -50,7 +50,12 @@ void drain(Entry &en)
 }
 }  // namespace
 
-bool profiling() { return g_on.load(std::memory_order_relaxed); }
+static thread_local bool t_suppress = false;
+
+bool profiling() { return !t_suppress && g_on.load(std::memory_order_relaxed); }
+
+NoProfileScope::NoProfileScope() : prev_(t_suppress) { t_suppress = true; }
+NoProfileScope::~NoProfileScope() { t_suppress = prev_; }
 
 ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st)
 {
