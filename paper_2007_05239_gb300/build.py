@@ -15,9 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlfastsum.so")
-SOURCES = ["apply_f32_d3.cu", "apply_f64_d3.cu", "apply_f32_d2.cu", "apply_f64_d2.cu", "apply_f32_d1.cu",
-           "apply_f64_d1.cu", "plan.cu", "apply_host.cu", "lanczos.cu", "profile.cu", "noalloc.cu",
-           "host_math.cpp"]
+SOURCES = sorted(f for f in os.listdir(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc"))
+                 if f.endswith((".cu", ".cpp")))
+# longest compiles first
+SOURCES.sort(key=lambda f: (not f.startswith("apply_f"), "_d3_" not in f, f))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,7 @@
+// F32 form, d = 3, window half-width m in {2}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_m<float, 3, 2>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

@@ -1,0 +1,9 @@
+// F64 form, d = 3, window half-width m in {5, 6}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_m<double, 3, 5>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_m<double, 3, 6>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

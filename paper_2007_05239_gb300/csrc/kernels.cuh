@@ -70,6 +70,7 @@ struct SpreadArgs {
     const int *perm;
     const void *coords;      // T [n][D]
     const double *wts;       // FP64 form: window weights [n][D][2M]
+    const int *offs;         // FP64 form: first tap per dim, packed o0 | o1 << 10 | o2 << 20
     const double *dinv;      // null: no pre-scaling
     const double *X;         // null: all-ones input
     int ldx;
@@ -79,10 +80,27 @@ struct SpreadArgs {
     float m2f, bf, normf;    // window constants (FP32 copies)
     double m2d, bd, normd;   // window constants (FP64)
     void *scratch;           // T [nsub][Pt^D][nv]
+    int sub_max;             // largest subproblem (smem staging size)
 };
 
+// Sum of the tiles of each group of consecutive subproblems of one bin
+// (fixed order): gtile[g] = sum_{s in group g} scratch[s].
+template <typename T>
+__global__ void __launch_bounds__(256) k_group_sum(const T *__restrict__ scratch, const int *__restrict__ grp_sub,
+                                                  int64_t tile_elems, T *gtile)
+{
+    const int g = blockIdx.y;
+    const int s0 = grp_sub[g], s1 = grp_sub[g + 1];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tile_elems;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        T acc = 0;
+        for (int s = s0; s < s1; ++s) acc += scratch[(int64_t)s * tile_elems + e];
+        gtile[(int64_t)g * tile_elems + e] = acc;
+    }
+}
+
 struct FoldArgs {
-    const int *bin_sub;      // nbins + 1
+    const int *bin_sub;      // nbins + 1 (first tile of each bin: subproblem or group)
     const void *scratch;
     void *grid;
     int nv, B, Pt, R;
@@ -95,6 +113,7 @@ struct InterpArgs {
     const int *perm;
     const void *coords;
     const double *wts;       // FP64 form: window weights [n][D][2M]
+    const int *offs;         // FP64 form: packed first taps
     const double *dinv;      // pre/post scale (normalized) or null
     const double *X;         // input (for the self term and the shift), null = ones
     int ldx;
@@ -205,6 +224,9 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
     __syncthreads();
 
     constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+    // full unrolling only for the small windows the throughput cases use
+    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
+    constexpr int UY = (M <= 4) ? ny : 1;
     const int ry = (D == 2) ? lane % ny : (D == 3 ? (lane / nz) % ny : 0);
     const int rz = (D == 3) ? lane % nz : 0;
     const float *coords = static_cast<const float *>(a.coords);
@@ -221,15 +243,37 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
         o[0] = window_row<M>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
         if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
         if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
-#pragma unroll 1
+        // rotated copies: row q of this lane is row (q + r) mod n of the point
+        float wyr[ny], wzr[nz];
+#pragma unroll
+        for (int q = 0; q < ny; ++q) {
+            int src = q + ry;
+            src -= (src >= ny) ? ny : 0;
+            float v = 1.0f;
+#pragma unroll
+            for (int k = 0; k < ny; ++k)
+                if (D >= 2 && k == src) v = wy[k];
+            wyr[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < nz; ++q) {
+            int src = q + rz;
+            src -= (src >= nz) ? nz : 0;
+            float v = 1.0f;
+#pragma unroll
+            for (int k = 0; k < nz; ++k)
+                if (D >= 3 && k == src) v = wz[k];
+            wzr[q] = v;
+        }
+#pragma unroll UZ
         for (int qz0 = 0; qz0 < nz; ++qz0) {
             int qz = qz0 + rz;
-            if (qz >= nz) qz -= nz;
-#pragma unroll 1
+            qz -= (qz >= nz) ? nz : 0;
+#pragma unroll UY
             for (int qy0 = 0; qy0 < ny; ++qy0) {
                 int qy = qy0 + ry;
-                if (qy >= ny) qy -= ny;
-                const float wyz = (D >= 3 ? wz[qz] : 1.0f) * (D >= 2 ? wy[qy] : 1.0f);
+                qy -= (qy >= ny) ? ny : 0;
+                const float wyz = wzr[qz0] * wyr[qy0];
                 int *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
 #pragma unroll
                 for (int qx = 0; qx < 2 * M; ++qx) {
@@ -257,23 +301,37 @@ __device__ __forceinline__ double warp_weight(double w0, double w1, int k)
     return k < 32 ? x : y;
 }
 
-constexpr int kF64Warps = 4;
+// smem staging of one subproblem's inputs for the FP64 kernels
+constexpr int kF64MaxWarps = 8;
 
 // FP64 form: one warp per point, each warp with a private tile, so no
-// atomics are needed.  Lane items are (qx, qy) pairs; each item walks qz and
-// adds u wx wy wz with one DFMA per tap.  The point's weights were computed
-// once at plan time (FP64, table wts[n][D][2M]).  At the end the warps'
-// tiles are summed in a fixed order.
+// atomics are needed.  The subproblem's scaled inputs u and packed first
+// taps are staged in shared memory; each warp prefetches its next point's
+// weights (computed once at plan time, FP64 table wts[n][D][2M]).  Lane
+// items are (qx, qy) pairs; each walks qz in chunks whose tile values are
+// loaded before the DFMAs (one per tap) and stored after, so the chunk's
+// read-modify-writes overlap.  The warps' tiles are summed in a fixed order.
 template <int D, int M, int NV>
-__global__ void __launch_bounds__(32 * kF64Warps) k_spread_f64(const SpreadArgs a)
+__global__ void __launch_bounds__(32 * kF64MaxWarps) k_spread_f64(const SpreadArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *tiles = reinterpret_cast<double *>(smem_raw);
     const int sub = blockIdx.x;
     const int start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int tc = tile_cells<D>(a.Pt);
     const int Pt = a.Pt;
-    for (int e = threadIdx.x; e < kF64Warps * tc * NV; e += blockDim.x) tiles[e] = 0.0;
+    const int nwarp = blockDim.x >> 5;
+    double *tiles = reinterpret_cast<double *>(smem_raw);
+    double *su = tiles + (int64_t)nwarp * NV * tc;
+    int *soff = reinterpret_cast<int *>(su + (int64_t)a.sub_max * NV);
+    for (int e = threadIdx.x; e < nwarp * tc * NV; e += blockDim.x) tiles[e] = 0.0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int j = start + i;
+        const int orig = a.perm[j];
+        const double ds = a.dinv ? a.dinv[j] : 1.0;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) su[i * NV + c] = (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds;
+        soff[i] = a.offs[j];
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *tile = tiles + (int64_t)warp * tc * NV;
@@ -282,54 +340,72 @@ __global__ void __launch_bounds__(32 * kF64Warps) k_spread_f64(const SpreadArgs 
     constexpr int ITEMS = (D >= 2) ? W * W : W;     // (qx, qy) pairs or qx
     constexpr int SLOTS = (ITEMS + 31) / 32;
     constexpr int nz = (D >= 3) ? W : 1;
-    const double *coords = static_cast<const double *>(a.coords);
-    for (int j = start + warp; j < start + cnt; j += kF64Warps) {
-        const double w0 = lane < NW ? a.wts[(int64_t)j * NW + lane] : 0.0;
-        const double w1 = (NW > 32 && lane + 32 < NW) ? a.wts[(int64_t)j * NW + 32 + lane] : 0.0;
-        const int orig = a.perm[j];
-        const double ds = a.dinv ? a.dinv[j] : 1.0;
-        double u[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) u[c] = (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds;
-        int o[3] = {0, 0, 0};
-#pragma unroll
-        for (int dd = 0; dd < D; ++dd) o[dd] = (int)floor(coords[(int64_t)j * D + dd]) - M + 1;
+    constexpr int QC = (nz % 4 == 0) ? 4 : ((nz % 3 == 0) ? 3 : ((nz % 2 == 0) ? 2 : 1));
+    const int zstride = Pt * Pt;
+    const double *wts = a.wts + (int64_t)start * NW;
+    int i = warp;
+    double w0 = 0.0, w1 = 0.0;
+    if (i < cnt) {
+        w0 = lane < NW ? wts[(int64_t)i * NW + lane] : 0.0;
+        w1 = (NW > 32 && lane + 32 < NW) ? wts[(int64_t)i * NW + 32 + lane] : 0.0;
+    }
+    for (; i < cnt; i += nwarp) {
+        const int inext = i + nwarp;
+        double n0 = 0.0, n1 = 0.0;
+        if (inext < cnt) {
+            n0 = lane < NW ? wts[(int64_t)inext * NW + lane] : 0.0;
+            n1 = (NW > 32 && lane + 32 < NW) ? wts[(int64_t)inext * NW + 32 + lane] : 0.0;
+        }
+        const int off = soff[i];
+        const int o0 = off & 1023, o1 = (off >> 10) & 1023, o2 = off >> 20;
         double uw[SLOTS][NV];
         int base[SLOTS];
+        bool valid[SLOTS];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
             const int p = lane + 32 * s;
-            const bool valid = p < ITEMS;
-            const int qx = valid ? p % W : 0;
-            const int qy = (D >= 2 && valid) ? p / W : 0;
+            valid[s] = p < ITEMS;
+            const int qx = valid[s] ? p % W : 0;
+            const int qy = (D >= 2 && valid[s]) ? p / W : 0;
             const double wxy = warp_weight(w0, w1, qx) * (D >= 2 ? warp_weight(w0, w1, W + qy) : 1.0);
 #pragma unroll
-            for (int c = 0; c < NV; ++c) uw[s][c] = valid ? u[c] * wxy : 0.0;
-            base[s] = (o[2] * Pt + o[1] + qy) * Pt + o[0] + qx;
+            for (int c = 0; c < NV; ++c) uw[s][c] = valid[s] ? su[i * NV + c] * wxy : 0.0;
+            base[s] = (o2 * Pt + o1 + qy) * Pt + o0 + qx;
         }
 #pragma unroll 1
-        for (int qz = 0; qz < nz; ++qz) {
-            const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz) : 1.0;
-            const int zoff = qz * Pt * Pt;
+        for (int qz0 = 0; qz0 < nz; qz0 += QC) {
+            double v[QC][SLOTS][NV];
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s) {
-                if (lane + 32 * s < ITEMS) {
+            for (int q = 0; q < QC; ++q)
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) {
-                        double *cell = tile + c * tc + base[s] + zoff;
-                        *cell = fma(uw[s][c], wzq, *cell);
-                    }
-                }
+                for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) v[q][s][c] = tile[c * tc + base[s] + (qz0 + q) * zstride];
+#pragma unroll
+            for (int q = 0; q < QC; ++q) {
+                const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz0 + q) : 1.0;
+#pragma unroll
+                for (int s = 0; s < SLOTS; ++s)
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) v[q][s][c] = fma(uw[s][c], wzq, v[q][s][c]);
             }
+#pragma unroll
+            for (int q = 0; q < QC; ++q)
+#pragma unroll
+                for (int s = 0; s < SLOTS; ++s)
+                    if (valid[s])
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) tile[c * tc + base[s] + (qz0 + q) * zstride] = v[q][s][c];
         }
+        w0 = n0;
+        w1 = n1;
     }
     __syncthreads();
     double *out = static_cast<double *>(a.scratch) + (int64_t)sub * tc * NV;
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
         const int c = e % NV, cell = e / NV;
         double acc = 0.0;
-#pragma unroll
-        for (int w = 0; w < kF64Warps; ++w) acc += tiles[(int64_t)w * tc * NV + c * tc + cell];
+        for (int w = 0; w < nwarp; ++w) acc += tiles[(int64_t)w * tc * NV + c * tc + cell];
         out[e] = acc;
     }
 }
@@ -478,6 +554,25 @@ __device__ __forceinline__ void load_interp_tile(const InterpArgs &a, int D, con
     }
 }
 
+// FP32 form: the epilogue runs in FP32 (the value carries FP32 accuracy);
+// only the accumulation into the FP64 output is done in FP64.
+__device__ __forceinline__ void interp_epilogue_f32(const InterpArgs &a, int i, int c, float acc)
+{
+    const int orig = a.perm[i];
+    const float ds = a.dinv ? (float)a.dinv[i] : 1.0f;
+    const float x = a.X ? (float)a.X[(int64_t)orig * a.ldx + c] : 1.0f;
+    const float r = acc - (float)a.self * (x * ds);
+    if (a.sorted_out) {
+        a.Y[(int64_t)i * a.ldy + c] = (double)r;
+    } else {
+        double outv = (double)((float)a.alpha * ds * r);
+        if (a.shift != 0.0) outv += a.shift * (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0);
+        double *yp = a.Y + (int64_t)orig * a.ldy + c;
+        if (a.accumulate) outv += *yp;
+        *yp = outv;
+    }
+}
+
 __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int c, double acc)
 {
     const int orig = a.perm[i];
@@ -510,6 +605,8 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
     __syncthreads();
     const float *coords = static_cast<const float *>(a.coords);
     constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+    constexpr int UY = (M <= 4) ? ny : 1;       // unroll the rows of small windows
+    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
         float wx[2 * M], wy[2 * M], wz[2 * M];
         int o[3] = {0, 0, 0};
@@ -519,12 +616,12 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
         float acc[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
-#pragma unroll 1
+#pragma unroll UZ
         for (int qz = 0; qz < nz; ++qz) {
             float pz[NV];
 #pragma unroll
             for (int c = 0; c < NV; ++c) pz[c] = 0.0f;
-#pragma unroll 1
+#pragma unroll UY
             for (int qy = 0; qy < ny; ++qy) {
                 const float *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
                 float r[NV];
@@ -543,14 +640,15 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
             for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
         }
 #pragma unroll
-        for (int c = 0; c < NV; ++c) interp_epilogue(a, i, c, (double)acc[c]);
+        for (int c = 0; c < NV; ++c) interp_epilogue_f32(a, i, c, acc[c]);
     }
 }
 
-// FP64 form: one warp per point with the precomputed FP64 weights; lanes
-// take (qx, qy) items, walk qz with one DFMA per tap, then the warp sums.
+// FP64 form: one thread per point, FP64 weights from the plan's table and
+// packed first taps; rows are summed with FP64 FMAs (no warp reduction, so
+// nearly every FP64 instruction is a tap).
 template <int D, int M, int NV>
-__global__ void __launch_bounds__(32 * kF64Warps) k_interp_f64(const InterpArgs a)
+__global__ void __launch_bounds__(256) k_interp_f64(const InterpArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *tile = reinterpret_cast<double *>(smem_raw);
@@ -562,55 +660,48 @@ __global__ void __launch_bounds__(32 * kF64Warps) k_interp_f64(const InterpArgs 
     bin_coords<D>(bin, a.nb0, a.nb1, bc);
     load_interp_tile<double, NV>(a, D, bc, tc, tile);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int W = 2 * M;
     constexpr int NW = D * W;
-    constexpr int ITEMS = (D >= 2) ? W * W : W;
-    constexpr int SLOTS = (ITEMS + 31) / 32;
-    constexpr int nz = (D >= 3) ? W : 1;
-    const double *coords = static_cast<const double *>(a.coords);
-    for (int j = start + warp; j < start + cnt; j += kF64Warps) {
-        const double w0 = lane < NW ? a.wts[(int64_t)j * NW + lane] : 0.0;
-        const double w1 = (NW > 32 && lane + 32 < NW) ? a.wts[(int64_t)j * NW + 32 + lane] : 0.0;
-        int o[3] = {0, 0, 0};
+    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int UY = (M <= 4) ? ny : 1;
+    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
+    for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
+        const double *wp = a.wts + (int64_t)i * NW;
+        double wx[W], wy[W], wz[W];
 #pragma unroll
-        for (int dd = 0; dd < D; ++dd) o[dd] = (int)floor(coords[(int64_t)j * D + dd]) - M + 1;
-        double wxy[SLOTS];
-        int base[SLOTS];
-        double acc[SLOTS][NV];
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-            const int p = lane + 32 * s;
-            const bool valid = p < ITEMS;
-            const int qx = valid ? p % W : 0;
-            const int qy = (D >= 2 && valid) ? p / W : 0;
-            const double v = warp_weight(w0, w1, qx) * (D >= 2 ? warp_weight(w0, w1, W + qy) : 1.0);
-            wxy[s] = valid ? v : 0.0;
-            base[s] = (o[2] * Pt + o[1] + qy) * Pt + o[0] + qx;
-#pragma unroll
-            for (int c = 0; c < NV; ++c) acc[s][c] = 0.0;
+        for (int q = 0; q < W; ++q) {
+            wx[q] = wp[q];
+            wy[q] = (D >= 2) ? wp[W + q] : 1.0;
+            wz[q] = (D >= 3) ? wp[2 * W + q] : 1.0;
         }
-#pragma unroll 1
+        const int off = a.offs[i];
+        const int o0 = off & 1023, o1 = (off >> 10) & 1023, o2 = off >> 20;
+        double acc[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+#pragma unroll UZ
         for (int qz = 0; qz < nz; ++qz) {
-            const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz) : 1.0;
-            const int zoff = qz * Pt * Pt;
+            double pz[NV];
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s)
+            for (int c = 0; c < NV; ++c) pz[c] = 0.0;
+#pragma unroll UY
+            for (int qy = 0; qy < ny; ++qy) {
+                const double *row = tile + ((o2 + qz) * Pt + o1 + qy) * Pt + o0;
+                double r[NV];
 #pragma unroll
-                for (int c = 0; c < NV; ++c) acc[s][c] = fma(wzq, tile[c * tc + base[s] + zoff], acc[s][c]);
+                for (int c = 0; c < NV; ++c) r[c] = 0.0;
+#pragma unroll
+                for (int qx = 0; qx < W; ++qx)
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) r[c] = fma(wx[qx], row[c * tc + qx], r[c]);
+#pragma unroll
+                for (int c = 0; c < NV; ++c) pz[c] = fma(wy[qy], r[c], pz[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc[c] = fma(wz[qz], pz[c], acc[c]);
         }
-        double part[NV];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) {
-            double v = 0.0;
-#pragma unroll
-            for (int s = 0; s < SLOTS; ++s) v = fma(wxy[s], acc[s][c], v);
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            part[c] = v;
-        }
-#pragma unroll
-        for (int c = 0; c < NV; ++c)
-            if (lane == c) interp_epilogue(a, j, c, part[c]);
+        for (int c = 0; c < NV; ++c) interp_epilogue(a, i, c, acc[c]);
     }
 }
 

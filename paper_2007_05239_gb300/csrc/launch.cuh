@@ -36,6 +36,8 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.perm = p->perm.as<int>();
     sa.coords = p->coords.p;
     sa.wts = p->wts.as<double>();
+    sa.offs = p->offs.as<int>();
+    sa.sub_max = p->sub_max;
     sa.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
     sa.X = v.X;
     sa.ldx = v.ldx;
@@ -58,16 +60,27 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
             ML_TRY(set_smem(k_spread_f32<D, M, NV>, smem));
             k_spread_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
-            const size_t smem = (size_t)tc * nv * sizeof(double) * kF64Warps;
+            const size_t smem = (size_t)tc * nv * sizeof(double) * p->f64_warps +
+                                (size_t)p->sub_max * (nv * sizeof(double) + sizeof(int));
             ML_TRY(set_smem(k_spread_f64<D, M, NV>, smem));
-            k_spread_f64<D, M, NV><<<p->nsub, 32 * kF64Warps, smem, st>>>(sa);
+            k_spread_f64<D, M, NV><<<p->nsub, 32 * p->f64_warps, smem, st>>>(sa);
         }
         ML_CUDA(cudaGetLastError());
     }
-    // ---- fold into the active grid (work[0])
+    // ---- sum each group of subproblem tiles, then fold the group tiles into
+    //      the active grid (work0)
+    const int64_t tile_elems = (int64_t)tc * nv;
+    T *gtile = static_cast<T *>(w.scratch) + (int64_t)p->nsub * tile_elems;
+    if (p->ngroups > 0) {
+        ProfScope pr("group_sum", st);
+        dim3 grid((unsigned)((tile_elems + 255) / 256), (unsigned)p->ngroups);
+        k_group_sum<T><<<grid, 256, 0, st>>>(static_cast<const T *>(w.scratch), p->grp_sub.as<int>(), tile_elems,
+                                             gtile);
+        ML_CUDA(cudaGetLastError());
+    }
     FoldArgs fa;
-    fa.bin_sub = p->bin_sub.as<int>();
-    fa.scratch = w.scratch;
+    fa.bin_sub = p->bin_grp.as<int>();
+    fa.scratch = gtile;
     fa.grid = w.work0;
     fa.nv = nv;
     fa.B = g.B;
@@ -124,6 +137,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.perm = sa.perm;
     ia.coords = sa.coords;
     ia.wts = sa.wts;
+    ia.offs = sa.offs;
     ia.dinv = sa.dinv;
     ia.X = v.X;
     ia.ldx = v.ldx;
@@ -158,7 +172,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
             k_interp_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
         } else {
             ML_TRY(set_smem(k_interp_f64<D, M, NV>, smem));
-            k_interp_f64<D, M, NV><<<p->nsub, 32 * kF64Warps, smem, st>>>(ia);
+            k_interp_f64<D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
         }
         ML_CUDA(cudaGetLastError());
     }
@@ -179,18 +193,31 @@ static ml_status run_layer_dmv(ml_plan_s *p, const ApplyVec &v, const ApplyOpts 
     return fail(ML_ERR_ARG, "unsupported vectors per pass");
 }
 
+// One layer pass for a given dimension and window half-width (instantiated
+// per translation unit; the d = 3 instances are split over several files to
+// keep each compile short).
+template <typename T, int D, int M>
+ml_status run_layer_m(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st)
+{
+    return run_layer_dmv<T, D, M>(p, v, o, w, st);
+}
+
+#define ML_DECL_LAYER_M(T, D, M)                                                                       \
+    extern template ml_status run_layer_m<T, D, M>(ml_plan_s *, const ApplyVec &, const ApplyOpts &, \
+                                                   const LayerWork &, cudaStream_t);
+
 template <typename T, int D>
 static ml_status run_layer_d(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                              cudaStream_t st)
 {
     switch (p->m) {
-    case 2: return run_layer_dmv<T, D, 2>(p, v, o, w, st);
-    case 3: return run_layer_dmv<T, D, 3>(p, v, o, w, st);
-    case 4: return run_layer_dmv<T, D, 4>(p, v, o, w, st);
-    case 5: return run_layer_dmv<T, D, 5>(p, v, o, w, st);
-    case 6: return run_layer_dmv<T, D, 6>(p, v, o, w, st);
-    case 7: return run_layer_dmv<T, D, 7>(p, v, o, w, st);
-    case 8: return run_layer_dmv<T, D, 8>(p, v, o, w, st);
+    case 2: return run_layer_m<T, D, 2>(p, v, o, w, st);
+    case 3: return run_layer_m<T, D, 3>(p, v, o, w, st);
+    case 4: return run_layer_m<T, D, 4>(p, v, o, w, st);
+    case 5: return run_layer_m<T, D, 5>(p, v, o, w, st);
+    case 6: return run_layer_m<T, D, 6>(p, v, o, w, st);
+    case 7: return run_layer_m<T, D, 7>(p, v, o, w, st);
+    case 8: return run_layer_m<T, D, 8>(p, v, o, w, st);
     default: return fail(ML_ERR_ARG, "window half-width out of range");
     }
 }

@@ -34,6 +34,7 @@ constexpr int kMaxVec = 8;       // vectors per spreading/interpolation pass
 constexpr int kMaxM = 8;         // window half-width limit
 constexpr int kMaxN = 512;       // bandwidth limit
 constexpr int kSubPoints = 1024; // points per subproblem (bounds per-cell counts)
+constexpr int kGroupSubs = 16;   // subproblem tiles summed per group before the fold
 
 // ------------------------------------------------------------ device buffer
 struct DevBuf {
@@ -86,6 +87,9 @@ struct ml_plan_s {
     int s0[3] = {0, 0, 0}; // torus index of active-grid cell 0 per dim
     ml::GridGeom g;
     int vp = 1;            // vectors per pass
+    int f64_warps = 8;     // FP64 form: warps (private tiles) per CTA
+    int sub_max = 0;       // largest subproblem (points)
+    int ngroups = 0;       // groups of <= kGroupSubs consecutive subproblems of one bin
     int nsub = 0;
     double deg_min = 0, deg_max = 0;
     int64_t applied = 0;   // vectors pushed through apply_layer
@@ -99,10 +103,13 @@ struct ml_plan_s {
     ml::DevBuf perm;      // int32 n: sorted position -> input index
     ml::DevBuf coords;    // T n*d local grid coordinates
     ml::DevBuf wts;       // FP64 form: double n*d*2m window weights
+    ml::DevBuf offs;      // FP64 form: int n packed first taps o0 | o1 << 10 | o2 << 20
     ml::DevBuf deg;       // double n: degrees
     ml::DevBuf dinv;      // double n: D^{-1/2}
     ml::DevBuf sub_bin, sub_start, sub_count;  // int32 nsub
     ml::DevBuf bin_sub;   // int32 nbins+1: first subproblem of each bin
+    ml::DevBuf grp_sub;   // int32 ngroups+1: first subproblem of each tile group
+    ml::DevBuf bin_grp;   // int32 nbins+1: first tile group of each bin
     ml::DevBuf trig_f[3]; // T K x L_a  (forward, cos rows then sin rows)
     ml::DevBuf trig_b[3]; // T L_a x K  (backward = transpose)
     ml::DevBuf mult_d;    // T K^d

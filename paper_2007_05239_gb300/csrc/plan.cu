@@ -207,6 +207,16 @@ __global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n,
 }
 
 
+// packed first tap of every point: o_a = floor(u_a) - m + 1 in [0, B]
+__global__ void k_first_taps(const double *__restrict__ coords, int64_t n, int d, int m, int *offs)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int packed = 0;
+        for (int a = 0; a < d; ++a) packed |= ((int)floor(coords[i * d + a]) - m + 1) << (10 * a);
+        offs[i] = packed;
+    }
+}
+
 // ------------------------------------------------------------ radix sort
 constexpr int RS_THREADS = 256;
 constexpr int RS_TILE = 4096;
@@ -367,8 +377,29 @@ static int auto_N(double sigma_s, double target)
     return std::max(N, 8);
 }
 
-// spreading bin edge: the largest B whose padded tile (B + 2m)^d of doubles
-// stays within 48 KB per vector
+// FP64 form: bin edge and warps per CTA.  Every warp owns a padded tile of
+// (B + 2m)^d doubles; the tiles plus the staged subproblem inputs (12 KB)
+// must fit 200 KB.  Prefer 8 warps as long as the bin keeps an edge >= 4.
+static void choose_f64_layout(int d, int m, int *B, int *nw)
+{
+    const double budget = 188.0 * 1024.0;
+    for (int w : {8, 4, 2, 1}) {
+        const double cells = budget / (8.0 * w);
+        const int Pt = (int)std::floor(std::pow(cells, 1.0 / d) + 1e-9);
+        int b = Pt - 2 * m;
+        if (d == 1) b = std::min(b, 512);
+        if (b >= 4 || (w == 1 && b >= 1)) {
+            *B = b;
+            *nw = w;
+            return;
+        }
+    }
+    *B = 1;
+    *nw = 1;
+}
+
+// FP32 form: the largest B whose padded tile (B + 2m)^d of 8-byte cells stays
+// within 48 KB per vector
 static int choose_bin(int d, int m)
 {
     const int budget = 48 * 1024 / 8;
@@ -398,7 +429,8 @@ void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work)
 {
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     const GridGeom &g = p->g;
-    *scratch = (size_t)p->nsub * g.tile_cells() * nv * ts;
+    // subproblem tiles, then one tile per group of subproblems
+    *scratch = (size_t)(p->nsub + p->ngroups) * g.tile_cells() * nv * ts;
     // transform stages: extents go from L to K one dim at a time and back
     int64_t mx = 1;
     for (int stage = 0; stage <= p->d; ++stage) {
@@ -517,15 +549,29 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         // its first tap one cell to the right
         g.L[a] = (int)(fmax - fmin) + 2 * p->m + 1;
     }
-    g.B = choose_bin(d, p->m);
+    if (p->prec == ML_F32) {
+        g.B = choose_bin(d, p->m);
+    } else {
+        choose_f64_layout(d, p->m, &g.B, &p->f64_warps);
+    }
     g.Pt = g.B + 2 * p->m;              // first tap offset in [0, B], 2m taps
     g.R = 1 + (2 * p->m - 1) / g.B;     // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
     {
-        // FP32: one shared tile per CTA; FP64: one tile per warp
+        // FP32: one shared tile per CTA; FP64: one tile per warp plus the
+        // staged inputs of a subproblem
         const int64_t tc = g.tile_cells();
-        const int64_t per_vec = p->prec == ML_F32 ? tc * 4 : tc * 8 * kF64Warps;
-        p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / per_vec));
+        if (p->prec == ML_F32) {
+            p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * 4)));
+        } else {
+            int vp = 1;
+            for (int v = kMaxVec; v >= 1; --v)
+                if ((int64_t)p->f64_warps * tc * 8 * v + (int64_t)kSubPoints * (8 * v + 4) <= 200 * 1024) {
+                    vp = v;
+                    break;
+                }
+            p->vp = vp;
+        }
     }
     // ---- keys, sort
     DevBuf urel, keys, keys2, idx, idx2;
@@ -573,6 +619,8 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         ProfScope pr_("plan", st);
         k_window_table_f64<<<grid_for(n * d * 2 * p->m), 256, 0, st>>>(
             p->coords.as<double>(), n, d, p->m, (double)p->m * p->m, p->kb_shape, p->kb_norm, p->wts.as<double>());
+        ML_TRY(p->offs.ensure((size_t)n * sizeof(int)));
+        k_first_taps<<<grid_for(n), 256, 0, st>>>(p->coords.as<double>(), n, d, p->m, p->offs.as<int>());
         ML_CUDA(cudaGetLastError());
     }
     // ---- bins -> subproblems
@@ -604,6 +652,8 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     }
     bs[nbins] = (int)sb.size();
     p->nsub = (int)sb.size();
+    p->sub_max = 0;
+    for (int c : sc) p->sub_max = std::max(p->sub_max, c);
     ML_TRY(p->sub_bin.ensure(sb.size() * 4));
     ML_TRY(p->sub_start.ensure(sb.size() * 4));
     ML_TRY(p->sub_count.ensure(sb.size() * 4));
@@ -612,6 +662,19 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_CUDA(cudaMemcpy(p->sub_start.p, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice));
     ML_CUDA(cudaMemcpy(p->sub_count.p, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice));
     ML_CUDA(cudaMemcpy(p->bin_sub.p, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice));
+    // groups of <= kGroupSubs consecutive subproblems of one bin
+    std::vector<int> gs, bg(nbins + 1);
+    for (int64_t b = 0; b < nbins; ++b) {
+        bg[b] = (int)gs.size();
+        for (int s = bs[b]; s < bs[b + 1]; s += kGroupSubs) gs.push_back(s);
+    }
+    bg[nbins] = (int)gs.size();
+    p->ngroups = (int)gs.size();
+    gs.push_back(p->nsub);
+    ML_TRY(p->grp_sub.ensure(gs.size() * 4));
+    ML_TRY(p->bin_grp.ensure(bg.size() * 4));
+    ML_CUDA(cudaMemcpy(p->grp_sub.p, gs.data(), gs.size() * 4, cudaMemcpyHostToDevice));
+    ML_CUDA(cudaMemcpy(p->bin_grp.p, bg.data(), bg.size() * 4, cudaMemcpyHostToDevice));
     urel.release();
     keys.release();
     keys2.release();
@@ -668,7 +731,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
 int64_t ml_plan_s::device_bytes() const
 {
     int64_t t = 0;
-    const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub,
+    const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
                                 &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status};
     for (auto *b : bufs) t += (int64_t)b->bytes;
@@ -677,8 +740,8 @@ int64_t ml_plan_s::device_bytes() const
 
 static void release_all(ml_plan_s *p)
 {
-    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
-                          &p->bin_sub, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
+    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
+                          &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
                           &p->stage_y, &p->status};
     for (auto *b : bufs) b->release();

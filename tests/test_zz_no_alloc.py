@@ -53,12 +53,11 @@ def test_noalloc_per_layer_and_raw():
 
 
 def test_noalloc_rejects_oversize_and_host_buffers():
-    # n = 1e6 clustered FP64 points need far more than 32 MiB of tiles
-    rng = np.random.default_rng(5)
-    mu = rng.uniform(0, 1, (4, 3))
-    big = mu[rng.integers(0, 4, 1_000_000)] + 0.02 * rng.standard_normal((1_000_000, 3))
-    plan = ml.ml_fastsum_plan(dev(big), 0.2, prec="f64")
-    X = dev(np.ones((1_000_000, 1)))
+    # 3e6 FP64 points need ~3000 subproblem tiles: far more than 32 MiB
+    n = 3_000_000
+    big = np.random.default_rng(5).uniform(0, 1, (n, 3))
+    plan = ml.ml_fastsum_plan(dev(big), 0.05, prec="f64")
+    X = dev(np.ones((n, 1)))
     Y = torch.empty_like(X)
     with pytest.raises(ml.MLError) as e:
         ml.ml_fastsum_apply_noalloc([plan], X, Y)
