@@ -207,6 +207,10 @@ def main():
     ap.add_argument("--p", type=float, default=None)
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--mode", default="eig", choices=["eig", "apply"],
+                    help="eig: plan + k eigenpairs per step (default); apply: one multilayer normalised "
+                         "product of b vectors per step on plans made before the timed region")
+    ap.add_argument("--b", type=int, default=1, help="vectors per product in --mode apply")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -241,7 +245,18 @@ def main():
     dev_layers = [torch.as_tensor(L, device="cuda") for L in layers]
     k, p, prec, target = spec["k"], spec["p"], spec["prec"], spec["target"]
 
+    apply_plans = None
+    if args.mode == "apply":
+        apply_plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dev_layers, sig)]
+        Xa = torch.as_tensor(np.random.default_rng(7).uniform(0, 1, (n, args.b)), device="cuda")
+        Ya = torch.empty_like(Xa)
+
     def step(dl, evecs):
+        if apply_plans is not None:
+            before = sum(pl.info["applied_vectors"] for pl in apply_plans)
+            ml.ml_fastsum_apply(apply_plans, Xa, Ya, mode="normalized")
+            applied = (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
+            return None, 0, applied, [pl.info["m"] for pl in apply_plans]
         plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dl, sig)]
         lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=p, tol=1e-8, seed=1, evecs=evecs)
         applied = sum(pl.info["applied_vectors"] for pl in plans) * n
@@ -308,13 +323,23 @@ def main():
     # ---- end to end through the C ABI with host buffers (pinned)
     host_layers = [torch.as_tensor(L).pin_memory() for L in layers]
     host_evecs = torch.empty(n * k, dtype=torch.float64).pin_memory()
-    h2d = sum(L.numel() * 8 for L in host_layers)
-    d2h = n * k * 8 + k * 8
+    if args.mode == "apply":
+        hx = Xa.cpu().pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        h2d, d2h = hx.numel() * 8, hy.numel() * 8
+    else:
+        h2d = sum(L.numel() * 8 for L in host_layers)
+        d2h = n * k * 8 + k * 8
     torch.cuda.synchronize()
     barrier()
     e0.record(stream)
     applied_e2e = 0
     for _ in range(args.steps):
+        if args.mode == "apply":
+            before = sum(pl.info["applied_vectors"] for pl in apply_plans)
+            ml.ml_fastsum_apply(apply_plans, hx, hy, mode="normalized")   # host buffers: staged by the library
+            applied_e2e += (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
+            continue
         dl = [x.to("cuda", non_blocking=True) for x in host_layers]
         lam_e, _, a, _ = step(dl, host_evecs)
         applied_e2e += a
@@ -333,8 +358,7 @@ def main():
         "metric": metric_name(spec), "value": value, "unit": "Gpts·vec/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic", "config": config_dict(args, spec, n, T),
-        "lanczos_s": t_max / args.steps / 1e3, "eigenvalues": [float(x) for x in lam[:min(5, k)]],
-        "nconv": int(nconv), "gpu_launches": launches,
+        "mode": args.mode, "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "Gpts·vec/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "clocks": clk,
     }
@@ -342,6 +366,14 @@ def main():
     # ---- CPU baseline (oracle on the host cores) and sampled accuracy, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch)
+    if args.mode == "eig":
+        line["lanczos_s"] = t_max / args.steps / 1e3
+        line["eigenvalues"] = [float(x) for x in lam[:min(5, k)]]
+        line["nconv"] = int(nconv)
+    else:
+        line["metric"] = (f"fast-summation Gpts·vec/s ({prec.upper()} form) of one multilayer normalised product, "
+                          f"b={args.b}")
+        line["config"]["b"] = args.b
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -356,12 +388,13 @@ def cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch):
     n, T = layers[0].shape[0], len(layers)
     rng = np.random.default_rng(123)
     v = rng.uniform(0, 1, n)
-    r0 = np.sort(rng.choice(n, size=min(n, 8), replace=False))
+    graph.W_apply(layers[0][:1000], sig[0], v[:1000], rows=np.arange(8))   # load the library, start threads
+    r0 = np.sort(rng.choice(n, size=min(n, 64), replace=False))
     t0 = time.perf_counter()
     for t in range(T):
         graph.W_apply(layers[t], sig[t], v, rows=r0)
     dt = max(time.perf_counter() - t0, 1e-6)
-    R = int(min(n, max(32, 8 * 12.0 / dt)))
+    R = int(min(n, max(64, 64 * 12.0 / dt)))
     rows = np.sort(rng.choice(n, size=R, replace=False))
     t0 = time.perf_counter()
     ref = sum(graph.W_apply(layers[t], sig[t], v, rows=rows) for t in range(T)) / T

@@ -59,14 +59,93 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__
     }
 }
 
-// out[c] = sum over blocks of part[b][c] (fixed order)
+// out[c] = sum over blocks of part[b][c]: one warp per column, lanes stride
+// over the blocks, then a shuffle tree (fixed order, deterministic)
 __global__ void k_reduce_cols(const double *__restrict__ part, int nblk, int ncol, double *out)
 {
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < ncol; c += nw) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ncol + c];
-        out[c] = s;
+        for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * ncol + c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[c] = s;
     }
+}
+
+// ---- conjugate gradient with device-resident scalars
+// sc[0] = r.r (current), sc[1] = p.Ap, sc[2] = alpha, sc[3] = beta, sc[4] = r.r (new)
+
+// partial sums of a.b per block
+__global__ void __launch_bounds__(256) k_dot_part(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                                  double *part)
+{
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        s = fma(x[r], y[r], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// one warp: total of the partials, then the CG scalar update
+//   which = 0: sc[1] = p.Ap, sc[2] = alpha = sc[0] / sc[1]
+//   which = 1: sc[4] = r.r, sc[3] = beta = sc[4] / sc[0], sc[0] = sc[4]
+//   which = 2: sc[0] = total (initial r.r)
+__global__ void k_cg_scalars(const double *__restrict__ part, int nblk, int which, double *sc)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += part[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+        if (which == 0) {
+            sc[1] = s;
+            sc[2] = (s > 0.0) ? sc[0] / s : 0.0;
+        } else if (which == 1) {
+            sc[4] = s;
+            sc[3] = (sc[0] > 0.0) ? s / sc[0] : 0.0;
+            sc[0] = s;
+        } else {
+            sc[0] = s;
+        }
+    }
+}
+
+// y += alpha p; r -= alpha Ap; partial sums of r.r
+__global__ void __launch_bounds__(256) k_cg_step(const double *__restrict__ sc, const double *__restrict__ p,
+                                                 const double *__restrict__ ap, int64_t n, double *y, double *r,
+                                                 double *part)
+{
+    __shared__ double red[8];
+    const double alpha = sc[2];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        y[i] = fma(alpha, p[i], y[i]);
+        const double ri = fma(-alpha, ap[i], r[i]);
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// p = r + beta p with beta on the device
+__global__ void k_cg_dir(const double *__restrict__ sc, const double *__restrict__ r, int64_t n, double *p)
+{
+    const double beta = sc[3];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
 }
 
 // x -= Q[:, 0:ncol] h
@@ -213,7 +292,7 @@ struct Workspace {
         }
         {
             ProfScope pr("dots_reduce", st);
-            k_reduce_cols<<<1, 128, 0, st>>>(part.as<double>(), nblk, ncol, out);
+            k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nblk, ncol, out);
         }
         ML_CUDA(cudaGetLastError());
         return ML_OK;
@@ -264,6 +343,10 @@ struct InverseOp {
     int inner_max = 200;
     double inner_tol = 1e-12;
     long long inner_iters = 0;
+    // the residual of iteration i is copied to pinned host memory and read
+    // while iteration i+1 runs (one iteration of lag, no pipeline bubble)
+    double *hrr = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 
     ml_status init()
     {
@@ -271,7 +354,16 @@ struct InverseOp {
         ML_TRY(p.ensure(n * 8));
         ML_TRY(ap.ensure(n * 8));
         ML_TRY(y.ensure(n * 8));
+        ML_CUDA(cudaMallocHost(&hrr, 2 * sizeof(double)));
+        ML_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        ML_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         return ML_OK;
+    }
+    ~InverseOp()
+    {
+        if (hrr) cudaFreeHost(hrr);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
     }
     // ap = (L_sym + delta I) v = (1 + delta) v - A v
     ml_status shifted(ml_plan_s *L, const double *v, double *out, cudaStream_t st)
@@ -286,38 +378,55 @@ struct InverseOp {
     ml_status apply(const double *x, double *out, cudaStream_t st)
     {
         const int nb = vec_blocks(n);
+        const int pb = ws->nblk;
+        double *part = ws->part.as<double>();
+        double *sc = ws->scal.as<double>() + 8;
         ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
+        // ||x||^2 for the relative stopping test
         double bb;
         ML_TRY(ws->dot_host(x, x, &bb));
-        const double bnorm = std::sqrt(bb);
+        const double stop2 = inner_tol * inner_tol * bb;
         for (int t = 0; t < T; ++t) {
-            // x0 = 0: r = x, p = x
+            // x0 = 0: r = x, p = x, r.r = ||x||^2
             ML_CUDA(cudaMemcpyAsync(r.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
             ML_CUDA(cudaMemcpyAsync(p.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
             ML_CUDA(cudaMemsetAsync(y.p, 0, n * 8, st));
-            double rr = bb;
-            for (int it = 0; it < inner_max && std::sqrt(rr) > inner_tol * bnorm; ++it) {
-                ML_TRY(shifted(layers[t], p.as<double>(), ap.as<double>(), st));
-                double pap;
-                ML_TRY(ws->dot_host(p.as<double>(), ap.as<double>(), &pap));
-                if (!(pap > 0)) return fail(ML_ERR_BREAKDOWN, "CG: operator not positive definite (p^T A p <= 0)");
-                const double alpha = rr / pap;
-                { ProfScope pr_("vector", st);
-                k_axpy<<<nb, 256, 0, st>>>(alpha, p.as<double>(), n, y.as<double>());
-                }
-                { ProfScope pr_("vector", st);
-                k_axpy<<<nb, 256, 0, st>>>(-alpha, ap.as<double>(), n, r.as<double>());
-                }
-                double rr2;
-                ML_TRY(ws->dot_host(r.as<double>(), r.as<double>(), &rr2));
-                { ProfScope pr_("vector", st);
-                k_xpby<<<nb, 256, 0, st>>>(r.as<double>(), rr2 / rr, n, p.as<double>());
-                }
-                rr = rr2;
-                ++inner_iters;
+            {
+                ProfScope pr("cg", st);
+                k_dot_part<<<pb, 256, 0, st>>>(x, x, n, part);
+                k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 2, sc);
             }
-            { ProfScope pr_("vector", st);
-            k_axpy<<<nb, 256, 0, st>>>(1.0 / T, y.as<double>(), n, out);
+            bool done = !(bb > 0);
+            for (int it = 0; it < inner_max && !done; ++it) {
+                ML_TRY(shifted(layers[t], p.as<double>(), ap.as<double>(), st));
+                {
+                    ProfScope pr("cg", st);
+                    k_dot_part<<<pb, 256, 0, st>>>(p.as<double>(), ap.as<double>(), n, part);
+                    k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 0, sc);
+                    k_cg_step<<<pb, 256, 0, st>>>(sc, p.as<double>(), ap.as<double>(), n, y.as<double>(),
+                                                  r.as<double>(), part);
+                    k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 1, sc);
+                    k_cg_dir<<<nb, 256, 0, st>>>(sc, r.as<double>(), n, p.as<double>());
+                }
+                ++inner_iters;
+                ML_CUDA(cudaMemcpyAsync(hrr + (it & 1), sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+                ML_CUDA(cudaEventRecord(ev[it & 1], st));
+                if (it >= 1) {
+                    ML_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));
+                    done = hrr[(it - 1) & 1] <= stop2;
+                }
+            }
+            ML_CUDA(cudaStreamSynchronize(st));
+            if (!done) {
+                double hs[2];
+                ML_CUDA(cudaMemcpy(hs, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+                if (hs[0] > stop2)
+                    return fail(ML_ERR_BREAKDOWN, !(hs[1] > 0) ? "CG: operator not positive definite (p^T A p <= 0)"
+                                                               : "CG: inner solve did not converge");
+            }
+            {
+                ProfScope pr("vector", st);
+                k_axpy<<<nb, 256, 0, st>>>(1.0 / T, y.as<double>(), n, out);
             }
             ML_CUDA(cudaGetLastError());
         }
