@@ -256,11 +256,11 @@ def main():
             before = sum(pl.info["applied_vectors"] for pl in apply_plans)
             ml.ml_fastsum_apply(apply_plans, Xa, Ya, mode="normalized")
             applied = (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
-            return None, 0, applied, [pl.info["m"] for pl in apply_plans]
+            return None, 0, applied, [pl.info["taps"] for pl in apply_plans]
         plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dl, sig)]
         lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=p, tol=1e-8, seed=1, evecs=evecs)
         applied = sum(pl.info["applied_vectors"] for pl in plans) * n
-        ms = [pl.info["m"] for pl in plans]
+        ms = [pl.info["taps"] for pl in plans]
         for pl in plans:
             pl.destroy()
         return lam, nconv, applied, ms
@@ -306,8 +306,8 @@ def main():
 
     # ---- roofline of the dominant kernel family
     d = spec["d"]
-    m = msz[0]
-    taps = (2 * m) ** d
+    W = msz[0]
+    taps = W ** d
     fam = max(("spread", "interp"), key=lambda f: prof.get(f, (0, 0.0))[1])
     fam_launches, fam_ms = prof.get(fam, (0, 0.0))
     flops = applied * 2.0 * taps                  # one multiply-add per tap and point-vector
@@ -317,7 +317,7 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"nominal {prec.upper()} ALU rate: 152 SMs x 2070 MHz x "
                                f"{4 if prec == 'f64' else 256} flop/clk/SM",
-                "work": f"2 flop per tap, (2m)^d = {taps} taps per point-vector, m = {m}",
+                "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}",
                 "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()}}
 
     # ---- end to end through the C ABI with host buffers (pinned)

@@ -76,7 +76,7 @@ typedef struct {
     int64_t n;
     int d;
     int N;              /* bandwidth of K_RF, I_N = {-N/2..N/2-1}^d (Eq. K_RF)  */
-    int m;              /* window half-width in grid cells (2m taps per dim)    */
+    int m;              /* window half-width in grid cells, rounded down        */
     int n_os;           /* oversampled grid size per dim (torus of n_os cells)  */
     int L[3];           /* active grid extent per dim (cells that can be nonzero) */
     int bin;            /* spreading tile (bin) edge in cells                   */
@@ -95,6 +95,8 @@ typedef struct {
     int64_t device_bytes;    /* device memory owned by the plan                  */
     int64_t applied_vectors; /* vectors pushed through this layer's fast summation
                                 since the plan was made (work counter)          */
+    int taps;                /* window width: taps per dimension (half-width taps/2;
+                                automatic choices may be odd)                    */
 } ml_plan_info;
 
 /*
@@ -106,7 +108,9 @@ typedef struct {
  *   n, d           n >= 2, d in {1,2,3}.
  *   sigma          Gaussian width > 0 in the units of `points`.
  *   N              bandwidth (even, 4..512), or 0 to choose from target_rel_err.
- *   m              window half-width (2..8), or 0 to choose from target_rel_err.
+ *   m              window half-width (2..8, i.e. 2m taps per dimension), or 0 to
+ *                  choose the width (4..8, 10, ..., 16 taps, odd widths allowed)
+ *                  from target_rel_err.
  *   eps_B, p_reg   eps_B = 0: box domain (periodised Gaussian, no regulariser);
  *                  0 < eps_B < 1/2: ball domain with the regularised kernel
  *                  K_R of degree 2*p_reg-1 on (1/2-eps_B, 1/2], p_reg in 1..8.

@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
                 ("eps_B", ctypes.c_double), ("sigma", ctypes.c_double), ("sigma_s", ctypes.c_double),
                 ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("target_rel_err", ctypes.c_double),
                 ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("applied_vectors", ctypes.c_int64)]
+                ("applied_vectors", ctypes.c_int64), ("taps", ctypes.c_int)]
 
     def as_dict(self):
         out = {}

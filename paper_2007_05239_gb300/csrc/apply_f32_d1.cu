@@ -1,14 +1,16 @@
-// F32 form, d = 1: dispatch over the window half-width (kernels in kernels.cuh).
+// F32 form, d = 1: dispatch over the window width (kernels in kernels.cuh).
 #include "launch.cuh"
 
 namespace ml {
-ML_DECL_LAYER_M(float, 1, 2)
-ML_DECL_LAYER_M(float, 1, 3)
-ML_DECL_LAYER_M(float, 1, 4)
-ML_DECL_LAYER_M(float, 1, 5)
-ML_DECL_LAYER_M(float, 1, 6)
-ML_DECL_LAYER_M(float, 1, 7)
-ML_DECL_LAYER_M(float, 1, 8)
+ML_DECL_LAYER_W(float, 1, 4)
+ML_DECL_LAYER_W(float, 1, 5)
+ML_DECL_LAYER_W(float, 1, 6)
+ML_DECL_LAYER_W(float, 1, 7)
+ML_DECL_LAYER_W(float, 1, 8)
+ML_DECL_LAYER_W(float, 1, 10)
+ML_DECL_LAYER_W(float, 1, 12)
+ML_DECL_LAYER_W(float, 1, 14)
+ML_DECL_LAYER_W(float, 1, 16)
 
 ml_status run_layer_f32_d1(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                            cudaStream_t st)

@@ -1,0 +1,9 @@
+// F32 form, d = 3, window widths {14, 16}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_w<float, 3, 14>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<float, 3, 16>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

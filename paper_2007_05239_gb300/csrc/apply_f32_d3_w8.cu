@@ -1,0 +1,7 @@
+// F32 form, d = 3, window widths {8}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_w<float, 3, 8>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

@@ -1,0 +1,23 @@
+// F64 form, d = 1, window widths {4, 5, 6, 7, 8, 10, 12, 14, 16}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_w<double, 1, 4>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 5>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 6>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 7>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 8>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 10>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 12>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 14>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 1, 16>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

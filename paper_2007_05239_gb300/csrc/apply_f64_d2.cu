@@ -1,14 +1,16 @@
-// F64 form, d = 2: dispatch over the window half-width (kernels in kernels.cuh).
+// F64 form, d = 2: dispatch over the window width (kernels in kernels.cuh).
 #include "launch.cuh"
 
 namespace ml {
-ML_DECL_LAYER_M(double, 2, 2)
-ML_DECL_LAYER_M(double, 2, 3)
-ML_DECL_LAYER_M(double, 2, 4)
-ML_DECL_LAYER_M(double, 2, 5)
-ML_DECL_LAYER_M(double, 2, 6)
-ML_DECL_LAYER_M(double, 2, 7)
-ML_DECL_LAYER_M(double, 2, 8)
+ML_DECL_LAYER_W(double, 2, 4)
+ML_DECL_LAYER_W(double, 2, 5)
+ML_DECL_LAYER_W(double, 2, 6)
+ML_DECL_LAYER_W(double, 2, 7)
+ML_DECL_LAYER_W(double, 2, 8)
+ML_DECL_LAYER_W(double, 2, 10)
+ML_DECL_LAYER_W(double, 2, 12)
+ML_DECL_LAYER_W(double, 2, 14)
+ML_DECL_LAYER_W(double, 2, 16)
 
 ml_status run_layer_f64_d2(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                            cudaStream_t st)

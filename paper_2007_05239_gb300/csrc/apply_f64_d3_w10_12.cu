@@ -1,0 +1,9 @@
+// F64 form, d = 3, window widths {10, 12}.
+#include "launch.cuh"
+
+namespace ml {
+template ml_status run_layer_w<double, 3, 10>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+template ml_status run_layer_w<double, 3, 12>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
+                                              const LayerWork &, cudaStream_t);
+}  // namespace ml

@@ -47,10 +47,10 @@ ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaS
 }
 
 // vectors in the next pass: 8 or 4 when the plan's tile holds them and the
-// window is small (M <= 4), else 1
+// window is small (W <= 8), else 1
 int pass_width(const ml_plan_s *p, int remaining)
 {
-    if (p->m <= 4) {
+    if (p->W <= 8) {
         if (remaining >= 8 && p->vp >= 8) return 8;
         if (remaining >= 4 && p->vp >= 4) return 4;
     }

@@ -28,19 +28,20 @@ double bessel_i0(double x)
 }
 
 // The Kaiser-Bessel pair used by the NFFT (window phi with shape
-// b = pi (2 - 1/sigma_os)):  phi(x) = (1/pi) sinh(b sqrt(m^2 - n^2 x^2)) /
-// sqrt(m^2 - n^2 x^2) on |x| <= m/n, with Fourier transform
-// phi_hat(k) = (1/n) I_0(m sqrt(b^2 - (2 pi k / n)^2)) for |k| <= n(1 - 1/(2 sigma_os)).
-// The device evaluates the normalised window phi_n = pi m / sinh(b m) * phi
+// b = pi (2 - 1/sigma_os)) with half-width h (in grid cells; h = W/2 for a
+// window of W taps, any real h > 0):  phi(x) = (1/pi) sinh(b sqrt(h^2 - n^2 x^2)) /
+// sqrt(h^2 - n^2 x^2) on |x| <= h/n, with Fourier transform
+// phi_hat(k) = (1/n) I_0(h sqrt(b^2 - (2 pi k / n)^2)) for |k| <= n(1 - 1/(2 sigma_os)).
+// The device evaluates the normalised window phi_n = pi h / sinh(b h) * phi
 // (phi_n(0) = 1), so its coefficients carry the same factor.
-void window_fourier(int n_os, int m, double b, int kmax, std::vector<double> &out)
+void window_fourier(int n_os, double h, double b, int kmax, std::vector<double> &out)
 {
     out.assign(kmax + 1, 0.0);
-    const double c = kPi * m / std::sinh(b * m);
+    const double c = kPi * h / std::sinh(b * h);
     for (int k = 0; k <= kmax; ++k) {
         const double w = 2.0 * kPi * k / n_os;
         const double arg = b * b - w * w;
-        out[k] = arg > 0 ? c * bessel_i0(m * std::sqrt(arg)) / n_os : 0.0;
+        out[k] = arg > 0 ? c * bessel_i0(h * std::sqrt(arg)) / n_os : 0.0;
     }
 }
 

@@ -1,10 +1,10 @@
 // Device kernels of one layer's fast summation (Alg. 1, Sec. 4), templated
 // on the precision T of the window/grid arithmetic, the dimension D and the
-// window half-width M.
+// window width W (taps per dimension).
 //
 // Data layout (all in the plan's sorted order, see plan.cu):
 //   coords   T [n][D]    local grid coordinate u of each point; the first tap
-//                        of dim a is f0 = floor(u_a) - M + 1 >= 0
+//                        of dim a is floor(u_a - W/2) + 1 >= 0
 //   perm     int [n]     sorted position -> input index
 //   dinv     double [n]  D^{-1/2} in sorted order
 //   grid     T [L2][L1][L0][nv]  active grid, dim 0 fastest, vectors innermost
@@ -43,26 +43,27 @@ __device__ __forceinline__ int fixed_round(float x)
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-// The 2M window weights of one dimension for a point with local coordinate x
-// (relative to its bin origin): taps start at o = floor(x) - M + 1 and the
-// weight of tap q is phi_n(frac(x) + M - 1 - q).
-template <int M>
+// The W window weights of one dimension for a point with local coordinate x
+// (relative to its bin origin): the taps are the W cells nearest to x, the
+// first at o = floor(x - W/2) + 1, and the weight of tap q is
+// phi_n(x - o - q), |x - o - q| <= W/2.
+template <int W>
 __device__ __forceinline__ int window_row(float x, float m2, float b, float norm2, float *w)
 {
-    const float fl = floorf(x);
-    const float fr = x - fl;
+    const float fl = floorf(x - 0.5f * (float)W);
+    const float t0 = x - fl - 1.0f;
 #pragma unroll
-    for (int q = 0; q < 2 * M; ++q) w[q] = kb_weight(fr + (float)(M - 1 - q), m2, b, norm2);
-    return (int)fl - M + 1;
+    for (int q = 0; q < W; ++q) w[q] = kb_weight(t0 - (float)q, m2, b, norm2);
+    return (int)fl + 1;
 }
-template <int M>
+template <int W>
 __device__ __forceinline__ int window_row(double x, double m2, double b, double norm2, double *w)
 {
-    const double fl = floor(x);
-    const double fr = x - fl;
+    const double fl = floor(x - 0.5 * (double)W);
+    const double t0 = x - fl - 1.0;
 #pragma unroll
-    for (int q = 0; q < 2 * M; ++q) w[q] = kb_weight(fr + (double)(M - 1 - q), m2, b, norm2);
-    return (int)fl - M + 1;
+    for (int q = 0; q < W; ++q) w[q] = kb_weight(t0 - (double)q, m2, b, norm2);
+    return (int)fl + 1;
 }
 
 struct SpreadArgs {
@@ -177,7 +178,7 @@ __device__ __forceinline__ float fixed_scale(float sum_abs, float max_abs)
 // 32-bit shared-memory atomics, which are exact and order-independent.  Each
 // lane walks its (qz, qy) rows starting at a lane-dependent offset, so lanes
 // whose points share a cell (clustered data) hit different addresses.
-template <int D, int M, int NV>
+template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -223,10 +224,10 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
     }
     __syncthreads();
 
-    constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
+    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
     // full unrolling only for the small windows the throughput cases use
-    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
-    constexpr int UY = (M <= 4) ? ny : 1;
+    constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
+    constexpr int UY = (W <= 8) ? ny : 1;
     const int ry = (D == 2) ? lane % ny : (D == 3 ? (lane / nz) % ny : 0);
     const int rz = (D == 3) ? lane % nz : 0;
     const float *coords = static_cast<const float *>(a.coords);
@@ -238,11 +239,11 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
 #pragma unroll
         for (int c = 0; c < NV; ++c)
             u[c] = (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c];
-        float wx[2 * M], wy[2 * M], wz[2 * M];
+        float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
-        o[0] = window_row<M>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
-        if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
-        if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
+        if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
+        if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
         // rotated copies: row q of this lane is row (q + r) mod n of the point
         float wyr[ny], wzr[nz];
 #pragma unroll
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
                 const float wyz = wzr[qz0] * wyr[qy0];
                 int *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
 #pragma unroll
-                for (int qx = 0; qx < 2 * M; ++qx) {
+                for (int qx = 0; qx < W; ++qx) {
                     const float wt = wyz * wx[qx];
 #pragma unroll
                     for (int c = 0; c < NV; ++c) atomicAdd(row + c * tc + qx, fixed_round(u[c] * wt));
@@ -311,7 +312,7 @@ constexpr int kF64MaxWarps = 8;
 // items are (qx, qy) pairs; each walks qz in chunks whose tile values are
 // loaded before the DFMAs (one per tap) and stored after, so the chunk's
 // read-modify-writes overlap.  The warps' tiles are summed in a fixed order.
-template <int D, int M, int NV>
+template <int D, int W, int NV>
 __global__ void __launch_bounds__(32 * kF64MaxWarps) k_spread_f64(const SpreadArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -335,7 +336,6 @@ __global__ void __launch_bounds__(32 * kF64MaxWarps) k_spread_f64(const SpreadAr
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *tile = tiles + (int64_t)warp * tc * NV;
-    constexpr int W = 2 * M;
     constexpr int NW = D * W;                       // weights per point
     constexpr int ITEMS = (D >= 2) ? W * W : W;     // (qx, qy) pairs or qx
     constexpr int SLOTS = (ITEMS + 31) / 32;
@@ -590,7 +590,7 @@ __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int 
 }
 
 // FP32 form: one thread per point.
-template <int D, int M, int NV>
+template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -604,15 +604,15 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
     load_interp_tile<float, NV>(a, D, bc, tc, tile);
     __syncthreads();
     const float *coords = static_cast<const float *>(a.coords);
-    constexpr int ny = (D >= 2) ? 2 * M : 1, nz = (D >= 3) ? 2 * M : 1;
-    constexpr int UY = (M <= 4) ? ny : 1;       // unroll the rows of small windows
-    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
+    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int UY = (W <= 8) ? ny : 1;       // unroll the rows of small windows
+    constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
-        float wx[2 * M], wy[2 * M], wz[2 * M];
+        float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
-        o[0] = window_row<M>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
-        if (D >= 2) o[1] = window_row<M>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
-        if (D >= 3) o[2] = window_row<M>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
+        if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
+        if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
         float acc[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 #pragma unroll
                 for (int c = 0; c < NV; ++c) r[c] = 0.0f;
 #pragma unroll
-                for (int qx = 0; qx < 2 * M; ++qx)
+                for (int qx = 0; qx < W; ++qx)
 #pragma unroll
                     for (int c = 0; c < NV; ++c) r[c] = fmaf(wx[qx], row[c * tc + qx], r[c]);
                 const float wyq = (D >= 2) ? wy[qy] : 1.0f;
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 // FP64 form: one thread per point, FP64 weights from the plan's table and
 // packed first taps; rows are summed with FP64 FMAs (no warp reduction, so
 // nearly every FP64 instruction is a tap).
-template <int D, int M, int NV>
+template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_interp_f64(const InterpArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -660,11 +660,10 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpArgs a)
     bin_coords<D>(bin, a.nb0, a.nb1, bc);
     load_interp_tile<double, NV>(a, D, bc, tc, tile);
     __syncthreads();
-    constexpr int W = 2 * M;
     constexpr int NW = D * W;
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
-    constexpr int UY = (M <= 4) ? ny : 1;
-    constexpr int UZ = (NV == 1 && M <= 4) ? nz : 1;
+    constexpr int UY = (W <= 8) ? ny : 1;
+    constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
         const double *wp = a.wts + (int64_t)i * NW;
         double wx[W], wy[W], wz[W];

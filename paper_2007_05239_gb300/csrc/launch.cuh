@@ -20,7 +20,7 @@ static ml_status set_smem(K kernel, size_t bytes)
     return ML_OK;
 }
 
-template <typename T, int D, int M, int NV>
+template <typename T, int D, int W, int NV>
 static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                               cudaStream_t st)
 {
@@ -46,7 +46,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.Pt = g.Pt;
     sa.nb0 = g.nb[0];
     sa.nb1 = g.nb[1];
-    sa.m2d = (double)M * M;
+    sa.m2d = 0.25 * (double)W * (double)W;   // (W/2)^2
     sa.bd = p->kb_shape;
     sa.normd = p->kb_norm;
     sa.m2f = (float)sa.m2d;
@@ -57,13 +57,13 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         ProfScope pr("spread", st);
         if (f32) {
             const size_t smem = (size_t)tc * nv * sizeof(int);
-            ML_TRY(set_smem(k_spread_f32<D, M, NV>, smem));
-            k_spread_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(sa);
+            ML_TRY(set_smem(k_spread_f32<D, W, NV>, smem));
+            k_spread_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
             const size_t smem = (size_t)tc * nv * sizeof(double) * p->f64_warps +
                                 (size_t)p->sub_max * (nv * sizeof(double) + sizeof(int));
-            ML_TRY(set_smem(k_spread_f64<D, M, NV>, smem));
-            k_spread_f64<D, M, NV><<<p->nsub, 32 * p->f64_warps, smem, st>>>(sa);
+            ML_TRY(set_smem(k_spread_f64<D, W, NV>, smem));
+            k_spread_f64<D, W, NV><<<p->nsub, 32 * p->f64_warps, smem, st>>>(sa);
         }
         ML_CUDA(cudaGetLastError());
     }
@@ -168,11 +168,11 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         const size_t smem = (size_t)tc * nv * sizeof(T);
         ProfScope pr("interp", st);
         if (f32) {
-            ML_TRY(set_smem(k_interp_f32<D, M, NV>, smem));
-            k_interp_f32<D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
+            ML_TRY(set_smem(k_interp_f32<D, W, NV>, smem));
+            k_interp_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(ia);
         } else {
-            ML_TRY(set_smem(k_interp_f64<D, M, NV>, smem));
-            k_interp_f64<D, M, NV><<<p->nsub, 256, smem, st>>>(ia);
+            ML_TRY(set_smem(k_interp_f64<D, W, NV>, smem));
+            k_interp_f64<D, W, NV><<<p->nsub, 256, smem, st>>>(ia);
         }
         ML_CUDA(cudaGetLastError());
     }
@@ -180,45 +180,48 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
 }
 
 // Vector passes use NV = 1, 4 or 8 vectors; the wide passes exist for the
-// small windows (M <= 4) where they matter for throughput.
-template <typename T, int D, int M>
+// small windows (W <= 8) where they matter for throughput.
+template <typename T, int D, int W>
 static ml_status run_layer_dmv(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                                cudaStream_t st)
 {
-    if constexpr (M <= 4) {
-        if (v.nv == 8) return run_layer_dm<T, D, M, 8>(p, v, o, w, st);
-        if (v.nv == 4) return run_layer_dm<T, D, M, 4>(p, v, o, w, st);
+    if constexpr (W <= 8) {
+        if (v.nv == 8) return run_layer_dm<T, D, W, 8>(p, v, o, w, st);
+        if (v.nv == 4) return run_layer_dm<T, D, W, 4>(p, v, o, w, st);
     }
-    if (v.nv == 1) return run_layer_dm<T, D, M, 1>(p, v, o, w, st);
+    if (v.nv == 1) return run_layer_dm<T, D, W, 1>(p, v, o, w, st);
     return fail(ML_ERR_ARG, "unsupported vectors per pass");
 }
 
-// One layer pass for a given dimension and window half-width (instantiated
-// per translation unit; the d = 3 instances are split over several files to
-// keep each compile short).
-template <typename T, int D, int M>
-ml_status run_layer_m(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st)
+// One layer pass for a given dimension and window width W (taps per
+// dimension), instantiated per translation unit; the d = 3 instances are
+// split over several files to keep each compile short.
+template <typename T, int D, int W>
+ml_status run_layer_w(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st)
 {
-    return run_layer_dmv<T, D, M>(p, v, o, w, st);
+    return run_layer_dmv<T, D, W>(p, v, o, w, st);
 }
 
-#define ML_DECL_LAYER_M(T, D, M)                                                                       \
-    extern template ml_status run_layer_m<T, D, M>(ml_plan_s *, const ApplyVec &, const ApplyOpts &, \
+#define ML_DECL_LAYER_W(T, D, W)                                                                       \
+    extern template ml_status run_layer_w<T, D, W>(ml_plan_s *, const ApplyVec &, const ApplyOpts &, \
                                                    const LayerWork &, cudaStream_t);
 
+// window widths with kernels: 4..8 and the even widths up to 16
 template <typename T, int D>
 static ml_status run_layer_d(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                              cudaStream_t st)
 {
-    switch (p->m) {
-    case 2: return run_layer_m<T, D, 2>(p, v, o, w, st);
-    case 3: return run_layer_m<T, D, 3>(p, v, o, w, st);
-    case 4: return run_layer_m<T, D, 4>(p, v, o, w, st);
-    case 5: return run_layer_m<T, D, 5>(p, v, o, w, st);
-    case 6: return run_layer_m<T, D, 6>(p, v, o, w, st);
-    case 7: return run_layer_m<T, D, 7>(p, v, o, w, st);
-    case 8: return run_layer_m<T, D, 8>(p, v, o, w, st);
-    default: return fail(ML_ERR_ARG, "window half-width out of range");
+    switch (p->W) {
+    case 4: return run_layer_w<T, D, 4>(p, v, o, w, st);
+    case 5: return run_layer_w<T, D, 5>(p, v, o, w, st);
+    case 6: return run_layer_w<T, D, 6>(p, v, o, w, st);
+    case 7: return run_layer_w<T, D, 7>(p, v, o, w, st);
+    case 8: return run_layer_w<T, D, 8>(p, v, o, w, st);
+    case 10: return run_layer_w<T, D, 10>(p, v, o, w, st);
+    case 12: return run_layer_w<T, D, 12>(p, v, o, w, st);
+    case 14: return run_layer_w<T, D, 14>(p, v, o, w, st);
+    case 16: return run_layer_w<T, D, 16>(p, v, o, w, st);
+    default: return fail(ML_ERR_ARG, "window width out of range");
     }
 }
 

@@ -48,12 +48,12 @@ struct DevBuf {
 // ------------------------------------------------------------------ plan
 struct GridGeom {
     int d = 1;
-    int m = 2;          // half-width: taps f0 .. f0+2m-1 per dim
+    int W = 4;          // window width: taps f0 .. f0+W-1 per dim
     int B = 8;          // bin edge (cells)
-    int Pt = 0;         // padded tile edge = B + 2m - 1
+    int Pt = 0;         // padded tile edge = B + W (first tap offset in [0, B])
     int L[3] = {1, 1, 1};
     int nb[3] = {1, 1, 1};
-    int R = 1;          // neighbour bins reaching into a bin per dim = ceil((2m-1)/B)
+    int R = 1;          // neighbour bins reaching into a bin per dim = 1 + (W-1)/B
     int K = 0;          // coefficient slots per dim = N + 1
     int64_t cells() const { return (int64_t)L[0] * L[1] * L[2]; }
     int64_t nbins() const { return (int64_t)nb[0] * nb[1] * nb[2]; }
@@ -73,7 +73,8 @@ struct ml_plan_s {
     int64_t n = 0;
     int d = 0;
     int N = 0;
-    int m = 0;
+    int m = 0;             // window half-width, W/2 rounded down (paper's m_NFFT)
+    int W = 0;             // window width in taps per dimension (half-width W/2)
     int n_os = 0;
     ml_prec prec = ML_F64;
     int domain = 0;
@@ -83,7 +84,7 @@ struct ml_plan_s {
     double center[3] = {0, 0, 0};
     double target = 0;
     double kb_shape = 0;   // b = pi (2 - 1/sigma_os)
-    double kb_norm = 0;    // m / (1 - exp(-2 b m)) * exp(-b m): phi_n(t) = norm * 2 sinh(b s)/s
+    double kb_norm = 0;    // h e^{-b h} / (1 - e^{-2 b h}), h = W/2: phi_n(t) = norm (e^{bs} - e^{-bs})/s
     int s0[3] = {0, 0, 0}; // torus index of active-grid cell 0 per dim
     ml::GridGeom g;
     int vp = 1;            // vectors per pass
@@ -128,7 +129,7 @@ namespace ml {
 double bessel_i0(double x);
 // Fourier coefficients phi_hat_n(k), k = 0..kmax, of the normalised window
 // phi_n(t) = sinh(b sqrt(m^2 - t^2)) / sqrt(m^2 - t^2) / (sinh(b m)/m).
-void window_fourier(int n_os, int m, double b, int kmax, std::vector<double> &out);
+void window_fourier(int n_os, double h, double b, int kmax, std::vector<double> &out);
 // b_l, l = 0..N/2 per dim, for the box domain (separable) or the ball domain.
 void kernel_fourier(double sigma_s, int N, int d, double eps_B, int p_reg, std::vector<double> &bhat);
 // the two-point Taylor regulariser's monomial coefficients in t = (r - r_I)/eps_B

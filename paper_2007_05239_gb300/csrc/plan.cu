@@ -115,11 +115,11 @@ __global__ void k_maxrad(const double *__restrict__ X, int64_t n, int d, double 
 struct TorusMap {
     double c[3];
     double s;      // scale into the Alg. 1 domain
-    int n_os, m, d;
+    int n_os, W, d;
 };
 
-// U_a = n_os (s (x_a - c_a) + 1/2): torus grid coordinate; F_a = floor(U_a) - m + 1
-// is the first tap.  Per-block min/max of F_a.
+// U_a = n_os (s (x_a - c_a) + 1/2): torus grid coordinate; F_a = floor(U_a - W/2) + 1
+// is the first of the W taps.  Per-block min/max of F_a.
 __global__ void k_first_tap_range(const double *__restrict__ X, int64_t n, TorusMap tm, long long *part)
 {
     __shared__ long long smin[3][256], smax[3][256];
@@ -127,7 +127,7 @@ __global__ void k_first_tap_range(const double *__restrict__ X, int64_t n, Torus
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         for (int a = 0; a < tm.d; ++a) {
             const double U = tm.n_os * (tm.s * (X[i * tm.d + a] - tm.c[a]) + 0.5);
-            const long long F = (long long)floor(U) - tm.m + 1;
+            const long long F = (long long)floor(U - 0.5 * tm.W) + 1;
             lo[a] = min(lo[a], F);
             hi[a] = max(hi[a], F);
         }
@@ -166,7 +166,7 @@ __global__ void k_keys(const double *__restrict__ X, int64_t n, KeyArgs ka, doub
         for (int a = 0; a < ka.tm.d; ++a) {
             const double U = ka.tm.n_os * (ka.tm.s * (X[i * ka.tm.d + a] - ka.tm.c[a]) + 0.5);
             const double u = U - ka.s0[a];                        // local active-grid coordinate
-            const long long f0 = (long long)floor(u) - ka.tm.m + 1; // >= 0 by construction of s0
+            const long long f0 = (long long)floor(u - 0.5 * ka.tm.W) + 1;  // >= 0 by construction of s0
             const int b = (int)(f0 / ka.B);
             bcoord[a] = b;
             urel[i * ka.tm.d + a] = u - (double)b * ka.B;
@@ -191,28 +191,28 @@ __global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, int *c
         atomicAdd(&counts[keys[i]], 1);
 }
 
-// FP64 window weights of every point (plan time): wts[i][a][q] = phi_n(frac(u_a) + M - 1 - q)
-__global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n, int d, int m, double m2, double b,
+// FP64 window weights of every point (plan time): wts[i][a][q] = phi_n(x - o - q),
+// o = floor(x - W/2) + 1 the first tap
+__global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n, int d, int W, double h2, double b,
                                    double norm2, double *wts)
 {
-    const int W = 2 * m;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d * W;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(e % W);
         const int64_t ia = e / W;   // point * d + dim
         const double x = coords[ia];
-        const double fr = x - floor(x);
-        wts[e] = kb_weight(fr + (double)(m - 1 - q), m2, b, norm2);
+        const double fl = floor(x - 0.5 * W);
+        wts[e] = kb_weight(x - fl - 1.0 - (double)q, h2, b, norm2);
     }
 }
 
 
-// packed first tap of every point: o_a = floor(u_a) - m + 1 in [0, B]
-__global__ void k_first_taps(const double *__restrict__ coords, int64_t n, int d, int m, int *offs)
+// packed first tap of every point: o_a = floor(u_a - W/2) + 1 in [0, B]
+__global__ void k_first_taps(const double *__restrict__ coords, int64_t n, int d, int W, int *offs)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int packed = 0;
-        for (int a = 0; a < d; ++a) packed |= ((int)floor(coords[i * d + a]) - m + 1) << (10 * a);
+        for (int a = 0; a < d; ++a) packed |= ((int)floor(coords[i * d + a] - 0.5 * W) + 1) << (10 * a);
         offs[i] = packed;
     }
 }
@@ -359,15 +359,33 @@ static int grid_for(int64_t n, int threads = 256)
 }
 
 // ---------------------------------------------------------- parameters
-static int auto_m(double target)
+// Window width W and oversampling sigma_os for a target error.  The
+// Kaiser-Bessel window's error falls like exp(-pi W sqrt(1 - 1/sigma_os));
+// measured worst cases (coincident or tightly clustered points, where the
+// window errors add up coherently; sigma_os = 2: W = 5 -> 1.4e-4, W = 7 ->
+// 1.2e-6) fit 9 exp(-pi W sqrt(1 - 1/sigma_os)).  Take the narrowest
+// available width that reaches target/2 at sigma_os <= 3, then the smallest
+// oversampling in {2, 2.5, 3} that reaches it with that width: the taps (W^d
+// per point) dominate the cost, the grid grows only with sigma_os^d.
+static double window_error(int W, double sig_os) { return 9.0 * std::exp(-M_PI * W * std::sqrt(1.0 - 1.0 / sig_os)); }
+
+static void auto_window(double target, int *W_out, double *sig_out)
 {
-    if (target >= 1e-3) return 2;
-    if (target >= 1e-5) return 3;
-    if (target >= 1e-7) return 4;
-    if (target >= 1e-9) return 5;
-    if (target >= 1e-11) return 6;
-    if (target >= 1e-13) return 7;
-    return 8;
+    static const int widths[] = {4, 5, 6, 7, 8, 10, 12, 14, 16};
+    int W = 16;
+    for (int w : widths)
+        if (window_error(w, 3.0) <= 0.5 * target) {
+            W = w;
+            break;
+        }
+    double sig = 3.0;
+    for (double s : {2.0, 2.5, 3.0})
+        if (window_error(W, s) <= 0.5 * target) {
+            sig = s;
+            break;
+        }
+    *W_out = W;
+    *sig_out = sig;
 }
 
 static int auto_N(double sigma_s, double target)
@@ -378,15 +396,15 @@ static int auto_N(double sigma_s, double target)
 }
 
 // FP64 form: bin edge and warps per CTA.  Every warp owns a padded tile of
-// (B + 2m)^d doubles; the tiles plus the staged subproblem inputs (12 KB)
+// (B + W)^d doubles; the tiles plus the staged subproblem inputs (12 KB)
 // must fit 200 KB.  Prefer 8 warps as long as the bin keeps an edge >= 4.
-static void choose_f64_layout(int d, int m, int *B, int *nw)
+static void choose_f64_layout(int d, int W, int *B, int *nw)
 {
     const double budget = 188.0 * 1024.0;
     for (int w : {8, 4, 2, 1}) {
         const double cells = budget / (8.0 * w);
         const int Pt = (int)std::floor(std::pow(cells, 1.0 / d) + 1e-9);
-        int b = Pt - 2 * m;
+        int b = Pt - W;
         if (d == 1) b = std::min(b, 512);
         if (b >= 4 || (w == 1 && b >= 1)) {
             *B = b;
@@ -398,9 +416,9 @@ static void choose_f64_layout(int d, int m, int *B, int *nw)
     *nw = 1;
 }
 
-// FP32 form: the largest B whose padded tile (B + 2m)^d of 8-byte cells stays
+// FP32 form: the largest B whose padded tile (B + W)^d of 8-byte cells stays
 // within 48 KB per vector
-static int choose_bin(int d, int m)
+static int choose_bin(int d, int W)
 {
     const int budget = 48 * 1024 / 8;
     int Pt = 1;
@@ -411,7 +429,7 @@ static int choose_bin(int d, int m)
         ++Pt;
         if (Pt >= 1024) break;
     }
-    int B = Pt - 2 * m;
+    int B = Pt - W;
     if (d == 1) B = std::min(B, 512);
     return std::max(B, 1);
 }
@@ -504,22 +522,23 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     p->sigma_s = p->scale * p->sigma;
     // ---- parameters
     if (p->N == 0) p->N = auto_N(p->sigma_s, p->target);
-    if (p->m == 0) p->m = auto_m(p->target);
+    double sig_os = 2.0;
+    if (p->W == 0) auto_window(p->target, &p->W, &sig_os);
+    p->m = p->W / 2;
     if (p->N > kMaxN)
         return fail(ML_ERR_DOMAIN, "bandwidth N=" + std::to_string(p->N) + " needed for the target exceeds the limit");
-    p->n_os = 2 * p->N;
-    const double sig_os = (double)p->n_os / p->N;
-    p->kb_shape = M_PI * (2.0 - 1.0 / sig_os);
+    p->n_os = 2 * (int)std::ceil(0.5 * sig_os * p->N);   // even torus size
+    p->kb_shape = M_PI * (2.0 - (double)p->N / p->n_os);  // b = pi (2 - 1/sigma_os)
     {
-        const double b = p->kb_shape, m = p->m;
-        p->kb_norm = m * std::exp(-b * m) / (1.0 - std::exp(-2.0 * b * m));
+        const double b = p->kb_shape, h = 0.5 * p->W;
+        p->kb_norm = h * std::exp(-b * h) / (1.0 - std::exp(-2.0 * b * h));
     }
     // ---- active grid
     TorusMap tm;
     for (int a = 0; a < 3; ++a) tm.c[a] = p->center[a];
     tm.s = p->scale;
     tm.n_os = p->n_os;
-    tm.m = p->m;
+    tm.W = p->W;
     tm.d = d;
     DevBuf lpart;
     ML_TRY(lpart.ensure((size_t)nblk * 6 * sizeof(long long)));
@@ -532,7 +551,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_CUDA(cudaStreamSynchronize(st));
     GridGeom &g = p->g;
     g.d = d;
-    g.m = p->m;
+    g.W = p->W;
     g.K = p->N + 1;
     for (int a = 0; a < 3; ++a) {
         g.L[a] = 1;
@@ -547,15 +566,15 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         p->s0[a] = (int)fmin;
         // +1: an FP32 coordinate just below an integer may round up, moving
         // its first tap one cell to the right
-        g.L[a] = (int)(fmax - fmin) + 2 * p->m + 1;
+        g.L[a] = (int)(fmax - fmin) + p->W + 1;
     }
     if (p->prec == ML_F32) {
-        g.B = choose_bin(d, p->m);
+        g.B = choose_bin(d, p->W);
     } else {
-        choose_f64_layout(d, p->m, &g.B, &p->f64_warps);
+        choose_f64_layout(d, p->W, &g.B, &p->f64_warps);
     }
-    g.Pt = g.B + 2 * p->m;              // first tap offset in [0, B], 2m taps
-    g.R = 1 + (2 * p->m - 1) / g.B;     // bins below that reach into a bin
+    g.Pt = g.B + p->W;                  // first tap offset in [0, B], W taps
+    g.R = 1 + (p->W - 1) / g.B;         // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
     {
         // FP32: one shared tile per CTA; FP64: one tile per warp plus the
@@ -615,12 +634,12 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_CUDA(cudaGetLastError());
     if (p->prec == ML_F64) {
         // FP64 window weights, once per plan
-        ML_TRY(p->wts.ensure((size_t)n * d * 2 * p->m * sizeof(double)));
+        ML_TRY(p->wts.ensure((size_t)n * d * p->W * sizeof(double)));
         ProfScope pr_("plan", st);
-        k_window_table_f64<<<grid_for(n * d * 2 * p->m), 256, 0, st>>>(
-            p->coords.as<double>(), n, d, p->m, (double)p->m * p->m, p->kb_shape, p->kb_norm, p->wts.as<double>());
+        k_window_table_f64<<<grid_for(n * d * p->W), 256, 0, st>>>(
+            p->coords.as<double>(), n, d, p->W, 0.25 * p->W * p->W, p->kb_shape, p->kb_norm, p->wts.as<double>());
         ML_TRY(p->offs.ensure((size_t)n * sizeof(int)));
-        k_first_taps<<<grid_for(n), 256, 0, st>>>(p->coords.as<double>(), n, d, p->m, p->offs.as<int>());
+        k_first_taps<<<grid_for(n), 256, 0, st>>>(p->coords.as<double>(), n, d, p->W, p->offs.as<int>());
         ML_CUDA(cudaGetLastError());
     }
     // ---- bins -> subproblems
@@ -681,7 +700,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     idx.release();
     idx2.release();
     // ---- Fourier tables (host FP64) -> device
-    window_fourier(p->n_os, p->m, p->kb_shape, p->N / 2, p->phihat);
+    window_fourier(p->n_os, 0.5 * p->W, p->kb_shape, p->N / 2, p->phihat);
     kernel_fourier(p->sigma_s, p->N, d, p->eps_B, p->p_reg, p->bhat);
     slot_multiplier(p->N, d, p->n_os, p->bhat, p->phihat, p->mult);
     for (int a = 0; a < d; ++a) {
@@ -778,6 +797,7 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
     p->sigma = sigma;
     p->N = N;
     p->m = m;
+    p->W = 2 * m;   // 0 = automatic
     p->eps_B = eps_B;
     p->p_reg = eps_B > 0 ? p_reg : 0;
     p->prec = prec;
@@ -808,6 +828,7 @@ ml_status ml_plan_get_info(ml_plan_t p, ml_plan_info *info)
     info->d = p->d;
     info->N = p->N;
     info->m = p->m;
+    info->taps = p->W;
     info->n_os = p->n_os;
     for (int a = 0; a < 3; ++a) {
         info->L[a] = p->g.L[a];

@@ -185,7 +185,7 @@ def test_two_points_closed_form():
     sigma = 0.1
     w = np.exp(-0.25)
     got, _ = W_gpu(X, sigma, np.array([2.0, -3.0]), "f64")
-    assert np.allclose(got, [-3 * w, 2 * w], rtol=1e-6)
+    assert rel2(got, [-3 * w, 2 * w]) <= 1e-6
 
 
 def test_identical_points():
