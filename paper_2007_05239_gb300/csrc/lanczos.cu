@@ -449,6 +449,9 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
     ML_TRY(Sd.ensure((size_t)ncv * ncv * 8));
     double *Q = Qb.as<double>(), *w = wv.as<double>();
     InverseOp inv{layers, T, std::log(2.0), n, &ws};
+    // inner solves two orders below the outer residual tolerance (the outer
+    // operator is then exact to well within what the Ritz test resolves)
+    inv.inner_tol = std::max(1e-12, 1e-2 * tol);
     if (pw < 0) ML_TRY(inv.init());
     auto op = [&](const double *x, double *y) -> ml_status {
         if (pw > 0) return apply_device(layers, T, x, 1, y, ML_NORMALIZED_A, st);

@@ -34,7 +34,7 @@ constexpr int kMaxVec = 8;       // vectors per spreading/interpolation pass
 constexpr int kMaxM = 8;         // window half-width limit
 constexpr int kMaxN = 512;       // bandwidth limit
 constexpr int kSubPoints = 1024; // points per subproblem (bounds per-cell counts)
-constexpr int kGroupSubs = 16;   // subproblem tiles summed per group before the fold
+constexpr int kGroupSubs = 64;   // most subproblem tiles summed per group before the fold
 
 // ------------------------------------------------------------ device buffer
 struct DevBuf {

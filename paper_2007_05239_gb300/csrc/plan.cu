@@ -573,6 +573,12 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     } else {
         choose_f64_layout(d, p->W, &g.B, &p->f64_warps);
     }
+    {
+        // a grid that fits in one bin: shrink the bin so the tile is the grid
+        int Lmax = 1;
+        for (int a = 0; a < d; ++a) Lmax = std::max(Lmax, g.L[a]);
+        if (g.B + p->W > Lmax) g.B = std::max(1, Lmax - p->W);
+    }
     g.Pt = g.B + p->W;                  // first tap offset in [0, B], W taps
     g.R = 1 + (p->W - 1) / g.B;         // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
@@ -681,11 +687,15 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_CUDA(cudaMemcpy(p->sub_start.p, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice));
     ML_CUDA(cudaMemcpy(p->sub_count.p, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice));
     ML_CUDA(cudaMemcpy(p->bin_sub.p, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice));
-    // groups of <= kGroupSubs consecutive subproblems of one bin
+    // groups of consecutive subproblems of one bin: a bin with S subproblems
+    // gets groups of ceil(sqrt(S)) (at most kGroupSubs), so that the group sums
+    // and the fold that follows both read about sqrt(S) tiles per cell
     std::vector<int> gs, bg(nbins + 1);
     for (int64_t b = 0; b < nbins; ++b) {
         bg[b] = (int)gs.size();
-        for (int s = bs[b]; s < bs[b + 1]; s += kGroupSubs) gs.push_back(s);
+        const int S = bs[b + 1] - bs[b];
+        const int G = std::max(1, std::min(kGroupSubs, (int)std::ceil(std::sqrt((double)S))));
+        for (int s = bs[b]; s < bs[b + 1]; s += G) gs.push_back(s);
     }
     bg[nbins] = (int)gs.size();
     p->ngroups = (int)gs.size();
