@@ -20,4 +20,22 @@ template ml_status run_layer_w<float, 1, 14>(ml_plan_s *, const ApplyVec &, cons
                                               const LayerWork &, cudaStream_t);
 template ml_status run_layer_w<float, 1, 16>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
                                               const LayerWork &, cudaStream_t);
+template ml_status run_batch_w<1, 4>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 5>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 6>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 7>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 8>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 10>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 12>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 14>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<1, 16>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
 }  // namespace ml

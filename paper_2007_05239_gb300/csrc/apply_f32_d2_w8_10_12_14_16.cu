@@ -12,4 +12,14 @@ template ml_status run_layer_w<float, 2, 14>(ml_plan_s *, const ApplyVec &, cons
                                               const LayerWork &, cudaStream_t);
 template ml_status run_layer_w<float, 2, 16>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
                                               const LayerWork &, cudaStream_t);
+template ml_status run_batch_w<2, 8>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<2, 10>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<2, 12>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<2, 14>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<2, 16>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
 }  // namespace ml

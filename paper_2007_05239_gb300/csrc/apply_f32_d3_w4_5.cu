@@ -6,4 +6,8 @@ template ml_status run_layer_w<float, 3, 4>(ml_plan_s *, const ApplyVec &, const
                                               const LayerWork &, cudaStream_t);
 template ml_status run_layer_w<float, 3, 5>(ml_plan_s *, const ApplyVec &, const ApplyOpts &,
                                               const LayerWork &, cudaStream_t);
+template ml_status run_batch_w<3, 4>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
+template ml_status run_batch_w<3, 5>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &,
+                                         cudaStream_t);
 }  // namespace ml

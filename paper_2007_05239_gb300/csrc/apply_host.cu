@@ -19,6 +19,32 @@ ML_DECL_LAYER(f32, 3)
 ML_DECL_LAYER(f64, 1)
 ML_DECL_LAYER(f64, 2)
 ML_DECL_LAYER(f64, 3)
+ml_status run_batch_f32_d1(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+ml_status run_batch_f32_d2(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+ml_status run_batch_f32_d3(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+
+bool batchable(ml_plan_s *const *L, int T)
+{
+    if (T < 2) return false;
+    const ml_plan_s *p0 = L[0];
+    for (int t = 0; t < T; ++t) {
+        const ml_plan_s *p = L[t];
+        if (p->prec != ML_F32 || p->d != p0->d || p->W != p0->W || p->g.nbins() != 1 || p->nsub != p0->nsub)
+            return false;
+        if (p->sub_max > kBatchPtsTotal) return false;
+    }
+    return true;
+}
+
+ml_status run_batch(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    for (int t = 0; t < T; ++t) ML_TRY(ensure_workspace(L[t], v.nv));
+    switch (L[0]->d) {
+    case 1: return run_batch_f32_d1(L, T, v, o, st);
+    case 2: return run_batch_f32_d2(L, T, v, o, st);
+    default: return run_batch_f32_d3(L, T, v, o, st);
+    }
+}
 
 ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st)
 {
@@ -95,6 +121,20 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             k_degree_out<<<blocks, 256, 0, st>>>(layers[t]->deg.as<double>(), layers[t]->perm.as<int>(), n, alpha,
                                                  acc, Yt);
             ML_CUDA(cudaGetLastError());
+        }
+        return ML_OK;
+    }
+    if (!per_layer && batchable(layers, T)) {
+        // every layer's grid is one tile and the points keep their input
+        // order: one launch per stage for all layers, layer sum in registers
+        for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+            nv = 8;
+            for (int t = 0; t < T; ++t) nv = std::min(nv, pass_width(layers[t], b - c0));
+            ApplyVec v{X + c0, b, Y + c0, b, nv};
+            ApplyOpts o;
+            o.normalized = base == ML_NORMALIZED_A;
+            o.alpha = 1.0 / T;
+            ML_TRY(run_batch(layers, T, v, o, st));
         }
         return ML_OK;
     }

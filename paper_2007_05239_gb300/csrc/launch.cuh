@@ -4,6 +4,8 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "kernels.cuh"
 #include "ml_internal.h"
@@ -224,5 +226,204 @@ static ml_status run_layer_d(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o
     default: return fail(ML_ERR_ARG, "window width out of range");
     }
 }
+
+// ------------------------------------------------------------------ batch
+// All layers of a batch (see batchable) in one launch per stage.  The
+// per-layer arguments live in one device blob owned by the first plan and
+// are re-uploaded only when they change.
+template <int D, int W, int NV>
+ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    using T_ = float;
+    std::vector<SpreadArgs> sa(T);
+    std::vector<GroupArgs> ga(T);
+    std::vector<FoldArgs> fa(T);
+    std::vector<AxisArgs> ax((size_t)2 * D * T);
+    std::vector<MultArgs> ma(T);
+    std::vector<InterpArgs> ia(T);
+    int max_nsub = 0, max_ng = 0, max_nbins = 0;
+    int64_t max_tile = 0, max_slots = 0;
+    unsigned max_px[2 * D], max_ky[2 * D];
+    for (int s = 0; s < 2 * D; ++s) max_px[s] = max_ky[s] = 1;
+    for (int t = 0; t < T; ++t) {
+        ml_plan_s *p = L[t];
+        const GridGeom &g = p->g;
+        const int tc = (int)g.tile_cells();
+        const int64_t tile_elems = (int64_t)tc * NV;
+        T_ *scratch = p->scratch.as<T_>();
+        T_ *gtile = scratch + (int64_t)p->nsub * tile_elems;
+        T_ *bufs[2] = {p->work[0].as<T_>(), p->work[1].as<T_>()};
+        SpreadArgs &a = sa[t];
+        a = SpreadArgs{};
+        a.sub_bin = p->sub_bin.as<int>();
+        a.sub_start = p->sub_start.as<int>();
+        a.sub_count = p->sub_count.as<int>();
+        a.perm = p->perm.as<int>();
+        a.coords = p->coords.p;
+        a.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
+        a.X = v.X;
+        a.ldx = v.ldx;
+        a.nv = NV;
+        a.B = g.B;
+        a.Pt = g.Pt;
+        a.nb0 = g.nb[0];
+        a.nb1 = g.nb[1];
+        a.m2d = 0.25 * (double)W * (double)W;
+        a.bd = p->kb_shape;
+        a.normd = p->kb_norm;
+        a.m2f = (float)a.m2d;
+        a.bf = (float)a.bd;
+        a.normf = (float)a.normd;
+        a.scratch = scratch;
+        a.nsub = p->nsub;
+        ga[t] = GroupArgs{scratch, p->grp_sub.as<int>(), tile_elems, gtile, p->ngroups};
+        FoldArgs &f = fa[t];
+        f.nbins = (int)g.nbins();
+        f.bin_sub = p->bin_grp.as<int>();
+        f.scratch = gtile;
+        f.grid = bufs[0];
+        f.nv = NV;
+        f.B = g.B;
+        f.Pt = g.Pt;
+        f.R = g.R;
+        f.nb0 = g.nb[0];
+        f.nb1 = g.nb[1];
+        f.nb2 = g.nb[2];
+        f.L0 = g.L[0];
+        f.L1 = g.L[1];
+        f.L2 = g.L[2];
+        int cur = 0;
+        int64_t Kpow = 1;
+        for (int ad = 0; ad < D; ++ad) {
+            int64_t A = 1;
+            for (int b2 = ad + 1; b2 < D; ++b2) A *= g.L[b2];
+            const int64_t C = Kpow * NV;
+            ax[(size_t)ad * T + t] = AxisArgs{bufs[cur], bufs[cur ^ 1], p->trig_f[ad].p, (int)A, g.L[ad], g.K, (int)C};
+            max_px[ad] = std::max(max_px[ad], (unsigned)((A * C + 63) / 64));
+            max_ky[ad] = std::max(max_ky[ad], (unsigned)((g.K + 31) / 32));
+            cur ^= 1;
+            Kpow *= g.K;
+        }
+        ma[t] = MultArgs{bufs[cur], p->mult_d.p, Kpow};
+        max_slots = std::max(max_slots, Kpow);
+        for (int ad = D - 1; ad >= 0; --ad) {
+            Kpow /= g.K;
+            int64_t A = 1;
+            for (int b2 = ad + 1; b2 < D; ++b2) A *= g.L[b2];
+            const int64_t C = Kpow * NV;
+            const int sidx = 2 * D - 1 - ad;
+            ax[(size_t)sidx * T + t] = AxisArgs{bufs[cur], bufs[cur ^ 1], p->trig_b[ad].p, (int)A, g.K, g.L[ad], (int)C};
+            max_px[sidx] = std::max(max_px[sidx], (unsigned)((A * C + 63) / 64));
+            max_ky[sidx] = std::max(max_ky[sidx], (unsigned)((g.L[ad] + 31) / 32));
+            cur ^= 1;
+        }
+        InterpArgs &ip = ia[t];
+        ip = InterpArgs{};
+        ip.sub_bin = a.sub_bin;
+        ip.sub_start = a.sub_start;
+        ip.sub_count = a.sub_count;
+        ip.perm = a.perm;
+        ip.coords = a.coords;
+        ip.dinv = a.dinv;
+        ip.X = v.X;
+        ip.ldx = v.ldx;
+        ip.Y = v.Y;
+        ip.ldy = v.ldy;
+        ip.nv = NV;
+        ip.B = g.B;
+        ip.Pt = g.Pt;
+        ip.nb0 = g.nb[0];
+        ip.nb1 = g.nb[1];
+        ip.L0 = g.L[0];
+        ip.L1 = g.L[1];
+        ip.L2 = g.L[2];
+        ip.m2f = a.m2f;
+        ip.bf = a.bf;
+        ip.normf = a.normf;
+        ip.m2d = a.m2d;
+        ip.bd = a.bd;
+        ip.normd = a.normd;
+        ip.grid = bufs[cur];
+        ip.alpha = o.alpha;
+        ip.shift = 0.0;
+        ip.self = o.self;
+        ip.normalized = o.normalized;
+        max_nsub = std::max(max_nsub, p->nsub);
+        max_ng = std::max(max_ng, p->ngroups);
+        max_nbins = std::max(max_nbins, (int)g.nbins());
+        max_tile = std::max(max_tile, (int64_t)tc);
+    }
+    // pack and upload
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_sa = 0, o_ga = align(o_sa + sizeof(SpreadArgs) * T), o_fa = align(o_ga + sizeof(GroupArgs) * T),
+                 o_ax = align(o_fa + sizeof(FoldArgs) * T), o_ma = align(o_ax + sizeof(AxisArgs) * ax.size()),
+                 o_ia = align(o_ma + sizeof(MultArgs) * T), total = align(o_ia + sizeof(InterpArgs) * T);
+    std::vector<unsigned char> blob(total, 0);
+    memcpy(blob.data() + o_sa, sa.data(), sizeof(SpreadArgs) * T);
+    memcpy(blob.data() + o_ga, ga.data(), sizeof(GroupArgs) * T);
+    memcpy(blob.data() + o_fa, fa.data(), sizeof(FoldArgs) * T);
+    memcpy(blob.data() + o_ax, ax.data(), sizeof(AxisArgs) * ax.size());
+    memcpy(blob.data() + o_ma, ma.data(), sizeof(MultArgs) * T);
+    memcpy(blob.data() + o_ia, ia.data(), sizeof(InterpArgs) * T);
+    ml_plan_s *p0 = L[0];
+    if (p0->batch_host != blob) {
+        ML_TRY(p0->batch_desc.ensure(total));
+        ML_CUDA(cudaMemcpyAsync(p0->batch_desc.p, blob.data(), total, cudaMemcpyHostToDevice, st));
+        ML_CUDA(cudaStreamSynchronize(st));   // the host blob is reused at once
+        p0->batch_host.swap(blob);
+    }
+    unsigned char *d = p0->batch_desc.as<unsigned char>();
+    {
+        ProfScope pr("spread", st);
+        const size_t smem = (size_t)max_tile * NV * sizeof(int);
+        ML_TRY(set_smem(k_spread_f32_batch<D, W, NV>, smem));
+        k_spread_f32_batch<D, W, NV><<<dim3(max_nsub, T), 256, smem, st>>>(reinterpret_cast<SpreadArgs *>(d + o_sa));
+        ML_CUDA(cudaGetLastError());
+    }
+    {
+        ProfScope pr("group_sum", st);
+        dim3 grid((unsigned)((max_tile * NV + 255) / 256), (unsigned)max_ng, (unsigned)T);
+        k_group_sum_batch<T_><<<grid, 256, 0, st>>>(reinterpret_cast<GroupArgs *>(d + o_ga));
+    }
+    {
+        ProfScope pr("fold", st);
+        k_fold_batch<T_, D><<<dim3(max_nbins, T), 256, 0, st>>>(reinterpret_cast<FoldArgs *>(d + o_fa));
+    }
+    for (int sidx = 0; sidx < 2 * D; ++sidx) {
+        if (sidx == D) {
+            ProfScope pr("mult", st);
+            const int blocks = (int)std::min<int64_t>((max_slots * NV + 255) / 256, 1024);
+            k_mult_batch<T_><<<dim3(blocks, T), 256, 0, st>>>(reinterpret_cast<MultArgs *>(d + o_ma), NV);
+        }
+        ProfScope pr("axis", st);
+        k_axis_batch<T_><<<dim3(max_px[sidx], max_ky[sidx], T), 256, 0, st>>>(
+            reinterpret_cast<AxisArgs *>(d + o_ax) + (size_t)sidx * T);
+    }
+    ML_CUDA(cudaGetLastError());
+    {
+        ProfScope pr("interp", st);
+        const size_t smem = (size_t)max_tile * NV * sizeof(float);
+        ML_TRY(set_smem(k_interp_f32_sum<D, W, NV>, smem));
+        k_interp_f32_sum<D, W, NV><<<max_nsub, 256, smem, st>>>(reinterpret_cast<InterpArgs *>(d + o_ia), T);
+        ML_CUDA(cudaGetLastError());
+    }
+    for (int t = 0; t < T; ++t) L[t]->applied += NV;
+    return ML_OK;
+}
+
+template <int D, int W>
+ml_status run_batch_w(ml_plan_s *const *L, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)
+{
+    if constexpr (W <= 8) {
+        if (v.nv == 8) return run_batch_dm<D, W, 8>(L, T, v, o, st);
+        if (v.nv == 4) return run_batch_dm<D, W, 4>(L, T, v, o, st);
+    }
+    if (v.nv == 1) return run_batch_dm<D, W, 1>(L, T, v, o, st);
+    return fail(ML_ERR_ARG, "unsupported vectors per pass");
+}
+
+#define ML_DECL_BATCH_W(D, W)                                                                             \
+    extern template ml_status run_batch_w<D, W>(ml_plan_s *const *, int, const ApplyVec &, const ApplyOpts &, \
+                                                cudaStream_t);
 
 }  // namespace ml

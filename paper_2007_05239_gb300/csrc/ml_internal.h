@@ -34,6 +34,7 @@ constexpr int kMaxVec = 8;       // vectors per spreading/interpolation pass
 constexpr int kMaxM = 8;         // window half-width limit
 constexpr int kMaxN = 512;       // bandwidth limit
 constexpr int kSubPoints = 1024; // points per subproblem (bounds per-cell counts)
+constexpr int kBatchPtsTotal = 1024; // points per CTA of the batched interpolation (4 per thread)
 constexpr int kGroupSubs = 64;   // most subproblem tiles summed per group before the fold
 
 // ------------------------------------------------------------ device buffer
@@ -120,6 +121,8 @@ struct ml_plan_s {
     ml::DevBuf work[2];   // transform ping-pong buffers
     ml::DevBuf stage_x, stage_y;  // staging for host X / Y
     ml::DevBuf status;    // int flags written by device code
+    ml::DevBuf batch_desc;               // per-layer descriptors of a batched apply led by this plan
+    std::vector<unsigned char> batch_host;  // host copy of the uploaded descriptors
     int64_t device_bytes() const;
 };
 
@@ -206,5 +209,9 @@ void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work);
 ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w, cudaStream_t st);
 // vectors in the next pass for `remaining` vectors
 int pass_width(const ml_plan_s *p, int remaining);
+// whether the layers can run as one batch (FP32, equal d and W, every grid a
+// single tile, identical subproblem split) and the batched pass itself
+bool batchable(ml_plan_s *const *layers, int T);
+ml_status run_batch(ml_plan_s *const *layers, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
 
 }  // namespace ml

@@ -574,12 +574,16 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         choose_f64_layout(d, p->W, &g.B, &p->f64_warps);
     }
     {
-        // a grid that fits in one bin: shrink the bin so the tile is the grid
+        // a grid that fits in one bin: one bin, and a tile the size of the grid
         int Lmax = 1;
         for (int a = 0; a < d; ++a) Lmax = std::max(Lmax, g.L[a]);
-        if (g.B + p->W > Lmax) g.B = std::max(1, Lmax - p->W);
+        if (g.B + p->W > Lmax) {
+            g.B = Lmax;
+            g.Pt = Lmax;                // every tap index is < L <= Pt
+        } else {
+            g.Pt = g.B + p->W;          // first tap offset in [0, B], W taps
+        }
     }
-    g.Pt = g.B + p->W;                  // first tap offset in [0, B], W taps
     g.R = 1 + (p->W - 1) / g.B;         // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
     {
@@ -772,7 +776,7 @@ static void release_all(ml_plan_s *p)
     ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
-                          &p->stage_y, &p->status};
+                          &p->stage_y, &p->status, &p->batch_desc};
     for (auto *b : bufs) b->release();
 }
 

@@ -220,3 +220,25 @@ def test_domain_error_for_unreachable_bandwidth():
     with pytest.raises(ml.MLError) as e:
         ml.ml_fastsum_plan(dev(X), 1e-4, prec="f64")
     assert e.value.status == ml.ML_ERR_DOMAIN
+
+
+@pytest.mark.parametrize("b", [1, 8])
+def test_batched_small_grid_layers(b):
+    # FP32 layers whose grids are single tiles run as one batch (one launch per
+    # stage, layer sum in registers); compare with the oracle and with the
+    # per-layer mode (launched layer by layer) summed on the host.
+    n = 5000
+    layers, _ = workloads.gmm_band_layers(n, 8, 4, seed=15)
+    sig = [0.5 * float((L.max(0) - L.min(0)).max()) for L in layers]
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f32") for L, s in zip(layers, sig)]
+    assert all(p.info["nbins"] == 1 for p in plans)
+    X = np.random.default_rng(16).uniform(0, 1, (n, b))
+    Y = torch.empty(n, b, dtype=torch.float64, device="cuda")
+    ml.ml_fastsum_apply(plans, dev(X), Y, mode="normalized")
+    Y = Y.cpu().numpy()
+    ref = graph.multilayer_A_apply(layers, sig, X)
+    assert rel2(Y, ref) <= 1e-4
+    T = len(layers)
+    Yp = torch.empty(T, n, b, dtype=torch.float64, device="cuda")
+    ml.ml_fastsum_apply(plans, dev(np.broadcast_to(X, (T, n, b))), Yp, mode="normalized", per_layer=True)
+    assert rel2(Y, Yp.cpu().numpy().mean(axis=0)) <= 2e-6
