@@ -184,6 +184,7 @@ def run_reference(args, rank, world):
 
 def metric_name(spec):
     tol = "1e-6" if spec["prec"] == "f64" else "1e-4"
+    tol = f"{spec['target']:.0e}"
     return (f"fast-summation Gpts·vec/s ({spec['prec'].upper()} form, <= {tol} rel err vs FP64) inside the "
             f"k={spec['k']} Lanczos step (p={int(spec['p'])})")
 
@@ -193,6 +194,19 @@ def config_dict(args, spec, n, T):
             "sigma": spec["sigma"], "prec": spec["prec"], "target_rel_err": spec["target"], "k": spec["k"],
             "p": spec["p"], "l2": "inputs exceed L2 (per-layer point data and the Krylov basis are > 129 MB)",
             "parallelism": f"replicas{args.gpus}"}
+
+
+# ------------------------------------------------------------- ranks
+def reduce_over_ranks(ms, work, device="cpu"):
+    """(max time over ranks, total work over ranks); the identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms), float(work)
+    t = torch.tensor([float(ms), float(work)], dtype=torch.float64, device=device)
+    parts = [torch.zeros_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, t)
+    return max(float(p[0]) for p in parts), sum(float(p[1]) for p in parts)
 
 
 # ------------------------------------------------------------- our arm
@@ -211,6 +225,7 @@ def main():
                     help="eig: plan + k eigenpairs per step (default); apply: one multilayer normalised "
                          "product of b vectors per step on plans made before the timed region")
     ap.add_argument("--b", type=int, default=1, help="vectors per product in --mode apply")
+    ap.add_argument("--target", type=float, default=None, help="relative error target (default per precision)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -224,6 +239,8 @@ def main():
         spec["p"] = args.p
     if args.k is not None:
         spec["k"] = args.k
+    if args.target is not None:
+        spec["target"] = args.target
     WORKLOADS[args.workload] = spec
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -293,14 +310,7 @@ def main():
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     prof = ml.ml_profile_read()
-    t_max = ms_total
-    tot_applied = applied
-    if world > 1:
-        tt = torch.tensor([ms_total, float(applied)], dtype=torch.float64, device="cuda")
-        t_all = [torch.zeros_like(tt) for _ in range(world)]
-        dist.all_gather(t_all, tt)
-        t_max = max(float(x[0]) for x in t_all)
-        tot_applied = sum(float(x[1]) for x in t_all)
+    t_max, tot_applied = reduce_over_ranks(ms_total, applied, "cuda")
     value = tot_applied / (t_max / 1e3) / 1e9
     launches = int(sum(v[0] for v in prof.values()))
 
@@ -347,12 +357,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    e2e_val = applied_e2e / (e2e_ms / 1e3) / 1e9
-    if world > 1:
-        tt = torch.tensor([e2e_ms, float(applied_e2e)], dtype=torch.float64, device="cuda")
-        t_all = [torch.zeros_like(tt) for _ in range(world)]
-        dist.all_gather(t_all, tt)
-        e2e_val = sum(float(x[1]) for x in t_all) / (max(float(x[0]) for x in t_all) / 1e3) / 1e9
+    e2e_t, e2e_work = reduce_over_ranks(e2e_ms, applied_e2e, "cuda")
+    e2e_val = e2e_work / (e2e_t / 1e3) / 1e9
 
     line = {
         "metric": metric_name(spec), "value": value, "unit": "Gpts·vec/s", "n_gpus": world, "steps": args.steps,
