@@ -126,6 +126,92 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
                           int N, int m, double eps_B, int p_reg, ml_prec prec,
                           double target_rel_err, void *stream);
 
+/* Explicit parameters for ml_fastsum_plan_ex (0 = automatic choice). */
+typedef struct {
+    int N;               /* bandwidth of K_RF (even, 4..512)                                 */
+    int taps;            /* window width W per dim: 4..8, 10, 12, 14 or 16                   */
+    double oversampling; /* n_os / N in [1.5, 4]; automatic with taps = 0, else 2 when 0    */
+    double eps_B;        /* as ml_fastsum_plan                                               */
+    int p_reg;
+    ml_prec prec;
+    double target_rel_err;
+} ml_plan_params;
+
+/*
+ * ml_fastsum_plan_ex - ml_fastsum_plan with the window width and the
+ * oversampling of the NFFT (Alg. 1 steps 1 and 3) chosen by the caller
+ * (e.g. the learned parameter model below, ml_fastsum_plan_learned).
+ * Same errors as ml_fastsum_plan, plus ML_ERR_ARG for out-of-range entries.
+ */
+ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
+                             const ml_plan_params *params, void *stream);
+
+/*
+ * ml_direct_sum_rows - the exact definition of the product on selected rows:
+ * out[r] = sum_{j != rows[r]} exp(-||x_{rows[r]} - x_j||^2 / sigma^2) v_j
+ * (W v of Sec. 2 / Sec. 4, direct O(nrows n) summation in FP64 on the GPU).
+ * It is the judge of the fast summation's error and the product of the dense
+ * regime for small graphs.
+ *   points  device, n x d FP64;  v device, n FP64;  rows device, nrows int64
+ *   (each in [0, n));  out device, nrows FP64.  Asynchronous on `stream`.
+ */
+ml_status ml_direct_sum_rows(const double *points, int64_t n, int d, double sigma, const double *v,
+                             const int64_t *rows, int64_t nrows, double *out, void *stream);
+
+/*
+ * Point-cloud statistics used by the parameter model (not from the paper):
+ *   [0] log10 n, [1] d, [2] log10(sigma / box) with box the largest bounding-box
+ *   extent, [3..5] the bounding-box extents / box in decreasing order (0 past d),
+ *   [6..8] log10 of the 5 %, 50 %, 95 % quantiles of the nearest-neighbour
+ *   distance / sigma within an evenly strided sample of min(n, 2048) points.
+ * points device n x d FP64; feat host, ML_FEATURES floats.  Synchronises `stream`.
+ */
+#define ML_FEATURES 9
+ml_status ml_cloud_features(const double *points, int64_t n, int d, double sigma, float *feat, void *stream);
+
+/*
+ * Learned parameter model (not from the paper): a small FP32 MLP,
+ * n_in -> hidden (tanh) -> hidden (tanh) -> n_out, with input and output
+ * standardisation, trained and evaluated on the GPU by the library's own
+ * kernels.  Parameters are packed [W1 (h x n_in), b1, W2 (h x h), b2,
+ * W3 (n_out x h), b3], row-major.
+ *   ml_mlp_create        random initialisation (SplitMix64 seed)
+ *   ml_mlp_set_norm      x -> (x - in_mean)/in_std, y = out_mean + out_std * net
+ *   ml_mlp_forward       X host or device (batch x n_in), Y same kind (batch x n_out)
+ *   ml_mlp_loss_grad     mean squared error on standardised targets and its
+ *                        gradient w.r.t. the packed parameters (host outputs)
+ *   ml_mlp_train         `epochs` full-batch Adam steps (lr, beta 0.9/0.999);
+ *                        loss per epoch to `losses` (host, may be NULL)
+ * All return ML_ERR_ARG on size mismatches.
+ */
+typedef struct ml_mlp_s *ml_mlp_t;
+ml_status ml_mlp_create(ml_mlp_t *out, int n_in, int hidden, int n_out, uint64_t seed);
+int64_t ml_mlp_param_count(ml_mlp_t mlp);
+ml_status ml_mlp_get_params(ml_mlp_t mlp, float *params, int64_t count);
+ml_status ml_mlp_set_params(ml_mlp_t mlp, const float *params, int64_t count);
+ml_status ml_mlp_set_norm(ml_mlp_t mlp, const float *in_mean, const float *in_std, const float *out_mean,
+                          const float *out_std);
+ml_status ml_mlp_forward(ml_mlp_t mlp, const float *X, int batch, float *Y);
+ml_status ml_mlp_loss_grad(ml_mlp_t mlp, const float *X, const float *Yt, int batch, float *loss, float *grad);
+ml_status ml_mlp_train(ml_mlp_t mlp, const float *X, const float *Yt, int batch, int epochs, float lr,
+                       float *losses);
+ml_status ml_mlp_destroy(ml_mlp_t mlp);
+
+/*
+ * ml_fastsum_plan_learned - plan with parameters chosen by a trained model
+ * (n_in = ML_FEATURES + 3, n_out = 2: predicted log10 relative error and
+ * log10 product time of a candidate).  Candidates: N = f * N0 for
+ * f in {0.7, 0.85, 1} (N0 the automatic bandwidth for the target),
+ * taps in {4..8}, oversampling in {2, 2.5, 3}; the model input is the cloud's
+ * features followed by (f, taps, oversampling).  The cheapest candidate whose
+ * predicted error is at most target / margin is used; if none qualifies, or
+ * mlp is NULL, the automatic choice of ml_fastsum_plan is used.
+ * `chosen` (host, may be NULL) receives {f, taps, oversampling}.
+ */
+ml_status ml_fastsum_plan_learned(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
+                                  ml_prec prec, double target_rel_err, ml_mlp_t mlp, double margin,
+                                  double *chosen, void *stream);
+
 /*
  * ml_fastsum_apply - Y = multilayer operator applied to X (Alg. 1 per layer,
  * then the D^{-1/2} scaling and the 1/T sum of Eq. I-L_1).

@@ -24,7 +24,10 @@ ML_RAW_W, ML_NORMALIZED_A, ML_DEGREE, ML_PER_LAYER = 0, 1, 2, 16
 MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
-EXPORTS = ["ml_fastsum_plan", "ml_fastsum_apply", "ml_fastsum_apply_noalloc", "ml_lanczos_eigs", "ml_plan_get_info",
+EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_learned", "ml_fastsum_apply",
+           "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
+           "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
+           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read"]
 
@@ -33,6 +36,15 @@ class MLError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
+
+
+ML_FEATURES = 9
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("taps", ctypes.c_int), ("oversampling", ctypes.c_double),
+                ("eps_B", ctypes.c_double), ("p_reg", ctypes.c_int), ("prec", ctypes.c_int),
+                ("target_rel_err", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -85,6 +97,33 @@ def load():
     lib.ml_last_error.argtypes = []
     lib.ml_version.restype = ctypes.c_char_p
     lib.ml_version.argtypes = []
+    lib.ml_fastsum_plan_ex.restype = ctypes.c_int
+    lib.ml_fastsum_plan_ex.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(PlanParams), P]
+    lib.ml_fastsum_plan_learned.restype = ctypes.c_int
+    lib.ml_fastsum_plan_learned.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_double, P, ctypes.c_double, P, P]
+    lib.ml_direct_sum_rows.restype = ctypes.c_int
+    lib.ml_direct_sum_rows.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, P, P, ctypes.c_int64, P, P]
+    lib.ml_cloud_features.restype = ctypes.c_int
+    lib.ml_cloud_features.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, P, P]
+    lib.ml_mlp_create.restype = ctypes.c_int
+    lib.ml_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.ml_mlp_param_count.restype = ctypes.c_int64
+    lib.ml_mlp_param_count.argtypes = [P]
+    for nm in ("ml_mlp_get_params", "ml_mlp_set_params"):
+        getattr(lib, nm).restype = ctypes.c_int
+        getattr(lib, nm).argtypes = [P, P, ctypes.c_int64]
+    lib.ml_mlp_set_norm.restype = ctypes.c_int
+    lib.ml_mlp_set_norm.argtypes = [P, P, P, P, P]
+    lib.ml_mlp_forward.restype = ctypes.c_int
+    lib.ml_mlp_forward.argtypes = [P, P, ctypes.c_int, P]
+    lib.ml_mlp_loss_grad.restype = ctypes.c_int
+    lib.ml_mlp_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P]
+    lib.ml_mlp_train.restype = ctypes.c_int
+    lib.ml_mlp_train.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, P]
+    lib.ml_mlp_destroy.restype = ctypes.c_int
+    lib.ml_mlp_destroy.argtypes = [P]
     lib.ml_profile_enable.restype = ctypes.c_int
     lib.ml_profile_enable.argtypes = [ctypes.c_int]
     lib.ml_profile_reset.restype = ctypes.c_int
@@ -169,6 +208,117 @@ def ml_fastsum_plan(points, sigma, N=0, m=0, eps_B=0.0, p_reg=0, prec="f64", tar
     _check(lib.ml_fastsum_plan(ctypes.byref(h), _ptr(points), n, d, float(sigma), int(N), int(m), float(eps_B),
                                int(p_reg), pr, float(target_rel_err), _stream(stream)))
     return Plan(h.value, n, d)
+
+
+def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
+                       target_rel_err=0.0, stream=None):
+    """Plan one layer with explicit window width / oversampling (0 = automatic)."""
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    prm = PlanParams(int(N), int(taps), float(oversampling), float(eps_B), int(p_reg),
+                     {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec),
+                     float(target_rel_err))
+    h = ctypes.c_void_p()
+    _check(lib.ml_fastsum_plan_ex(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
+                                  _stream(stream)))
+    return Plan(h.value, n, d)
+
+
+def ml_fastsum_plan_learned(points, sigma, model=None, prec="f32", target_rel_err=0.0, margin=2.0, stream=None):
+    """Plan with parameters chosen by a trained Mlp (None: the automatic rule).
+    Returns (plan, chosen) with chosen = (bandwidth factor, taps, oversampling) or zeros."""
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    h = ctypes.c_void_p()
+    ch = np.zeros(3)
+    pr = {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec)
+    _check(lib.ml_fastsum_plan_learned(ctypes.byref(h), _ptr(points), n, d, float(sigma), pr, float(target_rel_err),
+                                       None if model is None else model.handle, float(margin), ch.ctypes.data,
+                                       _stream(stream)))
+    return Plan(h.value, n, d), tuple(ch)
+
+
+def ml_direct_sum_rows(points, sigma, v, rows, out=None, stream=None):
+    """Exact (W v)[rows] on the GPU.  points (n, d), v (n,) float64 CUDA; rows int64 CUDA."""
+    import torch
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    if out is None:
+        out = torch.empty(int(rows.shape[0]), dtype=torch.float64, device=points.device)
+    _check(lib.ml_direct_sum_rows(_ptr(points), n, d, float(sigma), _ptr(v), rows.data_ptr(), int(rows.shape[0]),
+                                  _ptr(out), _stream(stream)))
+    return out
+
+
+def ml_cloud_features(points, sigma, stream=None):
+    lib = load()
+    f = np.zeros(ML_FEATURES, dtype=np.float32)
+    _check(lib.ml_cloud_features(_ptr(points), int(points.shape[0]), int(points.shape[1]), float(sigma),
+                                 f.ctypes.data, _stream(stream)))
+    return f
+
+
+class Mlp:
+    """The library's FP32 MLP (n_in -> h -> h -> n_out, tanh), on the GPU."""
+
+    def __init__(self, n_in, hidden, n_out, seed=0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.ml_mlp_create(ctypes.byref(h), int(n_in), int(hidden), int(n_out), ctypes.c_uint64(seed)))
+        self.handle = h
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+
+    @property
+    def nparam(self):
+        return int(load().ml_mlp_param_count(self.handle))
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        _check(load().ml_mlp_get_params(self.handle, p.ctypes.data, p.size))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().ml_mlp_set_params(self.handle, p.ctypes.data, p.size))
+
+    def set_norm(self, in_mean, in_std, out_mean, out_std):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mean, in_std, out_mean, out_std)]
+        _check(load().ml_mlp_set_norm(self.handle, *[a.ctypes.data for a in arrs]))
+        self._norm = arrs
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((X.shape[0], self.n_out), dtype=np.float32)
+        _check(load().ml_mlp_forward(self.handle, X.ctypes.data, X.shape[0], Y.ctypes.data))
+        return Y
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(self.nparam, dtype=np.float32)
+        _check(load().ml_mlp_loss_grad(self.handle, X.ctypes.data, Y.ctypes.data, X.shape[0], loss.ctypes.data,
+                                       g.ctypes.data))
+        return float(loss[0]), g
+
+    def train(self, X, Y, epochs, lr=1e-3):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        losses = np.empty(epochs, dtype=np.float32)
+        _check(load().ml_mlp_train(self.handle, X.ctypes.data, Y.ctypes.data, X.shape[0], int(epochs), float(lr),
+                                   losses.ctypes.data))
+        return losses
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            load().ml_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def _handles(layers):

@@ -76,6 +76,7 @@ struct ml_plan_s {
     int N = 0;
     int m = 0;             // window half-width, W/2 rounded down (paper's m_NFFT)
     int W = 0;             // window width in taps per dimension (half-width W/2)
+    double sig_os_req = 0; // requested oversampling (0: automatic / 2)
     int n_os = 0;
     ml_prec prec = ML_F64;
     int domain = 0;

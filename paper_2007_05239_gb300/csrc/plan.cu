@@ -352,7 +352,38 @@ __global__ void k_dinv(const double *__restrict__ deg, int64_t n, double *dinv, 
     }
 }
 
-static int grid_for(int64_t n, int threads = 256)
+static int grid_for(int64_t n, int threads = 256);
+
+// bounding box of n x d points (device), synchronises the stream
+ml_status bounding_box(const double *points, int64_t n, int d, cudaStream_t st, double lo[3], double hi[3])
+{
+    const int nblk = grid_for(n);
+    DevBuf part;
+    ML_TRY(part.ensure((size_t)nblk * 6 * sizeof(double)));
+    {
+        ProfScope pr_("plan", st);
+        k_bbox<<<nblk, 256, 0, st>>>(points, n, d, part.as<double>());
+    }
+    ML_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)nblk * 6);
+    ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = 0.0;
+        hi[a] = 0.0;
+    }
+    for (int a = 0; a < d; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+        for (int b = 0; b < nblk; ++b) {
+            lo[a] = std::min(lo[a], hp[b * 6 + 2 * a]);
+            hi[a] = std::max(hi[a], hp[b * 6 + 2 * a + 1]);
+        }
+    }
+    return ML_OK;
+}
+
+static int grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
@@ -388,11 +419,23 @@ static void auto_window(double target, int *W_out, double *sig_out)
     *sig_out = sig;
 }
 
+// automatic bandwidth for a box-domain layer from its largest bounding-box
+// extent (the scaling of the box reading, then auto_N)
+int auto_bandwidth_box(double sigma, double box, int d, double target);
+
 static int auto_N(double sigma_s, double target)
 {
     const double half = std::sqrt(std::log(10.0 / target)) / (M_PI * sigma_s);
     int N = 2 * (int)std::ceil(half);
     return std::max(N, 8);
+}
+
+int auto_bandwidth_box(double sigma, double box, int d, double target)
+{
+    double h = 0.5 * box;
+    if (!(h > 0)) h = sigma;
+    const double aa = std::min(0.25, 1.0 / (2.0 + (sigma / h) * std::sqrt(std::log(2.0 * d / (0.1 * target)))));
+    return auto_N(aa / h * sigma, target);
 }
 
 // FP64 form: bin edge and warps per CTA.  Every warp owns a padded tile of
@@ -522,7 +565,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     p->sigma_s = p->scale * p->sigma;
     // ---- parameters
     if (p->N == 0) p->N = auto_N(p->sigma_s, p->target);
-    double sig_os = 2.0;
+    double sig_os = p->sig_os_req > 0 ? p->sig_os_req : 2.0;
     if (p->W == 0) auto_window(p->target, &p->W, &sig_os);
     p->m = p->W / 2;
     if (p->N > kMaxN)
@@ -786,8 +829,9 @@ const char *ml_last_error(void) { return ml::g_err.c_str(); }
 
 const char *ml_version(void) { return "ml_fastsum 0.1 (sm_103a)"; }
 
-ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int m,
-                          double eps_B, int p_reg, ml_prec prec, double target_rel_err, void *stream)
+static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int W,
+                             double sig_os, double eps_B, int p_reg, ml_prec prec, double target_rel_err,
+                             void *stream)
 {
     using namespace ml;
     if (!out) return fail(ML_ERR_ARG, "out is null");
@@ -797,7 +841,9 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
     if (d < 1 || d > 3) return fail(ML_ERR_ARG, "d must be 1, 2 or 3");
     if (!(sigma > 0) || !std::isfinite(sigma)) return fail(ML_ERR_ARG, "sigma must be positive and finite");
     if (N != 0 && (N < 4 || N > kMaxN || (N & 1))) return fail(ML_ERR_ARG, "N must be 0 or even in [4, 512]");
-    if (m != 0 && (m < 2 || m > kMaxM)) return fail(ML_ERR_ARG, "m must be 0 or in [2, 8]");
+    if (W != 0 && !((W >= 4 && W <= 8) || W == 10 || W == 12 || W == 14 || W == 16))
+        return fail(ML_ERR_ARG, "window width must be 0, 4..8, 10, 12, 14 or 16 taps");
+    if (sig_os != 0 && !(sig_os >= 1.5 && sig_os <= 4.0)) return fail(ML_ERR_ARG, "oversampling must be in [1.5, 4]");
     if (!(eps_B >= 0 && eps_B < 0.5)) return fail(ML_ERR_ARG, "eps_B must be in [0, 1/2)");
     if (eps_B > 0 && (p_reg < 1 || p_reg > 8)) return fail(ML_ERR_ARG, "p_reg must be in [1, 8] when eps_B > 0");
     if (prec != ML_F32 && prec != ML_F64) return fail(ML_ERR_ARG, "prec must be ML_F32 or ML_F64");
@@ -810,8 +856,8 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
     p->d = d;
     p->sigma = sigma;
     p->N = N;
-    p->m = m;
-    p->W = 2 * m;   // 0 = automatic
+    p->W = W;   // 0 = automatic
+    p->sig_os_req = sig_os;
     p->eps_B = eps_B;
     p->p_reg = eps_B > 0 ? p_reg : 0;
     p->prec = prec;
@@ -824,6 +870,21 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
     }
     *out = p;
     return ML_OK;
+}
+
+ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int m,
+                          double eps_B, int p_reg, ml_prec prec, double target_rel_err, void *stream)
+{
+    if (m != 0 && (m < 2 || m > ml::kMaxM)) return ml::fail(ML_ERR_ARG, "m must be 0 or in [2, 8]");
+    return plan_common(out, points, n, d, sigma, N, 2 * m, 0.0, eps_B, p_reg, prec, target_rel_err, stream);
+}
+
+ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
+                             const ml_plan_params *prm, void *stream)
+{
+    if (!prm) return ml::fail(ML_ERR_ARG, "params is null");
+    return plan_common(out, points, n, d, sigma, prm->N, prm->taps, prm->oversampling, prm->eps_B, prm->p_reg,
+                       prm->prec, prm->target_rel_err, stream);
 }
 
 ml_status ml_plan_destroy(ml_plan_t plan)

@@ -217,3 +217,26 @@ def test_ball_domain_scaling():
     # pairwise distances stay below 1/2 - eps_B
     D = np.sqrt(((Xs[:, None] - Xs[None]) ** 2).sum(-1))
     assert D.max() <= 0.5 - 1.0 / 16 + 1e-14
+
+
+# ------------------------------------------------------------------ MLP oracle
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    n_in, h, n_out, B = 5, 7, 2, 11
+    npar = h * n_in + h + h * h + h + n_out * h + n_out
+    p = rng.normal(0, 0.5, npar)
+    X = rng.normal(0, 1, (B, n_in))
+    Y = rng.normal(0, 1, (B, n_out))
+    norm = (rng.normal(0, 1, n_in), rng.uniform(0.5, 2, n_in), rng.normal(0, 1, n_out), rng.uniform(0.5, 2, n_out))
+    loss, g = mlp.loss_grad(p, X, Y, n_in, h, n_out, norm)
+    eps = 1e-6
+    for i in rng.choice(npar, 25, replace=False):
+        e = np.zeros(npar)
+        e[i] = eps
+        fd = (mlp.loss_grad(p + e, X, Y, n_in, h, n_out, norm)[0] -
+              mlp.loss_grad(p - e, X, Y, n_in, h, n_out, norm)[0]) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd))
+    # the loss is the mean squared error of the standardised outputs
+    Z = (mlp.forward(p, X, n_in, h, n_out, norm) - norm[2]) / norm[3]
+    assert abs(loss - np.mean((Z - (Y - norm[2]) / norm[3]) ** 2)) < 1e-14
