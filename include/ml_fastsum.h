@@ -120,7 +120,11 @@ typedef struct {
  *   stream         cudaStream_t used for the set-up kernels.
  * The call synchronises `stream` (it reads bounding boxes and bin counts back
  * to the host).  Errors: ML_ERR_ARG, ML_ERR_DOMAIN (grid beyond limits),
- * ML_ERR_DEGREE (a degree <= 0 or non-finite), ML_ERR_OOM, ML_ERR_CUDA.
+ * ML_ERR_OOM, ML_ERR_CUDA.  A degree <= 0 or non-finite (an isolated point
+ * whose exact degree is below the approximation error) does not fail the
+ * plan: raw products stay available, while normalised products and
+ * ml_lanczos_eigs on that layer return ML_ERR_DEGREE (deg_min in
+ * ml_plan_info shows it).
  */
 ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
                           int N, int m, double eps_B, int p_reg, ml_prec prec,
@@ -226,7 +230,8 @@ ml_status ml_fastsum_plan_learned(ml_plan_t *out, const double *points, int64_t 
  * Asynchronous on `stream` for device X and Y; with host X or Y the call
  * copies through plan-owned buffers and synchronises `stream`.  Two calls
  * that use the same plan must not run concurrently (they share its
- * workspace).  Errors: ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA.
+ * workspace).  Errors: ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA, ML_ERR_DEGREE
+ * (ML_NORMALIZED_A on a layer with a degree <= 0).
  */
 ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int b, double *Y,
                            int mode, void *stream);

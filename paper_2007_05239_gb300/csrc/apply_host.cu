@@ -171,6 +171,12 @@ extern "C" ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const doub
     const int base = mode & ~ML_PER_LAYER;
     if ((mode & ~(ML_PER_LAYER | 3)) != 0 || base > ML_DEGREE) return fail(ML_ERR_ARG, "unknown mode");
     if (!Y) return fail(ML_ERR_ARG, "Y is null");
+    if (base == ML_NORMALIZED_A)
+        for (int t = 0; t < T; ++t)
+            if (!layers[t]->deg_ok)
+                return fail(ML_ERR_DEGREE, "layer " + std::to_string(t) +
+                                               " has a degree <= 0: D^{-1/2} is undefined (isolated point or too "
+                                               "coarse an approximation)");
     if (base != ML_DEGREE && !X) return fail(ML_ERR_ARG, "X is null");
     cudaStream_t st = (cudaStream_t)stream;
     const bool per_layer = (mode & ML_PER_LAYER) != 0;

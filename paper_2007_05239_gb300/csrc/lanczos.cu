@@ -608,6 +608,8 @@ extern "C" ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, doub
     if (k < 1 || k > n / 2) return fail(ML_ERR_ARG, "k must be in [1, n/2]");
     if (p != 1.0 && p != -1.0) return fail(ML_ERR_ARG, "p must be 1 or -1");
     if (block > 1) return fail(ML_ERR_ARG, "block Lanczos is not available (block must be 1)");
+    for (int t = 0; t < T; ++t)
+        if (!layers[t]->deg_ok) return fail(ML_ERR_DEGREE, "a layer has a degree <= 0: L_sym is undefined");
     if (!evals) return fail(ML_ERR_ARG, "evals is null");
     if (tol <= 0) tol = 1e-10;
     if (maxit <= 0) maxit = 2000;

@@ -95,6 +95,7 @@ struct ml_plan_s {
     int ngroups = 0;       // groups of <= kGroupSubs consecutive subproblems of one bin
     int nsub = 0;
     double deg_min = 0, deg_max = 0;
+    bool deg_ok = true;    // every degree positive and finite: D^{-1/2} defined
     int64_t applied = 0;   // vectors pushed through apply_layer
 
     // host tables (FP64)

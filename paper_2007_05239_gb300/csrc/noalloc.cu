@@ -78,6 +78,9 @@ extern "C" ml_status ml_fastsum_apply_noalloc(const ml_plan_t *layers, int T, co
         const size_t bytes = (size_t)elems * sizeof(double);
         if (xb < yb + bytes && yb < xb + bytes) return fail(ML_ERR_ARG, "X and Y overlap");
     }
+    if (base == ML_NORMALIZED_A)
+        for (int t = 0; t < T; ++t)
+            if (!layers[t]->deg_ok) return fail(ML_ERR_DEGREE, "a layer has a degree <= 0: D^{-1/2} is undefined");
     cudaStream_t st = (cudaStream_t)stream;
     if (base == ML_DEGREE) return apply_device(layers, T, X, b, Y, mode, st);  // stored degrees, no scratch
 

@@ -798,7 +798,8 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         p->deg_min = *std::min_element(hd.begin(), hd.end());
         p->deg_max = *std::max_element(hd.begin(), hd.end());
     }
-    if (bad) return fail(ML_ERR_DEGREE, "a degree D_i is not positive: D^{-1/2} is undefined (isolated point or too coarse an approximation)");
+    // raw products stay available; normalised ones report ML_ERR_DEGREE
+    p->deg_ok = !bad;
     return ML_OK;
 }
 

@@ -90,6 +90,8 @@ def make_dataset(first, count, per_cloud, prec, target, seed=0):
     Xs, Ys = [], []
     for i in range(first, first + count):
         pts, sigma, v, rows, ref = cloud(i)
+        if float(ref.norm()) == 0.0:
+            continue
         feat = ml.ml_cloud_features(pts, sigma)
         N0 = auto_bandwidth(pts, sigma, prec, target)
         for ci in rng.choice(len(CANDIDATES), size=per_cloud, replace=False):

@@ -242,3 +242,18 @@ def test_batched_small_grid_layers(b):
     Yp = torch.empty(T, n, b, dtype=torch.float64, device="cuda")
     ml.ml_fastsum_apply(plans, dev(np.broadcast_to(X, (T, n, b))), Yp, mode="normalized", per_layer=True)
     assert rel2(Y, Yp.cpu().numpy().mean(axis=0)) <= 2e-6
+
+
+def test_isolated_point_degree_error_only_for_normalised_products():
+    # a far isolated point: its exact degree underflows, the FP32 approximation
+    # may return <= 0; raw products must still work, normalised ones report it
+    rng = np.random.default_rng(17)
+    X = np.concatenate([rng.uniform(0, 0.6, (3000, 2)), [[1.0, 1.0]]])   # >= 11 sigma from the rest
+    plan = ml.ml_fastsum_plan(dev(X), 0.05, prec="f32")
+    V = dev(np.ones((X.shape[0], 1)))
+    Y = torch.empty_like(V)
+    ml.ml_fastsum_apply([plan], V, Y, mode="raw")
+    if plan.info["deg_min"] <= 0:
+        with pytest.raises(ml.MLError) as e:
+            ml.ml_fastsum_apply([plan], V, Y, mode="normalized")
+        assert e.value.status == ml.ML_ERR_DEGREE
