@@ -43,6 +43,73 @@ __device__ __forceinline__ int fixed_round(float x)
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
+// ------------------------------------------------------------ double-word
+// The FP64 form runs its taps on the FP32 pipes (GB300 issues FP64 at about
+// 1/60 of the FP32 rate).  A value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2 (about 48 significant bits).  Products use
+// the FMA-based exact product (p + e = a*b exactly for floats a, b); sums the
+// exact two-sum of Knuth (the "double-word" algorithms of Dekker 1971 and
+// Joldes, Muller and Popescu 2017; the dot-product accumulation follows
+// Dot2 of Ogita, Rump and Oishi 2005).  The _rn intrinsics keep the compiler
+// from contracting these steps into FMAs.
+__device__ __forceinline__ float2 dw_split(double x)
+{
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ double dw_value(float2 x)
+{
+    return (double)x.x + (double)x.y;
+}
+// x * y with a relative error of a few units of 2^-48
+__device__ __forceinline__ float2 dw_mul(float2 x, float2 y)
+{
+    const float ph = __fmul_rn(x.x, y.x);
+    float pl = fmaf(x.x, y.x, -ph);
+    pl = fmaf(x.x, y.y, pl);
+    pl = fmaf(x.y, y.x, pl);
+    const float h = __fadd_rn(ph, pl);
+    return make_float2(h, __fsub_rn(pl, __fsub_rn(h, ph)));
+}
+// s += g * w with s left unnormalised (s.y collects the rounding errors of
+// the running sum and of the products; renormalise with dw_norm)
+__device__ __forceinline__ void dw_fma_acc(float2 &s, float2 g, float2 w)
+{
+    const float p = __fmul_rn(g.x, w.x);
+    float e = fmaf(g.x, w.x, -p);
+    e = fmaf(g.x, w.y, e);
+    e = fmaf(g.y, w.x, e);
+    const float t = __fadd_rn(s.x, p);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s.y = __fadd_rn(s.y, __fadd_rn(err, e));
+    s.x = t;
+}
+// s += x (x a double-word value), s left unnormalised
+__device__ __forceinline__ void dw_acc(float2 &s, float2 x)
+{
+    const float t = __fadd_rn(s.x, x.x);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(x.x, bb));
+    s.y = __fadd_rn(s.y, __fadd_rn(err, x.y));
+    s.x = t;
+}
+__device__ __forceinline__ float2 dw_norm(float2 s)
+{
+    const float h = __fadd_rn(s.x, s.y);
+    return make_float2(h, __fsub_rn(s.y, __fsub_rn(h, s.x)));
+}
+// Fixed point of one tap p + e (p the rounded product, e its error) for
+// |p| < 2^22: hi = round(p), lo = round((p - hi + e) * 2^20); the tap is
+// hi + lo * 2^-20 to within 2^-21 + 2^-25.
+__device__ __forceinline__ void fixed_split(float p, float e, int &hi, int &lo)
+{
+    const float t = __fadd_rn(p, 12582912.0f);
+    hi = __float_as_int(t) - 0x4B400000;
+    const float r = __fadd_rn(__fsub_rn(p, __fsub_rn(t, 12582912.0f)), e);
+    lo = __float_as_int(fmaf(r, 1048576.0f, 12582912.0f)) - 0x4B400000;
+}
+
 // The W window weights of one dimension for a point with local coordinate x
 // (relative to its bin origin): the taps are the W cells nearest to x, the
 // first at o = floor(x - W/2) + 1, and the weight of tap q is
@@ -70,7 +137,7 @@ struct SpreadArgs {
     const int *sub_bin, *sub_start, *sub_count;
     const int *perm;
     const void *coords;      // T [n][D]
-    const double *wts;       // FP64 form: window weights [n][D][2M]
+    const float2 *wts;       // FP64 form: window weights [n][D][W] as double-word pairs
     const int *offs;         // FP64 form: first tap per dim, packed o0 | o1 << 10 | o2 << 20
     const double *dinv;      // null: no pre-scaling
     const double *X;         // null: all-ones input
@@ -140,7 +207,7 @@ struct InterpArgs {
     const int *sub_bin, *sub_start, *sub_count;
     const int *perm;
     const void *coords;
-    const double *wts;       // FP64 form: window weights [n][D][2M]
+    const float2 *wts;       // FP64 form: window weights [n][D][W] as double-word pairs
     const int *offs;         // FP64 form: packed first taps
     const double *dinv;      // pre/post scale (normalized) or null
     const double *X;         // input (for the self term and the shift), null = ones
@@ -334,128 +401,150 @@ __global__ void __launch_bounds__(256) k_spread_f32_batch(const SpreadArgs *__re
     spread_f32_block<D, W, NV>(a, blockIdx.x);
 }
 
-// A weight of the point held by the warp: lane l holds weights l and 32 + l
-// of the point's D x 2M row-major table (w0, w1); fetch entry k.
-__device__ __forceinline__ double warp_weight(double w0, double w1, int k)
-{
-    const double x = __shfl_sync(0xffffffffu, w0, k & 31);
-    const double y = __shfl_sync(0xffffffffu, w1, k & 31);
-    return k < 32 ? x : y;
-}
-
-// smem staging of one subproblem's inputs for the FP64 kernels
-constexpr int kF64MaxWarps = 8;
-
-// FP64 form: one warp per point, each warp with a private tile, so no
-// atomics are needed.  The subproblem's scaled inputs u and packed first
-// taps are staged in shared memory; each warp prefetches its next point's
-// weights (computed once at plan time, FP64 table wts[n][D][2M]).  Lane
-// items are (qx, qy) pairs; each walks qz in chunks whose tile values are
-// loaded before the DFMAs (one per tap) and stored after, so the chunk's
-// read-modify-writes overlap.  The warps' tiles are summed in a fixed order.
+// FP64 form: one thread per point, one shared tile per CTA, taps in
+// double-word arithmetic on the FP32 pipes, accumulated exactly as integers
+// with 32-bit shared-memory atomics (order-free, deterministic).
+//  - the subproblem's inputs u = D^{-1/2} x are staged (FP64) and each vector
+//    gets a power-of-two scale with every tap < 2^21 and scale * sum|u| <= 2^30
+//    (fixed_scale); a tap p + e then goes to its cell as hi = round(p) and
+//    lo = round((p - hi + e) * 2^20) (fixed_split), so each cell keeps
+//    |sum hi| < 2^31 and |sum lo| <= 1024 * 0.75 * 2^20 (a subproblem has at
+//    most 1024 points);
+//  - the weights are the plan's double-word table; a row (qy, qz) forms
+//    u * w_y * w_z once, each of its W taps one exact product with w_x;
+//  - each lane walks its (qz, qy) rows from a lane-dependent start, so lanes
+//    whose points share a first tap hit different cells.
+// The tile is converted to FP64 exactly (hi + lo * 2^-20 has <= 51 bits).
 template <int D, int W, int NV>
-__global__ void __launch_bounds__(32 * kF64MaxWarps) k_spread_f64(const SpreadArgs a)
+__global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float s_part[2][NV][8];
+    __shared__ float s_scale[NV];
     const int sub = blockIdx.x;
     const int start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int tc = tile_cells<D>(a.Pt);
     const int Pt = a.Pt;
-    const int nwarp = blockDim.x >> 5;
-    double *tiles = reinterpret_cast<double *>(smem_raw);
-    double *su = tiles + (int64_t)nwarp * NV * tc;
-    int *soff = reinterpret_cast<int *>(su + (int64_t)a.sub_max * NV);
-    for (int e = threadIdx.x; e < nwarp * tc * NV; e += blockDim.x) tiles[e] = 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int2 *tile = reinterpret_cast<int2 *>(smem_raw);                      // [NV][tc] (hi, lo)
+    double *su = reinterpret_cast<double *>(tile + (int64_t)NV * tc);      // [sub_max][NV]
+    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) tile[e] = make_int2(0, 0);
+    float lsum[NV], lmax[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) lsum[c] = lmax[c] = 0.0f;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int j = start + i;
         const int orig = a.perm[j];
         const double ds = a.dinv ? a.dinv[j] : 1.0;
 #pragma unroll
-        for (int c = 0; c < NV; ++c) su[i * NV + c] = (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds;
-        soff[i] = a.offs[j];
+        for (int c = 0; c < NV; ++c) {
+            const double u = (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds;
+            su[i * NV + c] = u;
+            const float au = fminf((float)fabs(u), 1e30f);
+            lsum[c] += au;
+            lmax[c] = fmaxf(lmax[c], au);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        const float sm = warp_sum(lsum[c]), mx = warp_max(lmax[c]);
+        if (lane == 0) {
+            s_part[0][c][warp] = sm;
+            s_part[1][c][warp] = mx;
+        }
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *tile = tiles + (int64_t)warp * tc * NV;
-    constexpr int NW = D * W;                       // weights per point
-    constexpr int ITEMS = (D >= 2) ? W * W : W;     // (qx, qy) pairs or qx
-    constexpr int SLOTS = (ITEMS + 31) / 32;
-    constexpr int nz = (D >= 3) ? W : 1;
-    constexpr int QC = (nz % 4 == 0) ? 4 : ((nz % 3 == 0) ? 3 : ((nz % 2 == 0) ? 2 : 1));
-    const int zstride = Pt * Pt;
-    const double *wts = a.wts + (int64_t)start * NW;
-    int i = warp;
-    double w0 = 0.0, w1 = 0.0;
-    if (i < cnt) {
-        w0 = lane < NW ? wts[(int64_t)i * NW + lane] : 0.0;
-        w1 = (NW > 32 && lane + 32 < NW) ? wts[(int64_t)i * NW + 32 + lane] : 0.0;
+    if (threadIdx.x < NV) {
+        float sm = 0.0f, mx = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sm += s_part[0][threadIdx.x][w];
+            mx = fmaxf(mx, s_part[1][threadIdx.x][w]);
+        }
+        s_scale[threadIdx.x] = fixed_scale(sm, mx);
     }
-    for (; i < cnt; i += nwarp) {
-        const int inext = i + nwarp;
-        double n0 = 0.0, n1 = 0.0;
-        if (inext < cnt) {
-            n0 = lane < NW ? wts[(int64_t)inext * NW + lane] : 0.0;
-            n1 = (NW > 32 && lane + 32 < NW) ? wts[(int64_t)inext * NW + 32 + lane] : 0.0;
+    __syncthreads();
+    constexpr int NW = D * W;
+    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int UY = (W <= 8) ? ny : 1;
+    const int ry = (D == 2) ? lane % ny : (D == 3 ? (lane / nz) % ny : 0);
+    const int rz = (D == 3) ? lane % nz : 0;
+    const float2 one2 = make_float2(1.0f, 0.0f);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t j = start + i;
+        float2 u[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) u[c] = dw_split(su[i * NV + c] * (double)s_scale[c]);
+        const float2 *wp = a.wts + j * NW;
+        float2 wx[W], wyr[ny];
+#pragma unroll
+        for (int q = 0; q < W; ++q) wx[q] = wp[q];
+        // rotated rows: row q of this lane is row (q + r) mod n of the point
+#pragma unroll
+        for (int q = 0; q < ny; ++q) {
+            int src = q + ry;
+            src -= (src >= ny) ? ny : 0;
+            wyr[q] = (D >= 2) ? wp[W + src] : one2;
         }
-        const int off = soff[i];
+        const int off = a.offs[j];
         const int o0 = off & 1023, o1 = (off >> 10) & 1023, o2 = off >> 20;
-        double uw[SLOTS][NV];
-        int base[SLOTS];
-        bool valid[SLOTS];
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-            const int p = lane + 32 * s;
-            valid[s] = p < ITEMS;
-            const int qx = valid[s] ? p % W : 0;
-            const int qy = (D >= 2 && valid[s]) ? p / W : 0;
-            const double wxy = warp_weight(w0, w1, qx) * (D >= 2 ? warp_weight(w0, w1, W + qy) : 1.0);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) uw[s][c] = valid[s] ? su[i * NV + c] * wxy : 0.0;
-            base[s] = (o2 * Pt + o1 + qy) * Pt + o0 + qx;
-        }
 #pragma unroll 1
-        for (int qz0 = 0; qz0 < nz; qz0 += QC) {
-            double v[QC][SLOTS][NV];
+        for (int qz0 = 0; qz0 < nz; ++qz0) {
+            int qz = qz0 + rz;
+            qz -= (qz >= nz) ? nz : 0;
+            const float2 wz = (D >= 3) ? wp[2 * W + qz] : one2;
+#pragma unroll UY
+            for (int qy0 = 0; qy0 < ny; ++qy0) {
+                int qy = qy0 + ry;
+                qy -= (qy >= ny) ? ny : 0;
+                const float2 wyz = (D >= 3) ? dw_mul(wz, wyr[qy0]) : wyr[qy0];
+                int *row = reinterpret_cast<int *>(tile + ((o2 + qz) * Pt + o1 + qy) * Pt + o0);
 #pragma unroll
-            for (int q = 0; q < QC; ++q)
+                for (int c = 0; c < NV; ++c) {
+                    const float2 ar = (D >= 2) ? dw_mul(u[c], wyz) : u[c];
 #pragma unroll
-                for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) v[q][s][c] = tile[c * tc + base[s] + (qz0 + q) * zstride];
-#pragma unroll
-            for (int q = 0; q < QC; ++q) {
-                const double wzq = (D >= 3) ? warp_weight(w0, w1, 2 * W + qz0 + q) : 1.0;
-#pragma unroll
-                for (int s = 0; s < SLOTS; ++s)
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) v[q][s][c] = fma(uw[s][c], wzq, v[q][s][c]);
+                    for (int qx = 0; qx < W; ++qx) {
+                        const float p = __fmul_rn(ar.x, wx[qx].x);
+                        float e = fmaf(ar.x, wx[qx].x, -p);
+                        e = fmaf(ar.x, wx[qx].y, e);
+                        e = fmaf(ar.y, wx[qx].x, e);
+                        int hi, lo;
+                        fixed_split(p, e, hi, lo);
+                        atomicAdd(row + 2 * (c * tc + qx), hi);
+                        atomicAdd(row + 2 * (c * tc + qx) + 1, lo);
+                    }
+                }
             }
-#pragma unroll
-            for (int q = 0; q < QC; ++q)
-#pragma unroll
-                for (int s = 0; s < SLOTS; ++s)
-                    if (valid[s])
-#pragma unroll
-                        for (int c = 0; c < NV; ++c) tile[c * tc + base[s] + (qz0 + q) * zstride] = v[q][s][c];
         }
-        w0 = n0;
-        w1 = n1;
     }
     __syncthreads();
     double *out = static_cast<double *>(a.scratch) + (int64_t)sub * tc * NV;
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
         const int c = e % NV, cell = e / NV;
-        double acc = 0.0;
-        for (int w = 0; w < nwarp; ++w) acc += tiles[(int64_t)w * tc * NV + c * tc + cell];
-        out[e] = acc;
+        const int2 t = tile[c * tc + cell];
+        // t.x + t.y * 2^-20 has at most 51 significant bits: exact in FP64
+        out[e] = fma((double)t.y, 0x1p-20, (double)t.x) * (double)(1.0f / s_scale[c]);
     }
 }
-
 // ==================================================================== fold
 // One CTA per bin: each active-grid cell of the bin sums, in a fixed order,
 // the tile values of every subproblem whose padded tile covers it (the bin
 // itself and up to R bins below it per dim).  Deterministic, no atomics.
-template <typename T, int D>
+// The FP64 form writes the grid as double-word pairs (TO = float2) for the
+// transforms that follow.
+__device__ __forceinline__ void grid_store(double *out, int64_t i, double v)
+{
+    out[i] = v;
+}
+__device__ __forceinline__ void grid_store(float *out, int64_t i, float v)
+{
+    out[i] = v;
+}
+__device__ __forceinline__ void grid_store(float2 *out, int64_t i, double v)
+{
+    out[i] = dw_split(v);
+}
+
+template <typename T, int D, typename TO = T>
 __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
 {
     int bc[3];
@@ -464,7 +553,7 @@ __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
     const int tc = tile_cells<D>(Pt);
     const int cells = (D == 1 ? B : (D == 2 ? B * B : B * B * B));
     const T *scr = static_cast<const T *>(a.scratch);
-    T *grid = static_cast<T *>(a.grid);
+    TO *grid = static_cast<TO *>(a.grid);
     for (int e = threadIdx.x; e < cells * nv; e += blockDim.x) {
         const int c = e % nv;
         const int cell = e / nv;
@@ -493,14 +582,14 @@ __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
                 }
             }
         }
-        grid[((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * nv + c] = acc;
+        grid_store(grid, ((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * nv + c, acc);
     }
 }
 
-template <typename T, int D>
+template <typename T, int D, typename TO = T>
 __global__ void __launch_bounds__(256) k_fold(const FoldArgs a)
 {
-    fold_block<T, D>(a, blockIdx.x);
+    fold_block<T, D, TO>(a, blockIdx.x);
 }
 
 template <typename T, int D>
@@ -583,6 +672,39 @@ __global__ void __launch_bounds__(256) k_axis(const T *__restrict__ in, T *__res
     axis_block<T>(in, out, M, A, J, Ko, C, blockIdx.x, blockIdx.y);
 }
 
+// FP64 form: the same transform in double-word arithmetic (grid, matrix and
+// result as hi/lo pairs).  One thread per output, p = (a, c) fastest so that
+// a warp mostly shares the row k of M; two compensated accumulators over
+// even and odd j, renormalised every 8 terms.
+template <typename F2>
+__global__ void __launch_bounds__(128) k_axis_dw(const F2 *__restrict__ in, F2 *__restrict__ out,
+                                                 const F2 *__restrict__ M, int A, int J, int Ko, int C)
+{
+    const int64_t P = (int64_t)A * C;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * Ko) return;
+    const int k = (int)(t / P);
+    const int64_t p = t - (int64_t)k * P;
+    const int64_t aa = p / C;
+    const int cc = (int)(p - aa * C);
+    const F2 *col = in + aa * J * C + cc;
+    const F2 *row = M + (int64_t)k * J;
+    float2 s0 = make_float2(0.0f, 0.0f), s1 = s0;
+    int j = 0;
+    for (; j + 1 < J; j += 2) {
+        dw_fma_acc(s0, col[(int64_t)j * C], row[j]);
+        dw_fma_acc(s1, col[(int64_t)(j + 1) * C], row[j + 1]);
+        if ((j & 15) == 14) {
+            s0 = dw_norm(s0);
+            s1 = dw_norm(s1);
+        }
+    }
+    if (j < J) dw_fma_acc(s0, col[(int64_t)j * C], row[j]);
+    s0 = dw_norm(s0);
+    dw_acc(s0, dw_norm(s1));
+    out[(aa * Ko + k) * C + cc] = dw_norm(s0);
+}
+
 struct AxisArgs {
     const void *in;
     void *out;
@@ -616,6 +738,14 @@ __global__ void k_mult_batch(const MultArgs *__restrict__ args, int nv)
         coef[e] *= mult[e / nv];
 }
 
+template <typename F2>
+__global__ void k_mult_dw(F2 *coef, const F2 *__restrict__ mult, int64_t slots, int nv)
+{
+    const int64_t tot = slots * nv;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+        coef[e] = dw_mul(coef[e], mult[e / nv]);
+}
+
 template <typename T>
 __global__ void k_mult(T *coef, const T *__restrict__ mult, int64_t slots, int nv)
 {
@@ -642,7 +772,7 @@ __device__ __forceinline__ void load_interp_tile(const InterpArgs &a, int D, con
         const int ly = (D >= 2) ? (cell / Pt) % Pt : 0;
         const int lz = (D >= 3) ? cell / (Pt * Pt) : 0;
         const int gx = bc[0] * a.B + lx, gy = bc[1] * a.B + ly, gz = bc[2] * a.B + lz;
-        T v = 0;
+        T v{};
         if (gx < a.L0 && gy < a.L1 && gz < a.L2) v = grid[((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * NV + c];
         tile[c * tc + cell] = v;
     }
@@ -738,63 +868,71 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
     }
 }
 
-// FP64 form: one thread per point, FP64 weights from the plan's table and
-// packed first taps; rows are summed with FP64 FMAs (no warp reduction, so
-// nearly every FP64 instruction is a tap).
+// FP64 form: one thread per point, on the FP32 pipes.  The grid arrives as
+// double-word pairs (written by the last backward transform), the weights
+// from the plan's double-word table; each row sum over qx is a compensated
+// dot product (dw_fma_acc), weighted by w_y and w_z in double-word products,
+// and the point's value enters the FP64 epilogue as hi + lo.
 template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_interp_f64(const InterpArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *tile = reinterpret_cast<double *>(smem_raw);
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     const int sub = blockIdx.x;
     const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int Pt = a.Pt;
     const int tc = tile_cells<D>(Pt);
     int bc[3];
     bin_coords<D>(bin, a.nb0, a.nb1, bc);
-    load_interp_tile<double, NV>(a, D, bc, tc, tile);
+    load_interp_tile<float2, NV>(a, D, bc, tc, tile);
     __syncthreads();
     constexpr int NW = D * W;
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
-    constexpr int UY = (W <= 8) ? ny : 1;
-    constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
+    constexpr int UY = (W <= 8) ? ny : 1;      // rows of one qz unrolled; qz not (code size)
+    const float2 zero2 = make_float2(0.0f, 0.0f);
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
-        const double *wp = a.wts + (int64_t)i * NW;
-        double wx[W], wy[W], wz[W];
+        const float2 *wp = a.wts + (int64_t)i * NW;
+        float2 wx[W], wy[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             wx[q] = wp[q];
-            wy[q] = (D >= 2) ? wp[W + q] : 1.0;
-            wz[q] = (D >= 3) ? wp[2 * W + q] : 1.0;
+            wy[q] = (D >= 2) ? wp[W + q] : zero2;
         }
         const int off = a.offs[i];
         const int o0 = off & 1023, o1 = (off >> 10) & 1023, o2 = off >> 20;
-        double acc[NV];
+        float2 acc[NV];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) acc[c] = 0.0;
-#pragma unroll UZ
+        for (int c = 0; c < NV; ++c) acc[c] = zero2;
+#pragma unroll 1
         for (int qz = 0; qz < nz; ++qz) {
-            double pz[NV];
+            const float2 wz = (D >= 3) ? wp[2 * W + qz] : zero2;
+            float2 pz[NV];
 #pragma unroll
-            for (int c = 0; c < NV; ++c) pz[c] = 0.0;
+            for (int c = 0; c < NV; ++c) pz[c] = zero2;
 #pragma unroll UY
             for (int qy = 0; qy < ny; ++qy) {
-                const double *row = tile + ((o2 + qz) * Pt + o1 + qy) * Pt + o0;
-                double r[NV];
+                const float2 *row = tile + ((o2 + qz) * Pt + o1 + qy) * Pt + o0;
+                float2 r[NV];
 #pragma unroll
-                for (int c = 0; c < NV; ++c) r[c] = 0.0;
+                for (int c = 0; c < NV; ++c) r[c] = zero2;
 #pragma unroll
                 for (int qx = 0; qx < W; ++qx)
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) r[c] = fma(wx[qx], row[c * tc + qx], r[c]);
+                    for (int c = 0; c < NV; ++c) dw_fma_acc(r[c], row[c * tc + qx], wx[qx]);
 #pragma unroll
-                for (int c = 0; c < NV; ++c) pz[c] = fma(wy[qy], r[c], pz[c]);
+                for (int c = 0; c < NV; ++c) {
+                    if (D >= 2) dw_acc(pz[c], dw_mul(dw_norm(r[c]), wy[qy]));
+                    else pz[c] = r[c];
+                }
             }
 #pragma unroll
-            for (int c = 0; c < NV; ++c) acc[c] = fma(wz[qz], pz[c], acc[c]);
+            for (int c = 0; c < NV; ++c) {
+                if (D >= 3) dw_acc(acc[c], dw_mul(dw_norm(pz[c]), wz));
+                else acc[c] = pz[c];
+            }
         }
 #pragma unroll
-        for (int c = 0; c < NV; ++c) interp_epilogue(a, i, c, acc[c]);
+        for (int c = 0; c < NV; ++c) interp_epilogue(a, i, c, dw_value(acc[c]));
     }
 }
 

@@ -37,7 +37,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.sub_count = p->sub_count.as<int>();
     sa.perm = p->perm.as<int>();
     sa.coords = p->coords.p;
-    sa.wts = p->wts.as<double>();
+    sa.wts = p->wts.as<float2>();
     sa.offs = p->offs.as<int>();
     sa.sub_max = p->sub_max;
     sa.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
@@ -62,10 +62,9 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
             ML_TRY(set_smem(k_spread_f32<D, W, NV>, smem));
             k_spread_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
-            const size_t smem = (size_t)tc * nv * sizeof(double) * p->f64_warps +
-                                (size_t)p->sub_max * (nv * sizeof(double) + sizeof(int));
+            const size_t smem = (size_t)tc * nv * sizeof(int2) + (size_t)p->sub_max * nv * sizeof(double);
             ML_TRY(set_smem(k_spread_f64<D, W, NV>, smem));
-            k_spread_f64<D, W, NV><<<p->nsub, 32 * p->f64_warps, smem, st>>>(sa);
+            k_spread_f64<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         }
         ML_CUDA(cudaGetLastError());
     }
@@ -96,10 +95,11 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     fa.L2 = g.L[2];
     {
         ProfScope pr("fold", st);
-        k_fold<T, D><<<(int)g.nbins(), 256, 0, st>>>(fa);
+        if (f32) k_fold<T, D><<<(int)g.nbins(), 256, 0, st>>>(fa);
+        else k_fold<T, D, float2><<<(int)g.nbins(), 256, 0, st>>>(fa);
     }
     ML_CUDA(cudaGetLastError());
-    // ---- transforms
+    // ---- transforms (FP64 form: double-word grids, matrices and multiplier)
     T *bufs[2] = {static_cast<T *>(w.work0), static_cast<T *>(w.work1)};
     int cur = 0;
     int64_t Kpow = 1;  // K^a
@@ -107,9 +107,17 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         int64_t A = 1;
         for (int b = a + 1; b < D; ++b) A *= g.L[b];
         const int64_t C = Kpow * nv;
-        dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.K + 31) / 32));
         ProfScope pr("axis", st);
-        k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_f[a].as<T>(), (int)A, g.L[a], g.K, (int)C);
+        if (f32) {
+            dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.K + 31) / 32));
+            k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_f[a].as<T>(), (int)A, g.L[a], g.K,
+                                            (int)C);
+        } else {
+            const int64_t outs = A * C * g.K;
+            k_axis_dw<float2><<<(unsigned)((outs + 127) / 128), 128, 0, st>>>(
+                reinterpret_cast<const float2 *>(bufs[cur]), reinterpret_cast<float2 *>(bufs[cur ^ 1]),
+                p->trig_f[a].as<float2>(), (int)A, g.L[a], g.K, (int)C);
+        }
         cur ^= 1;
         Kpow *= g.K;
     }
@@ -118,16 +126,28 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         const int64_t slots = Kpow;
         const int blocks = (int)std::min<int64_t>((slots * nv + 255) / 256, 4096);
         ProfScope pr("mult", st);
-        k_mult<T><<<blocks, 256, 0, st>>>(bufs[cur], p->mult_d.as<T>(), slots, nv);
+        if (f32)
+            k_mult<T><<<blocks, 256, 0, st>>>(bufs[cur], p->mult_d.as<T>(), slots, nv);
+        else
+            k_mult_dw<float2><<<blocks, 256, 0, st>>>(reinterpret_cast<float2 *>(bufs[cur]), p->mult_d.as<float2>(), slots,
+                                              nv);
     }
     for (int a = D - 1; a >= 0; --a) {
         Kpow /= g.K;
         int64_t A = 1;
         for (int b = a + 1; b < D; ++b) A *= g.L[b];
         const int64_t C = Kpow * nv;
-        dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.L[a] + 31) / 32));
         ProfScope pr("axis", st);
-        k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_b[a].as<T>(), (int)A, g.K, g.L[a], (int)C);
+        if (f32) {
+            dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.L[a] + 31) / 32));
+            k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_b[a].as<T>(), (int)A, g.K, g.L[a],
+                                            (int)C);
+        } else {
+            const int64_t outs = A * C * g.L[a];
+            k_axis_dw<float2><<<(unsigned)((outs + 127) / 128), 128, 0, st>>>(
+                reinterpret_cast<const float2 *>(bufs[cur]), reinterpret_cast<float2 *>(bufs[cur ^ 1]),
+                p->trig_b[a].as<float2>(), (int)A, g.K, g.L[a], (int)C);
+        }
         cur ^= 1;
     }
     ML_CUDA(cudaGetLastError());

@@ -90,7 +90,6 @@ struct ml_plan_s {
     int s0[3] = {0, 0, 0}; // torus index of active-grid cell 0 per dim
     ml::GridGeom g;
     int vp = 1;            // vectors per pass
-    int f64_warps = 8;     // FP64 form: warps (private tiles) per CTA
     int sub_max = 0;       // largest subproblem (points)
     int ngroups = 0;       // groups of <= kGroupSubs consecutive subproblems of one bin
     int nsub = 0;
@@ -106,7 +105,7 @@ struct ml_plan_s {
     // device data (sorted order unless noted)
     ml::DevBuf perm;      // int32 n: sorted position -> input index
     ml::DevBuf coords;    // T n*d local grid coordinates
-    ml::DevBuf wts;       // FP64 form: double n*d*2m window weights
+    ml::DevBuf wts;       // FP64 form: float2 [n][d][W] window weights (double-word pairs)
     ml::DevBuf offs;      // FP64 form: int n packed first taps o0 | o1 << 10 | o2 << 20
     ml::DevBuf deg;       // double n: degrees
     ml::DevBuf dinv;      // double n: D^{-1/2}
@@ -114,9 +113,9 @@ struct ml_plan_s {
     ml::DevBuf bin_sub;   // int32 nbins+1: first subproblem of each bin
     ml::DevBuf grp_sub;   // int32 ngroups+1: first subproblem of each tile group
     ml::DevBuf bin_grp;   // int32 nbins+1: first tile group of each bin
-    ml::DevBuf trig_f[3]; // T K x L_a  (forward, cos rows then sin rows)
-    ml::DevBuf trig_b[3]; // T L_a x K  (backward = transpose)
-    ml::DevBuf mult_d;    // T K^d
+    ml::DevBuf trig_f[3]; // K x L_a (forward, cos rows then sin rows): float, or float2 pairs (FP64 form)
+    ml::DevBuf trig_b[3]; // L_a x K (backward = transpose), same element type
+    ml::DevBuf mult_d;    // K^d slot multipliers, same element type
 
     // workspace
     ml::DevBuf scratch;   // spreading tiles: nsub * Pt^d * vp (T)

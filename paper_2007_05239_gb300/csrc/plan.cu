@@ -191,10 +191,11 @@ __global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, int *c
         atomicAdd(&counts[keys[i]], 1);
 }
 
-// FP64 window weights of every point (plan time): wts[i][a][q] = phi_n(x - o - q),
+// FP64 window weights of every point (plan time), stored as double-word
+// pairs: wts[i][a][q] = phi_n(x - o - q),
 // o = floor(x - W/2) + 1 the first tap
 __global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n, int d, int W, double h2, double b,
-                                   double norm2, double *wts)
+                                   double norm2, float2 *wts)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d * W;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -202,7 +203,7 @@ __global__ void k_window_table_f64(const double *__restrict__ coords, int64_t n,
         const int64_t ia = e / W;   // point * d + dim
         const double x = coords[ia];
         const double fl = floor(x - 0.5 * W);
-        wts[e] = kb_weight(x - fl - 1.0 - (double)q, h2, b, norm2);
+        wts[e] = dw_split(kb_weight(x - fl - 1.0 - (double)q, h2, b, norm2));
     }
 }
 
@@ -438,25 +439,19 @@ int auto_bandwidth_box(double sigma, double box, int d, double target)
     return auto_N(aa / h * sigma, target);
 }
 
-// FP64 form: bin edge and warps per CTA.  Every warp owns a padded tile of
-// (B + W)^d doubles; the tiles plus the staged subproblem inputs (12 KB)
-// must fit 200 KB.  Prefer 8 warps as long as the bin keeps an edge >= 4.
-static void choose_f64_layout(int d, int W, int *B, int *nw)
+// FP64 form: the largest B whose padded tile (B + W)^d of 8-byte cells stays
+// within 23.5 KB per vector (with the staged inputs, several CTAs per SM),
+// doubling the budget (up to 188 KB) while that leaves B < 4
+static int choose_bin_f64(int d, int W)
 {
-    const double budget = 188.0 * 1024.0;
-    for (int w : {8, 4, 2, 1}) {
-        const double cells = budget / (8.0 * w);
-        const int Pt = (int)std::floor(std::pow(cells, 1.0 / d) + 1e-9);
-        int b = Pt - W;
+    int b = 1;
+    for (double kb = 23.5; kb <= 188.0; kb *= 2.0) {
+        const int Pt = (int)std::floor(std::pow(kb * 1024.0 / 8.0, 1.0 / d) + 1e-9);
+        b = Pt - W;
         if (d == 1) b = std::min(b, 512);
-        if (b >= 4 || (w == 1 && b >= 1)) {
-            *B = b;
-            *nw = w;
-            return;
-        }
+        if (b >= 4) break;
     }
-    *B = 1;
-    *nw = 1;
+    return std::max(b, 1);
 }
 
 // FP32 form: the largest B whose padded tile (B + W)^d of 8-byte cells stays
@@ -483,6 +478,21 @@ static ml_status upload(DevBuf &buf, const std::vector<double> &src)
     std::vector<T> tmp(src.begin(), src.end());
     ML_TRY(buf.ensure(tmp.size() * sizeof(T)));
     ML_CUDA(cudaMemcpy(buf.p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ML_OK;
+}
+
+// FP64 form: tables as double-word pairs (hi = x rounded to float, lo = the
+// remainder rounded to float)
+static ml_status upload_dw(DevBuf &buf, const std::vector<double> &src)
+{
+    std::vector<float> tmp(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        const float hi = (float)src[i];
+        tmp[2 * i] = hi;
+        tmp[2 * i + 1] = (float)(src[i] - (double)hi);
+    }
+    ML_TRY(buf.ensure(tmp.size() * sizeof(float)));
+    ML_CUDA(cudaMemcpy(buf.p, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice));
     return ML_OK;
 }
 
@@ -614,7 +624,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     if (p->prec == ML_F32) {
         g.B = choose_bin(d, p->W);
     } else {
-        choose_f64_layout(d, p->W, &g.B, &p->f64_warps);
+        g.B = choose_bin_f64(d, p->W);
     }
     {
         // a grid that fits in one bin: one bin, and a tile the size of the grid
@@ -638,7 +648,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         } else {
             int vp = 1;
             for (int v = kMaxVec; v >= 1; --v)
-                if ((int64_t)p->f64_warps * tc * 8 * v + (int64_t)kSubPoints * (8 * v + 4) <= 200 * 1024) {
+                if ((int64_t)tc * 8 * v + (int64_t)kSubPoints * 8 * v <= 200 * 1024) {
                     vp = v;
                     break;
                 }
@@ -687,10 +697,10 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_CUDA(cudaGetLastError());
     if (p->prec == ML_F64) {
         // FP64 window weights, once per plan
-        ML_TRY(p->wts.ensure((size_t)n * d * p->W * sizeof(double)));
+        ML_TRY(p->wts.ensure((size_t)n * d * p->W * sizeof(float2)));
         ProfScope pr_("plan", st);
         k_window_table_f64<<<grid_for(n * d * p->W), 256, 0, st>>>(
-            p->coords.as<double>(), n, d, p->W, 0.25 * p->W * p->W, p->kb_shape, p->kb_norm, p->wts.as<double>());
+            p->coords.as<double>(), n, d, p->W, 0.25 * p->W * p->W, p->kb_shape, p->kb_norm, p->wts.as<float2>());
         ML_TRY(p->offs.ensure((size_t)n * sizeof(int)));
         k_first_taps<<<grid_for(n), 256, 0, st>>>(p->coords.as<double>(), n, d, p->W, p->offs.as<int>());
         ML_CUDA(cudaGetLastError());
@@ -770,12 +780,12 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
             ML_TRY(upload<float>(p->trig_f[a], M));
             ML_TRY(upload<float>(p->trig_b[a], Mt));
         } else {
-            ML_TRY(upload<double>(p->trig_f[a], M));
-            ML_TRY(upload<double>(p->trig_b[a], Mt));
+            ML_TRY(upload_dw(p->trig_f[a], M));
+            ML_TRY(upload_dw(p->trig_b[a], Mt));
         }
     }
     if (p->prec == ML_F32) ML_TRY(upload<float>(p->mult_d, p->mult));
-    else ML_TRY(upload<double>(p->mult_d, p->mult));
+    else ML_TRY(upload_dw(p->mult_d, p->mult));
     // ---- degrees D = W~ 1 - K(0) (sorted order), D^{-1/2}
     ML_TRY(ensure_workspace(p, 1));
     ML_TRY(p->deg.ensure((size_t)n * 8));

@@ -87,7 +87,7 @@ def auto_bandwidth(pts, sigma, prec, target):
 
 def make_dataset(first, count, per_cloud, prec, target, seed=0):
     rng = np.random.default_rng(seed)
-    Xs, Ys = [], []
+    Xs, Ys, ids = [], [], []
     for i in range(first, first + count):
         pts, sigma, v, rows, ref = cloud(i)
         if float(ref.norm()) == 0.0:
@@ -99,7 +99,8 @@ def make_dataset(first, count, per_cloud, prec, target, seed=0):
             le, lt = measure(pts, sigma, prec, target, cand, v, rows, ref, N0)
             Xs.append(np.concatenate([feat, np.asarray(cand, dtype=np.float32)]))
             Ys.append([le, lt])
-    return np.asarray(Xs, dtype=np.float32), np.asarray(Ys, dtype=np.float32)
+            ids.append(i)
+    return np.asarray(Xs, dtype=np.float32), np.asarray(Ys, dtype=np.float32), np.asarray(ids)
 
 
 def train(X, Y, hidden=64, epochs=4000, lr=3e-3, seed=1):
@@ -109,6 +110,15 @@ def train(X, Y, hidden=64, epochs=4000, lr=3e-3, seed=1):
     model.set_norm(mx, sx, my, sy)
     losses = model.train(X, Y, epochs, lr)
     return model, losses, (mx, sx, my, sy)
+
+
+def calibrate_margin(model, X, Y, quantile=0.99):
+    """Safety factor on the error target from held-out samples: the planner
+    keeps a candidate when its predicted error is at most target / margin, so
+    margin = 10^q with q the given quantile of (measured - predicted) log10
+    error; at least 1."""
+    r = Y[:, 0] - model.forward(X)[:, 0]
+    return float(10.0 ** max(0.0, float(np.quantile(r, quantile))))
 
 
 def evaluate(model, first, count, prec, target, margin=2.0):
@@ -134,17 +144,18 @@ def evaluate(model, first, count, prec, target, margin=2.0):
             "clouds": rows_out}
 
 
-def save(path, model, norm):
+def save(path, model, norm, margin):
     np.savez(path, params=model.get_params(), in_mean=norm[0], in_std=norm[1], out_mean=norm[2], out_std=norm[3],
-             hidden=model.hidden)
+             hidden=model.hidden, margin=margin)
 
 
 def load_model(path):
+    """(model, margin) saved by `save`."""
     z = np.load(path)
     model = ml.Mlp(len(z["in_mean"]), int(z["hidden"]), len(z["out_mean"]))
     model.set_params(z["params"])
     model.set_norm(z["in_mean"], z["in_std"], z["out_mean"], z["out_std"])
-    return model
+    return model, float(z["margin"])
 
 
 def main():
@@ -155,22 +166,27 @@ def main():
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--target", type=float, default=1e-4)
     ap.add_argument("--epochs", type=int, default=4000)
+    ap.add_argument("--holdout", type=float, default=0.1, help="share of training clouds held out for the margin")
+    ap.add_argument("--quantile", type=float, default=0.99, help="quantile of held-out error residuals")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     a = ap.parse_args()
     t0 = time.time()
-    X, Y = make_dataset(0, a.train, a.per_cloud, a.prec, a.target)
+    X, Y, ids = make_dataset(0, a.train, a.per_cloud, a.prec, a.target)
     t1 = time.time()
-    model, losses, norm = train(X, Y, epochs=a.epochs)
+    fit = ids < a.train * (1.0 - a.holdout)
+    model, losses, norm = train(X[fit], Y[fit], epochs=a.epochs)
+    margin = calibrate_margin(model, X[~fit], Y[~fit], a.quantile)
     t2 = time.time()
-    ev = evaluate(model, 5000, a.eval, a.prec, a.target)
+    ev = evaluate(model, 5000, a.eval, a.prec, a.target, margin=margin)
     t3 = time.time()
-    rep = {"samples": int(X.shape[0]), "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
+    rep = {"samples": int(X.shape[0]), "fit_samples": int(fit.sum()), "margin": margin,
+           "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
            "data_s": t1 - t0, "train_s": t2 - t1, "eval_s": t3 - t2,
            **{k: v for k, v in ev.items() if k != "clouds"}}
     print(json.dumps(rep))
     if a.out:
-        save(a.out, model, norm)
+        save(a.out, model, norm, margin)
     if a.report:
         with open(a.report, "w") as f:
             json.dump({**rep, "clouds": ev["clouds"]}, f)

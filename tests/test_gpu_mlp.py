@@ -91,11 +91,14 @@ def test_learned_choice_small_end_to_end():
     # a small version of the fifth workload: train on the method's own
     # measurements of 30 clouds, then compare with the fixed rule on 8 unseen
     # clouds (the full-size run is reported in the design doc)
-    X, Y = paramnet.make_dataset(0, 30, 8, "f32", 1e-4)
-    assert X.shape == (240, ml.ML_FEATURES + 3) and np.isfinite(Y).all()
-    model, losses, _ = paramnet.train(X, Y, epochs=1500)
+    X, Y, ids = paramnet.make_dataset(0, 30, 8, "f32", 1e-4)
+    assert X.shape == (240, ml.ML_FEATURES + 3) and np.isfinite(Y).all() and ids.shape == (240,)
+    fit = ids < 25
+    model, losses, _ = paramnet.train(X[fit], Y[fit], epochs=1500)
     assert losses[-1] < 0.5 * losses[0]
-    ev = paramnet.evaluate(model, 5000, 8, "f32", 1e-4)
+    margin = paramnet.calibrate_margin(model, X[~fit], Y[~fit])
+    assert margin >= 1.0
+    ev = paramnet.evaluate(model, 5000, 8, "f32", 1e-4, margin=max(margin, 2.0))
     assert ev["success_fixed"] == 1.0
     assert ev["success_learned"] >= 0.75
     # without a model the learned planner is the fixed rule
