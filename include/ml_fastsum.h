@@ -300,6 +300,38 @@ ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, doubl
                           int block, uint64_t seed, double *evals, double *evecs, int *nconv,
                           void *stream);
 
+/*
+ * ml_lanczos_eigs_layers - for every layer t separately, the k smallest
+ * eigenpairs of L_sym^(t) = I - D_t^{-1/2} W_t D_t^{-1/2} (Sec. 2), by block
+ * thick-restart Lanczos with full reorthogonalisation (the Lanczos method of
+ * Sec. 3 with `block` vectors per step).  All T eigenproblems advance
+ * together: each step applies every unfinished layer's operator to its own
+ * block in one batched fast summation (one launch per stage when the layers
+ * are FP32 plans of one d and window width) and orthogonalises all blocks
+ * with kernels batched over the layers.  A layer leaves the batch when its
+ * k pairs have converged.
+ *
+ *   layers, T  T >= 1 plans sharing n.
+ *   k          1 <= k <= n/2; the basis holds about max(2k+1, 20) + 2*block
+ *              columns and must stay within 96 (k <= ~30 at block = 8).
+ *   tol        relative residual ||A phi - theta phi|| <= tol * |theta_max|
+ *              per layer (<= 0: 1e-10).
+ *   maxit      limit on operator applications per layer (<= 0: 2000).
+ *   block      vectors per step, 1..8.
+ *   seed       seed of the start blocks (SplitMix64 counter streams, one per layer).
+ *   evals      host, T x k FP64 (row t: ascending eigenvalues of L_sym^(t)).
+ *   evecs      host or device, T blocks of n x k FP64 column-major (block t =
+ *              layer t), unit 2-norm, largest-magnitude entry positive; may be NULL.
+ *   nconv      host, T ints: converged pairs per layer (may be NULL).
+ * Synchronises `stream`.  Returns ML_WARN_NOT_CONVERGED when some layer
+ * reached maxit with fewer than k converged pairs; ML_ERR_ARG for k or block
+ * out of range; ML_ERR_DEGREE for a layer with a degree <= 0.  When a block
+ * becomes numerically rank-deficient its dependent directions are dropped
+ * (the block deflates) instead of failing.
+ */
+ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
+                                 uint64_t seed, double *evals, double *evecs, int *nconv, void *stream);
+
 /* Copy the plan's parameters into *info (host).  Never fails on a valid plan. */
 ml_status ml_plan_get_info(ml_plan_t plan, ml_plan_info *info);
 

@@ -27,7 +27,8 @@ MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_learned", "ml_fastsum_apply",
            "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
            "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
-           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_plan_get_info",
+           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers",
+           "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read"]
 
@@ -87,6 +88,9 @@ def load():
     lib.ml_lanczos_eigs.restype = ctypes.c_int
     lib.ml_lanczos_eigs.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P, P, P]
+    lib.ml_lanczos_eigs_layers.restype = ctypes.c_int
+    lib.ml_lanczos_eigs_layers.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_uint64, P, P, P, P]
     lib.ml_plan_get_info.restype = ctypes.c_int
     lib.ml_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.ml_plan_copy_table.restype = ctypes.c_int
@@ -365,6 +369,24 @@ def ml_lanczos_eigs(layers, k, p=1.0, tol=0.0, maxit=0, seed=0, evecs=None, stre
                              _stream(stream))
     _check(st)
     return ev, nconv.value, st
+
+
+def ml_lanczos_eigs_layers(layers, k, block=8, tol=0.0, maxit=0, seed=0, evecs=None, stream=None):
+    """For every layer separately, the k smallest eigenpairs of its L_sym,
+    all layers advancing together by block Lanczos with `block` vectors.
+
+    evecs: None, or a float64 buffer with T*n*k elements (CUDA or CPU): block
+    t holds layer t's eigenvectors column-major.  Returns (evals (T x k),
+    nconv (T), status)."""
+    lib = load()
+    T = len(layers)
+    ev = np.empty((T, k), dtype=np.float64)
+    nconv = np.zeros(T, dtype=np.int32)
+    arr = _handles(layers)
+    st = lib.ml_lanczos_eigs_layers(arr, T, int(k), float(tol), int(maxit), int(block), ctypes.c_uint64(seed),
+                                    ev.ctypes.data, _ptr(evecs), nconv.ctypes.data, _stream(stream))
+    _check(st)
+    return ev, nconv, st
 
 
 def ml_profile_enable(on=True):

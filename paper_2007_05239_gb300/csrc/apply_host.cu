@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "ml_internal.h"
 
@@ -33,6 +34,15 @@ bool batchable(ml_plan_s *const *L, int T)
             return false;
         if (p->sub_max > kBatchPtsTotal) return false;
     }
+    return true;
+}
+
+// per-layer outputs (ApplyOpts::layer_vecs): any FP32 layers of one d and W
+bool batchable_layers(ml_plan_s *const *L, int T)
+{
+    if (T < 2) return false;
+    for (int t = 0; t < T; ++t)
+        if (L[t]->prec != ML_F32 || L[t]->d != L[0]->d || L[t]->W != L[0]->W) return false;
     return true;
 }
 
@@ -135,6 +145,22 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             o.normalized = base == ML_NORMALIZED_A;
             o.alpha = 1.0 / T;
             ML_TRY(run_batch(layers, T, v, o, st));
+        }
+        return ML_OK;
+    }
+    if (per_layer && batchable_layers(layers, T)) {
+        // FP32 layers of one d and W: one launch per stage for all layers,
+        // each layer applying its operator to its own block
+        std::vector<ApplyVec> vs(T);
+        for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+            nv = 8;
+            for (int t = 0; t < T; ++t) nv = std::min(nv, pass_width(layers[t], b - c0));
+            for (int t = 0; t < T; ++t)
+                vs[t] = ApplyVec{X + (int64_t)t * n * b + c0, b, Y + (int64_t)t * n * b + c0, b, nv};
+            ApplyOpts o;
+            o.normalized = base == ML_NORMALIZED_A;
+            o.layer_vecs = vs.data();
+            ML_TRY(run_batch(layers, T, vs[0], o, st));
         }
         return ML_OK;
     }

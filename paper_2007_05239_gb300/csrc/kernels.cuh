@@ -223,6 +223,7 @@ struct InterpArgs {
     const void *grid;        // T [L2][L1][L0][nv]
     double alpha, shift, self;
     int normalized, accumulate, sorted_out;
+    int nsub;                // subproblems (batched launches)
 };
 
 template <int D>
@@ -401,19 +402,22 @@ __global__ void __launch_bounds__(256) k_spread_f32_batch(const SpreadArgs *__re
     spread_f32_block<D, W, NV>(a, blockIdx.x);
 }
 
-// FP64 form: one thread per point, one shared tile per CTA, taps in
-// double-word arithmetic on the FP32 pipes, accumulated exactly as integers
-// with 32-bit shared-memory atomics (order-free, deterministic).
+// FP64 form: one shared tile per CTA, taps in double-word arithmetic on the
+// FP32 pipes, accumulated exactly as integers with 32-bit shared-memory
+// atomics (order-free, deterministic).
 //  - the subproblem's inputs u = D^{-1/2} x are staged (FP64) and each vector
 //    gets a power-of-two scale with every tap < 2^21 and scale * sum|u| <= 2^30
 //    (fixed_scale); a tap p + e then goes to its cell as hi = round(p) and
 //    lo = round((p - hi + e) * 2^20) (fixed_split), so each cell keeps
 //    |sum hi| < 2^31 and |sum lo| <= 1024 * 0.75 * 2^20 (a subproblem has at
 //    most 1024 points);
-//  - the weights are the plan's double-word table; a row (qy, qz) forms
-//    u * w_y * w_z once, each of its W taps one exact product with w_x;
-//  - each lane walks its (qz, qy) rows from a lane-dependent start, so lanes
-//    whose points share a first tap hit different cells.
+//  - work items are (point, slab) pairs, the slab being the point's qz (d = 3)
+//    or qy (d = 2) plane of taps, numbered point-major and dealt to
+//    consecutive threads: the lanes that share a point write to different
+//    planes (distinct cells and banks, no same-address serialisation), and an
+//    item forms u * w_z (* w_y per row) once per row and one exact product
+//    with w_x per tap;
+//  - hi and lo live in separate planes so that each atomic spans all banks.
 // The tile is converted to FP64 exactly (hi + lo * 2^-20 has <= 51 bits).
 template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
@@ -426,9 +430,10 @@ __global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
     const int tc = tile_cells<D>(a.Pt);
     const int Pt = a.Pt;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int2 *tile = reinterpret_cast<int2 *>(smem_raw);                      // [NV][tc] (hi, lo)
-    double *su = reinterpret_cast<double *>(tile + (int64_t)NV * tc);      // [sub_max][NV]
-    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) tile[e] = make_int2(0, 0);
+    int *thi = reinterpret_cast<int *>(smem_raw);                          // [NV][tc]
+    int *tlo = thi + (int64_t)NV * tc;                                     // [NV][tc]
+    double *su = reinterpret_cast<double *>(tlo + (int64_t)NV * tc);       // [sub_max][NV]
+    for (int e = threadIdx.x; e < 2 * tc * NV; e += blockDim.x) thi[e] = 0;
     float lsum[NV], lmax[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) lsum[c] = lmax[c] = 0.0f;
@@ -464,54 +469,53 @@ __global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
     }
     __syncthreads();
     constexpr int NW = D * W;
-    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int NI = (D >= 2) ? W : 1;       // items per point: its qz (d = 3) or qy (d = 2) slabs
+    constexpr int ny = (D >= 3) ? W : 1;       // rows per item
     constexpr int UY = (W <= 8) ? ny : 1;
-    const int ry = (D == 2) ? lane % ny : (D == 3 ? (lane / nz) % ny : 0);
-    const int rz = (D == 3) ? lane % nz : 0;
-    const float2 one2 = make_float2(1.0f, 0.0f);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t j = start + i;
-        float2 u[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) u[c] = dw_split(su[i * NV + c] * (double)s_scale[c]);
+    const int nitems = cnt * NI;
+    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+        const int pl = it / NI;
+        const int o = it - pl * NI;
+        const int64_t j = start + pl;
         const float2 *wp = a.wts + j * NW;
-        float2 wx[W], wyr[ny];
+        float2 wx[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) wx[q] = wp[q];
-        // rotated rows: row q of this lane is row (q + r) mod n of the point
+        // u times the item's slab weight (w_z of qz = o in d = 3, w_y of qy = o in d = 2)
+        float2 us[NV];
 #pragma unroll
-        for (int q = 0; q < ny; ++q) {
-            int src = q + ry;
-            src -= (src >= ny) ? ny : 0;
-            wyr[q] = (D >= 2) ? wp[W + src] : one2;
+        for (int c = 0; c < NV; ++c) {
+            const float2 u = dw_split(su[pl * NV + c] * (double)s_scale[c]);
+            us[c] = (D >= 2) ? dw_mul(u, wp[(D - 1) * W + o]) : u;
         }
         const int off = a.offs[j];
         const int o0 = off & 1023, o1 = (off >> 10) & 1023, o2 = off >> 20;
-#pragma unroll 1
-        for (int qz0 = 0; qz0 < nz; ++qz0) {
-            int qz = qz0 + rz;
-            qz -= (qz >= nz) ? nz : 0;
-            const float2 wz = (D >= 3) ? wp[2 * W + qz] : one2;
+        const int base = (D == 1) ? o0 : ((D == 2) ? (o1 + o) * Pt + o0 : ((o2 + o) * Pt + o1) * Pt + o0);
 #pragma unroll UY
-            for (int qy0 = 0; qy0 < ny; ++qy0) {
-                int qy = qy0 + ry;
-                qy -= (qy >= ny) ? ny : 0;
-                const float2 wyz = (D >= 3) ? dw_mul(wz, wyr[qy0]) : wyr[qy0];
-                int *row = reinterpret_cast<int *>(tile + ((o2 + qz) * Pt + o1 + qy) * Pt + o0);
+        for (int qy = 0; qy < ny; ++qy) {
+            float2 ar[NV];
+            if (D >= 3) {
+                const float2 wy = wp[W + qy];
+#pragma unroll
+                for (int c = 0; c < NV; ++c) ar[c] = dw_mul(us[c], wy);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NV; ++c) ar[c] = us[c];
+            }
+            const int row = base + qy * Pt;
+#pragma unroll
+            for (int qx = 0; qx < W; ++qx) {
 #pragma unroll
                 for (int c = 0; c < NV; ++c) {
-                    const float2 ar = (D >= 2) ? dw_mul(u[c], wyz) : u[c];
-#pragma unroll
-                    for (int qx = 0; qx < W; ++qx) {
-                        const float p = __fmul_rn(ar.x, wx[qx].x);
-                        float e = fmaf(ar.x, wx[qx].x, -p);
-                        e = fmaf(ar.x, wx[qx].y, e);
-                        e = fmaf(ar.y, wx[qx].x, e);
-                        int hi, lo;
-                        fixed_split(p, e, hi, lo);
-                        atomicAdd(row + 2 * (c * tc + qx), hi);
-                        atomicAdd(row + 2 * (c * tc + qx) + 1, lo);
-                    }
+                    // exact product ar * w_x as p + e
+                    const float p = __fmul_rn(ar[c].x, wx[qx].x);
+                    float e = fmaf(ar[c].x, wx[qx].x, -p);
+                    e = fmaf(ar[c].x, wx[qx].y, e);
+                    e = fmaf(ar[c].y, wx[qx].x, e);
+                    int hi, lo;
+                    fixed_split(p, e, hi, lo);
+                    atomicAdd(thi + c * tc + row + qx, hi);
+                    atomicAdd(tlo + c * tc + row + qx, lo);
                 }
             }
         }
@@ -520,9 +524,9 @@ __global__ void __launch_bounds__(256) k_spread_f64(const SpreadArgs a)
     double *out = static_cast<double *>(a.scratch) + (int64_t)sub * tc * NV;
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
         const int c = e % NV, cell = e / NV;
-        const int2 t = tile[c * tc + cell];
-        // t.x + t.y * 2^-20 has at most 51 significant bits: exact in FP64
-        out[e] = fma((double)t.y, 0x1p-20, (double)t.x) * (double)(1.0f / s_scale[c]);
+        // hi + lo * 2^-20 has at most 51 significant bits: exact in FP64
+        out[e] = fma((double)tlo[c * tc + cell], 0x1p-20, (double)thi[c * tc + cell]) *
+                 (double)(1.0f / s_scale[c]);
     }
 }
 // ==================================================================== fold
@@ -815,11 +819,10 @@ __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int 
 
 // FP32 form: one thread per point.
 template <int D, int W, int NV>
-__global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
+__device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int sub)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);
-    const int sub = blockIdx.x;
     const int bin = a.sub_bin[sub], start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int Pt = a.Pt;
     const int tc = tile_cells<D>(Pt);
@@ -866,6 +869,22 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 #pragma unroll
         for (int c = 0; c < NV; ++c) interp_epilogue_f32(a, i, c, acc[c]);
     }
+}
+
+template <int D, int W, int NV>
+__global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
+{
+    interp_f32_block<D, W, NV>(a, blockIdx.x);
+}
+
+// all layers of a batch in one launch, each writing its own output block:
+// blockIdx.y is the layer
+template <int D, int W, int NV>
+__global__ void __launch_bounds__(256) k_interp_f32_batch(const InterpArgs *__restrict__ args)
+{
+    const InterpArgs a = args[blockIdx.y];
+    if ((int)blockIdx.x >= a.nsub) return;
+    interp_f32_block<D, W, NV>(a, blockIdx.x);
 }
 
 // FP64 form: one thread per point, on the FP32 pipes.  The grid arrives as
@@ -945,12 +964,18 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpArgs a)
 // order.  Up to kBatchPts points per thread.
 constexpr int kBatchPts = 4;
 
+// Layer groups: CTA (sub, g) sums the layers g*LG .. min(T, (g+1)*LG) - 1; with
+// more than one group each writes FP32 partial sums part[g][i][c] that
+// k_sum_parts adds up in group order.
 template <int D, int W, int NV>
-__global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__restrict__ args, int T)
+__global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__restrict__ args, int T, int LG,
+                                                        float *__restrict__ part, int64_t n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);
     const int sub = blockIdx.x;
+    const int g = blockIdx.y;
+    const int t0 = g * LG, t1 = min(T, t0 + LG);
     const InterpArgs a0 = args[0];
     const int start = a0.sub_start[sub], cnt = a0.sub_count[sub];
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
@@ -961,7 +986,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__rest
     for (int k = 0; k < kBatchPts; ++k)
 #pragma unroll
         for (int c = 0; c < NV; ++c) tot[k][c] = 0.0f;
-    for (int t = 0; t < T; ++t) {
+    for (int t = t0; t < t1; ++t) {
         const InterpArgs a = args[t];
         const int Pt = a.Pt;
         const int tc = tile_cells<D>(Pt);
@@ -1019,8 +1044,26 @@ __global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__rest
         const int li = threadIdx.x + k * blockDim.x;
         if (li >= cnt) break;
         const int i = start + li;
+        if (part) {
 #pragma unroll
-        for (int c = 0; c < NV; ++c) a0.Y[(int64_t)i * a0.ldy + c] = (double)tot[k][c];
+            for (int c = 0; c < NV; ++c) part[((int64_t)g * n + i) * NV + c] = tot[k][c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) a0.Y[(int64_t)i * a0.ldy + c] = (double)tot[k][c];
+        }
+    }
+}
+
+// Y[i, c] = sum over the G layer groups of part[g][i][c], in group order
+template <int NV>
+__global__ void k_sum_parts(const float *__restrict__ part, int G, int64_t n, double *Y, int ldy)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * NV; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / NV;
+        const int c = (int)(e - i * NV);
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += (double)part[(int64_t)g * n * NV + e];
+        Y[i * ldy + c] = s;
     }
 }
 

@@ -434,6 +434,44 @@ struct InverseOp {
     }
 };
 
+// Fix the sign of each column of V (n x k, column-major) so that its
+// largest-magnitude entry (the first one on ties) is positive.
+ml_status sign_fix_cols(double *V, int64_t n, int k, cudaStream_t st)
+{
+    const int cb = std::min(vec_blocks(n), 256);
+    DevBuf part, fd;
+    ML_TRY(part.ensure((size_t)cb * k * 3 * 8));
+    ML_TRY(fd.ensure((size_t)k * 8));
+    {
+        ProfScope pr_("vector", st);
+        k_colmax<<<cb, 256, 0, st>>>(V, n, n, k, part.as<double>());
+    }
+    std::vector<double> hp((size_t)cb * k * 3);
+    ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> f(k, 1.0);
+    for (int c = 0; c < k; ++c) {
+        double ba = -1, bv = 0, bi = 1e300;
+        for (int b = 0; b < cb; ++b) {
+            const double *e = &hp[((size_t)b * k + c) * 3];
+            if (e[0] > ba || (e[0] == ba && e[2] < bi)) {
+                ba = e[0];
+                bv = e[1];
+                bi = e[2];
+            }
+        }
+        f[c] = bv < 0 ? -1.0 : 1.0;
+    }
+    ML_CUDA(cudaMemcpyAsync(fd.p, f.data(), k * 8, cudaMemcpyHostToDevice, st));
+    {
+        ProfScope pr_("vector", st);
+        k_scale_cols<<<vec_blocks(n), 256, 0, st>>>(V, n, n, k, fd.as<double>());
+    }
+    ML_CUDA(cudaGetLastError());
+    ML_CUDA(cudaStreamSynchronize(st));
+    return ML_OK;
+}
+
 static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw, double tol, int maxit,
                               uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
 {
@@ -544,33 +582,7 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
             // ascending 1 - theta already; p = -1 maps descending mu to ascending 1/mu.
             if (evecs_dev) {
                 ML_CUDA(cudaMemcpyAsync(evecs_dev, Qtmp.p, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, st));
-                // sign: largest-magnitude entry positive
-                const int cb = std::min(nb, 256);
-                DevBuf part;
-                ML_TRY(part.ensure((size_t)cb * k * 3 * 8));
-                { ProfScope pr_("vector", st);
-                k_colmax<<<cb, 256, 0, st>>>(evecs_dev, n, n, k, part.as<double>());
-                }
-                std::vector<double> hp((size_t)cb * k * 3);
-                ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, st));
-                ML_CUDA(cudaStreamSynchronize(st));
-                std::vector<double> f(k, 1.0);
-                for (int c = 0; c < k; ++c) {
-                    double ba = -1, bv = 0, bi = 1e300;
-                    for (int b = 0; b < cb; ++b) {
-                        const double *e = &hp[((size_t)b * k + c) * 3];
-                        if (e[0] > ba || (e[0] == ba && e[2] < bi)) {
-                            ba = e[0];
-                            bv = e[1];
-                            bi = e[2];
-                        }
-                    }
-                    f[c] = bv < 0 ? -1.0 : 1.0;
-                }
-                ML_CUDA(cudaMemcpyAsync(Sd.p, f.data(), k * 8, cudaMemcpyHostToDevice, st));
-                { ProfScope pr_("vector", st);
-                k_scale_cols<<<nb, 256, 0, st>>>(evecs_dev, n, n, k, Sd.as<double>());
-                }
+                ML_TRY(sign_fix_cols(evecs_dev, n, k, st));
                 ML_CUDA(cudaGetLastError());
             }
             ML_CUDA(cudaStreamSynchronize(st));

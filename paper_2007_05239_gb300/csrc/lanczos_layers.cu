@@ -1,0 +1,689 @@
+// ml_lanczos_eigs_layers: for every layer t on its own, the k smallest
+// eigenpairs of L_sym^(t) = I - D_t^{-1/2} W_t D_t^{-1/2} (Sec. 2), i.e. the
+// k largest eigenpairs of the normalised operator A_t = D_t^{-1/2} W_t D_t^{-1/2},
+// by block thick-restart Lanczos with full reorthogonalisation (the Lanczos
+// method of Sec. 3 in block form).  All T problems advance in lockstep: each
+// block step applies every active layer's operator to its own block of b
+// vectors in one batched fast summation, then orthogonalises every layer's
+// block with kernels batched over the layers.
+//
+// Per layer t (FP64, device, point-major rows):
+//   Q_t  n x ldq, ldq = ncv + b: columns 0..ncv-1 the basis of the cycle,
+//        ncv..ncv+b-1 the next (residual) block;
+//   W_t  n x b, the product block.
+// One block step for the block Q[:, c:c+b] (cq = c + b):
+//   W = A_t Q[:, c:c+b]
+//   H1 = Q[:, 0:cq]^T W,  W -= Q[:, 0:cq] H1          (classical Gram-Schmidt)
+//   W = V1 R1                                         (SVQB)
+//   H2 = Q[:, 0:cq]^T V1, V1 -= Q[:, 0:cq] H2         (second Gram-Schmidt pass)
+//   V1 = V2 R2, Q[:, cq:cq+b] = V2                    (SVQB)
+// so that A Q[:, c:c+b] = Q[:, 0:cq] (H1 + H2 R1) + Q[:, cq:cq+b] (R2 R1): the
+// columns c..c+b-1 of the projected matrix T = Q^T A Q.
+// SVQB (Stathopoulos & Wu, SIAM J. Sci. Comput. 23 (2002)): G = W^T W,
+// S = diag(G)^{-1/2}, S G S = U L U^T, V = W S U L^{-1/2}, R = L^{1/2} U^T S^{-1};
+// directions with L_i <= 1e-20 max L are dropped (zero columns: the block
+// deflates instead of breaking down).
+// After ncv columns the host diagonalises each layer's T (ncv x ncv), checks
+// the residuals ||R_last S[last block, i]|| of the k largest Ritz values, and
+// restarts with the kkeep largest Ritz vectors plus the residual block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ml_internal.h"
+
+namespace ml {
+
+constexpr int kRows = 32;     // rows staged per chunk
+constexpr int kMaxLd = 96;    // basis columns incl. the residual block
+constexpr int kMaxBlk = 8;    // block size limit
+constexpr int kGramOut = 768; // Gram outputs per CTA (3 per thread)
+
+// per-layer row-major n x ld matrices at base + t * stride
+struct LMat {
+    double *base;
+    int64_t stride;
+    int ld;
+    __device__ __forceinline__ double *at(int t) const { return base + (int64_t)t * stride; }
+};
+
+// part[(y * gridDim.x + x) * rc * cb + r * cb + s] = sum over this CTA's rows i
+// of A_t[i, a0 + r] * B_t[i, b0 + s], t = lay[y]   (rc * cb <= kGramOut)
+__global__ void __launch_bounds__(256) k_lgram(LMat A, int a0, int rc, LMat B, int b0, int cb,
+                                              const int *__restrict__ lay, int64_t n, double *part)
+{
+    __shared__ double As[kRows][kMaxLd + 1];
+    __shared__ double Bs[kRows][kMaxBlk + 1];
+    const int t = lay[blockIdx.y];
+    const double *Ab = A.at(t), *Bb = B.at(t);
+    const int nout = rc * cb;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t i0 = (int64_t)blockIdx.x * kRows; i0 < n; i0 += (int64_t)gridDim.x * kRows) {
+        const int rows = (int)min((int64_t)kRows, n - i0);
+        for (int e = threadIdx.x; e < kRows * rc; e += blockDim.x) {
+            const int rr = e / rc, cc = e - rr * rc;
+            As[rr][cc] = rr < rows ? Ab[(i0 + rr) * A.ld + a0 + cc] : 0.0;
+        }
+        for (int e = threadIdx.x; e < kRows * cb; e += blockDim.x) {
+            const int rr = e / cb, cc = e - rr * cb;
+            Bs[rr][cc] = rr < rows ? Bb[(i0 + rr) * B.ld + b0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int e = threadIdx.x + q * 256;
+            if (e < nout) {
+                const int r = e / cb, s = e - r * cb;
+                double v = acc[q];
+#pragma unroll 8
+                for (int rr = 0; rr < kRows; ++rr) v = fma(As[rr][r], Bs[rr][s], v);
+                acc[q] = v;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = threadIdx.x + q * 256;
+        if (e < nout) part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * nout + e] = acc[q];
+    }
+}
+
+// out[y][e] = sum over the nbx partial blocks in a fixed order; with rec,
+// also rec[lay[y] * rstride + e] = out[y][e]
+__global__ void k_lreduce(const double *__restrict__ part, int nbx, int nout, const int *__restrict__ lay,
+                          double *out, double *rec, int64_t rstride)
+{
+    const int y = blockIdx.y;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nout; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int bx = 0; bx < nbx; ++bx) s += part[((int64_t)y * nbx + bx) * nout + e];
+        out[(int64_t)y * nout + e] = s;
+        if (rec) rec[(int64_t)lay[y] * rstride + e] = s;
+    }
+}
+
+// B_t[i, b0 + s] = x  or  B_t[i, b0 + s] -= x,  x = sum_{r < rc} A_t[i, a0 + r] M_y[r, s]
+// (M_y = M + y * rc * cb, row-major rc x cb).  Rows are staged per chunk, so
+// B may be A (in place on the same columns).
+__global__ void __launch_bounds__(256) k_lgemm(LMat A, int a0, int rc, const double *__restrict__ M, LMat B, int b0,
+                                              int cb, const int *__restrict__ lay, int64_t n, int sub)
+{
+    extern __shared__ double lsm[];
+    double *Ms = lsm;                 // rc * cb
+    double *As = lsm + rc * cb;       // kRows x (rc + 1)
+    const int t = lay[blockIdx.y];
+    const double *Ab = A.at(t);
+    double *Bb = B.at(t);
+    const double *My = M + (int64_t)blockIdx.y * rc * cb;
+    for (int e = threadIdx.x; e < rc * cb; e += blockDim.x) Ms[e] = My[e];
+    const int lda = rc + 1;
+    for (int64_t i0 = (int64_t)blockIdx.x * kRows; i0 < n; i0 += (int64_t)gridDim.x * kRows) {
+        const int rows = (int)min((int64_t)kRows, n - i0);
+        __syncthreads();   // the previous chunk is no longer read (and Ms is loaded)
+        for (int e = threadIdx.x; e < rows * rc; e += blockDim.x) {
+            const int rr = e / rc, cc = e - rr * rc;
+            As[rr * lda + cc] = Ab[(i0 + rr) * A.ld + a0 + cc];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * cb; e += blockDim.x) {
+            const int rr = e / cb, s = e - rr * cb;
+            double x = 0.0;
+            for (int r = 0; r < rc; ++r) x = fma(As[rr * lda + r], Ms[r * cb + s], x);
+            double *bp = Bb + (i0 + rr) * B.ld + b0 + s;
+            *bp = sub ? *bp - x : x;
+        }
+    }
+}
+
+// One thread per slot: SVQB of the B x B Gram G_y.  Writes the transform M_y
+// (V = W M) and R (W = V R): into Rs_y on the first pass, and R2 * Rs_y into
+// rec[lay[y] * rstride] on the second.  flags[lay[y]] |= 1 when a direction
+// was dropped.  B is a template parameter so that the matrices stay in
+// registers.
+template <int B>
+__global__ void k_lsvqb(const double *__restrict__ G, int nslots, const int *__restrict__ lay, double *M, double *Rs,
+                        double *rec, int64_t rstride, int pass, int *flags)
+{
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= nslots) return;
+    const int t = lay[y];
+    double g[B][B], u[B][B], sc[B], lam[B];
+    const double *Gy = G + (int64_t)y * B * B;
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const double d = Gy[i * B + i];
+        sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            g[i][j] = 0.5 * (Gy[i * B + j] + Gy[j * B + i]) * sc[i] * sc[j];
+            u[i][j] = (i == j) ? 1.0 : 0.0;
+        }
+    // cyclic Jacobi on the scaled Gram (entries below 1e-18 of the diagonal
+    // scale are not rotated; quadratic convergence ends it in a few sweeps)
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        bool rotated = false;
+#pragma unroll
+        for (int p = 0; p < B - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < B; ++q) {
+                const double apq = g[p][q];
+                if (fabs(apq) <= 1e-18 * (fabs(g[p][p]) + fabs(g[q][q])) + 1e-300) continue;
+                rotated = true;
+                const double tau = (g[q][q] - g[p][p]) / (2.0 * apq);
+                const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const double akp = g[k][p], akq = g[k][q];
+                    g[k][p] = c * akp - s * akq;
+                    g[k][q] = s * akp + c * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const double apk = g[p][k], aqk = g[q][k];
+                    g[p][k] = c * apk - s * aqk;
+                    g[q][k] = s * apk + c * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const double ukp = u[k][p], ukq = u[k][q];
+                    u[k][p] = c * ukp - s * ukq;
+                    u[k][q] = s * ukp + c * ukq;
+                }
+            }
+        if (!rotated) break;
+    }
+    double lmax = 0.0;
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        lam[i] = g[i][i];
+        lmax = fmax(lmax, lam[i]);
+    }
+    int dropped = 0;
+    double R[B][B];
+    double *My = M + (int64_t)y * B * B;
+#pragma unroll
+    for (int s = 0; s < B; ++s) {
+        const bool keep = lmax > 0.0 && lam[s] > 1e-20 * lmax;
+        dropped |= keep ? 0 : 1;
+        const double il = keep ? 1.0 / sqrt(lam[s]) : 0.0, sl = keep ? sqrt(lam[s]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < B; ++r) My[r * B + s] = sc[r] * u[r][s] * il;
+#pragma unroll
+        for (int q = 0; q < B; ++q) R[s][q] = (sc[q] > 0.0) ? sl * u[q][s] / sc[q] : 0.0;
+    }
+    double *Ry = Rs + (int64_t)y * B * B;
+    if (pass == 0) {
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int j = 0; j < B; ++j) Ry[i * B + j] = R[i][j];
+    } else if (rec) {
+        double *Rt = rec + (int64_t)t * rstride;
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                double x = 0.0;
+#pragma unroll
+                for (int q = 0; q < B; ++q) x = fma(R[i][q], Ry[q * B + j], x);
+                Rt[i * B + j] = x;
+            }
+    }
+    if (dropped && flags) flags[t] |= 1;
+}
+
+// rec_t[r, s] += sum_q H2_y[r, q] Rs_y[q, s]   (r < rc): the second pass's
+// coefficients mapped back to the product block
+__global__ void k_lhacc(const double *__restrict__ H2, const double *__restrict__ Rs, int rc, int b,
+                        const int *__restrict__ lay, double *rec, int64_t rstride)
+{
+    const int y = blockIdx.y;
+    const double *H = H2 + (int64_t)y * rc * b, *R = Rs + (int64_t)y * b * b;
+    double *out = rec + (int64_t)lay[y] * rstride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rc * b; e += gridDim.x * blockDim.x) {
+        const int r = e / b, s = e - r * b;
+        double x = 0.0;
+        for (int q = 0; q < b; ++q) x = fma(H[r * b + q], R[q * b + s], x);
+        out[e] += x;
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) of a counter, mapped to (-1, 1)
+__device__ __forceinline__ double lz_uniform(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// Q_t[i, c0 + s] = random, an independent stream per layer
+__global__ void k_lrandom(LMat Q, int c0, int b, const int *__restrict__ lay, uint64_t seed, int64_t n)
+{
+    const int t = lay[blockIdx.y];
+    double *Qt = Q.at(t);
+    const uint64_t sd = seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(t + 1));
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * b; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / b;
+        const int s = (int)(e - i * b);
+        Qt[i * Q.ld + c0 + s] = lz_uniform(sd, (uint64_t)e);
+    }
+}
+
+// B_t[i, b0 + s] = A_t[i, a0 + s], s < cols
+__global__ void k_lcopy(LMat A, int a0, LMat B, int b0, int cols, const int *__restrict__ lay, int64_t n)
+{
+    const int t = lay[blockIdx.y];
+    const double *At = A.at(t);
+    double *Bt = B.at(t);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols;
+        const int s = (int)(e - i * cols);
+        Bt[i * B.ld + b0 + s] = At[i * A.ld + a0 + s];
+    }
+}
+
+// out[j * n + i] = Q_t[i, j] for j < k (column-major n x k)
+__global__ void k_lcolmajor(LMat Q, int t, int k, int64_t n, double *out)
+{
+    const double *Qt = Q.at(t);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n);
+        const int64_t i = e - (int64_t)j * n;
+        out[e] = Qt[i * Q.ld + j];
+    }
+}
+
+// --------------------------------------------------------------------- host
+namespace {
+
+struct Solver {
+    ml_plan_s *const *L;
+    int T, k, b;
+    int64_t n;
+    int ncv = 0, ldq = 0, kkeep = 0, nsteps_max = 0;
+    int nbx = 1;
+    cudaStream_t st;
+    DevBuf Q[2], Wb, part, hcur, Gs, Ms, Rs, Hrec, Rrec, Sd, layd, flags;
+    DescSlot desc;
+    int64_t hstride = 0, rstride = 0;   // per layer record strides (doubles)
+    int nslots = 0;                     // active layers
+    std::vector<int> lay;               // slot -> layer
+
+    LMat q(int which) const { return LMat{Q[which].as<double>(), n * ldq, ldq}; }
+    LMat w() const { return LMat{Wb.as<double>(), n * b, b}; }
+
+    ml_status upload_lay()
+    {
+        nslots = (int)lay.size();
+        ML_CUDA(cudaMemcpyAsync(layd.p, lay.data(), lay.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        ML_CUDA(cudaStreamSynchronize(st));   // lay is host memory that changes later
+        nbx = (int)std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, (152 * 8 + nslots - 1) / nslots));
+        return ML_OK;
+    }
+
+    // out[y] (rc x cb) = A_t[:, a0:a0+rc]^T B_t[:, b0:b0+cb]; optionally recorded
+    ml_status gram(LMat A, int a0, int rc, LMat B, int b0, int cb, double *out, double *rec, int64_t rs)
+    {
+        const int nout = rc * cb;
+        if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
+        {
+            ProfScope pr("dots", st);
+            k_lgram<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>());
+        }
+        {
+            ProfScope pr("dots_reduce", st);
+            k_lreduce<<<dim3((nout + 127) / 128, nslots), 128, 0, st>>>(part.as<double>(), nbx, nout, layd.as<int>(),
+                                                                       out, rec, rs);
+        }
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+
+    ml_status gemm(LMat A, int a0, int rc, const double *M, LMat B, int b0, int cb, bool sub)
+    {
+        const size_t smem = ((size_t)rc * cb + (size_t)kRows * (rc + 1)) * sizeof(double);
+        ProfScope pr("update", st);
+        k_lgemm<<<dim3(nbx, nslots), 256, smem, st>>>(A, a0, rc, M, B, b0, cb, layd.as<int>(), n, sub ? 1 : 0);
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+
+    ml_status svqb(int pass, double *rec)
+    {
+        ProfScope pr("svqb", st);
+        const dim3 grid((nslots + 31) / 32);
+        double *G = Gs.as<double>(), *Mp = Ms.as<double>(), *Rp = Rs.as<double>();
+        const int *ly = layd.as<int>();
+        int *fl = flags.as<int>();
+        switch (b) {
+#define ML_SVQB_CASE(BB) \
+    case BB: k_lsvqb<BB><<<grid, 32, 0, st>>>(G, nslots, ly, Mp, Rp, rec, rstride, pass, fl); break;
+            ML_SVQB_CASE(1)
+            ML_SVQB_CASE(2)
+            ML_SVQB_CASE(3)
+            ML_SVQB_CASE(4)
+            ML_SVQB_CASE(5)
+            ML_SVQB_CASE(6)
+            ML_SVQB_CASE(7)
+            ML_SVQB_CASE(8)
+#undef ML_SVQB_CASE
+        default: return fail(ML_ERR_ARG, "block size out of range");
+        }
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+
+    // orthonormalise the block W (columns 0..b-1 of w()) against Q[:, 0:cq]
+    // (cq > 0) and within itself; result into Q_dst[:, d0:d0+b].  hrec/rrec:
+    // this step's records (hrec null: no Gram-Schmidt coefficients kept).
+    ml_status orthonormalise(int cur, int cq, LMat dst, int d0, double *hrec, double *rrec)
+    {
+        const LMat Qc = q(cur), Wm = w();
+        double *h = hcur.as<double>();
+        if (cq > 0) {
+            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, hrec, hstride));
+            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true));
+        }
+        ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
+        ML_TRY(svqb(0, nullptr));
+        ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), Wm, 0, b, false));
+        if (cq > 0) {
+            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, nullptr, 0));
+            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true));
+            if (hrec) {
+                ProfScope pr("svqb", st);
+                k_lhacc<<<dim3((cq * b + 127) / 128, nslots), 128, 0, st>>>(h, Rs.as<double>(), cq, b, layd.as<int>(),
+                                                                           hrec, hstride);
+                ML_CUDA(cudaGetLastError());
+            }
+        }
+        ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
+        ML_TRY(svqb(1, rrec));
+        ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), dst, d0, b, false));
+        return ML_OK;
+    }
+
+    // W_t = A_t Q_t[:, c:c+b] for the active layers
+    ml_status apply(int cur, int c)
+    {
+        std::vector<ml_plan_s *> pl(nslots);
+        for (int y = 0; y < nslots; ++y) pl[y] = L[lay[y]];
+        double *Qb = Q[cur].as<double>(), *Wp = Wb.as<double>();
+        ApplyOpts o;
+        o.normalized = true;
+        if (nslots >= 2 && batchable_layers(pl.data(), nslots)) {
+            std::vector<ApplyVec> vs(nslots);
+            for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+                nv = 8;
+                for (int y = 0; y < nslots; ++y) nv = std::min(nv, pass_width(pl[y], b - c0));
+                for (int y = 0; y < nslots; ++y) {
+                    const int t = lay[y];
+                    vs[y] = ApplyVec{Qb + (int64_t)t * n * ldq + c + c0, ldq, Wp + (int64_t)t * n * b + c0, b, nv};
+                }
+                o.layer_vecs = vs.data();
+                o.desc = &desc;
+                ML_TRY(run_batch(pl.data(), nslots, vs[0], o, st));
+            }
+            return ML_OK;
+        }
+        for (int y = 0; y < nslots; ++y) {
+            const int t = lay[y];
+            for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+                nv = pass_width(pl[y], b - c0);
+                ApplyVec v{Qb + (int64_t)t * n * ldq + c + c0, ldq, Wp + (int64_t)t * n * b + c0, b, nv};
+                ML_TRY(apply_layer(pl[y], v, o, st));
+            }
+        }
+        return ML_OK;
+    }
+};
+
+}  // namespace
+
+static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int maxit, int b, uint64_t seed,
+                             double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
+{
+    Solver S;
+    S.L = L;
+    S.T = T;
+    S.k = k;
+    S.b = b;
+    S.n = L[0]->n;
+    S.st = st;
+    const int64_t n = S.n;
+    const int target = std::max(2 * k + 1, 20);
+    int ncv = b * ((target + 2 * b - 1) / b);
+    ncv = (int)std::min<int64_t>(ncv, (int64_t)b * ((n - b) / b));
+    const int keep_goal = std::max(k + 1, (ncv + k) / 2);
+    int kkeep = ncv - b * ((ncv - keep_goal + b - 1) / b);
+    if (ncv + b > kMaxLd || (ncv + b) * b > kGramOut)
+        return fail(ML_ERR_ARG, "k too large for the block size (basis beyond " + std::to_string(kMaxLd) + " columns)");
+    if (kkeep < k + 1 || kkeep >= ncv) return fail(ML_ERR_ARG, "n too small for k and the block size");
+    S.ncv = ncv;
+    S.ldq = ncv + b;
+    S.kkeep = kkeep;
+    S.nsteps_max = ncv / b;
+    S.hstride = (int64_t)S.nsteps_max * S.ldq * b;
+    S.rstride = (int64_t)S.nsteps_max * b * b;
+    const int ldq = S.ldq;
+    for (int w = 0; w < 2; ++w) ML_TRY(S.Q[w].ensure((size_t)T * n * ldq * sizeof(double)));
+    ML_TRY(S.Wb.ensure((size_t)T * n * b * sizeof(double)));
+    const int64_t nbx_max = std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, 152 * 8));
+    ML_TRY(S.part.ensure((size_t)T * nbx_max * kGramOut * sizeof(double) + 64));
+    ML_TRY(S.hcur.ensure((size_t)T * ldq * b * sizeof(double)));
+    ML_TRY(S.Gs.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.Ms.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.Rs.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.Hrec.ensure((size_t)T * S.hstride * sizeof(double)));
+    ML_TRY(S.Rrec.ensure((size_t)T * S.rstride * sizeof(double)));
+    ML_TRY(S.Sd.ensure((size_t)T * ncv * kkeep * sizeof(double)));
+    ML_TRY(S.layd.ensure((size_t)T * sizeof(int)));
+    ML_TRY(S.flags.ensure((size_t)T * sizeof(int)));
+    ML_CUDA(cudaMemsetAsync(S.flags.p, 0, (size_t)T * sizeof(int), st));
+    {
+        const size_t smax = ((size_t)kMaxLd * kMaxLd + (size_t)kRows * (kMaxLd + 1)) * sizeof(double);
+        ML_CUDA(cudaFuncSetAttribute(k_lgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    }
+    S.lay.resize(T);
+    for (int t = 0; t < T; ++t) S.lay[t] = t;
+    ML_TRY(S.upload_lay());
+
+    // start blocks: random, orthonormalised
+    int cur = 0;
+    {
+        ProfScope pr("vector", st);
+        k_lrandom<<<dim3(std::max(1, S.nbx * 4), S.nslots), 256, 0, st>>>(S.w(), 0, b, S.layd.as<int>(), seed, n);
+    }
+    ML_CUDA(cudaGetLastError());
+    ML_TRY(S.orthonormalise(cur, 0, S.q(cur), 0, nullptr, nullptr));
+
+    std::vector<std::vector<double>> Tm(T, std::vector<double>((size_t)ncv * ncv, 0.0));
+    std::vector<int> nconv(T, 0), matvecs(T, 0);
+    std::vector<char> done(T, 0);
+    std::vector<double> hrec_h, rrec_h, theta, Sv;
+    int kk = 0;
+    while (S.nslots > 0) {
+        const int nsteps = (ncv - kk) / b;
+        for (int j = 0; j < nsteps; ++j) {
+            const int c = kk + j * b;
+            ML_TRY(S.apply(cur, c));
+            double *hr = S.Hrec.as<double>() + (int64_t)j * ldq * b;
+            double *rr = S.Rrec.as<double>() + (int64_t)j * b * b;
+            ML_TRY(S.orthonormalise(cur, c + b, S.q(cur), c + b, hr, rr));
+        }
+        for (int y = 0; y < S.nslots; ++y) matvecs[S.lay[y]] += nsteps * b;
+        // records of the cycle to the host
+        hrec_h.resize((size_t)T * S.hstride);
+        rrec_h.resize((size_t)T * S.rstride);
+        ML_CUDA(cudaMemcpyAsync(hrec_h.data(), S.Hrec.p, hrec_h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaMemcpyAsync(rrec_h.data(), S.Rrec.p, rrec_h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> Sh((size_t)S.nslots * ncv * kkeep, 0.0);
+        std::vector<std::vector<double>> th_keep(S.nslots), coup(S.nslots);
+        std::vector<int> finishing;
+        for (int y = 0; y < S.nslots; ++y) {
+            const int t = S.lay[y];
+            std::vector<double> &Tt = Tm[t];
+            const double *H = hrec_h.data() + (int64_t)t * S.hstride;
+            const double *R = rrec_h.data() + (int64_t)t * S.rstride;
+            for (int j = 0; j < nsteps; ++j) {
+                const int c = kk + j * b;
+                for (int s = 0; s < b; ++s) {
+                    const int col = c + s;
+                    for (int r = 0; r < c + b; ++r) {
+                        double v = H[(int64_t)j * ldq * b + (int64_t)r * b + s];
+                        if (r < kk && c != kk) v = 0.0;   // zero by the restart structure
+                        Tt[(size_t)r * ncv + col] = v;
+                        Tt[(size_t)col * ncv + r] = v;
+                    }
+                    if (j + 1 < nsteps)
+                        for (int qq = 0; qq < b; ++qq) {
+                            const double v = R[(int64_t)j * b * b + qq * b + s];
+                            Tt[(size_t)(c + b + qq) * ncv + col] = v;
+                            Tt[(size_t)col * ncv + c + b + qq] = v;
+                        }
+                }
+            }
+            const double *Rl = R + (int64_t)(nsteps - 1) * b * b;
+            std::vector<double> a = Tt;
+            sym_eig(ncv, a, theta, Sv);
+            double tmax = 0.0;
+            for (double x : theta) tmax = std::max(tmax, std::fabs(x));
+            // coupling of each Ritz vector to the residual block: Rl * S[last block, i]
+            auto coupling = [&](int col, int qq) {
+                double x = 0.0;
+                for (int s = 0; s < b; ++s) x += Rl[qq * b + s] * Sv[(size_t)(ncv - b + s) * ncv + col];
+                return x;
+            };
+            int nc = 0;
+            for (int i = ncv - 1; i >= ncv - k; --i) {
+                double r2 = 0.0;
+                for (int qq = 0; qq < b; ++qq) {
+                    const double x = coupling(i, qq);
+                    r2 += x * x;
+                }
+                if (std::sqrt(r2) <= tol * std::max(tmax, 1e-300)) ++nc;
+                else break;
+            }
+            nconv[t] = nc;
+            const bool fin = nc >= k || matvecs[t] >= maxit;
+            if (fin) finishing.push_back(y);
+            th_keep[y].resize(kkeep);
+            coup[y].assign((size_t)b * kkeep, 0.0);
+            for (int i = 0; i < kkeep; ++i) {
+                const int col = ncv - 1 - i;   // descending theta
+                th_keep[y][i] = theta[col];
+                for (int c2 = 0; c2 < ncv; ++c2) Sh[((size_t)y * ncv + c2) * kkeep + i] = Sv[(size_t)c2 * ncv + col];
+                for (int qq = 0; qq < b; ++qq) coup[y][(size_t)qq * kkeep + i] = coupling(col, qq);
+            }
+            if (fin)
+                for (int i = 0; i < k; ++i) evals[(size_t)t * k + i] = 1.0 - th_keep[y][i];
+        }
+        // Ritz vectors of every active layer -> the other basis buffer
+        ML_CUDA(cudaMemcpyAsync(S.Sd.p, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        {
+            ProfScope pr("ritz", st);
+            ML_TRY(S.gemm(S.q(cur), 0, ncv, S.Sd.as<double>(), S.q(cur ^ 1), 0, kkeep, false));
+            k_lcopy<<<dim3(std::max(1, S.nbx * 4), S.nslots), 256, 0, st>>>(S.q(cur), ncv, S.q(cur ^ 1), kkeep, b,
+                                                                             S.layd.as<int>(), n);
+        }
+        ML_CUDA(cudaGetLastError());
+        for (int y : finishing) {
+            const int t = S.lay[y];
+            done[t] = 1;
+            if (evecs_dev) {
+                double *out = evecs_dev + (int64_t)t * n * k;
+                {
+                    ProfScope pr("vector", st);
+                    k_lcolmajor<<<(int)std::min<int64_t>((n * k + 255) / 256, 152 * 16), 256, 0, st>>>(S.q(cur ^ 1), t,
+                                                                                                      k, n, out);
+                }
+                ML_CUDA(cudaGetLastError());
+                ML_TRY(sign_fix_cols(out, n, k, st));
+            }
+        }
+        // restart the others: T = diag(theta_keep) with the residual coupling
+        std::vector<int> next;
+        for (int y = 0; y < S.nslots; ++y) {
+            const int t = S.lay[y];
+            if (done[t]) continue;
+            next.push_back(t);
+            std::vector<double> &Tt = Tm[t];
+            std::fill(Tt.begin(), Tt.end(), 0.0);
+            for (int i = 0; i < kkeep; ++i) {
+                Tt[(size_t)i * ncv + i] = th_keep[y][i];
+                for (int qq = 0; qq < b; ++qq) {
+                    const double v = coup[y][(size_t)qq * kkeep + i];
+                    Tt[(size_t)(kkeep + qq) * ncv + i] = v;
+                    Tt[(size_t)i * ncv + kkeep + qq] = v;
+                }
+            }
+        }
+        cur ^= 1;
+        kk = kkeep;
+        if (next.size() != S.lay.size()) {
+            S.lay = next;
+            if (!S.lay.empty()) ML_TRY(S.upload_lay());
+            else S.nslots = 0;
+        }
+    }
+    ML_CUDA(cudaStreamSynchronize(st));
+    int all = 1;
+    for (int t = 0; t < T; ++t) {
+        if (nconv_out) nconv_out[t] = std::min(nconv[t], k);
+        if (nconv[t] < k) all = 0;
+    }
+    return all ? ML_OK : ML_WARN_NOT_CONVERGED;
+}
+
+}  // namespace ml
+
+extern "C" ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
+                                            uint64_t seed, double *evals, double *evecs, int *nconv, void *stream)
+{
+    using namespace ml;
+    if (!layers || T < 1) return fail(ML_ERR_ARG, "layers is null or T < 1");
+    for (int t = 0; t < T; ++t)
+        if (!layers[t]) return fail(ML_ERR_ARG, "null layer");
+    const int64_t n = layers[0]->n;
+    for (int t = 1; t < T; ++t)
+        if (layers[t]->n != n) return fail(ML_ERR_ARG, "layers do not share n");
+    if (block < 1 || block > kMaxBlk) return fail(ML_ERR_ARG, "block must be in [1, 8]");
+    if (k < 1 || k > n / 2) return fail(ML_ERR_ARG, "k must be in [1, n/2]");
+    for (int t = 0; t < T; ++t)
+        if (!layers[t]->deg_ok) return fail(ML_ERR_DEGREE, "a layer has a degree <= 0: L_sym is undefined");
+    if (!evals) return fail(ML_ERR_ARG, "evals is null");
+    if (tol <= 0) tol = 1e-10;
+    if (maxit <= 0) maxit = 2000;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *evd = nullptr;
+    DevBuf stage;
+    bool host_out = false;
+    if (evecs) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, evecs) == cudaSuccess &&
+            (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+            evd = evecs;
+        } else {
+            cudaGetLastError();
+            ML_TRY(stage.ensure((size_t)T * n * k * sizeof(double)));
+            evd = stage.as<double>();
+            host_out = true;
+        }
+    }
+    ml_status s = layers_impl(layers, T, k, tol, maxit, block, seed, evals, evd, nconv, st);
+    if ((s == ML_OK || s == ML_WARN_NOT_CONVERGED) && host_out)
+        ML_CUDA(cudaMemcpy(evecs, evd, (size_t)T * n * k * sizeof(double), cudaMemcpyDeviceToHost));
+    return s;
+}

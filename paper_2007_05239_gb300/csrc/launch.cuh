@@ -186,6 +186,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.normalized = o.normalized;
     ia.accumulate = o.accumulate;
     ia.sorted_out = o.sorted_out;
+    ia.nsub = p->nsub;
     if (p->nsub > 0) {
         const size_t smem = (size_t)tc * nv * sizeof(T);
         ProfScope pr("interp", st);
@@ -267,6 +268,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     for (int s = 0; s < 2 * D; ++s) max_px[s] = max_ky[s] = 1;
     for (int t = 0; t < T; ++t) {
         ml_plan_s *p = L[t];
+        const ApplyVec &vt = o.layer_vecs ? o.layer_vecs[t] : v;
         const GridGeom &g = p->g;
         const int tc = (int)g.tile_cells();
         const int64_t tile_elems = (int64_t)tc * NV;
@@ -281,8 +283,8 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         a.perm = p->perm.as<int>();
         a.coords = p->coords.p;
         a.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
-        a.X = v.X;
-        a.ldx = v.ldx;
+        a.X = vt.X;
+        a.ldx = vt.ldx;
         a.nv = NV;
         a.B = g.B;
         a.Pt = g.Pt;
@@ -345,11 +347,12 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         ip.perm = a.perm;
         ip.coords = a.coords;
         ip.dinv = a.dinv;
-        ip.X = v.X;
-        ip.ldx = v.ldx;
-        ip.Y = v.Y;
-        ip.ldy = v.ldy;
+        ip.X = vt.X;
+        ip.ldx = vt.ldx;
+        ip.Y = vt.Y;
+        ip.ldy = vt.ldy;
         ip.nv = NV;
+        ip.nsub = p->nsub;
         ip.B = g.B;
         ip.Pt = g.Pt;
         ip.nb0 = g.nb[0];
@@ -368,6 +371,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         ip.shift = 0.0;
         ip.self = o.self;
         ip.normalized = o.normalized;
+        ip.accumulate = o.accumulate;
         max_nsub = std::max(max_nsub, p->nsub);
         max_ng = std::max(max_ng, p->ngroups);
         max_nbins = std::max(max_nbins, (int)g.nbins());
@@ -386,13 +390,15 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     memcpy(blob.data() + o_ma, ma.data(), sizeof(MultArgs) * T);
     memcpy(blob.data() + o_ia, ia.data(), sizeof(InterpArgs) * T);
     ml_plan_s *p0 = L[0];
-    if (p0->batch_host != blob) {
-        ML_TRY(p0->batch_desc.ensure(total));
-        ML_CUDA(cudaMemcpyAsync(p0->batch_desc.p, blob.data(), total, cudaMemcpyHostToDevice, st));
+    DevBuf &ddev = o.desc ? o.desc->dev : p0->batch_desc;
+    std::vector<unsigned char> &dhost = o.desc ? o.desc->host : p0->batch_host;
+    if (dhost != blob) {
+        ML_TRY(ddev.ensure(total));
+        ML_CUDA(cudaMemcpyAsync(ddev.p, blob.data(), total, cudaMemcpyHostToDevice, st));
         ML_CUDA(cudaStreamSynchronize(st));   // the host blob is reused at once
-        p0->batch_host.swap(blob);
+        dhost.swap(blob);
     }
-    unsigned char *d = p0->batch_desc.as<unsigned char>();
+    unsigned char *d = ddev.as<unsigned char>();
     {
         ProfScope pr("spread", st);
         const size_t smem = (size_t)max_tile * NV * sizeof(int);
@@ -423,8 +429,31 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     {
         ProfScope pr("interp", st);
         const size_t smem = (size_t)max_tile * NV * sizeof(float);
-        ML_TRY(set_smem(k_interp_f32_sum<D, W, NV>, smem));
-        k_interp_f32_sum<D, W, NV><<<max_nsub, 256, smem, st>>>(reinterpret_cast<InterpArgs *>(d + o_ia), T);
+        if (o.layer_vecs) {
+            ML_TRY(set_smem(k_interp_f32_batch<D, W, NV>, smem));
+            k_interp_f32_batch<D, W, NV><<<dim3(max_nsub, T), 256, smem, st>>>(
+                reinterpret_cast<InterpArgs *>(d + o_ia));
+        } else {
+            // enough CTAs to fill the GPU: split the layers into groups whose
+            // partial sums are added in a fixed order afterwards
+            const int G = std::max(1, std::min(T, (152 * 6 + max_nsub - 1) / max_nsub));
+            const int LG = (T + G - 1) / G;
+            const int Gu = (T + LG - 1) / LG;
+            const int64_t n = p0->n;
+            float *part = nullptr;
+            if (Gu > 1) {
+                ML_TRY(p0->batch_part.ensure((size_t)Gu * n * NV * sizeof(float)));
+                part = p0->batch_part.as<float>();
+            }
+            ML_TRY(set_smem(k_interp_f32_sum<D, W, NV>, smem));
+            k_interp_f32_sum<D, W, NV><<<dim3(max_nsub, Gu), 256, smem, st>>>(reinterpret_cast<InterpArgs *>(d + o_ia),
+                                                                             T, LG, part, n);
+            if (Gu > 1) {
+                ML_CUDA(cudaGetLastError());
+                const int blocks = (int)std::min<int64_t>((n * NV + 255) / 256, 152 * 16);
+                k_sum_parts<NV><<<blocks, 256, 0, st>>>(part, Gu, n, v.Y, v.ldy);
+            }
+        }
         ML_CUDA(cudaGetLastError());
     }
     for (int t = 0; t < T; ++t) L[t]->applied += NV;

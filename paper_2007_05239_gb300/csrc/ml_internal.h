@@ -38,9 +38,26 @@ constexpr int kBatchPtsTotal = 1024; // points per CTA of the batched interpolat
 constexpr int kGroupSubs = 64;   // most subproblem tiles summed per group before the fold
 
 // ------------------------------------------------------------ device buffer
+// Owns one device allocation (freed on destruction; movable, not copyable).
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept
+    {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
     ml_status ensure(size_t nbytes);   // grow (contents not kept)
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
@@ -123,6 +140,7 @@ struct ml_plan_s {
     ml::DevBuf stage_x, stage_y;  // staging for host X / Y
     ml::DevBuf status;    // int flags written by device code
     ml::DevBuf batch_desc;               // per-layer descriptors of a batched apply led by this plan
+    ml::DevBuf batch_part;               // per-group partial sums of a batched multilayer apply
     std::vector<unsigned char> batch_host;  // host copy of the uploaded descriptors
     int64_t device_bytes() const;
 };
@@ -156,6 +174,13 @@ struct ApplyVec {      // one pass over up to kMaxVec vectors
     int nv;            // vectors in this pass
 };
 
+// Device copy of the per-layer argument records of a batched pass, with the
+// host image last uploaded (re-uploaded only when it changes).
+struct DescSlot {
+    DevBuf dev;
+    std::vector<unsigned char> host;
+};
+
 // layer apply: y (+)= alpha * post(D^{-1/2}) * (W~ u - u),  u = pre(D^{-1/2}) * x
 struct ApplyOpts {
     bool normalized = false;   // pre- and post-scale by D^{-1/2}
@@ -164,6 +189,11 @@ struct ApplyOpts {
     double alpha = 1.0;
     double shift = 0.0;        // adds shift * x (input order) to the output: used for L_sym + delta I
     double self = 1.0;         // K(0): subtracted self term coefficient
+    // batched passes only: per-layer input/output blocks (layer t applies its
+    // own operator to layer_vecs[t], no sum over layers), and where the
+    // argument records live (null: the first plan's slot)
+    const ApplyVec *layer_vecs = nullptr;
+    DescSlot *desc = nullptr;
 };
 
 ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
@@ -196,6 +226,8 @@ private:
     bool active_ = false;
 };
 ml_status ensure_workspace(ml_plan_s *p, int nv);
+// sign of each column of V (n x k, column-major): largest-magnitude entry positive
+ml_status sign_fix_cols(double *V, int64_t n, int k, cudaStream_t st);
 
 // Device workspace of one layer pass: the spreading tiles and the two
 // transform buffers.
@@ -213,6 +245,7 @@ int pass_width(const ml_plan_s *p, int remaining);
 // whether the layers can run as one batch (FP32, equal d and W, every grid a
 // single tile, identical subproblem split) and the batched pass itself
 bool batchable(ml_plan_s *const *layers, int T);
+bool batchable_layers(ml_plan_s *const *layers, int T);
 ml_status run_batch(ml_plan_s *const *layers, int T, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
 
 }  // namespace ml
