@@ -139,6 +139,8 @@ typedef struct {
     int p_reg;
     ml_prec prec;
     double target_rel_err;
+    int bin;             /* spreading tile (bin) edge in grid cells, 0 = automatic rule;
+                            larger tiles must fit the shared-memory budget (ML_ERR_ARG) */
 } ml_plan_params;
 
 /*
@@ -149,6 +151,24 @@ typedef struct {
  */
 ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
                              const ml_plan_params *params, void *stream);
+
+/*
+ * ml_fastsum_plan_autotune - ml_fastsum_plan_ex with the spreading tile (bin)
+ * edge chosen by measurement (not from the paper: a GPU tuning step).  Plans
+ * are built for the automatic rule's edge and a few edges around it, one
+ * nv-vector product W X (ML_RAW_W) is timed on `stream` with CUDA events for
+ * each (after one untimed product), and the fastest plan is returned; the
+ * others are destroyed.  The winner is cached per layer shape (d, precision,
+ * window width, grid size, active grid extents, nv, log2 n), so a later call
+ * for a layer of the same shape builds one plan only.  Layers whose active
+ * grid is a single tile have nothing to tune.
+ *   params     as ml_fastsum_plan_ex (its bin field is ignored).
+ *   nv         vectors per product the caller will apply (1..8).
+ *   bin_chosen host, may be NULL: the chosen edge.
+ * Synchronises `stream`.  Errors as ml_fastsum_plan_ex.
+ */
+ml_status ml_fastsum_plan_autotune(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
+                                   const ml_plan_params *params, int nv, int *bin_chosen, void *stream);
 
 /*
  * ml_direct_sum_rows - the exact definition of the product on selected rows:
@@ -186,6 +206,9 @@ ml_status ml_cloud_features(const double *points, int64_t n, int d, double sigma
  *                        gradient w.r.t. the packed parameters (host outputs)
  *   ml_mlp_train         `epochs` full-batch Adam steps (lr, beta 0.9/0.999);
  *                        loss per epoch to `losses` (host, may be NULL)
+ *   ml_mlp_set_margins   3 safety factors on the error target, one per
+ *                        bandwidth factor {0.7, 0.85, 1} of the planner below
+ *                        (0 = use the planner's `margin` argument)
  * All return ML_ERR_ARG on size mismatches.
  */
 typedef struct ml_mlp_s *ml_mlp_t;
@@ -199,6 +222,7 @@ ml_status ml_mlp_forward(ml_mlp_t mlp, const float *X, int batch, float *Y);
 ml_status ml_mlp_loss_grad(ml_mlp_t mlp, const float *X, const float *Yt, int batch, float *loss, float *grad);
 ml_status ml_mlp_train(ml_mlp_t mlp, const float *X, const float *Yt, int batch, int epochs, float lr,
                        float *losses);
+ml_status ml_mlp_set_margins(ml_mlp_t mlp, const double *margins, int count);
 ml_status ml_mlp_destroy(ml_mlp_t mlp);
 
 /*
@@ -208,7 +232,8 @@ ml_status ml_mlp_destroy(ml_mlp_t mlp);
  * f in {0.7, 0.85, 1} (N0 the automatic bandwidth for the target),
  * taps in {4..8}, oversampling in {2, 2.5, 3}; the model input is the cloud's
  * features followed by (f, taps, oversampling).  The cheapest candidate whose
- * predicted error is at most target / margin is used; if none qualifies, or
+ * predicted error is at most target / margin is used (margin: the model's
+ * per-factor margin when set, else the argument); if none qualifies, or
  * mlp is NULL, the automatic choice of ml_fastsum_plan is used.
  * `chosen` (host, may be NULL) receives {f, taps, oversampling}.
  */
@@ -312,12 +337,16 @@ ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, doubl
  * k pairs have converged.
  *
  *   layers, T  T >= 1 plans sharing n.
- *   k          1 <= k <= n/2; the basis holds about max(2k+1, 20) + 2*block
- *              columns and must stay within 96 (k <= ~30 at block = 8).
+ *   k          1 <= k <= n/2; the basis (ncv plus one block) must stay within
+ *              96 columns (k <= ~30 at block = 8 with the automatic ncv).
  *   tol        relative residual ||A phi - theta phi|| <= tol * |theta_max|
  *              per layer (<= 0: 1e-10).
  *   maxit      limit on operator applications per layer (<= 0: 2000).
  *   block      vectors per step, 1..8.
+ *   ncv        basis columns per restart cycle (rounded up to a multiple of
+ *              block), or 0 for max(2k+1, 20) + block rounded up; at most
+ *              96 - block.  After a cycle the largest Ritz vectors (about
+ *              (ncv+k)/2 of them) are kept.
  *   seed       seed of the start blocks (SplitMix64 counter streams, one per layer).
  *   evals      host, T x k FP64 (row t: ascending eigenvalues of L_sym^(t)).
  *   evecs      host or device, T blocks of n x k FP64 column-major (block t =
@@ -330,7 +359,7 @@ ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, doubl
  * (the block deflates) instead of failing.
  */
 ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
-                                 uint64_t seed, double *evals, double *evecs, int *nconv, void *stream);
+                                 int ncv, uint64_t seed, double *evals, double *evecs, int *nconv, void *stream);
 
 /* Copy the plan's parameters into *info (host).  Never fails on a valid plan. */
 ml_status ml_plan_get_info(ml_plan_t plan, ml_plan_info *info);

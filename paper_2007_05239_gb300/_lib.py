@@ -24,10 +24,11 @@ ML_RAW_W, ML_NORMALIZED_A, ML_DEGREE, ML_PER_LAYER = 0, 1, 2, 16
 MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
-EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_learned", "ml_fastsum_apply",
+EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", "ml_fastsum_plan_learned",
+           "ml_fastsum_apply",
            "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
            "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
-           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers",
+           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers",
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read"]
@@ -45,7 +46,7 @@ ML_FEATURES = 9
 class PlanParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("taps", ctypes.c_int), ("oversampling", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("p_reg", ctypes.c_int), ("prec", ctypes.c_int),
-                ("target_rel_err", ctypes.c_double)]
+                ("target_rel_err", ctypes.c_double), ("bin", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -90,7 +91,7 @@ def load():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P, P, P]
     lib.ml_lanczos_eigs_layers.restype = ctypes.c_int
     lib.ml_lanczos_eigs_layers.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                           ctypes.c_uint64, P, P, P, P]
+                                           ctypes.c_int, ctypes.c_uint64, P, P, P, P]
     lib.ml_plan_get_info.restype = ctypes.c_int
     lib.ml_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.ml_plan_copy_table.restype = ctypes.c_int
@@ -104,6 +105,9 @@ def load():
     lib.ml_fastsum_plan_ex.restype = ctypes.c_int
     lib.ml_fastsum_plan_ex.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(PlanParams), P]
+    lib.ml_fastsum_plan_autotune.restype = ctypes.c_int
+    lib.ml_fastsum_plan_autotune.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, P,
+                                             ctypes.c_int, P, P]
     lib.ml_fastsum_plan_learned.restype = ctypes.c_int
     lib.ml_fastsum_plan_learned.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_int, ctypes.c_double, P, ctypes.c_double, P, P]
@@ -126,6 +130,8 @@ def load():
     lib.ml_mlp_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P]
     lib.ml_mlp_train.restype = ctypes.c_int
     lib.ml_mlp_train.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, P]
+    lib.ml_mlp_set_margins.restype = ctypes.c_int
+    lib.ml_mlp_set_margins.argtypes = [P, P, ctypes.c_int]
     lib.ml_mlp_destroy.restype = ctypes.c_int
     lib.ml_mlp_destroy.argtypes = [P]
     lib.ml_profile_enable.restype = ctypes.c_int
@@ -214,18 +220,36 @@ def ml_fastsum_plan(points, sigma, N=0, m=0, eps_B=0.0, p_reg=0, prec="f64", tar
     return Plan(h.value, n, d)
 
 
+def _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin):
+    return PlanParams(int(N), int(taps), float(oversampling), float(eps_B), int(p_reg),
+                      {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec),
+                      float(target_rel_err), int(bin))
+
+
 def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
-                       target_rel_err=0.0, stream=None):
-    """Plan one layer with explicit window width / oversampling (0 = automatic)."""
+                       target_rel_err=0.0, bin=0, stream=None):
+    """Plan one layer with explicit window width / oversampling / bin edge (0 = automatic)."""
     lib = load()
     n, d = int(points.shape[0]), int(points.shape[1])
-    prm = PlanParams(int(N), int(taps), float(oversampling), float(eps_B), int(p_reg),
-                     {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec),
-                     float(target_rel_err))
+    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin)
     h = ctypes.c_void_p()
     _check(lib.ml_fastsum_plan_ex(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
                                   _stream(stream)))
     return Plan(h.value, n, d)
+
+
+def ml_fastsum_plan_autotune(points, sigma, nv=1, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
+                             target_rel_err=0.0, stream=None):
+    """Plan one layer with the bin edge chosen by timing nv-vector products.
+    Returns (plan, chosen bin edge)."""
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, 0)
+    h = ctypes.c_void_p()
+    chosen = ctypes.c_int(0)
+    _check(lib.ml_fastsum_plan_autotune(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
+                                        int(nv), ctypes.byref(chosen), _stream(stream)))
+    return Plan(h.value, n, d), chosen.value
 
 
 def ml_fastsum_plan_learned(points, sigma, model=None, prec="f32", target_rel_err=0.0, margin=2.0, stream=None):
@@ -313,6 +337,11 @@ class Mlp:
                                    losses.ctypes.data))
         return losses
 
+    def set_margins(self, margins):
+        """Per-bandwidth-factor safety margins of the learned planner (3 values)."""
+        m = np.ascontiguousarray(margins, dtype=np.float64)
+        _check(load().ml_mlp_set_margins(self.handle, m.ctypes.data, int(m.size)))
+
     def destroy(self):
         if self.handle is not None and self.handle.value:
             load().ml_mlp_destroy(self.handle)
@@ -371,7 +400,7 @@ def ml_lanczos_eigs(layers, k, p=1.0, tol=0.0, maxit=0, seed=0, evecs=None, stre
     return ev, nconv.value, st
 
 
-def ml_lanczos_eigs_layers(layers, k, block=8, tol=0.0, maxit=0, seed=0, evecs=None, stream=None):
+def ml_lanczos_eigs_layers(layers, k, block=8, tol=0.0, maxit=0, seed=0, evecs=None, stream=None, ncv=0):
     """For every layer separately, the k smallest eigenpairs of its L_sym,
     all layers advancing together by block Lanczos with `block` vectors.
 
@@ -383,7 +412,7 @@ def ml_lanczos_eigs_layers(layers, k, block=8, tol=0.0, maxit=0, seed=0, evecs=N
     ev = np.empty((T, k), dtype=np.float64)
     nconv = np.zeros(T, dtype=np.int32)
     arr = _handles(layers)
-    st = lib.ml_lanczos_eigs_layers(arr, T, int(k), float(tol), int(maxit), int(block), ctypes.c_uint64(seed),
+    st = lib.ml_lanczos_eigs_layers(arr, T, int(k), float(tol), int(maxit), int(block), int(ncv), ctypes.c_uint64(seed),
                                     ev.ctypes.data, _ptr(evecs), nconv.ctypes.data, _stream(stream))
     _check(st)
     return ev, nconv, st

@@ -451,8 +451,8 @@ struct Solver {
 
 }  // namespace
 
-static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int maxit, int b, uint64_t seed,
-                             double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
+static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int maxit, int b, int ncv_req,
+                             uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
 {
     Solver S;
     S.L = L;
@@ -462,7 +462,7 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
     S.n = L[0]->n;
     S.st = st;
     const int64_t n = S.n;
-    const int target = std::max(2 * k + 1, 20);
+    const int target = ncv_req > 0 ? ncv_req - b : std::max(2 * k + 1, 20);
     int ncv = b * ((target + 2 * b - 1) / b);
     ncv = (int)std::min<int64_t>(ncv, (int64_t)b * ((n - b) / b));
     const int keep_goal = std::max(k + 1, (ncv + k) / 2);
@@ -650,7 +650,8 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
 }  // namespace ml
 
 extern "C" ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
-                                            uint64_t seed, double *evals, double *evecs, int *nconv, void *stream)
+                                            int ncv, uint64_t seed, double *evals, double *evecs, int *nconv,
+                                            void *stream)
 {
     using namespace ml;
     if (!layers || T < 1) return fail(ML_ERR_ARG, "layers is null or T < 1");
@@ -682,7 +683,8 @@ extern "C" ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int 
             host_out = true;
         }
     }
-    ml_status s = layers_impl(layers, T, k, tol, maxit, block, seed, evals, evd, nconv, st);
+    if (ncv < 0 || ncv > kMaxLd - block) return fail(ML_ERR_ARG, "ncv must be 0 (automatic) or at most 96 - block");
+    ml_status s = layers_impl(layers, T, k, tol, maxit, block, ncv, seed, evals, evd, nconv, st);
     if ((s == ML_OK || s == ML_WARN_NOT_CONVERGED) && host_out)
         ML_CUDA(cudaMemcpy(evecs, evd, (size_t)T * n * k * sizeof(double), cudaMemcpyDeviceToHost));
     return s;

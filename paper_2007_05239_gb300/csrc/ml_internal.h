@@ -94,6 +94,7 @@ struct ml_plan_s {
     int m = 0;             // window half-width, W/2 rounded down (paper's m_NFFT)
     int W = 0;             // window width in taps per dimension (half-width W/2)
     double sig_os_req = 0; // requested oversampling (0: automatic / 2)
+    int bin_req = 0;       // requested bin edge (0: automatic rule)
     int n_os = 0;
     ml_prec prec = ML_F64;
     int domain = 0;

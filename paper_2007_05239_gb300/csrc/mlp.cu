@@ -15,6 +15,7 @@ struct ml_mlp_s {
     ml::DevBuf params, grad, adam_m, adam_v, norm, ws, part;
     int ws_batch = 0;
     int64_t adam_t = 0;
+    double margins[3] = {0.0, 0.0, 0.0};   // per bandwidth factor of the planner (0: unset)
     int64_t offW1() const { return 0; }
     int64_t offb1() const { return (int64_t)h * nin; }
     int64_t offW2() const { return offb1() + h; }
@@ -313,6 +314,16 @@ ml_status ml_mlp_set_norm(ml_mlp_t m, const float *in_mean, const float *in_std,
     return ML_OK;
 }
 
+ml_status ml_mlp_set_margins(ml_mlp_t mlp, const double *margins, int count)
+{
+    if (!mlp || !margins || count != 3) return fail(ML_ERR_ARG, "margins: a model and 3 values are needed");
+    for (int f = 0; f < 3; ++f) {
+        if (!(margins[f] >= 0.0) || !std::isfinite(margins[f])) return fail(ML_ERR_ARG, "margins must be >= 0");
+        mlp->margins[f] = margins[f];
+    }
+    return ML_OK;
+}
+
 ml_status ml_mlp_forward(ml_mlp_t m, const float *X, int batch, float *Y)
 {
     if (!m || !X || !Y || batch < 1) return fail(ML_ERR_ARG, "bad arguments");
@@ -419,10 +430,15 @@ ml_status ml_fastsum_plan_learned(ml_plan_t *out, const double *points, int64_t 
         const int B = (int)cand.size() / 3;
         std::vector<float> Yp((size_t)B * 2);
         ML_TRY(ml_mlp_forward(mlp, Xc.data(), B, Yp.data()));
-        const double lim = std::log10(target / (margin > 1.0 ? margin : 1.0));
+        // per bandwidth factor: the model's own calibrated margin when set, else the caller's
+        double lim[3];
+        for (int f = 0; f < 3; ++f) {
+            const double m = mlp->margins[f] > 0.0 ? mlp->margins[f] : margin;
+            lim[f] = std::log10(target / (m > 1.0 ? m : 1.0));
+        }
         double best = INFINITY;
         for (int i = 0; i < B; ++i)
-            if (Yp[2 * i] <= lim && Yp[2 * i + 1] < best) {
+            if (Yp[2 * i] <= lim[i / (B / 3)] && Yp[2 * i + 1] < best) {
                 best = Yp[2 * i + 1];
                 pick[0] = cand[3 * i];
                 pick[1] = cand[3 * i + 1];

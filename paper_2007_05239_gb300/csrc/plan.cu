@@ -621,7 +621,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         // its first tap one cell to the right
         g.L[a] = (int)(fmax - fmin) + p->W + 1;
     }
-    if (p->prec == ML_F32) {
+    if (p->bin_req > 0) {
+        g.B = p->bin_req;
+    } else if (p->prec == ML_F32) {
         g.B = choose_bin(d, p->W);
     } else {
         g.B = choose_bin_f64(d, p->W);
@@ -640,9 +642,12 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     g.R = 1 + (p->W - 1) / g.B;         // bins below that reach into a bin
     for (int a = 0; a < d; ++a) g.nb[a] = (g.L[a] + g.B - 1) / g.B;
     {
-        // FP32: one shared tile per CTA; FP64: one tile per warp plus the
-        // staged inputs of a subproblem
+        // one shared tile per CTA (FP32: 4-byte cells; FP64: two 4-byte
+        // fixed-point planes) plus, in FP64, the staged inputs of a subproblem
         const int64_t tc = g.tile_cells();
+        const int64_t need1 = p->prec == ML_F32 ? tc * 4 : tc * 8 + (int64_t)kSubPoints * 8;
+        if (need1 > 200 * 1024)
+            return fail(ML_ERR_ARG, "bin edge " + std::to_string(g.B) + " gives a tile beyond the shared-memory budget");
         if (p->prec == ML_F32) {
             p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * 4)));
         } else {
@@ -842,7 +847,7 @@ const char *ml_version(void) { return "ml_fastsum 0.1 (sm_103a)"; }
 
 static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int W,
                              double sig_os, double eps_B, int p_reg, ml_prec prec, double target_rel_err,
-                             void *stream)
+                             int bin, void *stream)
 {
     using namespace ml;
     if (!out) return fail(ML_ERR_ARG, "out is null");
@@ -858,6 +863,7 @@ static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, in
     if (!(eps_B >= 0 && eps_B < 0.5)) return fail(ML_ERR_ARG, "eps_B must be in [0, 1/2)");
     if (eps_B > 0 && (p_reg < 1 || p_reg > 8)) return fail(ML_ERR_ARG, "p_reg must be in [1, 8] when eps_B > 0");
     if (prec != ML_F32 && prec != ML_F64) return fail(ML_ERR_ARG, "prec must be ML_F32 or ML_F64");
+    if (bin < 0 || bin > 512) return fail(ML_ERR_ARG, "bin must be 0 (automatic) or in [1, 512]");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
@@ -869,6 +875,7 @@ static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, in
     p->N = N;
     p->W = W;   // 0 = automatic
     p->sig_os_req = sig_os;
+    p->bin_req = bin;
     p->eps_B = eps_B;
     p->p_reg = eps_B > 0 ? p_reg : 0;
     p->prec = prec;
@@ -887,7 +894,7 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
                           double eps_B, int p_reg, ml_prec prec, double target_rel_err, void *stream)
 {
     if (m != 0 && (m < 2 || m > ml::kMaxM)) return ml::fail(ML_ERR_ARG, "m must be 0 or in [2, 8]");
-    return plan_common(out, points, n, d, sigma, N, 2 * m, 0.0, eps_B, p_reg, prec, target_rel_err, stream);
+    return plan_common(out, points, n, d, sigma, N, 2 * m, 0.0, eps_B, p_reg, prec, target_rel_err, 0, stream);
 }
 
 ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
@@ -895,7 +902,7 @@ ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, in
 {
     if (!prm) return ml::fail(ML_ERR_ARG, "params is null");
     return plan_common(out, points, n, d, sigma, prm->N, prm->taps, prm->oversampling, prm->eps_B, prm->p_reg,
-                       prm->prec, prm->target_rel_err, stream);
+                       prm->prec, prm->target_rel_err, prm->bin, stream);
 }
 
 ml_status ml_plan_destroy(ml_plan_t plan)

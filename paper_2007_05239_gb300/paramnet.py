@@ -121,6 +121,20 @@ def calibrate_margin(model, X, Y, quantile=0.99):
     return float(10.0 ** max(0.0, float(np.quantile(r, quantile))))
 
 
+def calibrate_margins(model, X, Y, quantile=0.995):
+    """One safety factor per bandwidth factor f of the candidates: 10^q_f with
+    q_f the quantile of (measured - predicted) log10 error over the held-out
+    samples of that f (the cut bandwidths err more, and less predictably);
+    at least 1."""
+    r = Y[:, 0] - model.forward(X)[:, 0]
+    out = []
+    for f in FACTORS:
+        sel = np.isclose(X[:, ml.ML_FEATURES], f)
+        q = float(np.quantile(r[sel] if sel.any() else r, quantile))
+        out.append(float(10.0 ** max(0.0, q)))
+    return out
+
+
 def evaluate(model, first, count, prec, target, margin=2.0):
     """Learned choice vs the fixed rule on unseen clouds: error (direct-sum
     judge) and product time for both."""
@@ -144,17 +158,19 @@ def evaluate(model, first, count, prec, target, margin=2.0):
             "clouds": rows_out}
 
 
-def save(path, model, norm, margin):
+def save(path, model, norm, margin, margins=None):
     np.savez(path, params=model.get_params(), in_mean=norm[0], in_std=norm[1], out_mean=norm[2], out_std=norm[3],
-             hidden=model.hidden, margin=margin)
+             hidden=model.hidden, margin=margin, margins=np.zeros(3) if margins is None else np.asarray(margins))
 
 
 def load_model(path):
-    """(model, margin) saved by `save`."""
+    """(model, margin) saved by `save`; per-factor margins are set on the model."""
     z = np.load(path)
     model = ml.Mlp(len(z["in_mean"]), int(z["hidden"]), len(z["out_mean"]))
     model.set_params(z["params"])
     model.set_norm(z["in_mean"], z["in_std"], z["out_mean"], z["out_std"])
+    if "margins" in z:
+        model.set_margins(z["margins"])
     return model, float(z["margin"])
 
 
@@ -167,7 +183,8 @@ def main():
     ap.add_argument("--target", type=float, default=1e-4)
     ap.add_argument("--epochs", type=int, default=4000)
     ap.add_argument("--holdout", type=float, default=0.1, help="share of training clouds held out for the margin")
-    ap.add_argument("--quantile", type=float, default=0.99, help="quantile of held-out error residuals")
+    ap.add_argument("--quantile", type=float, default=0.995,
+                    help="quantile of held-out error residuals (per bandwidth factor)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     a = ap.parse_args()
@@ -176,17 +193,19 @@ def main():
     t1 = time.time()
     fit = ids < a.train * (1.0 - a.holdout)
     model, losses, norm = train(X[fit], Y[fit], epochs=a.epochs)
-    margin = calibrate_margin(model, X[~fit], Y[~fit], a.quantile)
+    margins = calibrate_margins(model, X[~fit], Y[~fit], a.quantile)
+    model.set_margins(margins)
+    margin = max(margins)
     t2 = time.time()
     ev = evaluate(model, 5000, a.eval, a.prec, a.target, margin=margin)
     t3 = time.time()
-    rep = {"samples": int(X.shape[0]), "fit_samples": int(fit.sum()), "margin": margin,
+    rep = {"samples": int(X.shape[0]), "fit_samples": int(fit.sum()), "margins": margins,
            "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
            "data_s": t1 - t0, "train_s": t2 - t1, "eval_s": t3 - t2,
            **{k: v for k, v in ev.items() if k != "clouds"}}
     print(json.dumps(rep))
     if a.out:
-        save(a.out, model, norm, margin)
+        save(a.out, model, norm, margin, margins)
     if a.report:
         with open(a.report, "w") as f:
             json.dump({**rep, "clouds": ev["clouds"]}, f)

@@ -106,3 +106,16 @@ def test_learned_choice_small_end_to_end():
     plan, chosen = ml.ml_fastsum_plan_learned(pts, sigma, None, prec="f32", target_rel_err=1e-4)
     ref = ml.ml_fastsum_plan(pts, sigma, prec="f32", target_rel_err=1e-4)
     assert chosen == (0.0, 0.0, 0.0) and plan.info["taps"] == ref.info["taps"] and plan.info["N"] == ref.info["N"]
+
+
+def test_per_factor_margins_exclude_cut_bandwidths():
+    # a model whose per-factor margins make every cut bandwidth (f < 1)
+    # unreachable may only pick the full bandwidth, or fall back to the rule
+    m = ml.Mlp(ml.ML_FEATURES + 3, 16, 2, seed=4)
+    m.set_norm(np.zeros(ml.ML_FEATURES + 3), np.ones(ml.ML_FEATURES + 3), np.array([-6.0, -1.0]), np.ones(2))
+    m.set_margins([1e30, 1e30, 0.0])
+    pts, sigma, *_ = paramnet.cloud(5001)
+    plan, chosen = ml.ml_fastsum_plan_learned(pts, sigma, m, prec="f32", target_rel_err=1e-4, margin=1.0)
+    assert chosen[0] in (0.0, 1.0)
+    with pytest.raises(ml.MLError):
+        m.set_margins([1.0, 2.0])
