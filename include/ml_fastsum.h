@@ -303,10 +303,14 @@ ml_status ml_fastsum_apply_noalloc(const ml_plan_t *layers, int T, const double 
  *
  *   p == 1   eigenpairs of L_1: the k largest theta of I - L_1 (Eq. I-L_1),
  *            lambda = 1 - theta.
- *   p == -1  eigenpairs of L_{-1,delta}, delta = log 2: the k largest mu of
- *            L_{-1,delta}^{-1} = (1/T) sum_t (L_sym^(t) + delta I)^{-1}
- *            (Eq. L_p_delta_power_p), each term applied by an inner conjugate
- *            gradient solve driven by the fast summation; lambda = 1/mu.
+ *   p < 0    eigenpairs of L_{p,delta}, delta = log(1+|p|): the k largest mu
+ *            of L_{p,delta}^p = (1/T) sum_t (L_sym^(t) + delta I)^p
+ *            (Eq. L_p_delta_power_p), lambda = mu^(1/p).  For p = -1 each
+ *            term is an inner conjugate gradient solve driven by the fast
+ *            summation; for other p in [-64, 0) it is the Lanczos
+ *            approximation of the matrix power (tridiagonal solves for
+ *            integer p, the tridiagonal eigendecomposition otherwise),
+ *            stopped at relative change max(1e-12, 1e-2 tol).
  *   tol      relative residual ||A phi - theta phi|| <= tol * |theta_max|
  *            (<= 0: 1e-10).
  *   maxit    limit on outer operator applications (<= 0: 2000).
@@ -319,7 +323,7 @@ ml_status ml_fastsum_apply_noalloc(const ml_plan_t *layers, int T, const double 
  *   nconv    host, number of converged pairs (may be NULL).
  * Synchronises `stream`.  Returns ML_WARN_NOT_CONVERGED when maxit is reached
  * with fewer than k converged pairs (evals/evecs then hold the best Ritz
- * pairs); ML_ERR_ARG for k < 1, k > n/2, p not in {1, -1}.
+ * pairs); ML_ERR_ARG for k < 1, k > n/2, p not 1 and not in [-64, 0).
  */
 ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, double tol, int maxit,
                           int block, uint64_t seed, double *evals, double *evecs, int *nconv,

@@ -385,7 +385,7 @@ def ml_fastsum_apply_noalloc(layers, X, Y, mode="normalized", per_layer=False, s
 
 
 def ml_lanczos_eigs(layers, k, p=1.0, tol=0.0, maxit=0, seed=0, evecs=None, stream=None, block=1):
-    """k smallest eigenpairs of L_1 (p=1) or L_{-1,delta} (p=-1).
+    """k smallest eigenpairs of L_1 (p=1) or L_{p,delta} (p < 0, e.g. -1 or -10).
 
     evecs: None, or a float64 buffer with n*k elements (CUDA or CPU) that
     receives the eigenvectors column-major.  Returns (evals, nconv, status)."""

@@ -3,7 +3,9 @@
 //
 // Thick-restart Lanczos (Wu & Simon) on the symmetric operator
 //   p =  1: Op = I - L_1 = (1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2}
-//   p = -1: Op = L_{-1,delta}^{-1} = (1/T) sum_t (L_sym^(t) + delta I)^{-1}
+//   p < 0:  Op = L_{p,delta}^p = (1/T) sum_t (L_sym^(t) + delta I)^p,
+//           delta = log(1 + |p|): for p = -1 each term by conjugate gradients,
+//           otherwise by the Lanczos approximation of the matrix power (PowerOp)
 // for its k largest eigenvalues.  The Krylov basis Q (n x (ncv+1), column
 // major, FP64) lives on the device; every new vector is orthogonalised
 // against all columns twice (classical Gram-Schmidt, CGS2) with
@@ -434,6 +436,148 @@ struct InverseOp {
     }
 };
 
+// f(T) e1 for the symmetric tridiagonal T (diagonal a[0..m-1], off-diagonal
+// b[0..m-2]) and f(x) = x^p, p < 0.  Integer p: |p| solves with T (Thomas
+// elimination; T is positive definite here, eigenvalues in [delta, 2+delta]);
+// otherwise through the eigendecomposition of T.
+static void tridiag_power_e1(const std::vector<double> &a, const std::vector<double> &b, int m, double p,
+                             std::vector<double> &c)
+{
+    c.assign(m, 0.0);
+    const double pr = std::round(p);
+    if (std::fabs(p - pr) < 1e-12 && pr < 0) {
+        std::vector<double> x(m, 0.0), cp(m), dp(m);
+        x[0] = 1.0;
+        for (int rep = 0; rep < (int)(-pr); ++rep) {
+            // solve T y = x in place (no pivoting: T is symmetric positive definite)
+            double den = a[0];
+            cp[0] = (m > 1 ? b[0] : 0.0) / den;
+            dp[0] = x[0] / den;
+            for (int i = 1; i < m; ++i) {
+                den = a[i] - b[i - 1] * cp[i - 1];
+                cp[i] = (i + 1 < m ? b[i] : 0.0) / den;
+                dp[i] = (x[i] - b[i - 1] * dp[i - 1]) / den;
+            }
+            x[m - 1] = dp[m - 1];
+            for (int i = m - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+        }
+        c = x;
+        return;
+    }
+    std::vector<double> A((size_t)m * m, 0.0), ev, V;
+    for (int i = 0; i < m; ++i) {
+        A[(size_t)i * m + i] = a[i];
+        if (i + 1 < m) A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = b[i];
+    }
+    sym_eig(m, A, ev, V);
+    for (int j = 0; j < m; ++j) {
+        const double w = std::pow(std::max(ev[j], 1e-300), p) * V[(size_t)0 * m + j];
+        for (int i = 0; i < m; ++i) c[i] += V[(size_t)i * m + j] * w;
+    }
+}
+
+// y = (1/T) sum_t (L_sym^(t) + delta I)^p x for p < 0, p != -1: each term by
+// the Lanczos approximation of the matrix function (Lanczos-FA): m steps of
+// the three-term recurrence on B_t = L_sym^(t) + delta I from q_1 = x/||x||,
+// then f(B_t) x ~ ||x|| Q_m f(T_m) e1, stopped when the coefficient vector
+// changes by less than the tolerance (relative).  The polynomial Krylov
+// approach of Sec. 3 for a general power.
+struct PowerOp {
+    ml_plan_s *const *layers;
+    int T;
+    double p, delta;
+    int64_t n;
+    Workspace *ws;
+    int mmax = 80;
+    double tol = 1e-12;
+    long long inner_iters = 0;
+    DevBuf Qf, w, cd;
+
+    ml_status init()
+    {
+        ML_TRY(Qf.ensure((size_t)n * (mmax + 1) * 8));
+        ML_TRY(w.ensure((size_t)n * 8));
+        ML_TRY(cd.ensure((size_t)mmax * 8));
+        return ML_OK;
+    }
+    ml_status apply(const double *x, double *out, cudaStream_t st)
+    {
+        const int nb = vec_blocks(n);
+        double *Q = Qf.as<double>(), *wp = w.as<double>();
+        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
+        double xx;
+        ML_TRY(ws->dot_host(x, x, &xx));
+        const double nrm = std::sqrt(xx);
+        if (!(nrm > 0)) return ML_OK;
+        std::vector<double> a, b, c, cprev;
+        for (int t = 0; t < T; ++t) {
+            {
+                ProfScope pr("vector", st);
+                k_scale<<<nb, 256, 0, st>>>(x, 1.0 / nrm, n, Q);
+            }
+            a.clear();
+            b.clear();
+            cprev.clear();
+            int m = 0;
+            bool done = false;
+            for (int j = 0; j < mmax && !done; ++j) {
+                double *qj = Q + (int64_t)j * n;
+                // w = B q_j - beta_{j-1} q_{j-1}
+                ApplyVec av{qj, 1, wp, 1, 1};
+                ApplyOpts o;
+                o.normalized = true;
+                o.alpha = -1.0;
+                o.shift = 1.0 + delta;
+                ML_TRY(apply_layer(layers[t], av, o, st));
+                ++inner_iters;
+                if (j > 0) {
+                    ProfScope pr("vector", st);
+                    k_axpy<<<nb, 256, 0, st>>>(-b[j - 1], Q + (int64_t)(j - 1) * n, n, wp);
+                }
+                double alpha;
+                ML_TRY(ws->dot_host(qj, wp, &alpha));
+                {
+                    ProfScope pr("vector", st);
+                    k_axpy<<<nb, 256, 0, st>>>(-alpha, qj, n, wp);
+                }
+                double ww;
+                ML_TRY(ws->dot_host(wp, wp, &ww));
+                const double beta = std::sqrt(std::max(ww, 0.0));
+                a.push_back(alpha);
+                m = j + 1;
+                tridiag_power_e1(a, b, m, p, c);
+                // change of the coefficient vector against the previous step
+                double dn = 0.0, cn = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    const double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
+                    dn += (c[i] - prev) * (c[i] - prev);
+                    cn += c[i] * c[i];
+                }
+                if (j > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) done = true;
+                if (beta <= 1e-14 * std::fabs(alpha)) done = true;   // invariant subspace: exact
+                cprev = c;
+                if (!done) {
+                    b.push_back(beta);
+                    ProfScope pr("vector", st);
+                    k_scale<<<nb, 256, 0, st>>>(wp, 1.0 / beta, n, Q + (int64_t)(j + 1) * n);
+                }
+            }
+            if (!done) return fail(ML_ERR_BREAKDOWN, "Lanczos-FA: the matrix power did not converge");
+            // out += (nrm / T) Q_m c
+            for (double &v : c) v *= nrm / T;
+            ML_CUDA(cudaMemcpyAsync(cd.p, c.data(), m * 8, cudaMemcpyHostToDevice, st));
+            {
+                ProfScope pr("ritz", st);
+                k_combine<<<nb, 256, 0, st>>>(Q, n, n, m, cd.as<double>(), 1, wp, n);
+                k_axpy<<<nb, 256, 0, st>>>(1.0, wp, n, out);
+            }
+            ML_CUDA(cudaGetLastError());
+            ML_CUDA(cudaStreamSynchronize(st));   // c (host) is reused by the next layer
+        }
+        return ML_OK;
+    }
+};
+
 // Fix the sign of each column of V (n x k, column-major) so that its
 // largest-magnitude entry (the first one on ties) is positive.
 ml_status sign_fix_cols(double *V, int64_t n, int k, cudaStream_t st)
@@ -486,14 +630,20 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
     ML_TRY(wv.ensure((size_t)n * 8));
     ML_TRY(Sd.ensure((size_t)ncv * ncv * 8));
     double *Q = Qb.as<double>(), *w = wv.as<double>();
-    InverseOp inv{layers, T, std::log(2.0), n, &ws};
+    const double delta = pw < 0 ? std::log1p(std::fabs(pw)) : 0.0;
+    InverseOp inv{layers, T, delta, n, &ws};
+    PowerOp pow_op{layers, T, pw, delta, n, &ws};
+    pow_op.tol = std::max(1e-12, 1e-2 * tol);
+    const bool use_cg = pw == -1.0;
     // inner solves two orders below the outer residual tolerance (the outer
     // operator is then exact to well within what the Ritz test resolves)
     inv.inner_tol = std::max(1e-12, 1e-2 * tol);
-    if (pw < 0) ML_TRY(inv.init());
+    if (pw < 0 && use_cg) ML_TRY(inv.init());
+    if (pw < 0 && !use_cg) ML_TRY(pow_op.init());
     auto op = [&](const double *x, double *y) -> ml_status {
         if (pw > 0) return apply_device(layers, T, x, 1, y, ML_NORMALIZED_A, st);
-        return inv.apply(x, y, st);
+        if (use_cg) return inv.apply(x, y, st);
+        return pow_op.apply(x, y, st);
     };
     const int nb = vec_blocks(n);
     // start vector
@@ -576,10 +726,10 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         if (done) {
             for (int i = 0; i < k; ++i) {
                 const double th = theta[ncv - 1 - i];
-                evals[i] = pw > 0 ? 1.0 - th : 1.0 / th;
+                evals[i] = pw > 0 ? 1.0 - th : std::pow(th, 1.0 / pw);
             }
             // ascending eigenvalues of the Laplacian: p = 1 maps descending theta to
-            // ascending 1 - theta already; p = -1 maps descending mu to ascending 1/mu.
+            // ascending 1 - theta already; p < 0 maps descending mu to ascending mu^(1/p).
             if (evecs_dev) {
                 ML_CUDA(cudaMemcpyAsync(evecs_dev, Qtmp.p, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, st));
                 ML_TRY(sign_fix_cols(evecs_dev, n, k, st));
@@ -618,7 +768,7 @@ extern "C" ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, doub
     for (int t = 1; t < T; ++t)
         if (layers[t]->n != n) return fail(ML_ERR_ARG, "layers do not share n");
     if (k < 1 || k > n / 2) return fail(ML_ERR_ARG, "k must be in [1, n/2]");
-    if (p != 1.0 && p != -1.0) return fail(ML_ERR_ARG, "p must be 1 or -1");
+    if (!(p == 1.0 || (p < 0 && p >= -64.0))) return fail(ML_ERR_ARG, "p must be 1 or in [-64, 0)");
     if (block > 1) return fail(ML_ERR_ARG, "block Lanczos is not available (block must be 1)");
     for (int t = 0; t < T; ++t)
         if (!layers[t]->deg_ok) return fail(ML_ERR_DEGREE, "a layer has a degree <= 0: L_sym is undefined");

@@ -79,3 +79,22 @@ def test_argument_errors():
     for bad in (dict(k=0), dict(k=51), dict(k=3, p=2.0)):
         with pytest.raises(ml.MLError):
             ml.ml_lanczos_eigs([plan], **bad)
+
+
+@pytest.mark.parametrize("p", [-10.0, -2.5])
+def test_power_mean_general_p(p):
+    # the paper's preferred p = -10 (integer power: tridiagonal solves) and a
+    # fractional power (tridiagonal eigendecomposition), each layer term by
+    # the Lanczos approximation of the matrix power
+    n = 600
+    layers = [workloads.uniform_cube(n, 3, seed=130), workloads.uniform_cube(n, 2, seed=131)]
+    sig = [0.1, 0.1]
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    k = 5
+    V = torch.empty(k * n, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=p, tol=1e-10, seed=7, evecs=V)
+    assert st == ml.ML_OK
+    lam_ref, V_ref = eigen.Lp_eigs(layers, sig, p, k + 3)
+    check_pairs(lam, V.cpu().numpy().reshape(k, n).T, lam_ref[:k], V_ref[:, :k], k, tol_val=1e-8, tol_ang=1e-6)
+    # every eigenvalue of L_{p,delta} is at least delta = log(1 + |p|)
+    assert lam[0] >= math.log1p(abs(p)) - 1e-10
