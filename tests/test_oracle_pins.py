@@ -240,3 +240,74 @@ def test_mlp_gradient_matches_finite_differences():
     # the loss is the mean squared error of the standardised outputs
     Z = (mlp.forward(p, X, n_in, h, n_out, norm) - norm[2]) / norm[3]
     assert abs(loss - np.mean((Z - (Y - norm[2]) / norm[3]) ** 2)) < 1e-14
+
+
+# ---------------------------------------------------------------- Alg. 2
+def test_allen_cahn_T_is_gradient_of_potential():
+    # Eq. def:T_ij is the gradient of the multi-well potential of
+    # Eq. def_multiwell at points where every entry lies in (0, 1)
+    from oracle import allen_cahn as ac
+    rng = np.random.default_rng(40)
+    for m in (2, 3, 4, 5):
+        U = rng.dirichlet(np.ones(m) * 3.0, size=20)
+        U = np.clip(U, 0.02, 0.98)
+        T = ac.T_matrix(U)
+        h = 1e-6
+        G = np.zeros_like(U)
+        for j in range(m):
+            E = np.zeros(m)
+            E[j] = h
+            G[:, j] = (ac.potential(U + E) - ac.potential(U - E)) / (2 * h)
+        assert np.abs(T - G).max() <= 1e-7 * max(1.0, np.abs(G).max())
+
+
+def test_simplex_projection_optimal():
+    from oracle import allen_cahn as ac
+    rng = np.random.default_rng(41)
+    # m = 2: the projection onto the segment has the closed form x1 = clip((y1 - y2 + 1)/2, 0, 1)
+    Y = rng.normal(0, 2, (50, 2))
+    X = ac.project_simplex(Y)
+    x1 = np.clip((Y[:, 0] - Y[:, 1] + 1.0) / 2.0, 0.0, 1.0)
+    assert np.abs(X[:, 0] - x1).max() <= 1e-14 and np.abs(X.sum(1) - 1).max() <= 1e-14
+    # m = 3..6: on the simplex, and no sampled simplex point is closer
+    for m in (3, 4, 6):
+        Y = rng.normal(0, 1, (30, m))
+        X = ac.project_simplex(Y)
+        assert (X >= 0).all() and np.abs(X.sum(1) - 1).max() <= 1e-13
+        Z = rng.dirichlet(np.ones(m), size=4000)
+        for i in range(len(Y)):
+            d_best = np.sum((X[i] - Y[i]) ** 2)
+            assert (np.sum((Z - Y[i]) ** 2, axis=1) >= d_best - 1e-12).all()
+            # and small moves within the simplex do not get closer
+            for _ in range(50):
+                D = rng.normal(0, 1e-3, m)
+                D -= D.mean()
+                Z1 = X[i] + D
+                if (Z1 >= 0).all():
+                    assert np.sum((Z1 - Y[i]) ** 2) >= d_best - 1e-15
+
+
+def test_allen_cahn_full_eigenbasis_matches_dense_scheme():
+    # with all n eigenpairs the projected iteration of Alg. 2 is the scheme of
+    # Eq. U_lp1 solved densely, followed by the simplex projection
+    from oracle import allen_cahn as ac
+    n, m = 60, 3
+    X = workloads.uniform_cube(n, 2, seed=42)
+    L = graph.L_sym_dense(X, 0.15)
+    lam, Phi = np.linalg.eigh(L)
+    labels = -np.ones(n, dtype=int)
+    labels[[0, 7, 19, 33, 51]] = [0, 1, 2, 0, 1]
+    eps, omega0, dt = 0.05, 1000.0, 0.01
+    c = omega0 + 3.0 / eps
+    U_alg, it, _ = ac.allen_cahn(Phi, lam, labels, m, eps, omega0, c, dt, tol=0.0, max_iter=6)
+    assert it == 6
+    B = (1.0 + c * dt) * np.eye(n) + eps * dt * L
+    F = np.zeros((n, m))
+    F[labels >= 0, labels[labels >= 0]] = 1.0
+    omega = np.where(labels >= 0, omega0, 0.0)
+    U = ac.initial_scores(labels, m)
+    for _ in range(6):
+        R = (1.0 + c * dt) * U - dt / (2 * eps) * ac.T_matrix(U) - dt * omega[:, None] * (U - F)
+        U = ac.project_simplex(np.linalg.solve(B, R))
+    assert np.abs(U_alg - U).max() <= 1e-12
+    assert (ac.predict(U_alg)[labels >= 0] == labels[labels >= 0]).all()
