@@ -365,6 +365,46 @@ ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, doubl
 ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
                                  int ncv, uint64_t seed, double *evals, double *evecs, int *nconv, void *stream);
 
+/* Parameters of the Allen-Cahn scheme (Sec. 6; the image experiments of Sec. 8
+ * use eps = 0.005, omega0 = 1000, c = omega0 + 3/eps, dt = 0.01, tol = 1e-6,
+ * max_iter = 500). */
+typedef struct {
+    double eps;     /* interface parameter epsilon > 0                        */
+    double omega0;  /* fidelity weight of the labelled nodes                  */
+    double c;       /* convexity-splitting constant; <= 0: omega0 + 3/eps      */
+    double dt;      /* time step                                              */
+    double tol;     /* stop when relative_change <= tol                        */
+    int max_iter;   /* iteration limit, >= 1                                   */
+} ml_ac_params;
+
+/*
+ * ml_allen_cahn - class scores of every node by the multiclass multilayer
+ * graph Allen-Cahn scheme (Alg. 2, steps 2-4) from k eigenpairs of L_1 or
+ * L_{p,delta} (e.g. ml_lanczos_eigs):
+ *   Z = [(1 + c dt) I + eps dt Lambda_k]^{-1} Phi_k^T;
+ *   U^0: e_j on labelled nodes of class j, (1/m) 1 elsewhere;
+ *   repeat: T^l = T(U^l) (Eq. def:T_ij),
+ *           V^{l+1} = Z((1 + c dt) U^l - dt/(2 eps) T^l - dt omega (U^l - F)),
+ *           U^{l+1} = rows of Phi_k V^{l+1} projected onto the Gibbs simplex
+ *                     (sort-and-threshold projection of Chen & Ye 2011),
+ *   until max_i ||u_i^{l+1} - u_i^l||^2 / max_i ||u_i^{l+1}||^2 <= tol or
+ *   max_iter iterations.
+ *   Phi        device, n x k FP64 column-major (the eigenvectors).
+ *   lambda     host, k FP64 (the eigenvalues of the Laplacian).
+ *   labels     device, n int32: class id in [0, m) of labelled nodes, -1 else.
+ *   m          classes, 2..16;  k in 1..64.
+ *   U          device, n x m FP64 point-major: the scores of the last iterate.
+ *   pred       device, n int32 (may be NULL): row-wise argmax of U, ties to
+ *              the lowest class id.
+ *   iters, last_change  host (may be NULL): iterations done and their last
+ *              relative change.
+ * All arithmetic FP64.  Synchronises `stream`.  ML_ERR_ARG for sizes or
+ * labels out of range.
+ */
+ml_status ml_allen_cahn(const double *Phi, const double *lambda, int64_t n, int k, const int *labels, int m,
+                        const ml_ac_params *params, double *U, int *pred, int *iters, double *last_change,
+                        void *stream);
+
 /* Copy the plan's parameters into *info (host).  Never fails on a valid plan. */
 ml_status ml_plan_get_info(ml_plan_t plan, ml_plan_info *info);
 

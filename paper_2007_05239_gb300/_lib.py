@@ -28,7 +28,7 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_fastsum_apply",
            "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
            "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
-           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers",
+           "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers", "ml_allen_cahn",
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read"]
@@ -47,6 +47,11 @@ class PlanParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("taps", ctypes.c_int), ("oversampling", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("p_reg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("target_rel_err", ctypes.c_double), ("bin", ctypes.c_int)]
+
+
+class AcParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("omega0", ctypes.c_double), ("c", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -92,6 +97,8 @@ def load():
     lib.ml_lanczos_eigs_layers.restype = ctypes.c_int
     lib.ml_lanczos_eigs_layers.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_uint64, P, P, P, P]
+    lib.ml_allen_cahn.restype = ctypes.c_int
+    lib.ml_allen_cahn.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P]
     lib.ml_plan_get_info.restype = ctypes.c_int
     lib.ml_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.ml_plan_copy_table.restype = ctypes.c_int
@@ -165,6 +172,15 @@ def _ptr(a):
         return a.ctypes.data
     if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
         raise ValueError("tensors must be contiguous float64")
+    return a.data_ptr()
+
+
+def _ptr_i32(a):
+    """Raw address of a contiguous int32 torch tensor (or None)."""
+    if a is None:
+        return None
+    if a.dtype.__str__() != "torch.int32" or not a.is_contiguous():
+        raise ValueError("tensors must be contiguous int32")
     return a.data_ptr()
 
 
@@ -416,6 +432,30 @@ def ml_lanczos_eigs_layers(layers, k, block=8, tol=0.0, maxit=0, seed=0, evecs=N
                                     ev.ctypes.data, _ptr(evecs), nconv.ctypes.data, _stream(stream))
     _check(st)
     return ev, nconv, st
+
+
+def ml_allen_cahn(Phi, lam, labels, m, eps=0.005, omega0=1000.0, c=0.0, dt=0.01, tol=1e-6, max_iter=500, U=None,
+                  pred=None, stream=None):
+    """Class scores by the graph Allen-Cahn scheme (Alg. 2) from eigenpairs.
+
+    Phi: CUDA float64 buffer of n*k (column-major n x k); lam: k eigenvalues;
+    labels: CUDA int32 n (class or -1).  Returns (U (n x m CUDA float64),
+    pred (n CUDA int32 or the given buffer), iterations, last relative change)."""
+    import torch
+    lib = load()
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    k = int(lam.size)
+    n = int(labels.numel())
+    if U is None:
+        U = torch.empty(n * m, dtype=torch.float64, device=labels.device)
+    if pred is None:
+        pred = torch.empty(n, dtype=torch.int32, device=labels.device)
+    prm = AcParams(float(eps), float(omega0), float(c), float(dt), float(tol), int(max_iter))
+    iters = ctypes.c_int(0)
+    chg = ctypes.c_double(0.0)
+    _check(lib.ml_allen_cahn(_ptr(Phi), lam.ctypes.data, n, k, _ptr_i32(labels), int(m), ctypes.byref(prm), _ptr(U),
+                             _ptr_i32(pred), ctypes.byref(iters), ctypes.byref(chg), _stream(stream)))
+    return U, pred, iters.value, chg.value
 
 
 def ml_profile_enable(on=True):

@@ -61,14 +61,16 @@ def _box3(img: np.ndarray) -> np.ndarray:
 
 
 def image_voronoi_layers(h: int = 1000, w: int = 1000, regions: int = 8, noise: float = 0.02,
-                         seed: int = 2, third_layer: bool = True):
+                         seed: int = 2, third_layer: bool = True, return_labels: bool = False):
     """Image-like multilayer graph (stands in for the 9.7 MP beach image, Sec. 8.2).
 
     The image is split into `regions` Voronoi cells of seeded sites; each cell
     has a colour drawn U[0,1]^3, plus N(0, noise^2) per channel and pixel.
     Layer 1 = RGB (d=3); layer 2 = (x/w, y/w, texture) (d=3) with a seeded
     smooth texture field in [0,1]; layer 3 (optional) = RGB of the 3x3
-    box-filtered image (d=3).  Pixels are vectorised row-major.
+    box-filtered image (d=3).  Pixels are vectorised row-major.  With
+    return_labels, also the Voronoi region of every pixel (the ground truth
+    of a segmentation).
     """
     rng = np.random.default_rng(seed)
     sites = rng.uniform(0.0, 1.0, size=(regions, 2)) * np.array([w, h])
@@ -87,6 +89,8 @@ def image_voronoi_layers(h: int = 1000, w: int = 1000, regions: int = 8, noise: 
               np.stack([xx.ravel() / w, yy.ravel() / w, tex.ravel()], axis=1)]
     if third_layer:
         layers.append(_box3(img).reshape(-1, 3).copy())
+    if return_labels:
+        return layers, label.ravel().copy()
     return layers
 
 
@@ -132,6 +136,21 @@ def gmm_band_layers(n: int = 250_000, features: int = 104, components: int = 12,
     T = features // group
     layers = [np.ascontiguousarray(X[:, [t + j * T for j in range(group)]]) for t in range(T)]
     return layers, labels
+
+
+def known_labels(truth: np.ndarray, fraction: float, seed: int) -> np.ndarray:
+    """Semi-supervised input: a seeded `fraction` of the nodes keep their
+    ground-truth class, the others get -1 (at least one node per class)."""
+    rng = np.random.default_rng(seed)
+    n = len(truth)
+    lab = -np.ones(n, dtype=np.int32)
+    pick = rng.choice(n, size=max(1, int(round(fraction * n))), replace=False)
+    lab[pick] = truth[pick]
+    for c in np.unique(truth):
+        if not (lab == c).any():
+            i = rng.choice(np.nonzero(truth == c)[0])
+            lab[i] = c
+    return lab
 
 
 def cloud_for_mlp(index: int, n_min: int = 10_000, n_max: int = 1_000_000):
