@@ -349,9 +349,15 @@ struct InverseOp {
     // while iteration i+1 runs (one iteration of lag, no pipeline bubble)
     double *hrr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // one CG iteration of each layer captured as a CUDA graph (its pointers
+    // never change during the solve) and replayed; used while kernel timing
+    // is off, since per-kernel events cannot be recorded inside a graph
+    std::vector<cudaGraphExec_t> graph;
+    bool graphs_ok = true;
 
     ml_status init()
     {
+        graph.assign(T, nullptr);
         ML_TRY(r.ensure(n * 8));
         ML_TRY(p.ensure(n * 8));
         ML_TRY(ap.ensure(n * 8));
@@ -363,6 +369,8 @@ struct InverseOp {
     }
     ~InverseOp()
     {
+        for (auto &g : graph)
+            if (g) cudaGraphExecDestroy(g);
         if (hrr) cudaFreeHost(hrr);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
@@ -399,7 +407,8 @@ struct InverseOp {
                 k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 2, sc);
             }
             bool done = !(bb > 0);
-            for (int it = 0; it < inner_max && !done; ++it) {
+            // one CG iteration: Ap, alpha, x/r update, beta, new direction
+            auto iteration = [&]() -> ml_status {
                 ML_TRY(shifted(layers[t], p.as<double>(), ap.as<double>(), st));
                 {
                     ProfScope pr("cg", st);
@@ -409,6 +418,37 @@ struct InverseOp {
                                                   r.as<double>(), part);
                     k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 1, sc);
                     k_cg_dir<<<nb, 256, 0, st>>>(sc, r.as<double>(), n, p.as<double>());
+                }
+                ML_CUDA(cudaGetLastError());
+                return ML_OK;
+            };
+            for (int it = 0; it < inner_max && !done; ++it) {
+                const bool use_graph = graphs_ok && !profiling() && it >= 1;
+                if (use_graph && !graph[t]) {
+                    // the first iteration ran eagerly (workspace, attributes): capture the second
+                    cudaGraph_t g = nullptr;
+                    const int64_t applied0 = layers[t]->applied;   // capturing runs no work
+                    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                    ml_status cs = ML_OK;
+                    if (e == cudaSuccess) {
+                        cs = iteration();
+                        e = cudaStreamEndCapture(st, &g);
+                    }
+                    if (e == cudaSuccess && cs == ML_OK && g) e = cudaGraphInstantiate(&graph[t], g, 0);
+                    if (g) cudaGraphDestroy(g);
+                    layers[t]->applied = applied0;
+                    if (e != cudaSuccess || cs != ML_OK || !graph[t]) {
+                        // capture not possible here: run eagerly from now on
+                        cudaGetLastError();
+                        graphs_ok = false;
+                        graph[t] = nullptr;
+                    }
+                }
+                if (graphs_ok && !profiling() && graph[t]) {
+                    ML_CUDA(cudaGraphLaunch(graph[t], st));
+                    layers[t]->applied += 1;   // the replayed product's work counter
+                } else {
+                    ML_TRY(iteration());
                 }
                 ++inner_iters;
                 ML_CUDA(cudaMemcpyAsync(hrr + (it & 1), sc, sizeof(double), cudaMemcpyDeviceToHost, st));

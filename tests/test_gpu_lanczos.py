@@ -98,3 +98,23 @@ def test_power_mean_general_p(p):
     check_pairs(lam, V.cpu().numpy().reshape(k, n).T, lam_ref[:k], V_ref[:, :k], k, tol_val=1e-8, tol_ang=1e-6)
     # every eigenvalue of L_{p,delta} is at least delta = log(1 + |p|)
     assert lam[0] >= math.log1p(abs(p)) - 1e-10
+
+
+def test_graph_replay_matches_eager_launches():
+    # with kernel timing on, every inner CG iteration launches eagerly; with
+    # it off, the iterations replay a captured CUDA graph: same kernels, same
+    # order, so the same eigenpairs and the same work counters
+    n = 700
+    layers = [workloads.uniform_cube(n, 3, seed=140), workloads.uniform_cube(n, 2, seed=141)]
+    sig = [0.1, 0.1]
+    out = []
+    for prof in (True, False):
+        plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-10) for L, s in zip(layers, sig)]
+        ml.ml_profile_enable(prof)
+        V = torch.empty(4 * n, dtype=torch.float64, device="cuda")
+        lam, nconv, st = ml.ml_lanczos_eigs(plans, 4, p=-1.0, tol=1e-9, seed=3, evecs=V)
+        ml.ml_profile_enable(False)
+        out.append((lam, V.cpu().numpy(), [pl.info["applied_vectors"] for pl in plans]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
