@@ -206,7 +206,8 @@ def metric_name(spec):
 def config_dict(args, spec, n, T):
     return {"workload": args.workload, "desc": spec["desc"], "n": n, "layers": T, "d": spec["d"],
             "sigma": spec["sigma"], "prec": spec["prec"], "target_rel_err": spec["target"], "k": spec["k"],
-            "p": spec["p"], "l2": "inputs exceed L2 (per-layer point data and the Krylov basis are > 129 MB)",
+            "p": spec["p"], "planner": getattr(args, "planner", "rule"),
+            "l2": "inputs exceed L2 (per-layer point data and the Krylov basis are > 129 MB)",
             "parallelism": f"replicas{args.gpus}"}
 
 
@@ -241,6 +242,9 @@ def main():
                          "Allen-Cahn classifier (Alg. 2) on eigenpairs computed before the timed region")
     ap.add_argument("--b", type=int, default=1, help="vectors per product in --mode apply")
     ap.add_argument("--target", type=float, default=None, help="relative error target (default per precision)")
+    ap.add_argument("--planner", default="rule", choices=["rule", "learned"],
+                    help="NFFT parameters of each layer: the automatic rule, or the learned model "
+                         "(paper_2007_05239_gb300/paramnet_<prec>_<target>.npz)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -280,9 +284,10 @@ def main():
     dev_layers = [torch.as_tensor(L, device="cuda") for L in layers]
     k, p, prec, target = spec["k"], spec["p"], spec["prec"], spec["target"]
 
+    planner = make_planner(args.planner, prec, target, ml)
     apply_plans = None
     if args.mode == "apply":
-        apply_plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dev_layers, sig)]
+        apply_plans = [planner(x, s) for x, s in zip(dev_layers, sig)]
         Xa = torch.as_tensor(np.random.default_rng(7).uniform(0, 1, (n, args.b)), device="cuda")
         Ya = torch.empty_like(Xa)
 
@@ -292,7 +297,7 @@ def main():
             ml.ml_fastsum_apply(apply_plans, Xa, Ya, mode="normalized")
             applied = (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
             return None, 0, applied, [pl.info["taps"] for pl in apply_plans]
-        plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dl, sig)]
+        plans = [planner(x, s) for x, s in zip(dl, sig)]
         if spec.get("per_layer"):
             lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=spec["block"], tol=1e-8, seed=1, evecs=evecs)
             lam, nconv = lam[0], int(nconv.min())
@@ -406,7 +411,7 @@ def main():
 
     # ---- CPU baseline (oracle on the host cores) and sampled accuracy, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_baseline:
-        line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch)
+        line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, planner, dev_layers, ml, torch)
     if args.mode == "eig":
         line["lanczos_s"] = t_max / args.steps / 1e3
         line["eigenvalues"] = [float(x) for x in lam[:min(5, k)]]
@@ -523,7 +528,22 @@ def run_ac(args, spec, rank, world, barrier):
     return 0
 
 
-def cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch):
+def make_planner(kind, prec, target, ml):
+    """plan(points, sigma) with the automatic rule, or with the learned model
+    trained for this precision and target (falls back to the rule where no
+    candidate qualifies)."""
+    if kind == "rule":
+        return lambda x, s: ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target)
+    from paper_2007_05239_gb300 import paramnet
+    path = os.path.join(ROOT, "paper_2007_05239_gb300", f"paramnet_{prec}_{target:.0e}.npz")
+    if not os.path.exists(path):
+        raise SystemExit(f"--planner learned needs {path}: python -m paper_2007_05239_gb300.paramnet "
+                         f"--prec {prec} --target {target:.0e} --out {path}")
+    model, margin = paramnet.load_model(path)
+    return lambda x, s: ml.ml_fastsum_plan_learned(x, s, model, prec=prec, target_rel_err=target, margin=margin)[0]
+
+
+def cpu_baseline(layers, sig, planner, dev_layers, ml, torch):
     """Time the oracle's direct FP64 sum of (1/T) sum_t W_t v on a bounded row
     sample (~12 s), and compare the GPU's FP64/FP32-form result on the same rows."""
     from oracle import graph
@@ -541,7 +561,7 @@ def cpu_baseline(layers, sig, prec, target, dev_layers, ml, torch):
     t0 = time.perf_counter()
     ref = sum(graph.W_apply(layers[t], sig[t], v, rows=rows) for t in range(T)) / T
     el = time.perf_counter() - t0
-    plans = [ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target) for x, s in zip(dev_layers, sig)]
+    plans = [planner(x, s) for x, s in zip(dev_layers, sig)]
     Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
     ml.ml_fastsum_apply(plans, torch.as_tensor(v[:, None].copy(), device="cuda"), Y, mode="raw")
     got = Y.cpu().numpy()[rows, 0]

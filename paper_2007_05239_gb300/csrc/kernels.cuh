@@ -153,15 +153,17 @@ struct SpreadArgs {
 };
 
 // Sum of the tiles of each group of consecutive subproblems of one bin
-// (fixed order): gtile[g] = sum_{s in group g} scratch[s].
+// (fixed order): gtile[g] = sum_{s in group g} scratch[s].  CTA b handles
+// group b / chunks and the tile chunk b % chunks (flattened so that the
+// group count is not limited by gridDim.y).
 template <typename T>
 __global__ void __launch_bounds__(256) k_group_sum(const T *__restrict__ scratch, const int *__restrict__ grp_sub,
-                                                  int64_t tile_elems, T *gtile)
+                                                  int64_t tile_elems, int chunks, T *gtile)
 {
-    const int g = blockIdx.y;
+    const int g = blockIdx.x / chunks;
+    const int ch = blockIdx.x - g * chunks;
     const int s0 = grp_sub[g], s1 = grp_sub[g + 1];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tile_elems;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = ch * (int64_t)blockDim.x + threadIdx.x; e < tile_elems; e += (int64_t)chunks * blockDim.x) {
         T acc = 0;
         for (int s = s0; s < s1; ++s) acc += scratch[(int64_t)s * tile_elems + e];
         gtile[(int64_t)g * tile_elems + e] = acc;
@@ -176,17 +178,18 @@ struct GroupArgs {
     int ngroups;
 };
 
+// batched: blockIdx.y is the layer, blockIdx.x = group * chunks + chunk
 template <typename T>
-__global__ void __launch_bounds__(256) k_group_sum_batch(const GroupArgs *__restrict__ args)
+__global__ void __launch_bounds__(256) k_group_sum_batch(const GroupArgs *__restrict__ args, int chunks)
 {
-    const GroupArgs a = args[blockIdx.z];
-    const int g = blockIdx.y;
+    const GroupArgs a = args[blockIdx.y];
+    const int g = blockIdx.x / chunks;
+    const int ch = blockIdx.x - g * chunks;
     if (g >= a.ngroups) return;
     const T *scratch = static_cast<const T *>(a.scratch);
     T *gtile = static_cast<T *>(a.gtile);
     const int s0 = a.grp_sub[g], s1 = a.grp_sub[g + 1];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.tile_elems;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = ch * (int64_t)blockDim.x + threadIdx.x; e < a.tile_elems; e += (int64_t)chunks * blockDim.x) {
         T acc = 0;
         for (int s = s0; s < s1; ++s) acc += scratch[(int64_t)s * a.tile_elems + e];
         gtile[(int64_t)g * a.tile_elems + e] = acc;

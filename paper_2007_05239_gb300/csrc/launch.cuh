@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "kernels.cuh"
@@ -12,11 +13,19 @@
 
 namespace ml {
 
+// Allow `bytes` of dynamic shared memory for `kernel`: the default limit
+// covers static plus dynamic shared memory up to 48 KB; above that the
+// per-kernel maximum is raised (refused beyond the device's opt-in limit).
 template <typename K>
 static ml_status set_smem(K kernel, size_t bytes)
 {
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes", __FILE__, __LINE__);
+    if (fa.sharedSizeBytes + bytes > 48 * 1024) {
+        if (fa.sharedSizeBytes + bytes > 227 * 1024)
+            return fail(ML_ERR_ARG, "a tile needs " + std::to_string(bytes) + " B of shared memory, beyond the limit");
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
     }
     return ML_OK;
@@ -66,7 +75,12 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
             ML_TRY(set_smem(k_spread_f64<D, W, NV>, smem));
             k_spread_f64<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         }
-        ML_CUDA(cudaGetLastError());
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess)
+            return fail(ML_ERR_CUDA, std::string("spread launch failed (") + cudaGetErrorString(le) + "): d=" +
+                                         std::to_string(D) + " W=" + std::to_string(W) + " nv=" + std::to_string(nv) +
+                                         " bin=" + std::to_string(g.B) + " tile=" + std::to_string(tc) +
+                                         " nsub=" + std::to_string(p->nsub) + " sub_max=" + std::to_string(p->sub_max));
     }
     // ---- sum each group of subproblem tiles, then fold the group tiles into
     //      the active grid (work0)
@@ -74,9 +88,9 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     T *gtile = static_cast<T *>(w.scratch) + (int64_t)p->nsub * tile_elems;
     if (p->ngroups > 0) {
         ProfScope pr("group_sum", st);
-        dim3 grid((unsigned)((tile_elems + 255) / 256), (unsigned)p->ngroups);
-        k_group_sum<T><<<grid, 256, 0, st>>>(static_cast<const T *>(w.scratch), p->grp_sub.as<int>(), tile_elems,
-                                             gtile);
+        const int chunks = (int)std::min<int64_t>((tile_elems + 255) / 256, 64);
+        k_group_sum<T><<<(unsigned)((int64_t)p->ngroups * chunks), 256, 0, st>>>(
+            static_cast<const T *>(w.scratch), p->grp_sub.as<int>(), tile_elems, chunks, gtile);
         ML_CUDA(cudaGetLastError());
     }
     FoldArgs fa;
@@ -408,8 +422,9 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     }
     {
         ProfScope pr("group_sum", st);
-        dim3 grid((unsigned)((max_tile * NV + 255) / 256), (unsigned)max_ng, (unsigned)T);
-        k_group_sum_batch<T_><<<grid, 256, 0, st>>>(reinterpret_cast<GroupArgs *>(d + o_ga));
+        const int chunks = (int)std::min<int64_t>((max_tile * NV + 255) / 256, 64);
+        dim3 grid((unsigned)((int64_t)max_ng * chunks), (unsigned)T);
+        k_group_sum_batch<T_><<<grid, 256, 0, st>>>(reinterpret_cast<GroupArgs *>(d + o_ga), chunks);
     }
     {
         ProfScope pr("fold", st);

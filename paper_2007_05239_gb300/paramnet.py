@@ -96,7 +96,11 @@ def make_dataset(first, count, per_cloud, prec, target, seed=0):
         N0 = auto_bandwidth(pts, sigma, prec, target)
         for ci in rng.choice(len(CANDIDATES), size=per_cloud, replace=False):
             cand = CANDIDATES[ci]
-            le, lt = measure(pts, sigma, prec, target, cand, v, rows, ref, N0)
+            try:
+                le, lt = measure(pts, sigma, prec, target, cand, v, rows, ref, N0)
+            except ml.MLError as e:   # a candidate the library refuses (e.g. a grid beyond the limits)
+                print(f"cloud {i} candidate {cand}: {e}", flush=True)
+                continue
             Xs.append(np.concatenate([feat, np.asarray(cand, dtype=np.float32)]))
             Ys.append([le, lt])
             ids.append(i)

@@ -257,3 +257,20 @@ def test_isolated_point_degree_error_only_for_normalised_products():
         with pytest.raises(ml.MLError) as e:
             ml.ml_fastsum_apply([plan], V, Y, mode="normalized")
         assert e.value.status == ml.ML_ERR_DEGREE
+
+
+def test_more_tile_groups_than_a_grid_dimension():
+    # a narrow kernel in a 3-D cloud at oversampling 3 spreads 158k points over
+    # more than 65,535 tiles: the tile sums must not depend on gridDim.y
+    X, sigma = workloads.cloud_for_mlp(17)
+    n = X.shape[0]
+    plan = ml.ml_fastsum_plan_ex(torch.as_tensor(X, device="cuda"), sigma, taps=8, oversampling=3.0, prec="f64",
+                                 target_rel_err=1e-6)
+    assert plan.info["nsub"] > 65535
+    v = np.random.default_rng(9).uniform(0, 1, n)
+    Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+    ml.ml_fastsum_apply([plan], torch.as_tensor(v[:, None].copy(), device="cuda"), Y, mode="raw")
+    rows = np.sort(np.random.default_rng(10).choice(n, 300, replace=False))
+    ref = graph.W_apply(X, sigma, v, rows=rows)
+    got = Y.cpu().numpy()[rows, 0]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
