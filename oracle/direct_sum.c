@@ -26,7 +26,7 @@
 int oracle_gauss_rows(const double *X, int64_t n, int d, double sigma, const double *V, int b,
                       const int64_t *rows, int64_t nrows, double *out, int nthreads)
 {
-    if (!X || !V || !out || n <= 0 || d < 1 || d > 16 || b < 1 || b > ORACLE_MAXB || !(sigma > 0))
+    if (!X || !V || !out || n <= 0 || d < 1 || b < 1 || b > ORACLE_MAXB || !(sigma > 0))
         return -1;
     if (rows == NULL) nrows = n;
     const double inv_s2 = 1.0 / (sigma * sigma);

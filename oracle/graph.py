@@ -57,10 +57,15 @@ def gaussian(r2, sigma):
 
 
 def weight_matrix(X, sigma):
-    """Dense W (n x n) with zero diagonal.  Small n only."""
+    """Dense W (n x n) with zero diagonal, squared distances summed from the
+    coordinate differences (blocks of rows, any dimension).  Small n only."""
     X = np.asarray(X, dtype=np.float64)
-    diff = X[:, None, :] - X[None, :, :]
-    W = gaussian(np.einsum("ijk,ijk->ij", diff, diff), sigma)
+    n = X.shape[0]
+    W = np.empty((n, n))
+    step = max(1, int(2 ** 24 // max(1, n * X.shape[1])))
+    for i0 in range(0, n, step):
+        diff = X[i0:i0 + step, None, :] - X[None, :, :]
+        W[i0:i0 + step] = gaussian(np.einsum("ijk,ijk->ij", diff, diff), sigma)
     np.fill_diagonal(W, 0.0)
     return W
 
