@@ -97,6 +97,8 @@ typedef struct {
                                 since the plan was made (work counter)          */
     int taps;                /* window width: taps per dimension (half-width taps/2;
                                 automatic choices may be odd)                    */
+    int dense;               /* 1: dense layer (ml_dense_plan*), W stored; the
+                                NFFT fields above are 0                          */
 } ml_plan_info;
 
 /*
@@ -151,6 +153,27 @@ typedef struct {
  */
 ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
                              const ml_plan_params *params, void *stream);
+
+/*
+ * ml_dense_plan - a dense layer for small graphs (the explicit regime, any
+ * feature dimension): W_ij = exp(-||x_i - x_j||^2 / sigma^2), i != j (Sec. 2),
+ * formed once on the GPU (squared distances summed from coordinate
+ * differences in FP64) and stored n x n in FP64 (ML_F64) or FP32 (ML_F32);
+ * the degrees are its row sums.  Products stream W once per pass of up to
+ * 8 vectors with FP64 accumulation.  The plan is accepted everywhere a
+ * fast-summation plan is (ml_fastsum_apply, the eigensolvers, layers mixed
+ * with fast-summation layers).
+ *   points  device, n x d row-major FP64, read during the call;  d >= 1.
+ *   n       2..131072 (W takes n^2 x 8 or 4 bytes of device memory).
+ * Synchronises `stream`.  Errors: ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA.
+ *
+ * ml_dense_plan_matrix - the same from a given symmetric weight matrix W
+ * (device, n x n row-major FP64, e.g. the adjacency matrix of a stochastic
+ * block model layer); its diagonal is taken as zero (no self-edges, Sec. 2).
+ */
+ml_status ml_dense_plan(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, ml_prec prec,
+                        void *stream);
+ml_status ml_dense_plan_matrix(ml_plan_t *out, const double *W, int64_t n, ml_prec prec, void *stream);
 
 /*
  * ml_fastsum_plan_autotune - ml_fastsum_plan_ex with the spreading tile (bin)

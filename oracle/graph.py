@@ -140,11 +140,17 @@ def multilayer_W_apply(layers, sigmas, V, nthreads=0):
     return acc / T
 
 
-def L_sym_dense(X, sigma):
-    """Dense L_sym = I - D^{-1/2} W D^{-1/2} (Sec. 2).  Small n only."""
-    W = weight_matrix(X, sigma)
+def L_sym_from_W(W):
+    """L_sym = I - D^{-1/2} W D^{-1/2}, D = diag(W 1) (Sec. 2), for a given
+    symmetric weight matrix with zero diagonal."""
+    W = np.asarray(W, dtype=np.float64)
     s = 1.0 / np.sqrt(W.sum(axis=1))
     return np.eye(W.shape[0]) - (s[:, None] * W) * s[None, :]
+
+
+def L_sym_dense(X, sigma):
+    """Dense L_sym = I - D^{-1/2} W D^{-1/2} (Sec. 2).  Small n only."""
+    return L_sym_from_W(weight_matrix(X, sigma))
 
 
 def shift_delta(p):

@@ -25,6 +25,7 @@ MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
 EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", "ml_fastsum_plan_learned",
+           "ml_dense_plan", "ml_dense_plan_matrix",
            "ml_fastsum_apply",
            "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
            "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
@@ -61,7 +62,7 @@ class PlanInfo(ctypes.Structure):
                 ("eps_B", ctypes.c_double), ("sigma", ctypes.c_double), ("sigma_s", ctypes.c_double),
                 ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("target_rel_err", ctypes.c_double),
                 ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("applied_vectors", ctypes.c_int64), ("taps", ctypes.c_int)]
+                ("applied_vectors", ctypes.c_int64), ("taps", ctypes.c_int), ("dense", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -112,6 +113,11 @@ def load():
     lib.ml_fastsum_plan_ex.restype = ctypes.c_int
     lib.ml_fastsum_plan_ex.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(PlanParams), P]
+    lib.ml_dense_plan.restype = ctypes.c_int
+    lib.ml_dense_plan.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                  P]
+    lib.ml_dense_plan_matrix.restype = ctypes.c_int
+    lib.ml_dense_plan_matrix.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, P]
     lib.ml_fastsum_plan_autotune.restype = ctypes.c_int
     lib.ml_fastsum_plan_autotune.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, P,
                                              ctypes.c_int, P, P]
@@ -252,6 +258,26 @@ def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, 
     _check(lib.ml_fastsum_plan_ex(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
                                   _stream(stream)))
     return Plan(h.value, n, d)
+
+
+def ml_dense_plan(points, sigma, prec="f64", stream=None):
+    """Dense layer (W stored, any feature dimension) from device points (n, d)."""
+    lib = load()
+    n, d = int(points.shape[0]), int(points.shape[1])
+    h = ctypes.c_void_p()
+    _check(lib.ml_dense_plan(ctypes.byref(h), _ptr(points), n, d, float(sigma),
+                             {"f32": ML_F32, "f64": ML_F64}[prec], _stream(stream)))
+    return Plan(h.value, n, d)
+
+
+def ml_dense_plan_matrix(W, prec="f64", stream=None):
+    """Dense layer from a given symmetric device weight matrix (n, n) float64."""
+    lib = load()
+    n = int(W.shape[0])
+    h = ctypes.c_void_p()
+    _check(lib.ml_dense_plan_matrix(ctypes.byref(h), _ptr(W), n, {"f32": ML_F32, "f64": ML_F64}[prec],
+                                    _stream(stream)))
+    return Plan(h.value, n, 0)
 
 
 def ml_fastsum_plan_autotune(points, sigma, nv=1, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",

@@ -30,7 +30,8 @@ bool batchable(ml_plan_s *const *L, int T)
     const ml_plan_s *p0 = L[0];
     for (int t = 0; t < T; ++t) {
         const ml_plan_s *p = L[t];
-        if (p->prec != ML_F32 || p->d != p0->d || p->W != p0->W || p->g.nbins() != 1 || p->nsub != p0->nsub)
+        if (p->dense || p->prec != ML_F32 || p->d != p0->d || p->W != p0->W || p->g.nbins() != 1 ||
+            p->nsub != p0->nsub)
             return false;
         if (p->sub_max > kBatchPtsTotal) return false;
     }
@@ -42,7 +43,7 @@ bool batchable_layers(ml_plan_s *const *L, int T)
 {
     if (T < 2) return false;
     for (int t = 0; t < T; ++t)
-        if (L[t]->prec != ML_F32 || L[t]->d != L[0]->d || L[t]->W != L[0]->W) return false;
+        if (L[t]->dense || L[t]->prec != ML_F32 || L[t]->d != L[0]->d || L[t]->W != L[0]->W) return false;
     return true;
 }
 
@@ -60,6 +61,7 @@ ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cons
 {
     if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
     p->applied += v.nv;
+    if (p->dense) return run_dense(p, v, o, st);
     if (p->prec == ML_F32) {
         switch (p->d) {
         case 1: return run_layer_f32_d1(p, v, o, w, st);

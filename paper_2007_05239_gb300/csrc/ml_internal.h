@@ -114,6 +114,7 @@ struct ml_plan_s {
     double deg_min = 0, deg_max = 0;
     bool deg_ok = true;    // every degree positive and finite: D^{-1/2} defined
     int64_t applied = 0;   // vectors pushed through apply_layer
+    bool dense = false;    // dense layer: W stored explicitly (Wd), no fast summation
 
     // host tables (FP64)
     std::vector<double> bhat;    // (N/2+1)^d
@@ -134,6 +135,7 @@ struct ml_plan_s {
     ml::DevBuf trig_f[3]; // K x L_a (forward, cos rows then sin rows): float, or float2 pairs (FP64 form)
     ml::DevBuf trig_b[3]; // L_a x K (backward = transpose), same element type
     ml::DevBuf mult_d;    // K^d slot multipliers, same element type
+    ml::DevBuf Wd;        // dense layers: W, n x n row-major (FP32 or FP64), zero diagonal
 
     // workspace
     ml::DevBuf scratch;   // spreading tiles: nsub * Pt^d * vp (T)
@@ -227,6 +229,8 @@ private:
     bool active_ = false;
 };
 ml_status ensure_workspace(ml_plan_s *p, int nv);
+// product of a dense layer (W stored in the plan), same options as apply_layer
+ml_status run_dense(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
 // sign of each column of V (n x k, column-major): largest-magnitude entry positive
 ml_status sign_fix_cols(double *V, int64_t n, int k, cudaStream_t st);
 

@@ -498,6 +498,11 @@ static ml_status upload_dw(DevBuf &buf, const std::vector<double> &src)
 
 void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work)
 {
+    if (p->dense) {   // a dense product needs no scratch
+        *scratch = 0;
+        *work = 0;
+        return;
+    }
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     const GridGeom &g = p->g;
     // subproblem tiles, then one tile per group of subproblems
@@ -825,7 +830,7 @@ int64_t ml_plan_s::device_bytes() const
     int64_t t = 0;
     const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
-                                &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status};
+                                &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status, &Wd};
     for (auto *b : bufs) t += (int64_t)b->bytes;
     return t;
 }
@@ -835,7 +840,7 @@ static void release_all(ml_plan_s *p)
     ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
-                          &p->stage_y, &p->status, &p->batch_desc, &p->batch_part};
+                          &p->stage_y, &p->status, &p->batch_desc, &p->batch_part, &p->Wd};
     for (auto *b : bufs) b->release();
 }
 
@@ -942,6 +947,7 @@ ml_status ml_plan_get_info(ml_plan_t p, ml_plan_info *info)
     info->deg_max = p->deg_max;
     info->device_bytes = p->device_bytes();
     info->applied_vectors = p->applied;
+    info->dense = p->dense ? 1 : 0;
     return ML_OK;
 }
 
