@@ -334,46 +334,81 @@ struct Workspace {
     }
 };
 
-// y = (1/T) sum_t (L_sym^(t) + delta I)^{-1} x by CG per layer
+// y = (1/T) sum_t (L_sym^(t) + delta I)^{-1} x by CG per layer.  The T
+// solves are independent: each runs on its own non-blocking stream with its
+// own vectors and scalars, so the layers' small kernels (transforms, folds,
+// CG scalars) overlap with the other layers' spreading and interpolation.
+// The streams fork from and join the caller's stream through events; the
+// layer results are summed on the caller's stream in layer order.
 struct InverseOp {
     ml_plan_s *const *layers;
     int T;
     double delta;
     int64_t n;
     Workspace *ws;
-    DevBuf r, p, ap, y;
     int inner_max = 200;
     double inner_tol = 1e-12;
     long long inner_iters = 0;
-    // the residual of iteration i is copied to pinned host memory and read
-    // while iteration i+1 runs (one iteration of lag, no pipeline bubble)
-    double *hrr = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    // one CG iteration of each layer captured as a CUDA graph (its pointers
-    // never change during the solve) and replayed; used while kernel timing
-    // is off, since per-kernel events cannot be recorded inside a graph
-    std::vector<cudaGraphExec_t> graph;
+    struct Lane {
+        DevBuf r, p, ap, y, part, sc;
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};   // residual of iterations i, i+1 (lagged host check)
+        cudaEvent_t join = nullptr;
+        // one CG iteration captured as a CUDA graph (its pointers never change
+        // during the solve) and replayed while kernel timing is off, since
+        // per-kernel events cannot be recorded inside a graph
+        cudaGraphExec_t graph = nullptr;
+    };
+    std::vector<Lane> lanes;
+    cudaEvent_t fork = nullptr;
+    double *hrr = nullptr;   // pinned: T x 2 residuals
     bool graphs_ok = true;
+
+    bool own_streams = true;   // false: one stream for all layers (a plan passed twice shares its
+                               // workspace; kernel timing wants kernels alone)
 
     ml_status init()
     {
-        graph.assign(T, nullptr);
-        ML_TRY(r.ensure(n * 8));
-        ML_TRY(p.ensure(n * 8));
-        ML_TRY(ap.ensure(n * 8));
-        ML_TRY(y.ensure(n * 8));
-        ML_CUDA(cudaMallocHost(&hrr, 2 * sizeof(double)));
-        ML_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-        ML_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        lanes.resize(T);
+        const int pb = ws->nblk;
+        for (int a = 0; a < T; ++a)
+            for (int b = a + 1; b < T; ++b)
+                if (layers[a] == layers[b]) own_streams = false;
+        // while kernels are timed, one stream: each event pair then brackets one kernel alone
+        if (profiling()) own_streams = false;
+        for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            ML_TRY(L.r.ensure(n * 8));
+            ML_TRY(L.p.ensure(n * 8));
+            ML_TRY(L.ap.ensure(n * 8));
+            ML_TRY(L.y.ensure(n * 8));
+            ML_TRY(L.part.ensure((size_t)pb * 8));
+            ML_TRY(L.sc.ensure(8 * 8));
+            if (own_streams || t == 0) ML_CUDA(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
+            else L.s = lanes[0].s;
+            for (auto &e : L.ev) ML_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ML_CUDA(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
+        }
+        ML_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        ML_CUDA(cudaMallocHost(&hrr, (size_t)2 * T * sizeof(double)));
         return ML_OK;
     }
     ~InverseOp()
     {
-        for (auto &g : graph)
-            if (g) cudaGraphExecDestroy(g);
+        // finish all work first (lanes may share one stream), then release
+        for (int t = 0; t < (int)lanes.size(); ++t)
+            if (lanes[t].s && (own_streams || t == 0)) cudaStreamSynchronize(lanes[t].s);
+        for (int t = 0; t < (int)lanes.size(); ++t) {
+            Lane &L = lanes[t];
+            if (L.graph) cudaGraphExecDestroy(L.graph);
+            for (auto &e : L.ev)
+                if (e) cudaEventDestroy(e);
+            if (L.join) cudaEventDestroy(L.join);
+            if (L.s && (own_streams || t == 0)) cudaStreamDestroy(L.s);
+        }
+        if (fork) cudaEventDestroy(fork);
         if (hrr) cudaFreeHost(hrr);
-        for (auto &e : ev)
-            if (e) cudaEventDestroy(e);
+        cudaGetLastError();   // nothing from the clean-up may leak into the caller's next check
     }
     // ap = (L_sym + delta I) v = (1 + delta) v - A v
     ml_status shifted(ml_plan_s *L, const double *v, double *out, cudaStream_t st)
@@ -385,93 +420,121 @@ struct InverseOp {
         o.shift = 1.0 + delta;
         return apply_layer(L, av, o, st);
     }
+    // one CG iteration of layer t on its stream: Ap, alpha, x/r update, beta, new direction
+    ml_status iteration(int t)
+    {
+        Lane &L = lanes[t];
+        const int nb = vec_blocks(n), pb = ws->nblk;
+        double *part = L.part.as<double>(), *sc = L.sc.as<double>();
+        ML_TRY(shifted(layers[t], L.p.as<double>(), L.ap.as<double>(), L.s));
+        {
+            ProfScope pr("cg", L.s);
+            k_dot_part<<<pb, 256, 0, L.s>>>(L.p.as<double>(), L.ap.as<double>(), n, part);
+            k_cg_scalars<<<1, 32, 0, L.s>>>(part, pb, 0, sc);
+            k_cg_step<<<pb, 256, 0, L.s>>>(sc, L.p.as<double>(), L.ap.as<double>(), n, L.y.as<double>(),
+                                           L.r.as<double>(), part);
+            k_cg_scalars<<<1, 32, 0, L.s>>>(part, pb, 1, sc);
+            k_cg_dir<<<nb, 256, 0, L.s>>>(sc, L.r.as<double>(), n, L.p.as<double>());
+        }
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+    // run iteration it of layer t: eagerly, or through its graph (captured at it = 1)
+    ml_status step(int t, int it)
+    {
+        Lane &L = lanes[t];
+        const bool use_graph = graphs_ok && !profiling() && it >= 1;
+        if (use_graph && !L.graph) {
+            // the first iteration ran eagerly (workspace, attributes): capture the second
+            cudaGraph_t g = nullptr;
+            const int64_t applied0 = layers[t]->applied;   // capturing runs no work
+            cudaError_t e = cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal);
+            ml_status cs = ML_OK;
+            if (e == cudaSuccess) {
+                cs = iteration(t);
+                e = cudaStreamEndCapture(L.s, &g);
+            }
+            if (e == cudaSuccess && cs == ML_OK && g) e = cudaGraphInstantiate(&L.graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            layers[t]->applied = applied0;
+            if (e != cudaSuccess || cs != ML_OK || !L.graph) {
+                cudaGetLastError();   // capture not possible here: run eagerly from now on
+                graphs_ok = false;
+                L.graph = nullptr;
+            }
+        }
+        if (graphs_ok && !profiling() && L.graph) {
+            ML_CUDA(cudaGraphLaunch(L.graph, L.s));
+            layers[t]->applied += 1;   // the replayed product's work counter
+        } else {
+            ML_TRY(iteration(t));
+        }
+        ++inner_iters;
+        return ML_OK;
+    }
     ml_status apply(const double *x, double *out, cudaStream_t st)
     {
-        const int nb = vec_blocks(n);
-        const int pb = ws->nblk;
-        double *part = ws->part.as<double>();
-        double *sc = ws->scal.as<double>() + 8;
-        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
-        // ||x||^2 for the relative stopping test
+        const int nb = vec_blocks(n), pb = ws->nblk;
+        // ||x||^2 for the relative stopping test (x is ready on st)
         double bb;
         ML_TRY(ws->dot_host(x, x, &bb));
         const double stop2 = inner_tol * inner_tol * bb;
+        ML_CUDA(cudaEventRecord(fork, st));
+        std::vector<char> done(T, !(bb > 0) ? 1 : 0);
         for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            ML_CUDA(cudaStreamWaitEvent(L.s, fork, 0));
             // x0 = 0: r = x, p = x, r.r = ||x||^2
-            ML_CUDA(cudaMemcpyAsync(r.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
-            ML_CUDA(cudaMemcpyAsync(p.p, x, n * 8, cudaMemcpyDeviceToDevice, st));
-            ML_CUDA(cudaMemsetAsync(y.p, 0, n * 8, st));
+            ML_CUDA(cudaMemcpyAsync(L.r.p, x, n * 8, cudaMemcpyDeviceToDevice, L.s));
+            ML_CUDA(cudaMemcpyAsync(L.p.p, x, n * 8, cudaMemcpyDeviceToDevice, L.s));
+            ML_CUDA(cudaMemsetAsync(L.y.p, 0, n * 8, L.s));
             {
-                ProfScope pr("cg", st);
-                k_dot_part<<<pb, 256, 0, st>>>(x, x, n, part);
-                k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 2, sc);
+                ProfScope pr("cg", L.s);
+                k_dot_part<<<pb, 256, 0, L.s>>>(x, x, n, L.part.as<double>());
+                k_cg_scalars<<<1, 32, 0, L.s>>>(L.part.as<double>(), pb, 2, L.sc.as<double>());
             }
-            bool done = !(bb > 0);
-            // one CG iteration: Ap, alpha, x/r update, beta, new direction
-            auto iteration = [&]() -> ml_status {
-                ML_TRY(shifted(layers[t], p.as<double>(), ap.as<double>(), st));
-                {
-                    ProfScope pr("cg", st);
-                    k_dot_part<<<pb, 256, 0, st>>>(p.as<double>(), ap.as<double>(), n, part);
-                    k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 0, sc);
-                    k_cg_step<<<pb, 256, 0, st>>>(sc, p.as<double>(), ap.as<double>(), n, y.as<double>(),
-                                                  r.as<double>(), part);
-                    k_cg_scalars<<<1, 32, 0, st>>>(part, pb, 1, sc);
-                    k_cg_dir<<<nb, 256, 0, st>>>(sc, r.as<double>(), n, p.as<double>());
-                }
-                ML_CUDA(cudaGetLastError());
-                return ML_OK;
-            };
-            for (int it = 0; it < inner_max && !done; ++it) {
-                const bool use_graph = graphs_ok && !profiling() && it >= 1;
-                if (use_graph && !graph[t]) {
-                    // the first iteration ran eagerly (workspace, attributes): capture the second
-                    cudaGraph_t g = nullptr;
-                    const int64_t applied0 = layers[t]->applied;   // capturing runs no work
-                    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-                    ml_status cs = ML_OK;
-                    if (e == cudaSuccess) {
-                        cs = iteration();
-                        e = cudaStreamEndCapture(st, &g);
-                    }
-                    if (e == cudaSuccess && cs == ML_OK && g) e = cudaGraphInstantiate(&graph[t], g, 0);
-                    if (g) cudaGraphDestroy(g);
-                    layers[t]->applied = applied0;
-                    if (e != cudaSuccess || cs != ML_OK || !graph[t]) {
-                        // capture not possible here: run eagerly from now on
-                        cudaGetLastError();
-                        graphs_ok = false;
-                        graph[t] = nullptr;
-                    }
-                }
-                if (graphs_ok && !profiling() && graph[t]) {
-                    ML_CUDA(cudaGraphLaunch(graph[t], st));
-                    layers[t]->applied += 1;   // the replayed product's work counter
-                } else {
-                    ML_TRY(iteration());
-                }
-                ++inner_iters;
-                ML_CUDA(cudaMemcpyAsync(hrr + (it & 1), sc, sizeof(double), cudaMemcpyDeviceToHost, st));
-                ML_CUDA(cudaEventRecord(ev[it & 1], st));
-                if (it >= 1) {
-                    ML_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));
-                    done = hrr[(it - 1) & 1] <= stop2;
-                }
+            ML_CUDA(cudaGetLastError());
+        }
+        // all layers advance together; the residual of iteration it is read
+        // while iteration it+1 runs (one iteration of lag, no pipeline bubble)
+        for (int it = 0; it < inner_max; ++it) {
+            bool any = false;
+            for (int t = 0; t < T; ++t) {
+                if (done[t]) continue;
+                any = true;
+                Lane &L = lanes[t];
+                ML_TRY(step(t, it));
+                ML_CUDA(cudaMemcpyAsync(hrr + 2 * t + (it & 1), L.sc.p, sizeof(double), cudaMemcpyDeviceToHost, L.s));
+                ML_CUDA(cudaEventRecord(L.ev[it & 1], L.s));
             }
-            ML_CUDA(cudaStreamSynchronize(st));
-            if (!done) {
+            if (!any) break;
+            if (it >= 1)
+                for (int t = 0; t < T; ++t) {
+                    if (done[t]) continue;
+                    ML_CUDA(cudaEventSynchronize(lanes[t].ev[(it - 1) & 1]));
+                    done[t] = hrr[2 * t + ((it - 1) & 1)] <= stop2;
+                }
+        }
+        for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            ML_CUDA(cudaStreamSynchronize(L.s));
+            if (!done[t]) {
                 double hs[2];
-                ML_CUDA(cudaMemcpy(hs, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+                ML_CUDA(cudaMemcpy(hs, L.sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost));
                 if (hs[0] > stop2)
                     return fail(ML_ERR_BREAKDOWN, !(hs[1] > 0) ? "CG: operator not positive definite (p^T A p <= 0)"
                                                                : "CG: inner solve did not converge");
             }
-            {
-                ProfScope pr("vector", st);
-                k_axpy<<<nb, 256, 0, st>>>(1.0 / T, y.as<double>(), n, out);
-            }
-            ML_CUDA(cudaGetLastError());
+            ML_CUDA(cudaEventRecord(L.join, L.s));
+            ML_CUDA(cudaStreamWaitEvent(st, L.join, 0));
         }
+        // out = (1/T) sum_t y_t in layer order, on the caller's stream
+        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
+        for (int t = 0; t < T; ++t) {
+            ProfScope pr("vector", st);
+            k_axpy<<<nb, 256, 0, st>>>(1.0 / T, lanes[t].y.as<double>(), n, out);
+        }
+        ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
 };

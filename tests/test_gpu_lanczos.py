@@ -118,3 +118,14 @@ def test_graph_replay_matches_eager_launches():
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2]
+
+
+def test_same_plan_twice_at_p_minus_one():
+    # T identical layers: L_{-1,delta} = L_sym + delta I (Eq. L_p_delta_power_p);
+    # the two CG solves share one plan and must not run concurrently on it
+    n = 800
+    X = workloads.uniform_cube(n, 3, seed=150)
+    plan = ml.ml_fastsum_plan(dev(X), 0.1, prec="f64", target_rel_err=1e-12)
+    lam, nconv, st = ml.ml_lanczos_eigs([plan, plan], 4, p=-1.0, tol=1e-10, seed=5)
+    lam_ref, _ = eigen.lsym_eigs(X, 0.1, 4)
+    assert np.abs(lam - (lam_ref + math.log(2.0))).max() <= 1e-8
