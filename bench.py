@@ -285,6 +285,7 @@ def main():
     k, p, prec, target = spec["k"], spec["p"], spec["prec"], spec["target"]
 
     planner = make_planner(args.planner, prec, target, ml)
+    plan_all = make_planner("many", prec, target, ml) if args.planner == "rule" else None
     apply_plans = None
     if args.mode == "apply":
         apply_plans = [planner(x, s) for x, s in zip(dev_layers, sig)]
@@ -297,7 +298,7 @@ def main():
             ml.ml_fastsum_apply(apply_plans, Xa, Ya, mode="normalized")
             applied = (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
             return None, 0, applied, [pl.info["taps"] for pl in apply_plans]
-        plans = [planner(x, s) for x, s in zip(dl, sig)]
+        plans = plan_all(dl, sig) if plan_all else [planner(x, s) for x, s in zip(dl, sig)]
         if spec.get("per_layer"):
             lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=spec["block"], tol=1e-8, seed=1, evecs=evecs)
             lam, nconv = lam[0], int(nconv.min())
@@ -534,6 +535,8 @@ def make_planner(kind, prec, target, ml):
     candidate qualifies)."""
     if kind == "rule":
         return lambda x, s: ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target)
+    if kind == "many":   # all layers at once (concurrent set-up)
+        return lambda xs, ss: ml.ml_fastsum_plan_many(xs, ss, prec=prec, target_rel_err=target)
     from paper_2007_05239_gb300 import paramnet
     path = os.path.join(ROOT, "paper_2007_05239_gb300", f"paramnet_{prec}_{target:.0e}.npz")
     if not os.path.exists(path):

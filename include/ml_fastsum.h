@@ -194,6 +194,21 @@ ml_status ml_fastsum_plan_autotune(ml_plan_t *out, const double *points, int64_t
                                    const ml_plan_params *params, int nv, int *bin_chosen, void *stream);
 
 /*
+ * ml_fastsum_plan_many - the plans of T layers sharing n (ml_fastsum_plan_ex
+ * with the same params for every layer), built concurrently by host threads,
+ * each on its own non-blocking stream (not from the paper: plan set-up is
+ * latency-bound, the layers are independent).
+ *   out     host array of T handles (all NULL on failure).
+ *   points  host array of T device pointers (layer t: n x d[t] FP64), ready
+ *           in stream order on `stream`.
+ *   d, sigma host arrays of T.
+ * Returns when every plan is complete.  Errors as ml_fastsum_plan_ex, with
+ * the failing layer named in ml_last_error().
+ */
+ml_status ml_fastsum_plan_many(ml_plan_t *out, const double *const *points, int64_t n, const int *d,
+                               const double *sigma, const ml_plan_params *params, int T, void *stream);
+
+/*
  * ml_direct_sum_rows - the exact definition of the product on selected rows:
  * out[r] = sum_{j != rows[r]} exp(-||x_{rows[r]} - x_j||^2 / sigma^2) v_j
  * (W v of Sec. 2 / Sec. 4, direct O(nrows n) summation in FP64 on the GPU).

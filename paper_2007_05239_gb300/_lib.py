@@ -25,7 +25,7 @@ MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
 # every symbol the header declares
 EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", "ml_fastsum_plan_learned",
-           "ml_dense_plan", "ml_dense_plan_matrix",
+           "ml_fastsum_plan_many", "ml_dense_plan", "ml_dense_plan_matrix",
            "ml_fastsum_apply",
            "ml_fastsum_apply_noalloc", "ml_direct_sum_rows", "ml_cloud_features", "ml_mlp_create",
            "ml_mlp_param_count", "ml_mlp_get_params", "ml_mlp_set_params", "ml_mlp_set_norm", "ml_mlp_forward",
@@ -113,6 +113,8 @@ def load():
     lib.ml_fastsum_plan_ex.restype = ctypes.c_int
     lib.ml_fastsum_plan_ex.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(PlanParams), P]
+    lib.ml_fastsum_plan_many.restype = ctypes.c_int
+    lib.ml_fastsum_plan_many.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int, P]
     lib.ml_dense_plan.restype = ctypes.c_int
     lib.ml_dense_plan.argtypes = [ctypes.POINTER(P), P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   P]
@@ -258,6 +260,21 @@ def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, 
     _check(lib.ml_fastsum_plan_ex(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
                                   _stream(stream)))
     return Plan(h.value, n, d)
+
+
+def ml_fastsum_plan_many(points, sigmas, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
+                         target_rel_err=0.0, stream=None):
+    """Plans of several layers (device point tensors sharing n), built concurrently."""
+    lib = load()
+    T = len(points)
+    n = int(points[0].shape[0])
+    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, 0)
+    handles = (ctypes.c_void_p * T)()
+    ptrs = (ctypes.c_void_p * T)(*[_ptr(x) for x in points])
+    dims = (ctypes.c_int * T)(*[int(x.shape[1]) for x in points])
+    sig = (ctypes.c_double * T)(*[float(s) for s in sigmas])
+    _check(lib.ml_fastsum_plan_many(handles, ptrs, n, dims, sig, ctypes.byref(prm), T, _stream(stream)))
+    return [Plan(handles[t], n, dims[t]) for t in range(T)]
 
 
 def ml_dense_plan(points, sigma, prec="f64", stream=None):

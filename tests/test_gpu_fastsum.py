@@ -274,3 +274,21 @@ def test_more_tile_groups_than_a_grid_dimension():
     ref = graph.W_apply(X, sigma, v, rows=rows)
     got = Y.cpu().numpy()[rows, 0]
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+def test_plan_many_equals_single_plans():
+    # concurrent set-up of several layers gives the same plans as one at a time
+    layers, _ = workloads.gmm_band_layers(20000, 16, 4, seed=60)
+    sig = [0.5 * float((L.max(0) - L.min(0)).max()) for L in layers]
+    dl = [torch.as_tensor(L, device="cuda") for L in layers]
+    many = ml.ml_fastsum_plan_many(dl, sig, prec="f32")
+    single = [ml.ml_fastsum_plan(x, s, prec="f32") for x, s in zip(dl, sig)]
+    v = torch.as_tensor(np.random.default_rng(61).uniform(0, 1, (20000, 1)), device="cuda")
+    for a, b in zip(many, single):
+        ia, ib = a.info, b.info
+        for key in ("N", "taps", "n_os", "bin", "nsub", "deg_min", "deg_max"):
+            assert ia[key] == ib[key], key
+        Ya, Yb = torch.empty_like(v), torch.empty_like(v)
+        ml.ml_fastsum_apply([a], v, Ya, mode="normalized")
+        ml.ml_fastsum_apply([b], v, Yb, mode="normalized")
+        assert torch.equal(Ya, Yb)
