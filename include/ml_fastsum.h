@@ -474,6 +474,9 @@ ml_status ml_plan_copy_table(ml_plan_t plan, int which, double *out, int64_t cou
 ml_status ml_profile_enable(int on);
 ml_status ml_profile_reset(void);
 ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *ms);
+/* CUDA-graph replays of captured inner solver iterations since the library
+ * was loaded (diagnostics: 0 means every iteration launched eagerly). */
+int64_t ml_graph_replays(void);
 
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 ml_status ml_plan_destroy(ml_plan_t plan);

@@ -32,7 +32,7 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers", "ml_allen_cahn",
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
-           "ml_profile_reset", "ml_profile_read"]
+           "ml_profile_reset", "ml_profile_read", "ml_graph_replays"]
 
 
 class MLError(RuntimeError):
@@ -149,6 +149,8 @@ def load():
     lib.ml_mlp_set_margins.argtypes = [P, P, ctypes.c_int]
     lib.ml_mlp_destroy.restype = ctypes.c_int
     lib.ml_mlp_destroy.argtypes = [P]
+    lib.ml_graph_replays.restype = ctypes.c_int64
+    lib.ml_graph_replays.argtypes = []
     lib.ml_profile_enable.restype = ctypes.c_int
     lib.ml_profile_enable.argtypes = [ctypes.c_int]
     lib.ml_profile_reset.restype = ctypes.c_int
@@ -499,6 +501,11 @@ def ml_allen_cahn(Phi, lam, labels, m, eps=0.005, omega0=1000.0, c=0.0, dt=0.01,
     _check(lib.ml_allen_cahn(_ptr(Phi), lam.ctypes.data, n, k, _ptr_i32(labels), int(m), ctypes.byref(prm), _ptr(U),
                              _ptr_i32(pred), ctypes.byref(iters), ctypes.byref(chg), _stream(stream)))
     return U, pred, iters.value, chg.value
+
+
+def ml_graph_replays():
+    """CUDA-graph replays of captured solver iterations since the library was loaded."""
+    return int(load().ml_graph_replays())
 
 
 def ml_profile_enable(on=True):

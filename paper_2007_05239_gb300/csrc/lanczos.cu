@@ -466,6 +466,7 @@ struct InverseOp {
         if (graphs_ok && !profiling() && L.graph) {
             ML_CUDA(cudaGraphLaunch(L.graph, L.s));
             layers[t]->applied += 1;   // the replayed product's work counter
+            count_graph_replay();
         } else {
             ML_TRY(iteration(t));
         }

@@ -203,6 +203,8 @@ ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaS
 
 // ---------------------------------------------------------------- tracing
 bool profiling();
+// counts one CUDA-graph replay of a captured solver iteration (diagnostics)
+void count_graph_replay();
 // Switches kernel timing off on this thread for its lifetime (timing creates
 // CUDA events, which callers that must not allocate cannot accept).
 class NoProfileScope {

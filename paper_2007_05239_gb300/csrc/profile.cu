@@ -21,6 +21,7 @@ struct Entry {
     std::vector<Pending> pending;
 };
 std::atomic<bool> g_on{false};
+std::atomic<long long> g_graph_replays{0};
 std::mutex g_mu;
 std::map<std::string, Entry> g_tab;
 std::vector<cudaEvent_t> g_pool;
@@ -53,6 +54,7 @@ void drain(Entry &en)
 static thread_local bool t_suppress = false;
 
 bool profiling() { return !t_suppress && g_on.load(std::memory_order_relaxed); }
+void count_graph_replay() { g_graph_replays.fetch_add(1, std::memory_order_relaxed); }
 
 NoProfileScope::NoProfileScope() : prev_(t_suppress) { t_suppress = true; }
 NoProfileScope::~NoProfileScope() { t_suppress = prev_; }
@@ -95,6 +97,8 @@ ml_status ml_profile_reset(void)
     ml::g_tab.clear();
     return ML_OK;
 }
+
+int64_t ml_graph_replays(void) { return (int64_t)ml::g_graph_replays.load(std::memory_order_relaxed); }
 
 ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *ms)
 {

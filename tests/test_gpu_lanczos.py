@@ -110,10 +110,13 @@ def test_graph_replay_matches_eager_launches():
     out = []
     for prof in (True, False):
         plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-10) for L, s in zip(layers, sig)]
+        replays0 = ml.ml_graph_replays()
         ml.ml_profile_enable(prof)
         V = torch.empty(4 * n, dtype=torch.float64, device="cuda")
         lam, nconv, st = ml.ml_lanczos_eigs(plans, 4, p=-1.0, tol=1e-9, seed=3, evecs=V)
         ml.ml_profile_enable(False)
+        replays = ml.ml_graph_replays() - replays0
+        assert (replays == 0) if prof else (replays > 0)   # eager while timing kernels, graphs otherwise
         out.append((lam, V.cpu().numpy(), [pl.info["applied_vectors"] for pl in plans]))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
