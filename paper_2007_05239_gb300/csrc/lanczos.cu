@@ -580,12 +580,42 @@ static void tridiag_power_e1(const std::vector<double> &a, const std::vector<dou
     }
 }
 
+// Device-scalar helpers of the Lanczos approximation of a matrix power:
+// *out = sum of the partials (or its square root), y += sign * (*a) * x,
+// y = x / (*b) (zero when *b is zero).
+__global__ void k_sum_to(const double *__restrict__ part, int nblk, int take_sqrt, double *out)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += part[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = take_sqrt ? sqrt(fmax(s, 0.0)) : s;
+}
+
+__global__ void k_axpy_dev(const double *__restrict__ a, double sign, const double *__restrict__ x, int64_t n,
+                           double *y)
+{
+    const double f = sign * (*a);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        y[r] = fma(f, x[r], y[r]);
+}
+
+__global__ void k_div_dev(const double *__restrict__ b, const double *__restrict__ x, int64_t n, double *y)
+{
+    const double bb = *b;
+    const double f = bb != 0.0 ? 1.0 / bb : 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        y[r] = f * x[r];
+}
+
 // y = (1/T) sum_t (L_sym^(t) + delta I)^p x for p < 0, p != -1: each term by
 // the Lanczos approximation of the matrix function (Lanczos-FA): m steps of
 // the three-term recurrence on B_t = L_sym^(t) + delta I from q_1 = x/||x||,
 // then f(B_t) x ~ ||x|| Q_m f(T_m) e1, stopped when the coefficient vector
 // changes by less than the tolerance (relative).  The polynomial Krylov
-// approach of Sec. 3 for a general power.
+// approach of Sec. 3 for a general power.  The recurrence scalars stay on
+// the device (alpha_j, beta_j are read on the host one step late, for the
+// convergence test only) and every layer runs on its own non-blocking
+// stream, as the conjugate-gradient solves do.
 struct PowerOp {
     ml_plan_s *const *layers;
     int T;
@@ -595,89 +625,169 @@ struct PowerOp {
     int mmax = 80;
     double tol = 1e-12;
     long long inner_iters = 0;
-    DevBuf Qf, w, cd;
+    struct Lane {
+        DevBuf Q, w, part, ab, cd;   // basis n x (mmax+1), product, partial sums, alpha|beta, coefficients
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        cudaEvent_t join = nullptr;
+        std::vector<double> a, b, c, cprev;
+        bool done = false;
+        int m = 0;
+    };
+    std::vector<Lane> lanes;
+    cudaEvent_t fork = nullptr;
+    double *hab = nullptr;   // pinned: T x 2 x 2 (alpha, beta of the last two steps)
+    bool own_streams = true;
 
     ml_status init()
     {
-        ML_TRY(Qf.ensure((size_t)n * (mmax + 1) * 8));
-        ML_TRY(w.ensure((size_t)n * 8));
-        ML_TRY(cd.ensure((size_t)mmax * 8));
+        lanes.resize(T);
+        for (int a = 0; a < T; ++a)
+            for (int b = a + 1; b < T; ++b)
+                if (layers[a] == layers[b]) own_streams = false;
+        if (profiling()) own_streams = false;
+        const int pb = ws->nblk;
+        for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            ML_TRY(L.Q.ensure((size_t)n * (mmax + 1) * 8));
+            ML_TRY(L.w.ensure((size_t)n * 8));
+            ML_TRY(L.part.ensure((size_t)pb * 8));
+            ML_TRY(L.ab.ensure((size_t)2 * mmax * 8));
+            ML_TRY(L.cd.ensure((size_t)mmax * 8));
+            if (own_streams || t == 0) ML_CUDA(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
+            else L.s = lanes[0].s;
+            for (auto &e : L.ev) ML_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ML_CUDA(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
+        }
+        ML_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        ML_CUDA(cudaMallocHost(&hab, (size_t)4 * T * sizeof(double)));
+        return ML_OK;
+    }
+    ~PowerOp()
+    {
+        for (int t = 0; t < (int)lanes.size(); ++t)
+            if (lanes[t].s && (own_streams || t == 0)) cudaStreamSynchronize(lanes[t].s);
+        for (int t = 0; t < (int)lanes.size(); ++t) {
+            Lane &L = lanes[t];
+            for (auto &e : L.ev)
+                if (e) cudaEventDestroy(e);
+            if (L.join) cudaEventDestroy(L.join);
+            if (L.s && (own_streams || t == 0)) cudaStreamDestroy(L.s);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (hab) cudaFreeHost(hab);
+        cudaGetLastError();
+    }
+    // step j of layer t on its stream: w = B q_j - beta_{j-1} q_{j-1}, alpha_j,
+    // w -= alpha_j q_j, beta_j = ||w||, q_{j+1} = w / beta_j
+    ml_status step(int t, int j)
+    {
+        Lane &L = lanes[t];
+        const int nb = vec_blocks(n), pb = ws->nblk;
+        double *Q = L.Q.as<double>(), *wp = L.w.as<double>(), *ab = L.ab.as<double>(), *part = L.part.as<double>();
+        double *qj = Q + (int64_t)j * n;
+        ApplyVec av{qj, 1, wp, 1, 1};
+        ApplyOpts o;
+        o.normalized = true;
+        o.alpha = -1.0;
+        o.shift = 1.0 + delta;
+        ML_TRY(apply_layer(layers[t], av, o, L.s));
+        ++inner_iters;
+        {
+            ProfScope pr("vector", L.s);
+            if (j > 0) k_axpy_dev<<<nb, 256, 0, L.s>>>(ab + mmax + j - 1, -1.0, Q + (int64_t)(j - 1) * n, n, wp);
+            k_dot_part<<<pb, 256, 0, L.s>>>(qj, wp, n, part);
+            k_sum_to<<<1, 32, 0, L.s>>>(part, pb, 0, ab + j);
+            k_axpy_dev<<<nb, 256, 0, L.s>>>(ab + j, -1.0, qj, n, wp);
+            k_dot_part<<<pb, 256, 0, L.s>>>(wp, wp, n, part);
+            k_sum_to<<<1, 32, 0, L.s>>>(part, pb, 1, ab + mmax + j);
+            k_div_dev<<<nb, 256, 0, L.s>>>(ab + mmax + j, wp, n, Q + (int64_t)(j + 1) * n);
+        }
+        ML_CUDA(cudaGetLastError());
+        ML_CUDA(cudaMemcpyAsync(hab + 4 * t + 2 * (j & 1), ab + j, sizeof(double), cudaMemcpyDeviceToHost, L.s));
+        ML_CUDA(cudaMemcpyAsync(hab + 4 * t + 2 * (j & 1) + 1, ab + mmax + j, sizeof(double), cudaMemcpyDeviceToHost,
+                                L.s));
+        ML_CUDA(cudaEventRecord(L.ev[j & 1], L.s));
+        return ML_OK;
+    }
+    // host side of step j (after its event): record alpha_j, beta_j, update f(T) e1, test
+    ml_status check(int t, int j)
+    {
+        Lane &L = lanes[t];
+        ML_CUDA(cudaEventSynchronize(L.ev[j & 1]));
+        const double alpha = hab[4 * t + 2 * (j & 1)], beta = hab[4 * t + 2 * (j & 1) + 1];
+        L.a.push_back(alpha);
+        L.m = j + 1;
+        tridiag_power_e1(L.a, L.b, L.m, p, L.c);
+        double dn = 0.0, cn = 0.0;
+        for (int i = 0; i < L.m; ++i) {
+            const double prev = i < (int)L.cprev.size() ? L.cprev[i] : 0.0;
+            dn += (L.c[i] - prev) * (L.c[i] - prev);
+            cn += L.c[i] * L.c[i];
+        }
+        if (j > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) L.done = true;
+        if (beta <= 1e-14 * std::fabs(alpha)) L.done = true;   // invariant subspace: exact
+        L.cprev = L.c;
+        if (!L.done) L.b.push_back(beta);
         return ML_OK;
     }
     ml_status apply(const double *x, double *out, cudaStream_t st)
     {
         const int nb = vec_blocks(n);
-        double *Q = Qf.as<double>(), *wp = w.as<double>();
-        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
         double xx;
         ML_TRY(ws->dot_host(x, x, &xx));
         const double nrm = std::sqrt(xx);
+        ML_CUDA(cudaMemsetAsync(out, 0, n * 8, st));
         if (!(nrm > 0)) return ML_OK;
-        std::vector<double> a, b, c, cprev;
+        ML_CUDA(cudaEventRecord(fork, st));
         for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            L.a.clear();
+            L.b.clear();
+            L.c.clear();
+            L.cprev.clear();
+            L.done = false;
+            L.m = 0;
+            ML_CUDA(cudaStreamWaitEvent(L.s, fork, 0));
+            ProfScope pr("vector", L.s);
+            k_scale<<<nb, 256, 0, L.s>>>(x, 1.0 / nrm, n, L.Q.as<double>());
+        }
+        ML_CUDA(cudaGetLastError());
+        // all layers advance together; step j's scalars are read while step j+1 runs
+        for (int j = 0; j < mmax; ++j) {
+            bool any = false;
+            for (int t = 0; t < T; ++t)
+                if (!lanes[t].done) {
+                    any = true;
+                    ML_TRY(step(t, j));
+                }
+            if (!any) break;
+            if (j >= 1)
+                for (int t = 0; t < T; ++t)
+                    if (!lanes[t].done) ML_TRY(check(t, j - 1));
+        }
+        for (int t = 0; t < T; ++t) {
+            Lane &L = lanes[t];
+            if (!L.done && L.m < mmax) ML_TRY(check(t, mmax - 1));
+            if (!L.done) return fail(ML_ERR_BREAKDOWN, "Lanczos-FA: the matrix power did not converge");
+            // y_t = (nrm / T) Q_m c, then joined into out on the caller's stream
+            std::vector<double> cs(L.c);
+            for (double &v : cs) v *= nrm / T;
+            ML_CUDA(cudaMemcpyAsync(L.cd.p, cs.data(), L.m * 8, cudaMemcpyHostToDevice, L.s));
             {
-                ProfScope pr("vector", st);
-                k_scale<<<nb, 256, 0, st>>>(x, 1.0 / nrm, n, Q);
-            }
-            a.clear();
-            b.clear();
-            cprev.clear();
-            int m = 0;
-            bool done = false;
-            for (int j = 0; j < mmax && !done; ++j) {
-                double *qj = Q + (int64_t)j * n;
-                // w = B q_j - beta_{j-1} q_{j-1}
-                ApplyVec av{qj, 1, wp, 1, 1};
-                ApplyOpts o;
-                o.normalized = true;
-                o.alpha = -1.0;
-                o.shift = 1.0 + delta;
-                ML_TRY(apply_layer(layers[t], av, o, st));
-                ++inner_iters;
-                if (j > 0) {
-                    ProfScope pr("vector", st);
-                    k_axpy<<<nb, 256, 0, st>>>(-b[j - 1], Q + (int64_t)(j - 1) * n, n, wp);
-                }
-                double alpha;
-                ML_TRY(ws->dot_host(qj, wp, &alpha));
-                {
-                    ProfScope pr("vector", st);
-                    k_axpy<<<nb, 256, 0, st>>>(-alpha, qj, n, wp);
-                }
-                double ww;
-                ML_TRY(ws->dot_host(wp, wp, &ww));
-                const double beta = std::sqrt(std::max(ww, 0.0));
-                a.push_back(alpha);
-                m = j + 1;
-                tridiag_power_e1(a, b, m, p, c);
-                // change of the coefficient vector against the previous step
-                double dn = 0.0, cn = 0.0;
-                for (int i = 0; i < m; ++i) {
-                    const double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
-                    dn += (c[i] - prev) * (c[i] - prev);
-                    cn += c[i] * c[i];
-                }
-                if (j > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) done = true;
-                if (beta <= 1e-14 * std::fabs(alpha)) done = true;   // invariant subspace: exact
-                cprev = c;
-                if (!done) {
-                    b.push_back(beta);
-                    ProfScope pr("vector", st);
-                    k_scale<<<nb, 256, 0, st>>>(wp, 1.0 / beta, n, Q + (int64_t)(j + 1) * n);
-                }
-            }
-            if (!done) return fail(ML_ERR_BREAKDOWN, "Lanczos-FA: the matrix power did not converge");
-            // out += (nrm / T) Q_m c
-            for (double &v : c) v *= nrm / T;
-            ML_CUDA(cudaMemcpyAsync(cd.p, c.data(), m * 8, cudaMemcpyHostToDevice, st));
-            {
-                ProfScope pr("ritz", st);
-                k_combine<<<nb, 256, 0, st>>>(Q, n, n, m, cd.as<double>(), 1, wp, n);
-                k_axpy<<<nb, 256, 0, st>>>(1.0, wp, n, out);
+                ProfScope pr("ritz", L.s);
+                k_combine<<<nb, 256, 0, L.s>>>(L.Q.as<double>(), n, n, L.m, L.cd.as<double>(), 1, L.w.as<double>(), n);
             }
             ML_CUDA(cudaGetLastError());
-            ML_CUDA(cudaStreamSynchronize(st));   // c (host) is reused by the next layer
+            ML_CUDA(cudaEventRecord(L.join, L.s));
+            ML_CUDA(cudaStreamWaitEvent(st, L.join, 0));
+            ML_CUDA(cudaStreamSynchronize(L.s));   // cs (host) is released at the end of this iteration
         }
+        for (int t = 0; t < T; ++t) {
+            ProfScope pr("vector", st);
+            k_axpy<<<nb, 256, 0, st>>>(1.0, lanes[t].w.as<double>(), n, out);
+        }
+        ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
 };
