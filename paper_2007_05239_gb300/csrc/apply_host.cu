@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,50 @@ int pass_width(const ml_plan_s *p, int remaining)
     return 1;
 }
 
+// Y[i, c] = sum_t parts[t][i, c] in layer order (the layers' terms of a
+// multilayer product computed concurrently)
+__global__ void k_sum_layers(const double *__restrict__ parts, int T, int64_t n, int b, double *Y, int ldy)
+{
+    const int64_t nb = n * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / b;
+        const int c = (int)(e - i * b);
+        double s = parts[e];
+        for (int t = 1; t < T; ++t) s += parts[(int64_t)t * nb + e];
+        Y[i * ldy + c] = s;
+    }
+}
+
+// Non-blocking streams and events kept for the process lifetime, one set
+// per device, for the concurrent layer terms of a multilayer product.
+struct LayerStreams {
+    std::vector<cudaStream_t> s;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+};
+static std::mutex g_ls_mu;
+static std::vector<LayerStreams> g_ls;   // by device
+
+static ml_status layer_streams(int T, LayerStreams **out)
+{
+    int dev = 0;
+    ML_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_ls_mu);
+    if ((int)g_ls.size() <= dev) g_ls.resize(dev + 1);
+    LayerStreams &L = g_ls[dev];
+    if (!L.fork) ML_CUDA(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
+    while ((int)L.s.size() < T) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        ML_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ML_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        L.s.push_back(s);
+        L.join.push_back(e);
+    }
+    *out = &L;
+    return ML_OK;
+}
+
 // Y[perm[i]] = (accumulate ? Y : 0) + alpha * deg[i]
 __global__ void k_degree_out(const double *__restrict__ deg, const int *__restrict__ perm, int64_t n, double alpha,
                              int accumulate, double *Y)
@@ -164,6 +209,38 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             o.layer_vecs = vs.data();
             ML_TRY(run_batch(layers, T, vs[0], o, st));
         }
+        return ML_OK;
+    }
+    bool distinct = true;
+    for (int a = 0; a < T; ++a)
+        for (int c = a + 1; c < T; ++c)
+            if (layers[a] == layers[c]) distinct = false;
+    if (!per_layer && T >= 2 && distinct && !profiling()) {
+        // the layers' terms on concurrent streams into per-layer buffers, then
+        // summed in layer order (the same FP64 additions as accumulating)
+        LayerStreams *ls = nullptr;
+        ML_TRY(layer_streams(T, &ls));
+        ml_plan_s *p0 = layers[0];
+        ML_TRY(p0->sum_parts.ensure((size_t)T * n * b * sizeof(double)));
+        double *parts = p0->sum_parts.as<double>();
+        ML_CUDA(cudaEventRecord(ls->fork, st));
+        for (int t = 0; t < T; ++t) {
+            cudaStream_t s = ls->s[t];
+            ML_CUDA(cudaStreamWaitEvent(s, ls->fork, 0));
+            for (int c0 = 0, nv = 0; c0 < b; c0 += nv) {
+                nv = pass_width(layers[t], b - c0);
+                ApplyVec v{X + c0, b, parts + (int64_t)t * n * b + c0, b, nv};
+                ApplyOpts o;
+                o.normalized = base == ML_NORMALIZED_A;
+                o.alpha = 1.0 / T;
+                ML_TRY(apply_layer(layers[t], v, o, s));
+            }
+            ML_CUDA(cudaEventRecord(ls->join[t], s));
+            ML_CUDA(cudaStreamWaitEvent(st, ls->join[t], 0));
+        }
+        ProfScope pr("vector", st);
+        k_sum_layers<<<(int)std::min<int64_t>((n * b + 255) / 256, 152 * 16), 256, 0, st>>>(parts, T, n, b, Y, b);
+        ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
     for (int t = 0; t < T; ++t) {

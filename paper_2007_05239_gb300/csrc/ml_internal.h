@@ -144,6 +144,7 @@ struct ml_plan_s {
     ml::DevBuf status;    // int flags written by device code
     ml::DevBuf batch_desc;               // per-layer descriptors of a batched apply led by this plan
     ml::DevBuf batch_part;               // per-group partial sums of a batched multilayer apply
+    ml::DevBuf sum_parts;                // per-layer terms of a concurrent multilayer apply led by this plan
     std::vector<unsigned char> batch_host;  // host copy of the uploaded descriptors
     int64_t device_bytes() const;
 };

@@ -840,7 +840,7 @@ static void release_all(ml_plan_s *p)
     ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
-                          &p->stage_y, &p->status, &p->batch_desc, &p->batch_part, &p->Wd};
+                          &p->stage_y, &p->status, &p->batch_desc, &p->batch_part, &p->Wd, &p->sum_parts};
     for (auto *b : bufs) b->release();
 }
 

@@ -292,3 +292,21 @@ def test_plan_many_equals_single_plans():
         ml.ml_fastsum_apply([a], v, Ya, mode="normalized")
         ml.ml_fastsum_apply([b], v, Yb, mode="normalized")
         assert torch.equal(Ya, Yb)
+
+
+def test_concurrent_layer_terms_equal_sequential():
+    # with kernel timing off the layers' terms run on concurrent streams and
+    # are summed in layer order; with it on they accumulate one after another:
+    # the same FP64 additions, so the same bits
+    layers = workloads.image_voronoi_layers(120, 150, 6, 0.02, seed=62)
+    n = layers[0].shape[0]
+    plans = [ml.ml_fastsum_plan(torch.as_tensor(L, device="cuda"), 0.2, prec="f64") for L in layers]
+    X = torch.as_tensor(np.random.default_rng(63).uniform(-1, 1, (n, 4)), device="cuda")
+    out = []
+    for prof in (True, False):
+        ml.ml_profile_enable(prof)
+        Y = torch.empty_like(X)
+        ml.ml_fastsum_apply(plans, X, Y, mode="normalized")
+        ml.ml_profile_enable(False)
+        out.append(Y.cpu())
+    assert torch.equal(out[0], out[1])
