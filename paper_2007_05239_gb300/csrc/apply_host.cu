@@ -120,11 +120,12 @@ struct LayerStreams {
 static std::mutex g_ls_mu;
 static std::vector<LayerStreams> g_ls;   // by device
 
+// the caller holds g_ls_mu for the whole fork / enqueue / join sequence, so
+// that calls from several host threads do not share the fork and join events
 static ml_status layer_streams(int T, LayerStreams **out)
 {
     int dev = 0;
     ML_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(g_ls_mu);
     if ((int)g_ls.size() <= dev) g_ls.resize(dev + 1);
     LayerStreams &L = g_ls[dev];
     if (!L.fork) ML_CUDA(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
@@ -218,6 +219,7 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
     if (!per_layer && T >= 2 && distinct && !profiling()) {
         // the layers' terms on concurrent streams into per-layer buffers, then
         // summed in layer order (the same FP64 additions as accumulating)
+        std::lock_guard<std::mutex> lk(g_ls_mu);
         LayerStreams *ls = nullptr;
         ML_TRY(layer_streams(T, &ls));
         ml_plan_s *p0 = layers[0];
