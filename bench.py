@@ -363,10 +363,23 @@ def main():
     flops = applied_prof * 2.0 * taps             # one multiply-add per tap and point-vector
     achieved = flops / (fam_ms / 1e3) / 1e12 if fam_ms > 0 else 0.0
     peak = ALU_PEAK_TFLOPS[prec]
+    # the same kernel against the HBM roof: algorithmic bytes per point and pass
+    # (window table 8 d W + packed taps 4 in the FP64 form, coordinates 4 d in the
+    # FP32 form; permutation 4, D^{-1/2} 8) plus 8 B per vector read (spread) or
+    # read and written (interp); a pass carries nv vectors
+    nv = min(args.b, 8) if args.mode == "apply" else (spec.get("block", 1) if spec.get("per_layer") else 1)
+    point_bytes = (8 * d * W + 4 if prec == "f64" else 4 * d) + 4 + 8
+    vec_bytes = 8 if fam == "spread" else 16
+    hbm_bytes = applied_prof / nv * point_bytes + applied_prof * vec_bytes
+    hbm_gbs = hbm_bytes / (fam_ms / 1e3) / 1e9 if fam_ms > 0 else 0.0
+    hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
     roofline = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": ALU_PEAK_SOURCE[prec],
                 "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}",
+                "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                        "bytes_per_point_pass": point_bytes, "bytes_per_point_vector": vec_bytes,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
                 "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()},
                 "region": "one extra step after the timed region with per-kernel CUDA events (eager launches), "
                           f"{prof_step_ms:.1f} ms"}
