@@ -242,6 +242,8 @@ def main():
                          "Allen-Cahn classifier (Alg. 2) on eigenpairs computed before the timed region")
     ap.add_argument("--b", type=int, default=1, help="vectors per product in --mode apply")
     ap.add_argument("--target", type=float, default=None, help="relative error target (default per precision)")
+    ap.add_argument("--combined", action="store_true",
+                    help="per-layer workloads: eigenpairs of the combined power mean operator instead")
     ap.add_argument("--planner", default="rule", choices=["rule", "learned"],
                     help="NFFT parameters of each layer: the automatic rule, or the learned model "
                          "(paper_2007_05239_gb300/paramnet_<prec>_<target>.npz)")
@@ -260,6 +262,8 @@ def main():
         spec["k"] = args.k
     if args.target is not None:
         spec["target"] = args.target
+    if args.combined:
+        spec["per_layer"] = False
     WORKLOADS[args.workload] = spec
     if args.impl == "reference":
         return run_reference(args, rank, world)
