@@ -57,8 +57,12 @@ typedef enum {
 } ml_status;
 
 typedef enum {
-    ML_F32 = 0, /* window weights, spreading, grid transforms, interpolation in FP32 */
-    ML_F64 = 1  /* the same steps in FP64 */
+    ML_F32 = 0, /* window weights, spreading, grid transforms, interpolation in FP32
+                   (spreading sums exact fixed-point integers)                       */
+    ML_F64 = 1  /* the same steps FP64-class: values as unevaluated float pairs (about
+                   48 significant bits) with exact FMA-based products on the FP32 pipes,
+                   spreading into exact fixed-point integers; window weights from an
+                   FP64 table                                                          */
 } ml_prec;
 /* In both precisions the degree normalisation, the multilayer accumulation,
  * the output vectors and every Lanczos quantity are FP64. */
