@@ -31,11 +31,25 @@ Readings of what the paper leaves open (listed in the design doc as well):
   and vanishing derivatives 1..p-1 at r = 1/2; beyond 1/2 (cube corners) it
   stays at K(1/2).
 
+* Laplacian kernel K(r) = exp(-r/sigma) (reading 16).  Its cusp at r = 0
+  makes the Fourier coefficients of K itself decay slowly, so (as in the
+  fast summation of non-smooth radial kernels that Sec. 4 refers to) K_R is
+  regularised at the origin as well: on r < eps_I it is the even polynomial
+  sum_{j<p} c_j r^{2j} matching K's derivatives 0..p-1 at r = eps_I (smooth
+  at 0 in every dimension).  Alg. 1 then sums K_R, and the near field
+      f_NE(x_i) = sum_{j: ||x_i - x_j|| < eps_I} (K - K_R)(||x_i - x_j||) v_j
+  (the pair j = i included, so that W v = f_RF + f_NE - K(0) v) is added by
+  direct summation.  The ball domain is required; its outer regulariser
+  matches the Laplacian's derivatives (-1/sigma)^k exp(-r/sigma).
+
 Pinned by tests/test_oracle_pins.py: b_l against the closed-form Fourier
 coefficients of the periodised Gaussian (Poisson summation); the adjoint
 transform on equispaced nodes against numpy's FFT; f_RF - K(0) v against the
 direct sum within the Fourier-tail bound; the regulariser's matching
-conditions.
+conditions; for the Laplacian, the continuity of K_R and of its first
+derivatives across r = eps_I by one-sided finite differences, and
+f_RF + f_NE - K(0) v against the direct sum within the kernel approximation
+error measured on the same grid.
 """
 from __future__ import annotations
 
@@ -83,11 +97,22 @@ def _gauss_derivs(r, sigma, p):
     return [((-1.0) ** k) * (sigma ** -k) * H[k] * e for k in range(p)]
 
 
-def regulariser_poly(sigma, eps_B, p):
+def _laplace_derivs(r, sigma, p):
+    """K^{(k)}(r) for k = 0..p-1, K(r) = exp(-r/sigma): (-1/sigma)^k exp(-r/sigma)."""
+    e = math.exp(-r / sigma)
+    return [((-1.0 / sigma) ** k) * e for k in range(p)]
+
+
+def _radial(r, sigma, kernel):
+    r = np.asarray(r, dtype=np.float64)
+    return np.exp(-(r * r) / (sigma * sigma)) if kernel == "gauss" else np.exp(-r / sigma)
+
+
+def regulariser_poly(sigma, eps_B, p, kernel="gauss"):
     """Monomial coefficients q_0..q_{2p-1} of the two-point Taylor polynomial
     in t = (r - r_I)/eps_B on [0, 1] (reading 2)."""
     rI = 0.5 - eps_B
-    dK = _gauss_derivs(rI, sigma, p)
+    dK = (_gauss_derivs if kernel == "gauss" else _laplace_derivs)(rI, sigma, p)
     n = 2 * p
     A = np.zeros((n, n))
     rhs = np.zeros(n)
@@ -97,23 +122,44 @@ def regulariser_poly(sigma, eps_B, p):
             A[k, j] = math.factorial(j) / math.factorial(j - k) * (0.0 ** (j - k))
             A[p + k, j] = math.factorial(j) / math.factorial(j - k)
         rhs[k] = dK[k] * eps_B ** k
-        rhs[p + k] = math.exp(-0.25 / sigma ** 2) if k == 0 else 0.0
+        rhs[p + k] = float(_radial(0.5, sigma, kernel)) if k == 0 else 0.0
     return np.linalg.solve(A, rhs)
 
 
-def K_R(r, sigma, eps_B=0.0, p=0):
-    """Regularised radial kernel of the ball domain (reading 2); the plain
-    Gaussian when eps_B = 0 (the box domain samples its periodisation instead,
-    see kernel_samples)."""
+def inner_poly(sigma, eps_I, p):
+    """Coefficients c_0..c_{p-1} of the inner regulariser of the Laplacian,
+    P(r) = sum_j c_j r^{2j}, with P^{(k)}(eps_I) = K^{(k)}(eps_I), k < p
+    (reading 16).  The k-th derivative of r^{2j} is (2j)!/(2j-k)! r^{2j-k}."""
+    dK = _laplace_derivs(eps_I, sigma, p)
+    A = np.zeros((p, p))
+    for k in range(p):
+        for j in range(p):
+            e = 2 * j
+            if e >= k:
+                A[k, j] = math.factorial(e) / math.factorial(e - k) * eps_I ** (e - k)
+    return np.linalg.solve(A, np.array(dK))
+
+
+def K_R(r, sigma, eps_B=0.0, p=0, kernel="gauss", eps_I=0.0):
+    """Regularised radial kernel of the ball domain (reading 2; reading 16 for
+    the Laplacian's inner part); the plain Gaussian when eps_B = 0 (the box
+    domain samples its periodisation instead, see kernel_samples)."""
     r = np.asarray(r, dtype=np.float64)
-    K = np.exp(-(r * r) / (sigma * sigma))
+    K = _radial(r, sigma, kernel)
     if eps_B <= 0:
+        if kernel != "gauss":
+            raise ValueError("the Laplacian kernel needs the ball domain (eps_B > 0)")
         return K
-    q = regulariser_poly(sigma, eps_B, p)
+    q = regulariser_poly(sigma, eps_B, p, kernel)
     rI = 0.5 - eps_B
     t = np.clip((r - rI) / eps_B, 0.0, 1.0)
     P = np.polyval(q[::-1], t)
-    return np.where(r <= rI, K, P)
+    out = np.where(r <= rI, K, P)
+    if kernel == "laplace":
+        c = inner_poly(sigma, eps_I, p)
+        Pin = np.polyval(c[::-1], r * r)
+        out = np.where(r < eps_I, Pin, out)
+    return out
 
 
 def periodised_gaussian_1d(y, sigma, images=None):
@@ -124,10 +170,10 @@ def periodised_gaussian_1d(y, sigma, images=None):
 
 
 # ------------------------------------------------------- Fourier coefficients
-def kernel_samples(sigma_s, N, d, eps_B=0.0, p=0):
+def kernel_samples(sigma_s, N, d, eps_B=0.0, p=0, kernel="gauss", eps_I=0.0):
     """K_R on the grid k/N, k in I_N^d (reading 2), shape (N,)*d indexed by k + N/2."""
     k = np.arange(-N // 2, N // 2) / N
-    if eps_B <= 0:
+    if eps_B <= 0 and kernel == "gauss":
         g1 = periodised_gaussian_1d(k, sigma_s)
         out = g1
         for _ in range(d - 1):
@@ -135,15 +181,15 @@ def kernel_samples(sigma_s, N, d, eps_B=0.0, p=0):
         return out
     grids = np.meshgrid(*([k] * d), indexing="ij")
     r = np.sqrt(sum(g * g for g in grids))
-    return K_R(r, sigma_s, eps_B, p)
+    return K_R(r, sigma_s, eps_B, p, kernel, eps_I)
 
 
-def bhat(sigma_s, N, d, eps_B=0.0, p=0):
+def bhat(sigma_s, N, d, eps_B=0.0, p=0, kernel="gauss", eps_I=0.0):
     """b_l, l in I_N^d, from N^d samples of K_R on k/N and a d-dim FFT.
 
     Returned as a real array of shape (N,)*d indexed by l + N/2 on every axis.
     """
-    samples = kernel_samples(sigma_s, N, d, eps_B, p)
+    samples = kernel_samples(sigma_s, N, d, eps_B, p, kernel, eps_I)
     # FFT wants index 0 at k = 0: shift, transform, shift back to l + N/2 order.
     F = np.fft.fftn(np.fft.ifftshift(samples)) / float(N) ** d
     return np.real(np.fft.fftshift(F))
@@ -190,3 +236,18 @@ def fastsum_W(Xs, v, b, K0=1.0):
     """W v = W~ v - K(0) v  (Sec. 4)."""
     v = np.asarray(v, dtype=np.float64)
     return fastsum_Wtilde(Xs, v, b) - K0 * v
+
+
+def near_field(Xs, v, sigma_s, eps_I, p):
+    """f_NE(x_i) = sum_{j: ||x_i - x_j|| < eps_I} (K - K_R)(||x_i - x_j||) v_j for the
+    Laplacian, the pair j = i included (reading 16).  Direct O(n^2) sum."""
+    Xs = np.asarray(Xs, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    c = inner_poly(sigma_s, eps_I, p)
+    out = np.zeros(Xs.shape[0])
+    for i in range(Xs.shape[0]):
+        r = np.sqrt(((Xs - Xs[i]) ** 2).sum(axis=1))
+        near = r < eps_I
+        rn = r[near]
+        out[i] = np.dot(np.exp(-rn / sigma_s) - np.polyval(c[::-1], rn * rn), v[near])
+    return out

@@ -1,11 +1,14 @@
 /*
- * Oracle (test infrastructure only): direct O(n^2) Gaussian kernel sums in FP64.
+ * Oracle (test infrastructure only): direct O(n^2) kernel sums in FP64.
  *
  * Computes, for each requested row r,
- *     out[r, c] = sum_{j != r} exp(-||x_r - x_j||^2 / sigma^2) * V[j, c]
+ *     out[r, c] = sum_{j != r} K(x_r - x_j) * V[j, c]
  * which is (W V)_r for the weight matrix of Sec. 2 (w(x_i,x_j) = K(x_i - x_j)
- * for i != j, zero diagonal because self-edges are excluded) with the
- * Gaussian kernel of Sec. 4.  Points X are n x d row-major, V is n x b
+ * for i != j, zero diagonal because self-edges are excluded) with one of the
+ * two radial kernels named in Sec. 4:
+ *     kernel 0 (Gaussian)   K(y) = exp(-||y||^2 / sigma^2)
+ *     kernel 1 (Laplacian)  K(y) = exp(-||y|| / sigma)
+ * Points X are n x d row-major, V is n x b
  * row-major, out is nrows x b row-major.  rows == NULL means all rows.
  *
  * The sum over j is blocked (partial sums of 1024 terms, then summed) so the
@@ -23,13 +26,15 @@
 #define ORACLE_BLOCK 1024
 #define ORACLE_MAXB 64
 
-int oracle_gauss_rows(const double *X, int64_t n, int d, double sigma, const double *V, int b,
-                      const int64_t *rows, int64_t nrows, double *out, int nthreads)
+int oracle_kernel_rows(const double *X, int64_t n, int d, double sigma, int kernel, const double *V, int b,
+                       const int64_t *rows, int64_t nrows, double *out, int nthreads)
 {
-    if (!X || !V || !out || n <= 0 || d < 1 || b < 1 || b > ORACLE_MAXB || !(sigma > 0))
+    if (!X || !V || !out || n <= 0 || d < 1 || b < 1 || b > ORACLE_MAXB || !(sigma > 0) ||
+        (kernel != 0 && kernel != 1))
         return -1;
     if (rows == NULL) nrows = n;
     const double inv_s2 = 1.0 / (sigma * sigma);
+    const double inv_s = 1.0 / sigma;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -55,7 +60,7 @@ int oracle_gauss_rows(const double *X, int64_t n, int d, double sigma, const dou
                     const double t = xr[a] - xj[a];
                     r2 += t * t;
                 }
-                const double w = exp(-r2 * inv_s2);
+                const double w = kernel == 0 ? exp(-r2 * inv_s2) : exp(-sqrt(r2) * inv_s);
                 const double *vj = V + j * b;
                 for (int c = 0; c < b; ++c) part[c] += w * vj[c];
             }
@@ -64,6 +69,12 @@ int oracle_gauss_rows(const double *X, int64_t n, int d, double sigma, const dou
         for (int c = 0; c < b; ++c) out[rr * b + c] = total[c];
     }
     return 0;
+}
+
+int oracle_gauss_rows(const double *X, int64_t n, int d, double sigma, const double *V, int b,
+                      const int64_t *rows, int64_t nrows, double *out, int nthreads)
+{
+    return oracle_kernel_rows(X, n, d, sigma, 0, V, b, rows, nrows, out, nthreads);
 }
 
 /* Number of threads OpenMP would use (for the baseline's core count). */

@@ -43,17 +43,17 @@ def largest_eigs(M, k):
     return lam[order].copy(), fix_signs(Phi[:, order])
 
 
-def lsym_eigs(X, sigma, k):
-    return smallest_eigs(graph.L_sym_dense(X, sigma), k)
+def lsym_eigs(X, sigma, k, kernel="gauss"):
+    return smallest_eigs(graph.L_sym_dense(X, sigma, kernel), k)
 
 
-def L1_eigs(layers, sigmas, k):
+def L1_eigs(layers, sigmas, k, kernel="gauss"):
     """k smallest eigenpairs of L_1 via the k largest theta of I - L_1 (Sec. 3)."""
     T = len(layers)
     n = layers[0].shape[0]
     IL1 = np.zeros((n, n))
     for t in range(T):
-        IL1 += np.eye(n) - graph.L_sym_dense(layers[t], sigmas[t])
+        IL1 += np.eye(n) - graph.L_sym_dense(layers[t], sigmas[t], kernel)
     IL1 /= T
     theta, Phi = largest_eigs(IL1, k)
     return 1.0 - theta, Phi

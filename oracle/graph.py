@@ -3,7 +3,9 @@
 Definitions followed, each written out directly:
 
 * weight function  w(x_i, x_j) = K(x_i - x_j) for i != j, w(x_i, x_i) = 0
-  (Sec. 2: no self-edges; Sec. 4: K(y) = exp(-||y||^2 / sigma^2)).
+  (Sec. 2: no self-edges) with one of the radial kernels of Sec. 4:
+  the Gaussian K(y) = exp(-||y||^2 / sigma^2) (kernel="gauss", the default)
+  or the Laplacian K(y) = exp(-||y|| / sigma) (kernel="laplace").
 * degree           deg(x_i) = sum_j w(x_i, x_j),  D = diag(W 1)      (Sec. 2)
 * normalised       L_sym = I - D^{-1/2} W D^{-1/2}                   (Sec. 2)
 * multilayer p=1   I - L_1 = (1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2}    (Eq. I-L_1)
@@ -13,7 +15,10 @@ Definitions followed, each written out directly:
 
 Pinned by tests/test_oracle_pins.py: two-point and equilateral closed forms,
 the Poisson-summation value of a lattice degree, the sigma -> infinity limit,
-and the invariants A D^{1/2} 1 = D^{1/2} 1, trace A = 0.
+and the invariants A D^{1/2} 1 = D^{1/2} 1, trace A = 0; for the Laplacian,
+the geometric-series degrees of an equispaced 1-d lattice, and the same
+lattice laid along a rotated line in 3-d (the Euclidean norm, not its square
+nor the l1 norm).
 """
 from __future__ import annotations
 
@@ -41,6 +46,10 @@ def _lib():
         lib.oracle_gauss_rows.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
             ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_kernel_rows.restype = ctypes.c_int
+        lib.oracle_kernel_rows.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+            ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
         lib.oracle_num_threads.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -56,7 +65,20 @@ def gaussian(r2, sigma):
     return np.exp(-np.asarray(r2, dtype=np.float64) / (sigma * sigma))
 
 
-def weight_matrix(X, sigma):
+KERNELS = {"gauss": 0, "laplace": 1}
+
+
+def kernel_of_r2(r2, sigma, kernel="gauss"):
+    """K as a function of the squared distance for either kernel of Sec. 4."""
+    r2 = np.asarray(r2, dtype=np.float64)
+    if kernel == "gauss":
+        return gaussian(r2, sigma)
+    if kernel == "laplace":
+        return np.exp(-np.sqrt(r2) / sigma)
+    raise ValueError(f"unknown kernel {kernel!r}")
+
+
+def weight_matrix(X, sigma, kernel="gauss"):
     """Dense W (n x n) with zero diagonal, squared distances summed from the
     coordinate differences (blocks of rows, any dimension).  Small n only."""
     X = np.asarray(X, dtype=np.float64)
@@ -65,12 +87,12 @@ def weight_matrix(X, sigma):
     step = max(1, int(2 ** 24 // max(1, n * X.shape[1])))
     for i0 in range(0, n, step):
         diff = X[i0:i0 + step, None, :] - X[None, :, :]
-        W[i0:i0 + step] = gaussian(np.einsum("ijk,ijk->ij", diff, diff), sigma)
+        W[i0:i0 + step] = kernel_of_r2(np.einsum("ijk,ijk->ij", diff, diff), sigma, kernel)
     np.fill_diagonal(W, 0.0)
     return W
 
 
-def W_apply(X, sigma, V, rows=None, nthreads=0):
+def W_apply(X, sigma, V, rows=None, nthreads=0, kernel="gauss"):
     """(W V)[rows] by direct summation over all n points (FP64).
 
     X: (n, d) points, V: (n,) or (n, b).  rows: None (all) or an index array.
@@ -87,55 +109,55 @@ def W_apply(X, sigma, V, rows=None, nthreads=0):
     out = np.empty((nrows, b), dtype=np.float64)
     lib = _lib()
     if lib is not None:
-        rc = lib.oracle_gauss_rows(X.ctypes.data, n, d, float(sigma), V2.ctypes.data, b,
-                                   None if r is None else r.ctypes.data, nrows,
-                                   out.ctypes.data, int(nthreads))
+        rc = lib.oracle_kernel_rows(X.ctypes.data, n, d, float(sigma), KERNELS[kernel], V2.ctypes.data, b,
+                                    None if r is None else r.ctypes.data, nrows,
+                                    out.ctypes.data, int(nthreads))
         if rc != 0:
-            raise ValueError("oracle_gauss_rows rejected its arguments")
+            raise ValueError("oracle_kernel_rows rejected its arguments")
     else:
         idx = np.arange(n) if r is None else r
         for s in range(0, nrows, 256):
             ii = idx[s:s + 256]
             diff = X[ii, None, :] - X[None, :, :]
-            K = gaussian(np.einsum("ijk,ijk->ij", diff, diff), sigma)
+            K = kernel_of_r2(np.einsum("ijk,ijk->ij", diff, diff), sigma, kernel)
             K[np.arange(len(ii)), ii] = 0.0
             out[s:s + 256] = K @ V2
     return out[:, 0] if squeeze else out
 
 
-def degrees(X, sigma, rows=None, nthreads=0):
+def degrees(X, sigma, rows=None, nthreads=0, kernel="gauss"):
     """deg(x_i) = sum_{j != i} K(x_i - x_j)  (Sec. 2, D = diag(W 1))."""
     n = np.asarray(X).shape[0]
-    return W_apply(X, sigma, np.ones(n), rows=rows, nthreads=nthreads)
+    return W_apply(X, sigma, np.ones(n), rows=rows, nthreads=nthreads, kernel=kernel)
 
 
-def A_apply(X, sigma, V, deg=None, nthreads=0):
+def A_apply(X, sigma, V, deg=None, nthreads=0, kernel="gauss"):
     """D^{-1/2} W D^{-1/2} V, the matrix I - L_sym of one layer (Sec. 2)."""
     if deg is None:
-        deg = degrees(X, sigma, nthreads=nthreads)
+        deg = degrees(X, sigma, nthreads=nthreads, kernel=kernel)
     s = 1.0 / np.sqrt(deg)
     V = np.asarray(V, dtype=np.float64)
     sv = s[:, None] * V.reshape(V.shape[0], -1)
-    out = s[:, None] * W_apply(X, sigma, sv, nthreads=nthreads)
+    out = s[:, None] * W_apply(X, sigma, sv, nthreads=nthreads, kernel=kernel)
     return out[:, 0] if V.ndim == 1 else out
 
 
-def multilayer_A_apply(layers, sigmas, V, degs=None, nthreads=0):
+def multilayer_A_apply(layers, sigmas, V, degs=None, nthreads=0, kernel="gauss"):
     """(1/T) sum_t D_t^{-1/2} W_t D_t^{-1/2} V  =  (I - L_1) V   (Eq. I-L_1)."""
     T = len(layers)
     acc = None
     for t in range(T):
-        y = A_apply(layers[t], sigmas[t], V, None if degs is None else degs[t], nthreads)
+        y = A_apply(layers[t], sigmas[t], V, None if degs is None else degs[t], nthreads, kernel)
         acc = y if acc is None else acc + y
     return acc / T
 
 
-def multilayer_W_apply(layers, sigmas, V, nthreads=0):
+def multilayer_W_apply(layers, sigmas, V, nthreads=0, kernel="gauss"):
     """(1/T) sum_t W_t V  (the raw multilayer weight product)."""
     T = len(layers)
     acc = None
     for t in range(T):
-        y = W_apply(layers[t], sigmas[t], V, nthreads=nthreads)
+        y = W_apply(layers[t], sigmas[t], V, nthreads=nthreads, kernel=kernel)
         acc = y if acc is None else acc + y
     return acc / T
 
@@ -148,9 +170,9 @@ def L_sym_from_W(W):
     return np.eye(W.shape[0]) - (s[:, None] * W) * s[None, :]
 
 
-def L_sym_dense(X, sigma):
+def L_sym_dense(X, sigma, kernel="gauss"):
     """Dense L_sym = I - D^{-1/2} W D^{-1/2} (Sec. 2).  Small n only."""
-    return L_sym_from_W(weight_matrix(X, sigma))
+    return L_sym_from_W(weight_matrix(X, sigma, kernel))
 
 
 def shift_delta(p):

@@ -219,6 +219,76 @@ def test_ball_domain_scaling():
     assert D.max() <= 0.5 - 1.0 / 16 + 1e-14
 
 
+
+# ------------------------------------------------------- Laplacian kernel
+def _geometric_lattice_degrees(n, h, sigma):
+    # sum_{j != i} q^{|i-j|}, q = exp(-h/sigma): two finite geometric series
+    q = math.exp(-h / sigma)
+    i = np.arange(n)
+    return q * (1 - q ** i) / (1 - q) + q * (1 - q ** (n - 1 - i)) / (1 - q)
+
+
+def test_laplace_lattice_degrees_geometric_series():
+    n, h, sigma = 60, 0.3, 0.7
+    X = (h * np.arange(n))[:, None]
+    deg = graph.degrees(X, sigma, kernel="laplace")
+    assert np.allclose(deg, _geometric_lattice_degrees(n, h, sigma), rtol=1e-13, atol=0)
+
+
+def test_laplace_rotated_line_in_3d():
+    # the same lattice along a unit direction: the Euclidean norm gives the same
+    # degrees (the l1 norm or the squared norm would not)
+    n, h, sigma = 40, 0.25, 0.5
+    u = np.array([1.0, 2.0, 2.0]) / 3.0
+    X = (h * np.arange(n))[:, None] * u[None, :] + np.array([0.3, -1.0, 2.0])
+    deg = graph.degrees(X, sigma, kernel="laplace")
+    assert np.allclose(deg, _geometric_lattice_degrees(n, h, sigma), rtol=1e-12, atol=0)
+    W = graph.weight_matrix(X, sigma, kernel="laplace")
+    assert np.allclose(W.sum(1), deg, rtol=1e-13)
+
+
+def test_laplace_inner_regulariser_matches_kernel():
+    # one-sided finite differences of K_R just inside eps_I against the
+    # analytic derivatives (-1/sigma)^k exp(-eps_I/sigma) of the Laplacian,
+    # and K_R even and smooth at the origin
+    sigma, eps_I, p = 0.05, 0.03, 8
+    f = lambda r: alg1.K_R(np.asarray(r, dtype=float), sigma, 1.0 / 8, p, "laplace", eps_I)
+    x = eps_I * (1 - 1e-13)
+    hh = 1e-4 * eps_I
+    f0, f1, f2, f3 = (float(f(x - k * hh)) for k in range(4))
+    e = math.exp(-eps_I / sigma)
+    assert abs(f0 - e) <= 1e-12
+    d1 = (3 * f0 - 4 * f1 + f2) / (2 * hh)
+    assert abs(d1 - (-e / sigma)) <= 1e-6 * e / sigma
+    d2 = (2 * f0 - 5 * f1 + 4 * f2 - f3) / hh ** 2
+    assert abs(d2 - e / sigma ** 2) <= 1e-3 * e / sigma ** 2
+    # smooth at 0: K_R(t) - K_R(0) is quadratic in t (a cusp would be linear)
+    t = 1e-4
+    ratio = (float(f(2 * t)) - float(f(0.0))) / (float(f(t)) - float(f(0.0)))
+    assert abs(ratio - 4.0) <= 1e-3
+    # outside eps_I it is the kernel itself
+    r = np.linspace(eps_I, 0.5 - 1.0 / 8, 50)
+    assert np.allclose(f(r), np.exp(-r / sigma), rtol=1e-15)
+
+
+@pytest.mark.parametrize("d,N,c,tol", [(1, 64, 8, 1e-6), (2, 64, 8, 1e-5), (3, 48, 6, 1e-4)])
+def test_laplace_alg1_with_near_field_against_direct_sum(d, N, c, tol):
+    rng = np.random.default_rng(20 + d)
+    X = rng.normal(size=(220, d))
+    sigma, p = 0.8, 8
+    eps_I = c / N
+    eps_B = max(1.0 / 16, eps_I)
+    Xs, ss, _, _ = alg1.scale_to_domain(X, sigma, eps_B=eps_B)
+    v = rng.random(220)
+    b = alg1.bhat(ss, N, d, eps_B, p, "laplace", eps_I)
+    far = alg1.fastsum_W(Xs, v, b)
+    near = alg1.near_field(Xs, v, ss, eps_I, p)
+    ref = graph.W_apply(X, sigma, v, kernel="laplace")
+    l1 = np.abs(v).sum()
+    assert np.abs(far + near - ref).max() <= tol * l1
+    # the near field carries the cusp: without it the error is orders larger
+    assert np.abs(far - ref).max() >= 100 * tol * l1
+
 # ------------------------------------------------------------------ MLP oracle
 def test_mlp_gradient_matches_finite_differences():
     from oracle import mlp
