@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,6 +52,9 @@ WORKLOADS = {
                                 n=10_000_000, T=2, d=3, sigma=0.15, prec="f32", target=1e-4, k=10, p=1.0),
     "single_n2000_d3": dict(desc="n=2000 uniform in [-1/4,1/4]^3", n=2000, T=1, d=3, sigma=0.1, prec="f64",
                             target=1e-12, k=10, p=1.0),
+    "laplace_disc_n1e6_d2": dict(desc="n=1e6 uniform in the unit disc, Laplacian kernel exp(-r/sigma) (Sec. 4) "
+                                      "with its near-field correction", n=1_000_000, T=1, d=2, sigma=0.05,
+                                 prec="f32", target=1e-4, k=10, p=1.0, kernel="laplace"),
 }
 
 
@@ -63,6 +67,8 @@ def make_layers(name):
         layers, _ = wl.gmm_band_layers(250_000, 104, 12, seed=3)
     elif name == "image_discs_n1e7_T2":
         layers = wl.image_discs_layers(2500, 4000, 5, 0.02, seed=4)
+    elif name == "laplace_disc_n1e6_d2":
+        layers = [wl.uniform_ball(1_000_000, 2, seed=9)]
     else:
         layers = [wl.uniform_cube(2000, 3, seed=1)]
     if spec["sigma"] == "half_range":
@@ -161,9 +167,11 @@ def run_reference(args, rank, world):
     rng = np.random.default_rng(0)
     v = rng.uniform(0, 1, n)
 
+    kernel = spec.get("kernel", "gauss")
+
     def step(rows):
         for t in range(T):
-            graph.W_apply(layers[t], sig[t], v, rows=rows)
+            graph.W_apply(layers[t], sig[t], v, rows=rows, kernel=kernel)
 
     # size the per-step row sample to ~4 s
     r0 = np.sort(rng.choice(n, size=min(n, 16), replace=False))
@@ -206,7 +214,7 @@ def metric_name(spec):
 def config_dict(args, spec, n, T):
     return {"workload": args.workload, "desc": spec["desc"], "n": n, "layers": T, "d": spec["d"],
             "sigma": spec["sigma"], "prec": spec["prec"], "target_rel_err": spec["target"], "k": spec["k"],
-            "p": spec["p"], "planner": getattr(args, "planner", "rule"),
+            "p": spec["p"], "kernel": spec.get("kernel", "gauss"), "planner": getattr(args, "planner", "rule"),
             "l2": "inputs exceed L2 (per-layer point data and the Krylov basis are > 129 MB)",
             "parallelism": f"replicas{args.gpus}"}
 
@@ -288,8 +296,11 @@ def main():
     dev_layers = [torch.as_tensor(L, device="cuda") for L in layers]
     k, p, prec, target = spec["k"], spec["p"], spec["prec"], spec["target"]
 
-    planner = make_planner(args.planner, prec, target, ml)
-    plan_all = make_planner("many", prec, target, ml) if args.planner == "rule" else None
+    kernel = spec.get("kernel", "gauss")
+    if kernel != "gauss" and args.planner != "rule":
+        raise SystemExit("the learned planner covers the Gaussian kernel only")
+    planner = make_planner(args.planner, prec, target, ml, kernel)
+    plan_all = make_planner("many", prec, target, ml, kernel) if args.planner == "rule" else None
     apply_plans = None
     if args.mode == "apply":
         apply_plans = [planner(x, s) for x, s in zip(dev_layers, sig)]
@@ -301,7 +312,7 @@ def main():
             before = sum(pl.info["applied_vectors"] for pl in apply_plans)
             ml.ml_fastsum_apply(apply_plans, Xa, Ya, mode="normalized")
             applied = (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
-            return None, 0, applied, [pl.info["taps"] for pl in apply_plans]
+            return None, 0, applied, [pl.info for pl in apply_plans]
         plans = plan_all(dl, sig) if plan_all else [planner(x, s) for x, s in zip(dl, sig)]
         if spec.get("per_layer"):
             lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=spec["block"], tol=1e-8, seed=1, evecs=evecs)
@@ -309,10 +320,10 @@ def main():
         else:
             lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=p, tol=1e-8, seed=1, evecs=evecs)
         applied = sum(pl.info["applied_vectors"] for pl in plans) * n
-        ms = [pl.info["taps"] for pl in plans]
+        infos = [pl.info for pl in plans]
         for pl in plans:
             pl.destroy()
-        return lam, nconv, applied, ms
+        return lam, nconv, applied, infos
 
     nev = n * k * (T if spec.get("per_layer") else 1)
     evecs = torch.empty(nev, dtype=torch.float64, device="cuda")
@@ -360,9 +371,9 @@ def main():
 
     # ---- roofline of the dominant kernel family
     d = spec["d"]
-    W = msz[0]
+    W = msz[0]["taps"]
     taps = W ** d
-    fam = max(("spread", "interp"), key=lambda f: prof.get(f, (0, 0.0))[1])
+    fam = max(("spread", "interp", "near"), key=lambda f: prof.get(f, (0, 0.0))[1])
     fam_launches, fam_ms = prof.get(fam, (0, 0.0))
     flops = applied_prof * 2.0 * taps             # one multiply-add per tap and point-vector
     achieved = flops / (fam_ms / 1e3) / 1e12 if fam_ms > 0 else 0.0
@@ -372,21 +383,24 @@ def main():
     # FP32 form; permutation 4, D^{-1/2} 8) plus 8 B per vector read (spread) or
     # read and written (interp); a pass carries nv vectors
     nv = min(args.b, 8) if args.mode == "apply" else (spec.get("block", 1) if spec.get("per_layer") else 1)
+    if fam == "near":
+        roofline = near_roofline(prof, msz, applied_prof, n, T, d, nv, prec, prof_step_ms)
     point_bytes = (8 * d * W + 4 if prec == "f64" else 4 * d) + 4 + 8
     vec_bytes = 8 if fam == "spread" else 16
     hbm_bytes = applied_prof / nv * point_bytes + applied_prof * vec_bytes
     hbm_gbs = hbm_bytes / (fam_ms / 1e3) / 1e9 if fam_ms > 0 else 0.0
     hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
-    roofline = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": ALU_PEAK_SOURCE[prec],
-                "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}",
-                "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
-                        "bytes_per_point_pass": point_bytes, "bytes_per_point_vector": vec_bytes,
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
-                "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()},
-                "region": "one extra step after the timed region with per-kernel CUDA events (eager launches), "
-                          f"{prof_step_ms:.1f} ms"}
+    if fam != "near":
+        roofline = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": ALU_PEAK_SOURCE[prec],
+                    "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}",
+                    "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                            "bytes_per_point_pass": point_bytes, "bytes_per_point_vector": vec_bytes,
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
+                    "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()},
+                    "region": "one extra step after the timed region with per-kernel CUDA events (eager launches), "
+                              f"{prof_step_ms:.1f} ms"}
 
     # ---- end to end through the C ABI with host buffers (pinned)
     host_layers = [torch.as_tensor(L).pin_memory() for L in layers]
@@ -429,7 +443,8 @@ def main():
 
     # ---- CPU baseline (oracle on the host cores) and sampled accuracy, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_baseline:
-        line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, planner, dev_layers, ml, torch)
+        line["cpu_baseline"], line["rel_err_sampled"] = cpu_baseline(layers, sig, planner, dev_layers, ml, torch,
+                                                                     kernel)
     if args.mode == "eig":
         line["lanczos_s"] = t_max / args.steps / 1e3
         line["eigenvalues"] = [float(x) for x in lam[:min(5, k)]]
@@ -556,14 +571,16 @@ def run_ac(args, spec, rank, world, barrier):
     return 0
 
 
-def make_planner(kind, prec, target, ml):
+def make_planner(kind, prec, target, ml, kernel="gauss"):
     """plan(points, sigma) with the automatic rule, or with the learned model
     trained for this precision and target (falls back to the rule where no
     candidate qualifies)."""
     if kind == "rule":
+        if kernel != "gauss":
+            return lambda x, s: ml.ml_fastsum_plan_ex(x, s, prec=prec, target_rel_err=target, kernel=kernel)
         return lambda x, s: ml.ml_fastsum_plan(x, s, prec=prec, target_rel_err=target)
     if kind == "many":   # all layers at once (concurrent set-up)
-        return lambda xs, ss: ml.ml_fastsum_plan_many(xs, ss, prec=prec, target_rel_err=target)
+        return lambda xs, ss: ml.ml_fastsum_plan_many(xs, ss, prec=prec, target_rel_err=target, kernel=kernel)
     from paper_2007_05239_gb300 import paramnet
     path = os.path.join(ROOT, "paper_2007_05239_gb300", f"paramnet_{prec}_{target:.0e}.npz")
     if not os.path.exists(path):
@@ -573,7 +590,38 @@ def make_planner(kind, prec, target, ml):
     return lambda x, s: ml.ml_fastsum_plan_learned(x, s, model, prec=prec, target_rel_err=target, margin=margin)[0]
 
 
-def cpu_baseline(layers, sig, planner, dev_layers, ml, torch):
+# in-range share of the pairs the near-field pass examines, for a uniform
+# cloud and cells of edge eps_I: ball(eps_I) / (3 eps_I)^d
+NEAR_IN_RANGE = {1: 2.0 / 3.0, 2: math.pi / 9.0, 3: 4.0 * math.pi / 81.0}
+FP64_PIPE_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12   # 2 DFMA per SM and clock
+
+
+def near_roofline(prof, infos, applied, n, T, d, nv, prec, prof_step_ms):
+    """ALU roofline of the Laplacian's near-field pass: per examined pair 2d
+    flop (coordinate differences and squares), and for the in-range share
+    18 flop (square root, scaling, exponential, 7 polynomial multiply-adds,
+    difference) plus 2 per vector; one pass per nv vectors."""
+    launches, ms = prof.get("near", (0, 0.0))
+    passes = applied / n / T / nv          # near-field passes per layer
+    f_in = NEAR_IN_RANGE[d]
+    per_pair = 2 * d + f_in * (18 + 2 * nv)
+    pairs = sum(i["near_pairs"] for i in infos) * passes
+    flops = pairs * per_pair
+    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    peak = ALU_PEAK_TFLOPS["f32"] if prec == "f32" else FP64_PIPE_TFLOPS
+    return {"bound": "alu", "kernel": "near", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": ALU_PEAK_SOURCE["f32"] if prec == "f32" else
+            "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop",
+            "work": f"{per_pair:.2f} flop per examined pair ({2 * d} for the distance, in-range share "
+                    f"{f_in:.3f} x (18 + 2 x {nv})); {pairs:.3g} examined pairs in the profiled step",
+            "pairs_per_s": pairs / (ms / 1e3) if ms > 0 else 0.0,
+            "family_ms": {f: v[1] for f, v in prof.items()}, "family_launches": {f: v[0] for f, v in prof.items()},
+            "region": "one extra step after the timed region with per-kernel CUDA events (eager launches), "
+                      f"{prof_step_ms:.1f} ms"}
+
+
+def cpu_baseline(layers, sig, planner, dev_layers, ml, torch, kernel="gauss"):
     """Time the oracle's direct FP64 sum of (1/T) sum_t W_t v on a bounded row
     sample (~12 s), and compare the GPU's FP64/FP32-form result on the same rows."""
     from oracle import graph
@@ -584,12 +632,12 @@ def cpu_baseline(layers, sig, planner, dev_layers, ml, torch):
     r0 = np.sort(rng.choice(n, size=min(n, 64), replace=False))
     t0 = time.perf_counter()
     for t in range(T):
-        graph.W_apply(layers[t], sig[t], v, rows=r0)
+        graph.W_apply(layers[t], sig[t], v, rows=r0, kernel=kernel)
     dt = max(time.perf_counter() - t0, 1e-6)
     R = int(min(n, max(64, 64 * 12.0 / dt)))
     rows = np.sort(rng.choice(n, size=R, replace=False))
     t0 = time.perf_counter()
-    ref = sum(graph.W_apply(layers[t], sig[t], v, rows=rows) for t in range(T)) / T
+    ref = sum(graph.W_apply(layers[t], sig[t], v, rows=rows, kernel=kernel) for t in range(T)) / T
     el = time.perf_counter() - t0
     plans = [planner(x, s) for x, s in zip(dev_layers, sig)]
     Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")

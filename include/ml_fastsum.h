@@ -103,6 +103,13 @@ typedef struct {
                                 automatic choices may be odd)                    */
     int dense;               /* 1: dense layer (ml_dense_plan*), W stored; the
                                 NFFT fields above are 0                          */
+    int kernel;              /* ml_kernel of the layer                           */
+    double eps_I;            /* Laplacian: near-field radius in the scaled domain
+                                (0 for the Gaussian)                             */
+    double kernel_err;       /* Laplacian: largest |K_RF - K_R| the plan measured
+                                on its probe distances (0 for the Gaussian)      */
+    int64_t near_pairs;      /* Laplacian: point pairs the near-field pass
+                                examines per vector (cell-list neighbours)       */
 } ml_plan_info;
 
 /*
@@ -136,6 +143,10 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
                           int N, int m, double eps_B, int p_reg, ml_prec prec,
                           double target_rel_err, void *stream);
 
+/* Radial kernels of Sec. 4: the Gaussian exp(-||y||^2/sigma^2) and the
+ * Laplacian exp(-||y||/sigma). */
+typedef enum { ML_KERNEL_GAUSS = 0, ML_KERNEL_LAPLACE = 1 } ml_kernel;
+
 /* Explicit parameters for ml_fastsum_plan_ex (0 = automatic choice). */
 typedef struct {
     int N;               /* bandwidth of K_RF (even, 4..512)                                 */
@@ -147,6 +158,8 @@ typedef struct {
     double target_rel_err;
     int bin;             /* spreading tile (bin) edge in grid cells, 0 = automatic rule;
                             larger tiles must fit the shared-memory budget (ML_ERR_ARG) */
+    int kernel;          /* ml_kernel; 0 = the Gaussian                                      */
+    double eps_I;        /* Laplacian: near-field radius in the scaled domain, 0 = automatic */
 } ml_plan_params;
 
 /*
@@ -154,6 +167,25 @@ typedef struct {
  * oversampling of the NFFT (Alg. 1 steps 1 and 3) chosen by the caller
  * (e.g. the learned parameter model below, ml_fastsum_plan_learned).
  * Same errors as ml_fastsum_plan, plus ML_ERR_ARG for out-of-range entries.
+ *
+ * kernel = ML_KERNEL_LAPLACE selects K(y) = exp(-||y||/sigma) (Sec. 4).  Its
+ * cusp at y = 0 is handled by the near-field scheme of the fast summation of
+ * non-smooth radial kernels that Sec. 4 cites: the ball domain is always used
+ * (eps_B = 0 picks eps_B = max(1/16, eps_I)); K_R is in addition replaced on
+ * ||y|| < eps_I by the even polynomial sum_{j<p_reg} c_j ||y||^{2j} matching
+ * K's derivatives 0..p_reg-1 at eps_I (p_reg = 0: 8); Alg. 1 sums K_R and a
+ * direct pass over a cell list of edge eps_I adds
+ *     sum_{j: ||x_i - x_j|| < eps_I} (K - K_R)(x_i - x_j) u_j
+ * (the pair j = i included).  Automatic choices: eps_I = c/N with c from
+ * target_rel_err (c = 4..16 grid cells), and N by a cost model that balances
+ * the grid transforms against the near-field pairs of a uniform cloud.  After
+ * the Fourier coefficients are formed the plan measures max |K_RF - K_R| on
+ * probe distances; above target_rel_err/2 it returns ML_ERR_DOMAIN.  The
+ * near-field pass evaluates K - K_R in FP32 (ML_F32, FP64 accumulation) or
+ * entirely in FP64 (ML_F64).  The inner polynomial's system (powers of eps_I
+ * up to 2 p_reg - 2) limits the attainable error near 1e-10: target_rel_err
+ * below 1e-10 returns ML_ERR_DOMAIN.  Dense clusters make the near field
+ * quadratic: more than 2^40 examined pairs return ML_ERR_DOMAIN.
  */
 ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
                              const ml_plan_params *params, void *stream);

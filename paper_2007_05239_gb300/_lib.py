@@ -20,6 +20,7 @@ ML_OK, ML_ERR_ARG, ML_ERR_CUDA, ML_ERR_OOM, ML_ERR_DOMAIN, ML_ERR_DEGREE, ML_ERR
 STATUS_NAMES = ["ML_OK", "ML_ERR_ARG", "ML_ERR_CUDA", "ML_ERR_OOM", "ML_ERR_DOMAIN", "ML_ERR_DEGREE",
                 "ML_ERR_BREAKDOWN", "ML_ERR_TIMEOUT", "ML_WARN_NOT_CONVERGED"]
 ML_F32, ML_F64 = 0, 1
+ML_KERNEL_GAUSS, ML_KERNEL_LAPLACE = 0, 1
 ML_RAW_W, ML_NORMALIZED_A, ML_DEGREE, ML_PER_LAYER = 0, 1, 2, 16
 MODES = {"raw": ML_RAW_W, "normalized": ML_NORMALIZED_A, "degree": ML_DEGREE}
 
@@ -47,7 +48,8 @@ ML_FEATURES = 9
 class PlanParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("taps", ctypes.c_int), ("oversampling", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("p_reg", ctypes.c_int), ("prec", ctypes.c_int),
-                ("target_rel_err", ctypes.c_double), ("bin", ctypes.c_int)]
+                ("target_rel_err", ctypes.c_double), ("bin", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("eps_I", ctypes.c_double)]
 
 
 class AcParams(ctypes.Structure):
@@ -62,7 +64,9 @@ class PlanInfo(ctypes.Structure):
                 ("eps_B", ctypes.c_double), ("sigma", ctypes.c_double), ("sigma_s", ctypes.c_double),
                 ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("target_rel_err", ctypes.c_double),
                 ("deg_min", ctypes.c_double), ("deg_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("applied_vectors", ctypes.c_int64), ("taps", ctypes.c_int), ("dense", ctypes.c_int)]
+                ("applied_vectors", ctypes.c_int64), ("taps", ctypes.c_int), ("dense", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("eps_I", ctypes.c_double), ("kernel_err", ctypes.c_double),
+                ("near_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -246,18 +250,23 @@ def ml_fastsum_plan(points, sigma, N=0, m=0, eps_B=0.0, p_reg=0, prec="f64", tar
     return Plan(h.value, n, d)
 
 
-def _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin):
+KERNELS = {"gauss": ML_KERNEL_GAUSS, "laplace": ML_KERNEL_LAPLACE}
+
+
+def _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin, kernel="gauss", eps_I=0.0):
     return PlanParams(int(N), int(taps), float(oversampling), float(eps_B), int(p_reg),
                       {"f32": ML_F32, "f64": ML_F64}[prec] if isinstance(prec, str) else int(prec),
-                      float(target_rel_err), int(bin))
+                      float(target_rel_err), int(bin),
+                      KERNELS[kernel] if isinstance(kernel, str) else int(kernel), float(eps_I))
 
 
 def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
-                       target_rel_err=0.0, bin=0, stream=None):
-    """Plan one layer with explicit window width / oversampling / bin edge (0 = automatic)."""
+                       target_rel_err=0.0, bin=0, kernel="gauss", eps_I=0.0, stream=None):
+    """Plan one layer with explicit window width / oversampling / bin edge (0 = automatic);
+    kernel "gauss" (exp(-r^2/sigma^2)) or "laplace" (exp(-r/sigma), with its near-field radius eps_I)."""
     lib = load()
     n, d = int(points.shape[0]), int(points.shape[1])
-    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin)
+    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, bin, kernel, eps_I)
     h = ctypes.c_void_p()
     _check(lib.ml_fastsum_plan_ex(ctypes.byref(h), _ptr(points), n, d, float(sigma), ctypes.byref(prm),
                                   _stream(stream)))
@@ -265,12 +274,12 @@ def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, 
 
 
 def ml_fastsum_plan_many(points, sigmas, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
-                         target_rel_err=0.0, stream=None):
+                         target_rel_err=0.0, kernel="gauss", eps_I=0.0, stream=None):
     """Plans of several layers (device point tensors sharing n), built concurrently."""
     lib = load()
     T = len(points)
     n = int(points[0].shape[0])
-    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, 0)
+    prm = _params(N, taps, oversampling, eps_B, p_reg, prec, target_rel_err, 0, kernel, eps_I)
     handles = (ctypes.c_void_p * T)()
     ptrs = (ctypes.c_void_p * T)(*[_ptr(x) for x in points])
     dims = (ctypes.c_int * T)(*[int(x.shape[1]) for x in points])

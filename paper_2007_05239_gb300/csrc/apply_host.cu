@@ -31,8 +31,8 @@ bool batchable(ml_plan_s *const *L, int T)
     const ml_plan_s *p0 = L[0];
     for (int t = 0; t < T; ++t) {
         const ml_plan_s *p = L[t];
-        if (p->dense || p->prec != ML_F32 || p->d != p0->d || p->W != p0->W || p->g.nbins() != 1 ||
-            p->nsub != p0->nsub)
+        if (p->dense || p->kernel != ML_KERNEL_GAUSS || p->prec != ML_F32 || p->d != p0->d || p->W != p0->W ||
+            p->g.nbins() != 1 || p->nsub != p0->nsub)
             return false;
         if (p->sub_max > kBatchPtsTotal) return false;
     }
@@ -44,7 +44,9 @@ bool batchable_layers(ml_plan_s *const *L, int T)
 {
     if (T < 2) return false;
     for (int t = 0; t < T; ++t)
-        if (L[t]->dense || L[t]->prec != ML_F32 || L[t]->d != L[0]->d || L[t]->W != L[0]->W) return false;
+        if (L[t]->dense || L[t]->kernel != ML_KERNEL_GAUSS || L[t]->prec != ML_F32 || L[t]->d != L[0]->d ||
+            L[t]->W != L[0]->W)
+            return false;
     return true;
 }
 
@@ -63,18 +65,23 @@ ml_status run_layer_ws(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cons
     if (v.nv < 1 || v.nv > kMaxVec) return fail(ML_ERR_ARG, "vectors per pass out of range");
     p->applied += v.nv;
     if (p->dense) return run_dense(p, v, o, st);
+    ml_status r;
     if (p->prec == ML_F32) {
         switch (p->d) {
-        case 1: return run_layer_f32_d1(p, v, o, w, st);
-        case 2: return run_layer_f32_d2(p, v, o, w, st);
-        default: return run_layer_f32_d3(p, v, o, w, st);
+        case 1: r = run_layer_f32_d1(p, v, o, w, st); break;
+        case 2: r = run_layer_f32_d2(p, v, o, w, st); break;
+        default: r = run_layer_f32_d3(p, v, o, w, st); break;
+        }
+    } else {
+        switch (p->d) {
+        case 1: r = run_layer_f64_d1(p, v, o, w, st); break;
+        case 2: r = run_layer_f64_d2(p, v, o, w, st); break;
+        default: r = run_layer_f64_d3(p, v, o, w, st); break;
         }
     }
-    switch (p->d) {
-    case 1: return run_layer_f64_d1(p, v, o, w, st);
-    case 2: return run_layer_f64_d2(p, v, o, w, st);
-    default: return run_layer_f64_d3(p, v, o, w, st);
-    }
+    // Laplacian: the near-field term, added to the same output after Alg. 1
+    if (r == ML_OK && p->kernel == ML_KERNEL_LAPLACE) r = run_near(p, v, o, st);
+    return r;
 }
 
 ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st)

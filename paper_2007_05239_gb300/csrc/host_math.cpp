@@ -59,6 +59,18 @@ static void gauss_derivs(double r, double s, int p, std::vector<double> &dk)
     for (int k = 0; k < p; ++k) dk[k] = ((k & 1) ? -1.0 : 1.0) * std::pow(s, -k) * H[k] * e;
 }
 
+// Derivatives of the Laplacian exp(-r/s): d^k/dr^k = (-1/s)^k exp(-r/s).
+static void laplace_derivs(double r, double s, int p, std::vector<double> &dk)
+{
+    const double e = std::exp(-r / s);
+    dk.assign(p, 0.0);
+    double f = 1.0;
+    for (int k = 0; k < p; ++k) {
+        dk[k] = f * e;
+        f *= -1.0 / s;
+    }
+}
+
 // Solve A x = rhs (n x n, row-major) by Gaussian elimination with partial pivoting.
 static bool solve_dense(int n, std::vector<double> A, std::vector<double> &x)
 {
@@ -85,14 +97,17 @@ static bool solve_dense(int n, std::vector<double> A, std::vector<double> &x)
 
 // Regulariser of the ball domain: on t = (r - r_I)/eps_B in [0, 1], a
 // polynomial of degree 2p-1 whose derivatives 0..p-1 at t = 0 equal those of
-// the Gaussian at r_I = 1/2 - eps_B (chain rule factor eps_B^k), whose value
-// at t = 1 is K(1/2) and whose derivatives 1..p-1 vanish at t = 1.
-bool regulariser_coeffs(double s, double eps_B, int p, std::vector<double> &q)
+// the kernel (Gaussian or Laplacian) at r_I = 1/2 - eps_B (chain rule factor
+// eps_B^k), whose value at t = 1 is K(1/2) and whose derivatives 1..p-1
+// vanish at t = 1.
+bool regulariser_coeffs(double s, double eps_B, int p, std::vector<double> &q, int kernel)
 {
     const int n = 2 * p;
     const double rI = 0.5 - eps_B;
     std::vector<double> dK;
-    gauss_derivs(rI, s, p, dK);
+    if (kernel == ML_KERNEL_LAPLACE) laplace_derivs(rI, s, p, dK);
+    else gauss_derivs(rI, s, p, dK);
+    const double k_half = kernel == ML_KERNEL_LAPLACE ? std::exp(-0.5 / s) : std::exp(-0.25 / (s * s));
     std::vector<double> A((size_t)n * (n + 1), 0.0);
     for (int k = 0; k < p; ++k) {
         for (int j = k; j < n; ++j) {
@@ -102,9 +117,122 @@ bool regulariser_coeffs(double s, double eps_B, int p, std::vector<double> &q)
             A[(p + k) * (n + 1) + j] = f;                    // at t = 1
         }
         A[k * (n + 1) + n] = dK[k] * std::pow(eps_B, k);
-        A[(p + k) * (n + 1) + n] = (k == 0) ? std::exp(-0.25 / (s * s)) : 0.0;
+        A[(p + k) * (n + 1) + n] = (k == 0) ? k_half : 0.0;
     }
     return solve_dense(n, A, q);
+}
+
+// Inner regulariser of the Laplacian: P(r) = sum_{j<p} c_j r^{2j} with
+// P^{(k)}(eps_I) = K^{(k)}(eps_I), k = 0..p-1; the k-th derivative of r^{2j}
+// is (2j)!/(2j-k)! r^{2j-k}.  An even polynomial, hence smooth at the origin
+// in every dimension.
+bool inner_coeffs(double s, double eps_I, int p, std::vector<double> &c)
+{
+    std::vector<double> dK;
+    laplace_derivs(eps_I, s, p, dK);
+    std::vector<double> A((size_t)p * (p + 1), 0.0);
+    for (int k = 0; k < p; ++k) {
+        for (int j = 0; j < p; ++j) {
+            const int e = 2 * j;
+            if (e < k) continue;
+            double f = 1.0;
+            for (int i = 0; i < k; ++i) f *= (double)(e - i);
+            A[k * (p + 1) + j] = f * std::pow(eps_I, e - k);
+        }
+        A[k * (p + 1) + p] = dK[k];
+    }
+    return solve_dense(p, A, c);
+}
+
+// The Laplacian's K_R at distance r (ball domain): the inner polynomial on
+// r < eps_I, the kernel up to 1/2 - eps_B, the two-point Taylor regulariser on
+// (1/2 - eps_B, 1/2] and its end value beyond.
+double laplace_regularised(double r, const LaplaceReg &g)
+{
+    if (r < g.eps_I) {
+        const double r2 = r * r;
+        double v = 0.0;
+        for (int j = (int)g.c.size() - 1; j >= 0; --j) v = v * r2 + g.c[j];
+        return v;
+    }
+    if (r <= 0.5 - g.eps_B) return std::exp(-r / g.s);
+    double t = (r - (0.5 - g.eps_B)) / g.eps_B;
+    if (t > 1.0) t = 1.0;
+    double v = 0.0;
+    for (int j = (int)g.q.size() - 1; j >= 0; --j) v = v * t + g.q[j];
+    return v;
+}
+
+bool laplace_reg_init(double s, double eps_B, double eps_I, int p, LaplaceReg &g)
+{
+    g.s = s;
+    g.eps_B = eps_B;
+    g.eps_I = eps_I;
+    return regulariser_coeffs(s, eps_B, p, g.q, ML_KERNEL_LAPLACE) && inner_coeffs(s, eps_I, p, g.c);
+}
+
+// Largest |K_RF(y) - K_R(y)| over probe points y with ||y|| <= 1/2 - eps_B.
+// b_l is even in every l_a, so the real trigonometric polynomial folds onto
+// l_a = 0..N/2 with factors 1, 2, ..., 2, 1 (the half weight of the unpaired
+// edge frequency counted on both sides) and cosines:
+//   K_RF(y) = sum_{kappa} b_kappa prod_a f_a(kappa_a) cos(2 pi kappa_a y_a).
+// Probes: radii spread over [0, 1/2 - eps_B] (a third of them inside 2 eps_I)
+// along quasi-random directions (golden-angle spiral in 2-d, Fibonacci
+// sphere in 3-d).
+double kernel_probe_error(const std::vector<double> &bhat, int N, int d, const LaplaceReg &g, int probes)
+{
+    const int H = N / 2 + 1;
+    const double rmax = 0.5 - g.eps_B;
+    const double golden = kPi * (3.0 - std::sqrt(5.0));
+    double worst = 0.0;
+    std::vector<double> f((size_t)3 * H);
+    for (int k = 0; k < probes; ++k) {
+        const double frac = (k + 0.5) / probes;
+        double r;
+        if (k % 3 == 0) r = std::min(rmax, 2.0 * g.eps_I * std::fmod(0.618034 * (k + 1), 1.0));
+        else r = rmax * std::pow(std::fmod(0.754878 * (k + 1), 1.0), 1.0 / d);
+        double u[3] = {1.0, 0.0, 0.0};
+        if (d == 1) {
+            u[0] = (k & 1) ? -1.0 : 1.0;
+        } else if (d == 2) {
+            u[0] = std::cos(golden * k);
+            u[1] = std::sin(golden * k);
+        } else {
+            const double z = 1.0 - 2.0 * frac;
+            const double rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+            u[0] = rho * std::cos(golden * k);
+            u[1] = rho * std::sin(golden * k);
+            u[2] = z;
+        }
+        for (int a = 0; a < d; ++a)
+            for (int q = 0; q < H; ++q) {
+                const double w = (q == 0 || q == N / 2) ? 1.0 : 2.0;
+                f[(size_t)a * H + q] = w * std::cos(2.0 * kPi * q * r * u[a]);
+            }
+        double val = 0.0;
+        if (d == 1) {
+            for (int q = 0; q < H; ++q) val += bhat[q] * f[q];
+        } else if (d == 2) {
+            for (int q1 = 0; q1 < H; ++q1) {
+                double acc = 0.0;
+                for (int q0 = 0; q0 < H; ++q0) acc += bhat[(size_t)q1 * H + q0] * f[q0];
+                val += acc * f[H + q1];
+            }
+        } else {
+            for (int q2 = 0; q2 < H; ++q2) {
+                double acc2 = 0.0;
+                for (int q1 = 0; q1 < H; ++q1) {
+                    const double *row = &bhat[((size_t)q2 * H + q1) * H];
+                    double acc = 0.0;
+                    for (int q0 = 0; q0 < H; ++q0) acc += row[q0] * f[q0];
+                    acc2 += acc * f[H + q1];
+                }
+                val += acc2 * f[2 * H + q2];
+            }
+        }
+        worst = std::max(worst, std::fabs(val - laplace_regularised(r, g)));
+    }
+    return worst;
 }
 
 static double kernel_regularised(double r, double s, double eps_B, const std::vector<double> &q)
@@ -157,7 +285,7 @@ void kernel_fourier(double s, int N, int d, double eps_B, int p_reg, std::vector
         return;
     }
     std::vector<double> q;
-    regulariser_coeffs(s, eps_B, p_reg, q);
+    regulariser_coeffs(s, eps_B, p_reg, q, ML_KERNEL_GAUSS);
     // samples on the full grid, then cosine sums one axis at a time
     std::vector<size_t> ext(3, 1);
     for (int a = 0; a < d; ++a) ext[a] = N;

@@ -115,6 +115,16 @@ struct ml_plan_s {
     bool deg_ok = true;    // every degree positive and finite: D^{-1/2} defined
     int64_t applied = 0;   // vectors pushed through apply_layer
     bool dense = false;    // dense layer: W stored explicitly (Wd), no fast summation
+    int kernel = 0;        // ml_kernel
+    double eps_I_req = 0;  // Laplacian: requested near-field radius (0: automatic)
+    double eps_B_req = 0;  // requested eps_B (the Laplacian picks one when 0)
+    double eps_I = 0;      // Laplacian: near-field radius (scaled domain)
+    double kernel_err = 0; // Laplacian: measured max |K_RF - K_R| on the probes
+    int64_t near_pairs = 0;   // Laplacian: pairs the near-field pass examines per vector
+    int nf_nc[3] = {1, 1, 1}; // near-field cells per dim
+    double nf_h = 0;          // near-field cell edge (scaled domain)
+    int nf_ntask = 0;         // near-field tasks (<= kNearThreads targets of one cell)
+    std::vector<double> nf_poly;  // inner polynomial c_j of r^{2j}
 
     // host tables (FP64)
     std::vector<double> bhat;    // (N/2+1)^d
@@ -136,6 +146,12 @@ struct ml_plan_s {
     ml::DevBuf trig_b[3]; // L_a x K (backward = transpose), same element type
     ml::DevBuf mult_d;    // K^d slot multipliers, same element type
     ml::DevBuf Wd;        // dense layers: W, n x n row-major (FP32 or FP64), zero diagonal
+    // Laplacian near field (cell order)
+    ml::DevBuf nf_loc;    // float4 n: coordinates relative to the point's cell corner
+    ml::DevBuf nf_orig;   // int32 n: input index
+    ml::DevBuf nf_sidx;   // int32 n: position in the sorted (spreading) order
+    ml::DevBuf nf_start;  // int32 cells+1: first point of each cell
+    ml::DevBuf nf_task;   // int4 nf_ntask: cell, first point, count
 
     // workspace
     ml::DevBuf scratch;   // spreading tiles: nsub * Pt^d * vp (T)
@@ -159,7 +175,32 @@ void window_fourier(int n_os, double h, double b, int kmax, std::vector<double> 
 // b_l, l = 0..N/2 per dim, for the box domain (separable) or the ball domain.
 void kernel_fourier(double sigma_s, int N, int d, double eps_B, int p_reg, std::vector<double> &bhat);
 // the two-point Taylor regulariser's monomial coefficients in t = (r - r_I)/eps_B
-bool regulariser_coeffs(double sigma_s, double eps_B, int p, std::vector<double> &q);
+bool regulariser_coeffs(double sigma_s, double eps_B, int p, std::vector<double> &q, int kernel);
+// the Laplacian's regularised kernel K_R (inner polynomial c in r^2 on r < eps_I,
+// outer two-point Taylor polynomial q on (1/2 - eps_B, 1/2])
+struct LaplaceReg {
+    double s = 0, eps_B = 0, eps_I = 0;
+    std::vector<double> q, c;
+};
+bool inner_coeffs(double sigma_s, double eps_I, int p, std::vector<double> &c);
+bool laplace_reg_init(double sigma_s, double eps_B, double eps_I, int p, LaplaceReg &g);
+double laplace_regularised(double r, const LaplaceReg &g);
+// largest |K_RF - K_R| on probe distances, b_l given on l_a = 0..N/2
+double kernel_probe_error(const std::vector<double> &bhat, int N, int d, const LaplaceReg &g, int probes);
+
+// ---------------------------------------------------- Laplacian kernel
+constexpr int kNearThreads = 128;  // targets per near-field task
+// grid cells across the inner region (c = N eps_I) for a target accuracy
+int laplace_cells(double target);
+// bandwidth N minimising the transform + near-field cost model
+int laplace_bandwidth(int64_t n, int d, int c, int W, ml_prec prec);
+// b_l of the Laplacian's K_R (FP64, on the device), copied to p->bhat
+ml_status laplace_fourier(ml_plan_s *p, const LaplaceReg &g, cudaStream_t st);
+// cell list of the near field (after the spreading order is fixed)
+ml_status near_plan(ml_plan_s *p, const double *points, cudaStream_t st);
+// LSD radix sort of (key, value) pairs over the low `bits` key bits
+ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int64_t n, int bits,
+                     cudaStream_t st, int **result_vals);
 // multiplier over coefficient slots
 void slot_multiplier(int N, int d, int n_os, const std::vector<double> &bhat,
                      const std::vector<double> &phihat, std::vector<double> &mult);
@@ -201,6 +242,8 @@ struct ApplyOpts {
 };
 
 ml_status apply_layer(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
+// adds the Laplacian's near-field term of one layer pass to its output
+ml_status run_near(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, cudaStream_t st);
 
 // ---------------------------------------------------------------- tracing
 bool profiling();

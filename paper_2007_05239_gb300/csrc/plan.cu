@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
     }
 }
 
-static ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int64_t n, int bits,
-                            cudaStream_t st, int **result_vals)
+ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int64_t n, int bits,
+                     cudaStream_t st, int **result_vals)
 {
     const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
     DevBuf hist;
@@ -528,6 +528,71 @@ ml_status ensure_workspace(ml_plan_s *p, int nv)
     return ML_OK;
 }
 
+// Laplacian (ball domain always): window, cells across the inner region c,
+// bandwidth N, eps_I = c/N and eps_B = max(1/16, eps_I) unless given; the
+// scaling; b_l of K_R; and the measured max |K_RF - K_R| on probe distances.
+// Above target/2 the automatic choices widen the inner region (c += 2, or a
+// larger N when eps_I is fixed) and try again.
+static ml_status laplace_setup(ml_plan_s *p, const double *points, int nblk, DevBuf &part, cudaStream_t st)
+{
+    const int64_t n = p->n;
+    const int d = p->d;
+    {
+        ProfScope pr_("plan", st);
+        k_maxrad<<<nblk, 256, 0, st>>>(points, n, d, p->center[0], p->center[1], p->center[2], part.as<double>());
+    }
+    ML_CUDA(cudaGetLastError());
+    std::vector<double> hp(nblk);
+    ML_CUDA(cudaMemcpyAsync(hp.data(), part.p, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaStreamSynchronize(st));
+    double r2 = 0.0;
+    for (int b = 0; b < nblk; ++b) r2 = std::max(r2, hp[b]);
+    double rmax = std::sqrt(r2);
+    if (!(rmax > 0)) rmax = p->sigma;
+    if (p->p_reg == 0) p->p_reg = 8;
+    if (p->W == 0) {
+        double sig_os = 2.0;
+        auto_window(p->target, &p->W, &sig_os);
+        if (p->sig_os_req == 0) p->sig_os_req = sig_os;
+    }
+    const bool fixN = p->N > 0, fixI = p->eps_I_req > 0;
+    int c = laplace_cells(p->target);
+    int N = p->N;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        double eI;
+        if (fixI) {
+            eI = p->eps_I_req;
+            if (!fixN) N = std::max(16, 2 * (int)std::ceil(0.5 * c / eI));
+        } else {
+            if (!fixN) N = laplace_bandwidth(n, d, c, p->W, p->prec);
+            eI = (double)c / N;
+        }
+        if (N > kMaxN)
+            return fail(ML_ERR_DOMAIN, "Laplacian: bandwidth N=" + std::to_string(N) + " needed for eps_I beyond the limit");
+        const double eB = p->eps_B_req > 0 ? p->eps_B_req : std::max(1.0 / 16, eI);
+        if (!(eI < 0.5 - eB)) return fail(ML_ERR_ARG, "Laplacian: eps_I must stay below 1/2 - eps_B");
+        p->N = N;
+        p->eps_I = eI;
+        p->eps_B = eB;
+        p->scale = (0.25 - 0.5 * eB) / rmax;
+        p->domain = 1;
+        p->sigma_s = p->scale * p->sigma;
+        LaplaceReg g;
+        if (!laplace_reg_init(p->sigma_s, eB, eI, p->p_reg, g))
+            return fail(ML_ERR_DOMAIN, "Laplacian: regulariser system is singular");
+        ML_TRY(laplace_fourier(p, g, st));
+        p->kernel_err = kernel_probe_error(p->bhat, N, d, g, d == 3 ? 48 : 96);
+        p->nf_poly = g.c;
+        if (p->kernel_err <= 0.5 * p->target) return ML_OK;
+        if ((fixN && fixI) || c >= 24) break;
+        c += 2;
+    }
+    char buf[160];
+    snprintf(buf, sizeof buf, "Laplacian: kernel approximation error %.3g above target/2 (N=%d, eps_I=%.4g)",
+             p->kernel_err, p->N, p->eps_I);
+    return fail(ML_ERR_DOMAIN, buf);
+}
+
 static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
 {
     const int64_t n = p->n;
@@ -555,7 +620,9 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         p->center[a] = 0.5 * (lo[a] + hi[a]);
     }
     // ---- domain scaling (isotropic, exact for W)
-    if (p->eps_B > 0) {
+    if (p->kernel == ML_KERNEL_LAPLACE) {
+        ML_TRY(laplace_setup(p, points, nblk, part, st));
+    } else if (p->eps_B > 0) {
         { ProfScope pr_("plan", st);
         k_maxrad<<<nblk, 256, 0, st>>>(points, n, d, p->center[0], p->center[1], p->center[2], part.as<double>());
         }
@@ -778,7 +845,8 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     idx2.release();
     // ---- Fourier tables (host FP64) -> device
     window_fourier(p->n_os, 0.5 * p->W, p->kb_shape, p->N / 2, p->phihat);
-    kernel_fourier(p->sigma_s, p->N, d, p->eps_B, p->p_reg, p->bhat);
+    if (p->kernel != ML_KERNEL_LAPLACE)   // the Laplacian's b_l were formed with its scaling
+        kernel_fourier(p->sigma_s, p->N, d, p->eps_B, p->p_reg, p->bhat);
     slot_multiplier(p->N, d, p->n_os, p->bhat, p->phihat, p->mult);
     for (int a = 0; a < d; ++a) {
         std::vector<double> M, Mt;
@@ -796,6 +864,8 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     }
     if (p->prec == ML_F32) ML_TRY(upload<float>(p->mult_d, p->mult));
     else ML_TRY(upload_dw(p->mult_d, p->mult));
+    // ---- near-field cell list (Laplacian)
+    if (p->kernel == ML_KERNEL_LAPLACE) ML_TRY(near_plan(p, points, st));
     // ---- degrees D = W~ 1 - K(0) (sorted order), D^{-1/2}
     ML_TRY(ensure_workspace(p, 1));
     ML_TRY(p->deg.ensure((size_t)n * 8));
@@ -830,7 +900,8 @@ int64_t ml_plan_s::device_bytes() const
     int64_t t = 0;
     const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
-                                &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status, &Wd};
+                                &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status, &Wd,
+                                &nf_loc, &nf_orig, &nf_sidx, &nf_start, &nf_task};
     for (auto *b : bufs) t += (int64_t)b->bytes;
     return t;
 }
@@ -852,7 +923,7 @@ const char *ml_version(void) { return "ml_fastsum 0.1 (sm_103a)"; }
 
 static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, int d, double sigma, int N, int W,
                              double sig_os, double eps_B, int p_reg, ml_prec prec, double target_rel_err,
-                             int bin, void *stream)
+                             int bin, int kernel, double eps_I, void *stream)
 {
     using namespace ml;
     if (!out) return fail(ML_ERR_ARG, "out is null");
@@ -866,7 +937,18 @@ static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, in
         return fail(ML_ERR_ARG, "window width must be 0, 4..8, 10, 12, 14 or 16 taps");
     if (sig_os != 0 && !(sig_os >= 1.5 && sig_os <= 4.0)) return fail(ML_ERR_ARG, "oversampling must be in [1.5, 4]");
     if (!(eps_B >= 0 && eps_B < 0.5)) return fail(ML_ERR_ARG, "eps_B must be in [0, 1/2)");
-    if (eps_B > 0 && (p_reg < 1 || p_reg > 8)) return fail(ML_ERR_ARG, "p_reg must be in [1, 8] when eps_B > 0");
+    if (kernel != ML_KERNEL_GAUSS && kernel != ML_KERNEL_LAPLACE)
+        return fail(ML_ERR_ARG, "kernel must be ML_KERNEL_GAUSS or ML_KERNEL_LAPLACE");
+    if (kernel == ML_KERNEL_GAUSS) {
+        if (eps_B > 0 && (p_reg < 1 || p_reg > 8)) return fail(ML_ERR_ARG, "p_reg must be in [1, 8] when eps_B > 0");
+        if (eps_I != 0) return fail(ML_ERR_ARG, "eps_I applies to the Laplacian kernel only");
+    } else {
+        if (p_reg < 0 || p_reg > 8) return fail(ML_ERR_ARG, "p_reg must be 0 (automatic) or in [1, 8]");
+        if (!(eps_I == 0 || (eps_I >= 1.0 / 1024 && eps_I <= 0.25)))
+            return fail(ML_ERR_ARG, "eps_I must be 0 (automatic) or in [1/1024, 1/4]");
+        if (target_rel_err > 0 && target_rel_err < 1e-10)
+            return fail(ML_ERR_DOMAIN, "Laplacian: the inner polynomial's conditioning bounds the accuracy near 1e-10");
+    }
     if (prec != ML_F32 && prec != ML_F64) return fail(ML_ERR_ARG, "prec must be ML_F32 or ML_F64");
     if (bin < 0 || bin > 512) return fail(ML_ERR_ARG, "bin must be 0 (automatic) or in [1, 512]");
     int dev = 0;
@@ -883,6 +965,12 @@ static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, in
     p->bin_req = bin;
     p->eps_B = eps_B;
     p->p_reg = eps_B > 0 ? p_reg : 0;
+    p->kernel = kernel;
+    if (kernel == ML_KERNEL_LAPLACE) {
+        p->eps_B_req = eps_B;
+        p->eps_I_req = eps_I;
+        p->p_reg = p_reg;
+    }
     p->prec = prec;
     p->target = target_rel_err > 0 ? target_rel_err : (prec == ML_F32 ? 1e-4 : 1e-6);
     ml_status st = plan_impl(p, points, (cudaStream_t)stream);
@@ -899,7 +987,8 @@ ml_status ml_fastsum_plan(ml_plan_t *out, const double *points, int64_t n, int d
                           double eps_B, int p_reg, ml_prec prec, double target_rel_err, void *stream)
 {
     if (m != 0 && (m < 2 || m > ml::kMaxM)) return ml::fail(ML_ERR_ARG, "m must be 0 or in [2, 8]");
-    return plan_common(out, points, n, d, sigma, N, 2 * m, 0.0, eps_B, p_reg, prec, target_rel_err, 0, stream);
+    return plan_common(out, points, n, d, sigma, N, 2 * m, 0.0, eps_B, p_reg, prec, target_rel_err, 0,
+                       ML_KERNEL_GAUSS, 0.0, stream);
 }
 
 ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, int d, double sigma,
@@ -907,7 +996,7 @@ ml_status ml_fastsum_plan_ex(ml_plan_t *out, const double *points, int64_t n, in
 {
     if (!prm) return ml::fail(ML_ERR_ARG, "params is null");
     return plan_common(out, points, n, d, sigma, prm->N, prm->taps, prm->oversampling, prm->eps_B, prm->p_reg,
-                       prm->prec, prm->target_rel_err, prm->bin, stream);
+                       prm->prec, prm->target_rel_err, prm->bin, prm->kernel, prm->eps_I, stream);
 }
 
 ml_status ml_plan_destroy(ml_plan_t plan)
@@ -948,6 +1037,10 @@ ml_status ml_plan_get_info(ml_plan_t p, ml_plan_info *info)
     info->device_bytes = p->device_bytes();
     info->applied_vectors = p->applied;
     info->dense = p->dense ? 1 : 0;
+    info->kernel = p->kernel;
+    info->eps_I = p->eps_I;
+    info->kernel_err = p->kernel_err;
+    info->near_pairs = p->near_pairs;
     return ML_OK;
 }
 

@@ -17,6 +17,7 @@ import numpy as np
 
 __all__ = [
     "uniform_cube",
+    "uniform_ball",
     "image_voronoi_layers",
     "image_discs_layers",
     "gmm_band_layers",
@@ -29,6 +30,15 @@ def uniform_cube(n: int = 2000, d: int = 3, half: float = 0.25, seed: int = 1) -
     """n points i.i.d. uniform in [-half, half]^d."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-half, half, size=(n, d))
+
+
+def uniform_ball(n: int = 2000, d: int = 3, radius: float = 1.0, seed: int = 1) -> np.ndarray:
+    """n points i.i.d. uniform in the d-ball of the given radius (a Gaussian
+    direction scaled by radius * U^(1/d))."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    X /= np.linalg.norm(X, axis=1)[:, None]
+    return radius * X * rng.random(n)[:, None] ** (1.0 / d)
 
 
 def _smooth_texture(h: int, w: int, rng: np.random.Generator, terms: int = 6) -> np.ndarray:
