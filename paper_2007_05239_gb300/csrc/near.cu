@@ -382,10 +382,16 @@ struct NearArgs {
     int sorted_out;
 };
 
-__device__ __forceinline__ float exp_t(float x) { return expf(x); }
-__device__ __forceinline__ double exp_t(double x) { return exp(x); }
-__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
-__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+// exp(-r / sigma') from r^2.  FP32: r = r^2 rsqrt(r^2) (the self pair r^2 = 0
+// kept at r = 0) and 2^(-r k) with k = log2(e) / sigma' on the special-function
+// unit, each within a few ulp, far inside the FP32 form's accuracy; FP64: the
+// correctly rounded library functions.
+__device__ __forceinline__ float kernel_of_r2(float r2, float k)
+{
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    return exp2f(-r * k);
+}
+__device__ __forceinline__ double kernel_of_r2(double r2, double k) { return exp(-sqrt(r2) * k); }
 
 // y_i += alpha * s_i * sum_{j: r_ij < eps_I} (exp(-r_ij/sigma') - P(r_ij^2)) u_j,
 // u_j = s_j x_j (s = D^{-1/2} for normalised products, else 1); in sorted
@@ -407,7 +413,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near(const NearArgs a)
     const bool act = t < tk.z;
     const int k = tk.y + t;
     const V4 xi = act ? loc[k] : Vec4<T>::make(0, 0, 0);
-    const T h = (T)a.h, eps2 = (T)a.eps2, inv_s = (T)a.inv_s;
+    const T h = (T)a.h, eps2 = (T)a.eps2;
+    const T kexp = sizeof(T) == 4 ? (T)(a.inv_s * 1.4426950408889634) : (T)a.inv_s;   // log2(e) / sigma' in FP32
     T cf[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) cf[j] = (T)a.c[j];
@@ -444,6 +451,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(const NearArgs a)
                     T acc[NV];
 #pragma unroll
                     for (int c = 0; c < NV; ++c) acc[c] = 0;
+#pragma unroll 4
                     for (int s = 0; s < m; ++s) {
                         const V4 q = sp[s];
                         const T ex = xi.x - q.x;
@@ -457,11 +465,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near(const NearArgs a)
                             r2 = fma(ez, ez, r2);
                         }
                         if (r2 < eps2) {
-                            const T r = sqrt_t(r2);
                             T P = cf[7];
 #pragma unroll
                             for (int jj = 6; jj >= 0; --jj) P = fma(P, r2, cf[jj]);
-                            const T delta = exp_t(-r * inv_s) - P;
+                            const T delta = kernel_of_r2(r2, kexp) - P;
 #pragma unroll
                             for (int c = 0; c < NV; ++c) acc[c] = fma(delta, su[s * NV + c], acc[c]);
                         }
