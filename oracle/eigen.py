@@ -59,11 +59,11 @@ def L1_eigs(layers, sigmas, k, kernel="gauss"):
     return 1.0 - theta, Phi
 
 
-def Lp_eigs(layers, sigmas, p, k):
+def Lp_eigs(layers, sigmas, p, k, kernel="gauss"):
     """k smallest eigenpairs of L_{p,delta} for p < 0 (Sec. 3)."""
     if p >= 0:
         raise ValueError("use L1_eigs for p = 1")
-    M = graph.power_mean_p_dense(layers, sigmas, p)
+    M = graph.power_mean_p_dense(layers, sigmas, p, kernel)
     mu, Phi = largest_eigs(M, k)
     return mu ** (1.0 / p), Phi
 

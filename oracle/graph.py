@@ -182,17 +182,19 @@ def shift_delta(p):
     return float(np.log1p(abs(p))) if p < 0 else 0.0
 
 
-def power_mean_p_dense(layers, sigmas, p):
+def power_mean_p_dense(layers, sigmas, p, kernel="gauss"):
     """L_{p,delta}^p = (1/T) sum_t (L_sym^(t) + delta I)^p  (Eq. L_p_delta_power_p).
 
     The matrix power of each symmetric layer term is formed through its
-    eigendecomposition, f(A) = Phi f(Lambda) Phi^T (Sec. 2).
+    eigendecomposition, f(A) = Phi f(Lambda) Phi^T (Sec. 2).  `kernel` is one
+    kernel name for every layer or a list with one per layer.
     """
     delta = shift_delta(p)
     T = len(layers)
+    kernels = [kernel] * T if isinstance(kernel, str) else list(kernel)
     M = None
     for t in range(T):
-        L = L_sym_dense(layers[t], sigmas[t]) + delta * np.eye(layers[t].shape[0])
+        L = L_sym_dense(layers[t], sigmas[t], kernels[t]) + delta * np.eye(layers[t].shape[0])
         lam, Phi = np.linalg.eigh(L)
         if p < 0 and lam.min() <= 0:
             raise ValueError("shifted Laplacian is not positive definite")

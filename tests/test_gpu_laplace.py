@@ -182,6 +182,48 @@ def test_eigenpairs_small_graph():
         assert eigen.subspace_angle(V[:, g], V_ref[:, g]) <= 1e-6
 
 
+def test_power_mean_p_minus_one_mixed_kernels():
+    # L_{-1,delta} of a Laplacian and a Gaussian layer: the inner CG solves
+    # replay CUDA graphs that contain the near-field pass
+    n, k = 700, 6
+    A = ball(n, 3, 90)
+    B = workloads.uniform_cube(n, 2, seed=91)
+    pl = plan_lap(A, 0.4, "f64", target_rel_err=1e-8)
+    pg = ml.ml_fastsum_plan(dev(B), 0.1, prec="f64", target_rel_err=1e-12)
+    replays = ml.ml_graph_replays()
+    V = torch.empty(k * n, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs([pl, pg], k, p=-1.0, tol=1e-10, seed=7, evecs=V)
+    assert st == ml.ML_OK and nconv == k
+    assert ml.ml_graph_replays() > replays
+    lam_ref, V_ref = eigen.Lp_eigs([A, B], [0.4, 0.1], -1.0, k + 3, kernel=["laplace", "gauss"])
+    assert np.abs(lam - lam_ref[:k]).max() <= 1e-8, (lam, lam_ref[:k])
+    V = V.cpu().numpy().reshape(k, n).T
+    for g in eigen.eigen_groups(lam_ref[:k + 3], rel_gap=1e-6):
+        if max(g) >= k:
+            continue
+        assert eigen.subspace_angle(V[:, g], V_ref[:, g]) <= 1e-6
+
+
+@pytest.mark.parametrize("block", [1, 3])
+def test_per_layer_block_lanczos(block):
+    # every layer's L_sym at once (Laplacian layers run their own kernels)
+    n, k = 900, 5
+    layers = [ball(n, 3, 95), workloads.uniform_cube(n, 2, seed=96)]
+    sig = [0.3, 0.1]
+    plans = [plan_lap(L, s, "f64", target_rel_err=1e-8) for L, s in zip(layers, sig)]
+    V = torch.empty(len(layers) * n * k, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=block, tol=1e-10, seed=11, evecs=V)
+    assert st == ml.ML_OK and (nconv == k).all()
+    V = V.cpu().numpy().reshape(len(layers), k, n)
+    for t, (X, s) in enumerate(zip(layers, sig)):
+        lam_ref, V_ref = eigen.lsym_eigs(X, s, k + 3, kernel="laplace")
+        assert np.abs(lam[t] - lam_ref[:k]).max() <= 1e-8, (t, lam[t], lam_ref[:k])
+        for g in eigen.eigen_groups(lam_ref, rel_gap=1e-6):
+            if max(g) >= k:
+                continue
+            assert eigen.subspace_angle(V[t][g].T, V_ref[:, g]) <= 1e-6
+
+
 def test_argument_errors():
     X = dev(ball(500, 2, 80))
     with pytest.raises(ml.MLError) as e:
