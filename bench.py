@@ -390,9 +390,17 @@ def main():
     hbm_bytes = applied_prof / nv * point_bytes + applied_prof * vec_bytes
     hbm_gbs = hbm_bytes / (fam_ms / 1e3) / 1e9 if fam_ms > 0 else 0.0
     hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    # DRAM traffic per launch from the ncu capture of this kernel on this workload
+    # (dram__bytes_read.sum + dram__bytes_write.sum; one launch = one layer,
+    # 1e6 points, one vector), only where that capture applies
+    traffic, traffic_src = None, None
+    key = (args.workload, prec, fam, W, nv)
+    if key in NCU_TRAFFIC:
+        traffic, traffic_src = NCU_TRAFFIC[key]
     if fam != "near":
         roofline = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                    "algorithmic_bytes_per_launch": hbm_bytes / fam_launches if fam_launches else None,
                     "peak_source": ALU_PEAK_SOURCE[prec],
                     "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}",
                     "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
@@ -594,6 +602,16 @@ def make_planner(kind, prec, target, ml, kernel="gauss"):
 # cloud and cells of edge eps_I: ball(eps_I) / (3 eps_I)^d
 NEAR_IN_RANGE = {1: 2.0 / 3.0, 2: math.pi / 9.0, 3: 4.0 * math.pi / 81.0}
 FP64_PIPE_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12   # 2 DFMA per SM and clock
+
+# ncu DRAM bytes (read + write) of one launch, keyed by (workload, form, kernel
+# family, window width, vectors per pass); valid while the kernel is unchanged
+# since the capture named beside it
+NCU_TRAFFIC = {
+    ("image_voronoi_n1e6_T3", "f64", "spread", 7, 1):
+        (192.6e6 + 10.4e6, "profiles/spread_interp_f64_image_n1e6.md: k_spread_f64<3,7,1>, one layer"),
+    ("image_voronoi_n1e6_T3", "f64", "interp", 7, 1):
+        (195.7e6 + 7.6e6, "profiles/spread_interp_f64_image_n1e6.md: k_interp_f64<3,7,1>, one layer"),
+}
 
 
 def near_roofline(prof, infos, applied, n, T, d, nv, prec, prof_step_ms):
