@@ -189,16 +189,24 @@ def power_mean_p_dense(layers, sigmas, p, kernel="gauss"):
     eigendecomposition, f(A) = Phi f(Lambda) Phi^T (Sec. 2).  `kernel` is one
     kernel name for every layer or a list with one per layer.
     """
-    delta = shift_delta(p)
     T = len(layers)
     kernels = [kernel] * T if isinstance(kernel, str) else list(kernel)
+    return power_mean_of_laplacians([L_sym_dense(layers[t], sigmas[t], kernels[t]) for t in range(T)], p)
+
+
+def power_mean_of_laplacians(Ls, p):
+    """(1/T) sum_t (L_t + delta I)^p for given symmetric layer Laplacians L_t
+    (Eq. L_p_delta_power_p; delta = log(1+|p|) for p < 0, 0 for p > 0, Sec. 2),
+    each power through the layer's eigendecomposition.  For p > 0 the
+    eigenvalues of the positive semi-definite L_t are clipped at 0 against
+    rounding."""
+    delta = shift_delta(p)
     M = None
-    for t in range(T):
-        L = L_sym_dense(layers[t], sigmas[t], kernels[t]) + delta * np.eye(layers[t].shape[0])
-        lam, Phi = np.linalg.eigh(L)
+    for L in Ls:
+        lam, Phi = np.linalg.eigh(np.asarray(L, dtype=np.float64) + delta * np.eye(L.shape[0]))
         if p < 0 and lam.min() <= 0:
             raise ValueError("shifted Laplacian is not positive definite")
         lam = np.maximum(lam, 0.0) if p > 0 else lam
         F = (Phi * lam ** p) @ Phi.T
         M = F if M is None else M + F
-    return 0.5 * (M + M.T) / T
+    return 0.5 * (M + M.T) / len(Ls)

@@ -9,7 +9,8 @@ the same sizes, dimensions and value structure (Sec. 7 feature grouping;
 Sec. 8.2 image workload, Sec. 8.4 hyperspectral workload).
 
 All generators use numpy's PCG64 with an explicit seed and return float64
-arrays of shape (n, d_t), one per layer.
+arrays of shape (n, d_t), one per layer (the block model: n x n weight
+matrices, one per layer).
 """
 from __future__ import annotations
 
@@ -21,6 +22,7 @@ __all__ = [
     "image_voronoi_layers",
     "image_discs_layers",
     "gmm_band_layers",
+    "block_model_layers",
     "cloud_for_mlp",
     "WORKLOADS",
 ]
@@ -161,6 +163,26 @@ def known_labels(truth: np.ndarray, fraction: float, seed: int) -> np.ndarray:
             i = rng.choice(np.nonzero(truth == c)[0])
             lab[i] = c
     return lab
+
+
+def block_model_layers(sizes, p_in, p_out, seed: int):
+    """Multilayer stochastic block model (Holland, Laskey, Leinhardt 1983), the
+    synthetic graphs of the paper's Sec. 9 examples.
+
+    Nodes are grouped into classes of the given sizes.  Layer t connects two
+    distinct nodes of one class with probability p_in[t] and of different
+    classes with p_out[t], independently per node pair; the layer's weight
+    matrix is the symmetric 0/1 adjacency with zero diagonal.  Returns
+    (list of n x n float64 matrices, class of each node)."""
+    rng = np.random.default_rng(seed)
+    truth = np.repeat(np.arange(len(sizes)), sizes).astype(np.int32)
+    n = len(truth)
+    same = truth[:, None] == truth[None, :]
+    layers = []
+    for pi, po in zip(p_in, p_out):
+        A = np.triu((rng.uniform(size=(n, n)) < np.where(same, pi, po)).astype(np.float64), 1)
+        layers.append(A + A.T)
+    return layers, truth
 
 
 def cloud_for_mlp(index: int, n_min: int = 10_000, n_max: int = 1_000_000):
