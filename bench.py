@@ -430,7 +430,9 @@ def main():
             ml.ml_fastsum_apply(apply_plans, hx, hy, mode="normalized")   # host buffers: staged by the library
             applied_e2e += (sum(pl.info["applied_vectors"] for pl in apply_plans) - before) * n
             continue
-        dl = [x.to("cuda", non_blocking=True) for x in host_layers]
+        # the plans take the pinned host layers through the C ABI and copy them
+        # to the device themselves (the learned planner reads device points)
+        dl = host_layers if args.planner == "rule" else [x.to("cuda", non_blocking=True) for x in host_layers]
         lam_e, _, a, _ = step(dl, host_evecs)
         applied_e2e += a
     e1.record(stream)

@@ -117,7 +117,9 @@ typedef struct {
  * and compute its degrees (Sec. 2).
  *
  *   out            receives the plan handle (caller destroys it).
- *   points         device, n x d row-major FP64, read during the call only.
+ *   points         n x d row-major FP64, read during the call only: device
+ *                  memory, or host memory, which the call copies to a device
+ *                  buffer of its own on `stream` (freed on return).
  *   n, d           n >= 2, d in {1,2,3}.
  *   sigma          Gaussian width > 0 in the units of `points`.
  *   N              bandwidth (even, 4..512), or 0 to choose from target_rel_err.
@@ -235,8 +237,9 @@ ml_status ml_fastsum_plan_autotune(ml_plan_t *out, const double *points, int64_t
  * each on its own non-blocking stream (not from the paper: plan set-up is
  * latency-bound, the layers are independent).
  *   out     host array of T handles (all NULL on failure).
- *   points  host array of T device pointers (layer t: n x d[t] FP64), ready
- *           in stream order on `stream`.
+ *   points  host array of T pointers (layer t: n x d[t] FP64), device memory
+ *           ready in stream order on `stream`, or host memory (copied to the
+ *           device by the layer's plan, as in ml_fastsum_plan).
  *   d, sigma host arrays of T.
  * Returns when every plan is complete.  Errors as ml_fastsum_plan_ex, with
  * the failing layer named in ml_last_error().

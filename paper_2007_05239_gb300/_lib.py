@@ -240,7 +240,8 @@ class Plan:
 
 
 def ml_fastsum_plan(points, sigma, N=0, m=0, eps_B=0.0, p_reg=0, prec="f64", target_rel_err=0.0, stream=None):
-    """Plan one layer.  `points`: CUDA float64 tensor (n, d)."""
+    """Plan one layer.  `points`: float64 (n, d), a CUDA tensor, or host
+    memory (numpy array or CPU tensor) that the library copies to the device."""
     lib = load()
     n, d = int(points.shape[0]), int(points.shape[1])
     h = ctypes.c_void_p()
@@ -275,7 +276,8 @@ def ml_fastsum_plan_ex(points, sigma, N=0, taps=0, oversampling=0.0, eps_B=0.0, 
 
 def ml_fastsum_plan_many(points, sigmas, N=0, taps=0, oversampling=0.0, eps_B=0.0, p_reg=0, prec="f64",
                          target_rel_err=0.0, kernel="gauss", eps_I=0.0, stream=None):
-    """Plans of several layers (device point tensors sharing n), built concurrently."""
+    """Plans of several layers (point tensors or arrays sharing n, device or
+    host memory; host points are copied by the library), built concurrently."""
     lib = load()
     T = len(points)
     n = int(points[0].shape[0])

@@ -973,7 +973,33 @@ static ml_status plan_common(ml_plan_t *out, const double *points, int64_t n, in
     }
     p->prec = prec;
     p->target = target_rel_err > 0 ? target_rel_err : (prec == ML_F32 ? 1e-4 : 1e-6);
-    ml_status st = plan_impl(p, points, (cudaStream_t)stream);
+    // host points: copied to a device buffer on the call's stream, freed on
+    // return (the set-up reads the points only before its last synchronisation)
+    DevBuf staged;
+    const double *dpts = points;
+    {
+        cudaPointerAttributes at;
+        bool on_device = false;
+        if (cudaPointerGetAttributes(&at, points) == cudaSuccess)
+            on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();   // an unregistered host pointer
+        if (!on_device) {
+            const size_t bytes = (size_t)n * d * sizeof(double);
+            ml_status sst = staged.ensure(bytes);
+            cudaError_t ce = cudaSuccess;
+            if (sst == ML_OK) {
+                ce = cudaMemcpyAsync(staged.p, points, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+                if (ce != cudaSuccess) sst = cuda_fail(ce, "cudaMemcpyAsync (points)", __FILE__, __LINE__);
+            }
+            if (sst != ML_OK) {
+                delete p;
+                return sst;
+            }
+            dpts = staged.as<double>();
+        }
+    }
+    ml_status st = plan_impl(p, dpts, (cudaStream_t)stream);
     if (st != ML_OK) {
         release_all(p);
         delete p;

@@ -179,6 +179,25 @@ def test_host_buffers_match_device():
     assert np.array_equal(Yd.cpu().numpy(), Yh)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_plans_from_host_points_match_device(prec):
+    # host point arrays (numpy, pinned torch) are copied by the plan call; the
+    # plans then equal those made from device points, bit for bit
+    layers = [workloads.uniform_cube(3000, 3, seed=92), workloads.uniform_cube(3000, 2, seed=93)]
+    pd = [ml.ml_fastsum_plan(dev(L), 0.1, prec=prec) for L in layers]
+    ph = [ml.ml_fastsum_plan(L.copy(), 0.1, prec=prec) for L in layers]
+    pm = ml.ml_fastsum_plan_many([torch.as_tensor(L).pin_memory() for L in layers], [0.1, 0.1], prec=prec)
+    v = dev(np.random.default_rng(12).uniform(0, 1, (3000, 2)))
+    ref = torch.empty_like(v)
+    ml.ml_fastsum_apply(pd, v, ref, mode="normalized")
+    for plans in (ph, pm):
+        got = torch.empty_like(v)
+        ml.ml_fastsum_apply(plans, v, got, mode="normalized")
+        assert torch.equal(got, ref)
+        for a, b in zip(plans, pd):
+            assert np.array_equal(a.table(2), b.table(2))     # degrees
+
+
 # ------------------------------------------------------------ edge cases
 def test_two_points_closed_form():
     X = np.array([[0.0, 0.0, 0.0], [0.05, 0.0, 0.0]])
