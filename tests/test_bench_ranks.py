@@ -46,3 +46,21 @@ def test_reference_arm_other_ranks_do_nothing():
     import bench
     args = argparse.Namespace(workload="single_n2000_d3", steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, rank=1, world=2) == 0
+
+
+def test_reference_arm_line_on_the_small_workload(capsys):
+    # the oracle timed on the host cores: one JSON line with the contract's keys
+    import argparse
+    import json
+
+    import bench
+    args = argparse.Namespace(workload="single_n2000_d3", steps=1, warmup=1, gpus=1)
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 1
+    for key in ("metric", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "single_n2000_d3"
