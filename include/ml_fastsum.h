@@ -251,7 +251,7 @@ ml_status ml_fastsum_plan_many(ml_plan_t *out, const double *const *points, int6
  * ml_direct_sum_rows - the exact definition of the product on selected rows:
  * out[r] = sum_{j != rows[r]} exp(-||x_{rows[r]} - x_j||^2 / sigma^2) v_j
  * (W v of Sec. 2 / Sec. 4, direct O(nrows n) summation in FP64 on the GPU).
- * It is the judge of the fast summation's error and the product of the dense
+ * It is the reference for the fast summation's error and the product of the dense
  * regime for small graphs.
  *   points  device, n x d FP64;  v device, n FP64;  rows device, nrows int64
  *   (each in [0, n));  out device, nrows FP64.  Asynchronous on `stream`.

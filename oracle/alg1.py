@@ -12,7 +12,7 @@ non-equispaced sums they approximate; the output is real up to the term of
 the unpaired frequency -N/2, and the real part is returned.  W v then follows
 as f_RF - K(0) v (Sec. 4, W = W~ - K(0) I).
 
-Readings of what the paper leaves open (listed in the design doc as well):
+Readings of what the paper leaves open:
 
 * Domain (reading 1).  Alg. 1 wants nodes in [-1/4, 1/4]^d.  W depends only
   on ||x_i - x_j|| / sigma, so each layer is mapped by one isotropic affine

@@ -4,7 +4,7 @@ oversampling) from point-cloud statistics.
 Every number used for training comes from the method itself through the C
 ABI: `ml_fastsum_plan_ex` with the candidate parameters, `ml_fastsum_apply`
 for the product (its time measured with CUDA events) and `ml_direct_sum_rows`,
-the exact product on sampled rows, as the judge of the error.  The model is
+the exact product on sampled rows, as the measure of the error.  The model is
 the library's FP32 MLP (`ml_mlp_*`, trained on the GPU by the library's own
 kernels); `ml_fastsum_plan_learned` uses it, and falls back to the calibrated
 fixed rule of `ml_fastsum_plan` when no candidate qualifies.
@@ -140,8 +140,8 @@ def calibrate_margins(model, X, Y, quantile=0.995):
 
 
 def evaluate(model, first, count, prec, target, margin=2.0):
-    """Learned choice vs the fixed rule on unseen clouds: error (direct-sum
-    judge) and product time for both."""
+    """Learned choice vs the fixed rule on unseen clouds: error (against the
+    direct sum) and product time for both."""
     rows_out = []
     for i in range(first, first + count):
         pts, sigma, v, rows, ref = cloud(i)

@@ -14,8 +14,8 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests are skipped, not failed, where no GPU is visible; on a GPU machine a
-    # missing library is a failure (the product path never falls back).
+    # GPU tests are skipped, not failed, where no GPU is visible; where one is,
+    # a missing library is a failure (the product path never falls back).
     try:
         import torch
         has_gpu = torch.cuda.is_available()

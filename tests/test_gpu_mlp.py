@@ -88,9 +88,10 @@ def test_explicit_window_parameters(taps, over):
 
 
 def test_learned_choice_small_end_to_end():
-    # a small version of the fifth workload: train on the method's own
-    # measurements of 30 clouds, then compare with the fixed rule on 8 unseen
-    # clouds (the full-size run is reported in the design doc)
+    # a small version of the learned-parameter workload (the full run trains on
+    # 500 clouds and evaluates 200: python -m paper_2007_05239_gb300.paramnet):
+    # train on the method's own measurements of 30 clouds, then compare with
+    # the fixed rule on 8 unseen clouds
     X, Y, ids = paramnet.make_dataset(0, 30, 8, "f32", 1e-4)
     assert X.shape == (240, ml.ML_FEATURES + 3) and np.isfinite(Y).all() and ids.shape == (240,)
     fit = ids < 25
