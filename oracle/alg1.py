@@ -14,7 +14,7 @@ as f_RF - K(0) v (Sec. 4, W = W~ - K(0) I).
 
 Readings of what the paper leaves open:
 
-* Domain (reading 1).  Alg. 1 wants nodes in [-1/4, 1/4]^d.  W depends only
+* Domain (the node condition of Alg. 1 is garbled).  Alg. 1 wants nodes in [-1/4, 1/4]^d.  W depends only
   on ||x_i - x_j|| / sigma, so each layer is mapped by one isotropic affine
   map x' = s (x - c), sigma' = s sigma, with c the bounding-box centre.
   - eps_B > 0 ("ball"): s = (1/4 - eps_B/2) / max_i ||x_i - c||_2, so every
@@ -22,7 +22,7 @@ Readings of what the paper leaves open:
   - eps_B = 0 ("box"): s = a / h with h the largest bounding-box half-extent
     and a = min(1/4, 1 / (2 + (sigma/h) sqrt(ln(2d/eps_wrap)))), which keeps
     the periodisation error 2d exp(-(1-2a)^2/sigma'^2) below eps_wrap.
-* Regulariser (reading 2).  K_R is the smooth 1-periodic regularised kernel
+* Regulariser (deferred by the paper to the NFFT literature).  K_R is the smooth 1-periodic regularised kernel
   of the footnote to Sec. 4.  For eps_B = 0 it is the 1-periodisation of the
   Gaussian, K_R(y) = sum_{r in Z^d} K(y + r), which equals K up to the wrap
   error above for every difference of two nodes.  For eps_B > 0, K_R(r) = K(r) for
@@ -31,7 +31,7 @@ Readings of what the paper leaves open:
   and vanishing derivatives 1..p-1 at r = 1/2; beyond 1/2 (cube corners) it
   stays at K(1/2).
 
-* Laplacian kernel K(r) = exp(-r/sigma) (reading 16).  Its cusp at r = 0
+* Laplacian kernel K(r) = exp(-r/sigma) (named in Sec. 4).  Its cusp at r = 0
   makes the Fourier coefficients of K itself decay slowly, so (as in the
   fast summation of non-smooth radial kernels that Sec. 4 refers to) K_R is
   regularised at the origin as well: on r < eps_I it is the even polynomial
@@ -60,7 +60,7 @@ import numpy as np
 
 # ----------------------------------------------------------------- domain
 def scale_to_domain(X, sigma, eps_B=0.0, eps_wrap=1e-9):
-    """Isotropic map of one layer into the Alg. 1 domain (reading 1).
+    """Isotropic map of one layer into the Alg. 1 domain (Domain, above).
 
     Returns (Xs, sigma_s, c, s) with Xs = s (X - c) and sigma_s = s sigma.
     """
@@ -110,7 +110,7 @@ def _radial(r, sigma, kernel):
 
 def regulariser_poly(sigma, eps_B, p, kernel="gauss"):
     """Monomial coefficients q_0..q_{2p-1} of the two-point Taylor polynomial
-    in t = (r - r_I)/eps_B on [0, 1] (reading 2)."""
+    in t = (r - r_I)/eps_B on [0, 1] (Regulariser, above)."""
     rI = 0.5 - eps_B
     dK = (_gauss_derivs if kernel == "gauss" else _laplace_derivs)(rI, sigma, p)
     n = 2 * p
@@ -129,7 +129,7 @@ def regulariser_poly(sigma, eps_B, p, kernel="gauss"):
 def inner_poly(sigma, eps_I, p):
     """Coefficients c_0..c_{p-1} of the inner regulariser of the Laplacian,
     P(r) = sum_j c_j r^{2j}, with P^{(k)}(eps_I) = K^{(k)}(eps_I), k < p
-    (reading 16).  The k-th derivative of r^{2j} is (2j)!/(2j-k)! r^{2j-k}."""
+    (Laplacian kernel, above).  The k-th derivative of r^{2j} is (2j)!/(2j-k)! r^{2j-k}."""
     dK = _laplace_derivs(eps_I, sigma, p)
     A = np.zeros((p, p))
     for k in range(p):
@@ -141,8 +141,8 @@ def inner_poly(sigma, eps_I, p):
 
 
 def K_R(r, sigma, eps_B=0.0, p=0, kernel="gauss", eps_I=0.0):
-    """Regularised radial kernel of the ball domain (reading 2; reading 16 for
-    the Laplacian's inner part); the plain Gaussian when eps_B = 0 (the box
+    """Regularised radial kernel of the ball domain (Regulariser, above; the
+    Laplacian kernel, above, for its inner part); the plain Gaussian when eps_B = 0 (the box
     domain samples its periodisation instead, see kernel_samples)."""
     r = np.asarray(r, dtype=np.float64)
     K = _radial(r, sigma, kernel)
@@ -171,7 +171,7 @@ def periodised_gaussian_1d(y, sigma, images=None):
 
 # ------------------------------------------------------- Fourier coefficients
 def kernel_samples(sigma_s, N, d, eps_B=0.0, p=0, kernel="gauss", eps_I=0.0):
-    """K_R on the grid k/N, k in I_N^d (reading 2), shape (N,)*d indexed by k + N/2."""
+    """K_R on the grid k/N, k in I_N^d (Regulariser, above), shape (N,)*d indexed by k + N/2."""
     k = np.arange(-N // 2, N // 2) / N
     if eps_B <= 0 and kernel == "gauss":
         g1 = periodised_gaussian_1d(k, sigma_s)
@@ -240,7 +240,7 @@ def fastsum_W(Xs, v, b, K0=1.0):
 
 def near_field(Xs, v, sigma_s, eps_I, p):
     """f_NE(x_i) = sum_{j: ||x_i - x_j|| < eps_I} (K - K_R)(||x_i - x_j||) v_j for the
-    Laplacian, the pair j = i included (reading 16).  Direct O(n^2) sum."""
+    Laplacian, the pair j = i included (Laplacian kernel, above).  Direct O(n^2) sum."""
     Xs = np.asarray(Xs, dtype=np.float64)
     v = np.asarray(v, dtype=np.float64)
     c = inner_poly(sigma_s, eps_I, p)

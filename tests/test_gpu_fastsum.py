@@ -68,7 +68,7 @@ def test_raw_W_matches_direct_sum(name, gen, sigma, prec):
 
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_matches_alg1_oracle_tightly(d):
-    # Same bandwidth and the box-domain scaling of reading 1 on both sides;
+    # Same bandwidth and the same box-domain scaling (isotropic map) on both sides;
     # the widest window makes the NFFT error negligible.
     n = {1: 900, 2: 1200, 3: 1500}[d]
     X = workloads.uniform_cube(n, d, seed=40 + d)
