@@ -118,6 +118,37 @@ def test_power_mean_two_commuting_layers():
     assert np.allclose(lp, [math.log(2), 2 + math.log(2)], atol=1e-12)
 
 
+@pytest.mark.parametrize("p", [10.0, 2.0, 1.0, -1.0, -20.0])
+def test_power_mean_of_commuting_layers_is_the_scalar_power_mean(p):
+    # Two symmetric layers with a common eigenbasis Q and spectra a, b: the
+    # power mean (Eq. power_mean_laplacian_shifted) has the same eigenvectors
+    # and the eigenvalues ((a_i + delta)^p + (b_i + delta)^p)/2)^(1/p), delta =
+    # log(1 + |p|) for p < 0 and 0 for p > 0 (Sec. 2); p = 1 is the plain mean.
+    rng = np.random.default_rng(12)
+    Q, _ = np.linalg.qr(rng.standard_normal((7, 7)))
+    a = np.array([0.0, 0.3, 0.9, 1.4, 2.0, 0.05, 1.7])
+    b = np.array([0.0, 1.1, 0.2, 1.9, 0.5, 0.6, 1.2])
+    La, Lb = (Q * a) @ Q.T, (Q * b) @ Q.T
+    delta = math.log1p(abs(p)) if p < 0 else 0.0
+    mu = (((a + delta) ** p + (b + delta) ** p) / 2.0) ** (1.0 / p) if p != 1 else (a + b) / 2.0
+    order = np.argsort(mu)
+    k = 4
+    lam, Phi = eigen.power_mean_eigs([La, Lb], p, k)
+    ref = mu[order][:k]
+    if p == 1:
+        assert np.allclose(lam, ref, rtol=1e-10, atol=1e-12)
+    else:
+        # lambda^p is the mean of the shifted powers (well conditioned); lambda
+        # itself is checked away from 0, where the p-th root of a rounding-level
+        # eigenvalue is not (p > 0: (1e-17)^(1/p) is far from 0)
+        scale = np.abs(ref ** p).max()
+        assert np.allclose(lam ** p, ref ** p, rtol=1e-10, atol=1e-14 * scale)
+        big = ref > 1e-3
+        assert np.allclose(lam[big], ref[big], rtol=1e-10)
+    for i in range(k):
+        assert abs(abs(Phi[:, i] @ Q[:, order[i]]) - 1.0) <= 1e-8
+
+
 # ------------------------------------------------------------------ Alg. 1
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_bhat_box_matches_poisson(d):
