@@ -460,3 +460,35 @@ def test_sbm_example_of_the_paper():
             assert err >= 0.5 * paper, (case, p, err, paper)
     good = max(got[("noisy", 1.0)], got[("noisy", -20.0)], got[("noisy", -30.0)])
     assert got[("noisy", 10.0)] >= 5.0 * good + 10.0, got
+
+
+# ------------------------------------------------------ comparison helpers
+def test_subspace_angle_known_angles():
+    # the GPU parity tests bound eigenvector errors by this angle, so it is
+    # pinned on subspaces with known principal angles
+    rng = np.random.default_rng(21)
+    Q, _ = np.linalg.qr(rng.standard_normal((9, 9)))
+    for theta in (0.0, 1e-7, 0.3, 1.2):
+        u = Q[:, 0]
+        v = math.cos(theta) * Q[:, 0] + math.sin(theta) * Q[:, 1]
+        assert abs(eigen.subspace_angle(u[:, None], v[:, None]) - theta) <= 1e-9
+        # sign and scale of the basis do not matter
+        assert abs(eigen.subspace_angle(u[:, None], -3.0 * v[:, None]) - theta) <= 1e-9
+    # two planes: principal angles 0.2 and 0.7; the largest is reported
+    U = Q[:, :2]
+    V = np.stack([math.cos(0.2) * Q[:, 0] + math.sin(0.2) * Q[:, 2],
+                  math.cos(0.7) * Q[:, 1] + math.sin(0.7) * Q[:, 3]], axis=1)
+    assert abs(eigen.subspace_angle(U, V) - 0.7) <= 1e-9
+    # a rotation inside the same plane is angle 0
+    R = np.array([[math.cos(0.4), -math.sin(0.4)], [math.sin(0.4), math.cos(0.4)]])
+    assert eigen.subspace_angle(U, U @ R) <= 1e-7
+
+
+def test_eigen_groups_and_sign_convention():
+    lam = np.array([0.0, 0.5, 0.5 + 1e-9, 0.5 + 2e-9, 1.0, 2.0 - 1e-8, 2.0])
+    assert eigen.eigen_groups(lam, rel_gap=1e-6) == [[0], [1, 2, 3], [4], [5, 6]]
+    assert eigen.eigen_groups(lam, rel_gap=1e-12) == [[i] for i in range(7)]
+    Phi = np.array([[0.1, -0.9], [-0.8, 0.2], [0.3, 0.1]])
+    F = eigen.fix_signs(Phi)
+    assert np.array_equal(F[:, 0], -Phi[:, 0]) and np.array_equal(F[:, 1], -Phi[:, 1])
+    assert np.all(F[np.argmax(np.abs(F), axis=0), [0, 1]] > 0)
