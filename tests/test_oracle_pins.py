@@ -492,3 +492,21 @@ def test_eigen_groups_and_sign_convention():
     F = eigen.fix_signs(Phi)
     assert np.array_equal(F[:, 0], -Phi[:, 0]) and np.array_equal(F[:, 1], -Phi[:, 1])
     assert np.all(F[np.argmax(np.abs(F), axis=0), [0, 1]] > 0)
+
+
+def test_oracle_reproduces_stored_values():
+    # values written by tests/golden/make_oracle_golden.py from the oracle alone;
+    # a change to the oracle's arithmetic shows here first
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_single_n2000_d3.txt")
+    stored = {"eigenvalue": {}, "degree": {}}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                kind, i, v = line.split()
+                stored[kind][int(i)] = float(v)
+    X = workloads.uniform_cube(2000, 3, seed=1)
+    lam, _ = eigen.lsym_eigs(X, 0.1, 10)
+    deg = graph.degrees(X, 0.1)[:16]
+    assert np.allclose(lam, [stored["eigenvalue"][i] for i in range(10)], rtol=0, atol=1e-12)
+    assert np.allclose(deg, [stored["degree"][j] for j in range(16)], rtol=1e-13, atol=0)
+    assert abs(stored["eigenvalue"][0]) <= 1e-12            # lambda_0 = 0 (connected graph)
