@@ -209,6 +209,38 @@ def test_alg1_against_direct_sum(d, N):
     assert err2 > 10 * err
 
 
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 24)])
+def test_alg1_ball_domain_against_direct_sum(d, N):
+    # ball domain (eps_B = 1/16, K_R = K on every pair distance): Alg. 1 with
+    # exact Fourier sums reproduces the direct sum of W v, and half the
+    # bandwidth is visibly worse
+    X = workloads.uniform_ball(400, d, radius=1.0, seed=22)
+    sigma, eps_B = 0.5, 1.0 / 16
+    Xs, ss, _, _ = alg1.scale_to_domain(X, sigma, eps_B=eps_B)
+    assert np.linalg.norm(Xs, axis=1).max() <= 0.25 - eps_B / 2 + 1e-15
+    v = np.random.default_rng(3).uniform(0, 1, X.shape[0])
+    ref = graph.W_apply(X, sigma, v)
+    err = np.abs(alg1.fastsum_W(Xs, v, alg1.bhat(ss, N, d, eps_B, 4)) - ref).max() / np.abs(v).sum()
+    err2 = np.abs(alg1.fastsum_W(Xs, v, alg1.bhat(ss, N // 2, d, eps_B, 4)) - ref).max() / np.abs(v).sum()
+    assert err <= 1e-9 and err2 >= 100 * err
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_regulariser_smoothness_sets_the_convergence_rate(p):
+    # a wide kernel (K = 0.37 at the ball's edge) makes the outer regulariser
+    # matter: K_R matches p derivatives, so its Fourier coefficients decay like
+    # N^-(p+1) and the truncation error of Alg. 1 at least like N^-p; from
+    # N = 64 to 256 it must fall by 4^p (a factor 2 of slack)
+    X = workloads.uniform_cube(400, 1, seed=22)
+    sigma, eps_B = 0.5, 1.0 / 16
+    Xs, ss, _, _ = alg1.scale_to_domain(X, sigma, eps_B=eps_B)
+    v = np.random.default_rng(3).uniform(0, 1, X.shape[0])
+    ref = graph.W_apply(X, sigma, v)
+    err = [np.abs(alg1.fastsum_W(Xs, v, alg1.bhat(ss, N, 1, eps_B, p)) - ref).max() / np.abs(v).sum()
+           for N in (64, 256)]
+    assert err[0] / err[1] >= 0.5 * 4.0 ** p, err
+
+
 def test_regulariser_matching_conditions():
     sigma, eps_B, p = 0.3, 1.0 / 16, 4
     rI = 0.5 - eps_B
