@@ -45,8 +45,9 @@ Readings of what the paper leaves open:
 Pinned by tests/test_oracle_pins.py: b_l against the closed-form Fourier
 coefficients of the periodised Gaussian (Poisson summation); the adjoint
 transform on equispaced nodes against numpy's FFT; f_RF - K(0) v against the
-direct sum within the Fourier-tail bound; the regulariser's matching
-conditions; for the Laplacian, the continuity of K_R and of its first
+direct sum within the Fourier-tail bound, also on the ball domain; the
+regulariser's matching conditions, and its smoothness setting the rate at
+which the error falls with N (at least N^-p); for the Laplacian, the continuity of K_R and of its first
 derivatives across r = eps_I by one-sided finite differences, and
 f_RF + f_NE - K(0) v against the direct sum within the kernel approximation
 error measured on the same grid.
