@@ -18,7 +18,13 @@ the Poisson-summation value of a lattice degree, the sigma -> infinity limit,
 and the invariants A D^{1/2} 1 = D^{1/2} 1, trace A = 0; for the Laplacian,
 the geometric-series degrees of an equispaced 1-d lattice, and the same
 lattice laid along a rotated line in 3-d (the Euclidean norm, not its square
-nor the l1 norm).
+nor the l1 norm).  The layer means multilayer_A_apply / multilayer_W_apply:
+two-point layers (the normalised mean swaps v exactly; the raw mean scales the
+swap by the mean weight), a three-point line plus an equilateral triangle in
+closed form, T identical layers against the single layer, invariance under the
+layer order, W 1 = the mean degrees, and the identity's image against the
+dense I - L_1 of numpy weight matrices (symmetric, zero trace, spectrum in
+[-1, 1], eigenvalues of eigen.L1_eigs).
 """
 from __future__ import annotations
 

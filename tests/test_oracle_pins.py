@@ -74,6 +74,79 @@ def test_normalised_operator_invariants():
     assert np.allclose(graph.weight_matrix(X, sigma) @ v, graph.W_apply(X, sigma, v), rtol=1e-12, atol=1e-12)
 
 
+# ------------------------------------------------------------ multilayer mean
+def test_multilayer_two_point_layers_closed_form():
+    # Every connected two-point layer has D^{-1/2} W D^{-1/2} = [[0, 1], [1, 0]]
+    # whatever its weight w_t, so the mean over layers (Eq. I-L_1) swaps the two
+    # entries of v exactly, while the raw mean (1/T) sum_t W_t scales the swap
+    # by the mean weight.  A dropped 1/T, or W summed in place of the
+    # normalised A, fails here.
+    dists, sigmas = [0.1, 0.3, 0.5], [0.2, 0.25, 0.4]
+    layers = [np.array([[0.0, 0.0], [r, 0.0]]) for r in dists]
+    v = np.array([2.0, -3.0])
+    got = graph.multilayer_A_apply(layers, sigmas, v)
+    assert np.allclose(got, [-3.0, 2.0], rtol=1e-15, atol=0)
+    wbar = np.mean([math.exp(-r * r / s ** 2) for r, s in zip(dists, sigmas)])
+    got_w = graph.multilayer_W_apply(layers, sigmas, v)
+    assert np.allclose(got_w, [-3.0 * wbar, 2.0 * wbar], rtol=1e-14, atol=0)
+
+
+def test_multilayer_three_point_layers_closed_form():
+    # Layer 1: three points on a line at 0, r, 2r: weights a = e^{-r^2/s^2}
+    # (neighbours) and c = e^{-4r^2/s^2} (ends), degrees (a + c, 2a, a + c).
+    # Layer 2: an equilateral triangle: D^{-1/2} W D^{-1/2} = (J - I)/2.
+    r, s1 = 0.2, 0.3
+    a, c = math.exp(-r * r / s1 ** 2), math.exp(-4 * r * r / s1 ** 2)
+    line = np.array([[0.0, 0.0], [r, 0.0], [2 * r, 0.0]])
+    tri = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, math.sqrt(3) / 2]])
+    x = math.sqrt(a / (2 * (a + c)))            # a / sqrt((a + c) 2a)
+    A1 = np.array([[0, x, c / (a + c)], [x, 0, x], [c / (a + c), x, 0]])
+    A2 = (np.ones((3, 3)) - np.eye(3)) / 2
+    V = np.random.default_rng(1).standard_normal((3, 2))
+    got = graph.multilayer_A_apply([line, tri], [s1, 0.7], V)
+    assert np.allclose(got, (A1 + A2) @ V / 2, rtol=1e-13, atol=1e-15)
+    w = math.exp(-1.0 / 0.49)
+    W1 = np.array([[0, a, c], [a, 0, a], [c, a, 0]])
+    W2 = w * (np.ones((3, 3)) - np.eye(3))
+    got_w = graph.multilayer_W_apply([line, tri], [s1, 0.7], V)
+    assert np.allclose(got_w, (W1 + W2) @ V / 2, rtol=1e-13, atol=1e-15)
+
+
+def test_multilayer_identical_layers_and_order():
+    # T copies of one layer give that layer's operator; the mean does not
+    # depend on the order of the layers; W applied to ones is the mean of the
+    # layers' degrees.
+    X = workloads.uniform_cube(250, 3, seed=21)
+    Y = workloads.uniform_cube(250, 2, seed=22)
+    V = np.random.default_rng(2).standard_normal((250, 3))
+    one = graph.A_apply(X, 0.12, V)
+    assert np.allclose(graph.multilayer_A_apply([X] * 4, [0.12] * 4, V), one, rtol=1e-13, atol=1e-14)
+    assert np.allclose(graph.multilayer_W_apply([X] * 3, [0.12] * 3, V), graph.W_apply(X, 0.12, V),
+                       rtol=1e-13, atol=1e-14)
+    ab = graph.multilayer_A_apply([X, Y], [0.12, 0.2], V)
+    ba = graph.multilayer_A_apply([Y, X], [0.2, 0.12], V)
+    assert np.allclose(ab, ba, rtol=1e-14, atol=1e-15)
+    dmean = graph.multilayer_W_apply([X, Y], [0.12, 0.2], np.ones(250))
+    assert np.allclose(dmean, (graph.degrees(X, 0.12) + graph.degrees(Y, 0.2)) / 2, rtol=1e-14)
+
+
+def test_multilayer_mean_matches_dense_L1():
+    # The product with the identity is the dense I - L_1 (numpy weight matrices,
+    # a code path separate from the C direct sum); its spectrum is that of
+    # eigen.L1_eigs; it is symmetric with zero trace (no self-edges), and every
+    # eigenvalue of I - L_1 lies in [-1, 1] (each layer's lies there).
+    X = workloads.uniform_cube(120, 3, seed=23)
+    Y = workloads.uniform_cube(120, 1, seed=24)
+    M = np.hstack([graph.multilayer_A_apply([X, Y], [0.1, 0.05], E) for E in np.split(np.eye(120), 8, axis=1)])
+    dense = (2 * np.eye(120) - graph.L_sym_dense(X, 0.1) - graph.L_sym_dense(Y, 0.05)) / 2
+    assert np.abs(M - dense).max() <= 1e-13
+    assert np.abs(M - M.T).max() <= 1e-14 and abs(np.trace(M)) <= 1e-12
+    theta = np.linalg.eigvalsh(0.5 * (M + M.T))
+    assert theta.min() >= -1 - 1e-12 and theta.max() <= 1 + 1e-12
+    lam, _ = eigen.L1_eigs([X, Y], [0.1, 0.05], 8)
+    assert np.allclose(np.sort(1 - theta)[:8], lam, atol=1e-12)
+
+
 def test_spectrum_bounds_and_null_vector():
     X = workloads.uniform_cube(200, 3, seed=3)
     sigma = 0.1
