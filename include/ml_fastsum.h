@@ -364,7 +364,10 @@ ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int 
  *   - kernel timing (ml_profile_enable) is not recorded for these calls.
  * Set-up: the first call on each device looks the array's device address up
  * with cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.
+ * before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys the
+ * device's primary context) do not call this entry point again in that
+ * process.
  * Sharing: every call uses the same array and leaves its contents behind; the
  * kernels overwrite every scratch value before reading it, so nothing needs
  * clearing, but calls whose executions overlap on the GPU (other streams,
@@ -513,6 +516,24 @@ ml_status ml_plan_copy_table(ml_plan_t plan, int which, double *out, int64_t cou
 ml_status ml_profile_enable(int on);
 ml_status ml_profile_reset(void);
 ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *ms);
+/*
+ * ml_measure_peak - measured throughput of one GPU resource, the denominator
+ * of a roofline fraction (measurement aid; the paper has no counterpart).
+ * Runs a micro-kernel on the current device, 8 CTAs of 256 threads per SM,
+ * one untimed and three timed launches on `stream` (CUDA events), and
+ * returns the best of the three:
+ *   what = 0   FP32 FMA pipe: 8 independent fmaf chains per thread, in
+ *              TFLOP/s (2 flop per FMA);
+ *   what = 1   FP64 FMA pipe, the same with doubles, in TFLOP/s;
+ *   what = 2   32-bit integer shared-memory atomic adds on conflict-free
+ *              addresses (one wavefront per warp instruction), in 1e12
+ *              atomics per second.
+ *   rate       host, receives the figure.
+ * Synchronises `stream`.  Errors: ML_ERR_ARG (what out of range, rate
+ * NULL), ML_ERR_OOM, ML_ERR_CUDA.
+ */
+ml_status ml_measure_peak(int what, double *rate, void *stream);
+
 /* CUDA-graph replays of captured inner solver iterations since the library
  * was loaded (diagnostics: 0 means every iteration launched eagerly). */
 int64_t ml_graph_replays(void);

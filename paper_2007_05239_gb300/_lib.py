@@ -33,7 +33,7 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers", "ml_allen_cahn",
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
-           "ml_profile_reset", "ml_profile_read", "ml_graph_replays"]
+           "ml_profile_reset", "ml_profile_read", "ml_graph_replays", "ml_measure_peak"]
 
 
 class MLError(RuntimeError):
@@ -155,6 +155,8 @@ def load():
     lib.ml_mlp_destroy.argtypes = [P]
     lib.ml_graph_replays.restype = ctypes.c_int64
     lib.ml_graph_replays.argtypes = []
+    lib.ml_measure_peak.restype = ctypes.c_int
+    lib.ml_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     lib.ml_profile_enable.restype = ctypes.c_int
     lib.ml_profile_enable.argtypes = [ctypes.c_int]
     lib.ml_profile_reset.restype = ctypes.c_int
@@ -517,6 +519,17 @@ def ml_allen_cahn(Phi, lam, labels, m, eps=0.005, omega0=1000.0, c=0.0, dt=0.01,
 def ml_graph_replays():
     """CUDA-graph replays of captured solver iterations since the library was loaded."""
     return int(load().ml_graph_replays())
+
+
+PEAKS = {"fp32": 0, "fp64": 1, "smem_atomic": 2}
+
+
+def ml_measure_peak(what, stream=None):
+    """Measured throughput of one resource: "fp32" / "fp64" FMA pipes in
+    TFLOP/s, "smem_atomic" conflict-free 32-bit shared atomics in 1e12/s."""
+    rate = ctypes.c_double()
+    _check(load().ml_measure_peak(PEAKS[what], ctypes.byref(rate), _stream(stream)))
+    return rate.value
 
 
 def ml_profile_enable(on=True):

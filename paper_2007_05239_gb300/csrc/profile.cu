@@ -1,6 +1,7 @@
 // Kernel timing registry: CUDA events around each launch on its stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -114,3 +115,96 @@ ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *m
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ peaks
+// Throughput micro-kernels for the roofline denominators: independent FMA
+// chains on the FP32 or FP64 pipe, and conflict-free 32-bit shared-memory
+// atomic adds (lane l of a warp adds to word l of the warp's own 32-word
+// row, so every atomic instruction is one wavefront).
+namespace ml {
+namespace {
+constexpr int kPeakChains = 8;
+constexpr int kPeakUnroll = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T *sink, int iters, T a, T b)
+{
+    T x[kPeakChains];
+#pragma unroll
+    for (int i = 0; i < kPeakChains; ++i) x[i] = (T)(threadIdx.x + 1) * (T)(i + 1) * (T)1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kPeakUnroll; ++k) {
+#pragma unroll
+            for (int i = 0; i < kPeakChains; ++i) x[i] = fma(x[i], a, b);
+        }
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < kPeakChains; ++i) s += x[i];
+    if (s == (T)-1.0) sink[blockIdx.x] = s;   // never true for these inputs; keeps the chains live
+}
+
+__global__ void __launch_bounds__(256) k_atomic_peak(int *sink, int iters)
+{
+    __shared__ int s[256];
+    s[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, row = threadIdx.x & ~31;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kPeakUnroll; ++k) atomicAdd(&s[row + ((lane + k) & 31)], it + k);
+    }
+    __syncthreads();
+    if (s[threadIdx.x] == 0x7fffffff) sink[blockIdx.x] = 1;
+}
+}  // namespace
+
+static ml_status time_peak(int what, double *rate, cudaStream_t st)
+{
+    const int sms = sm_count();
+    const int blocks = sms * 8, threads = 256;
+    DevBuf sink;
+    ML_TRY(sink.ensure((size_t)blocks * sizeof(double)));
+    cudaEvent_t e0, e1;
+    ML_CUDA(cudaEventCreate(&e0));
+    ML_CUDA(cudaEventCreate(&e1));
+    const int iters = what == 0 ? 4096 : (what == 1 ? 96 : 2048);
+    double best = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {   // first launch untimed (warm-up)
+        cudaEventRecord(e0, st);
+        if (what == 0)
+            k_fma_peak<float><<<blocks, threads, 0, st>>>(sink.as<float>(), iters, 0.9999f, 1e-4f);
+        else if (what == 1)
+            k_fma_peak<double><<<blocks, threads, 0, st>>>(sink.as<double>(), iters, 0.9999, 1e-4);
+        else
+            k_atomic_peak<<<blocks, threads, 0, st>>>(sink.as<int>(), iters);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "peak micro-kernel", __FILE__, __LINE__);
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double ops = (double)blocks * threads * iters * kPeakUnroll * (what == 2 ? 1 : kPeakChains);
+        // FMA: 2 flop each, in TFLOP/s; atomics: in 1e12 per second
+        const double r = ops * (what == 2 ? 1.0 : 2.0) / (ms * 1e-3) / 1e12;
+        if (rep > 0) best = std::max(best, r);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ML_CUDA(cudaGetLastError());
+    *rate = best;
+    return ML_OK;
+}
+
+}  // namespace ml
+
+extern "C" ml_status ml_measure_peak(int what, double *rate, void *stream)
+{
+    if (what < 0 || what > 2 || !rate) return ml::fail(ML_ERR_ARG, "what must be 0, 1 or 2 and rate non-null");
+    ml::NoProfileScope no_events;
+    return ml::time_peak(what, rate, (cudaStream_t)stream);
+}
