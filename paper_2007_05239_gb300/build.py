@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import subprocess
 import sys
 
@@ -54,8 +55,24 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
+def _stamp(extra):
+    """Objects are reused only when built on the same machine type with the
+    same flags; anything else (e.g. a copy of the tree moved to another
+    architecture) rebuilds everything."""
+    return f"{platform.machine()} {' '.join(ARCH)} {' '.join(extra)}\n"
+
+
 def build(verbose: bool = False, extra=()):
     os.makedirs(OUT, exist_ok=True)
+    stamp_path = os.path.join(OUT, "STAMP")
+    want = _stamp(list(extra))
+    have = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    if have != want:
+        for f in os.listdir(OUT):
+            if f.endswith(".o"):
+                os.remove(os.path.join(OUT, f))
+        if os.path.exists(LIB):
+            os.remove(LIB)
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
     objs = [o for o, _ in results]
@@ -68,6 +85,8 @@ def build(verbose: bool = False, extra=()):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    with open(stamp_path, "w") as f:
+        f.write(want)
     return LIB
 
 

@@ -324,7 +324,7 @@ extern "C" ml_status ml_allen_cahn(const double *Phi, const double *lambda, int6
     const double c = prm->c > 0 ? prm->c : prm->omega0 + 3.0 / prm->eps;
     cudaStream_t st = (cudaStream_t)stream;
     const int KM = k * m;
-    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kAcWarps * 32 - 1) / (kAcWarps * 32), 152 * 8));
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kAcWarps * 32 - 1) / (kAcWarps * 32), sm_count() * 8));
     DevBuf Ub, partV, partC, Vd, dinv, scal;
     ML_TRY(Ub.ensure((size_t)n * m * sizeof(double)));
     ML_TRY(partV.ensure((size_t)nblk * KM * sizeof(double)));
@@ -334,7 +334,7 @@ extern "C" ml_status ml_allen_cahn(const double *Phi, const double *lambda, int6
     ML_TRY(scal.ensure(4 * sizeof(double)));
     {
         ML_CUDA(cudaMemsetAsync(scal.p, 0, sizeof(int), st));
-        k_ac_labels_ok<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(labels, n, m, scal.as<int>());
+        k_ac_labels_ok<<<(int)std::min<int64_t>((n + 255) / 256, sm_count() * 8), 256, 0, st>>>(labels, n, m, scal.as<int>());
         int bad = 0;
         ML_CUDA(cudaMemcpyAsync(&bad, scal.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         ML_CUDA(cudaStreamSynchronize(st));
@@ -347,7 +347,7 @@ extern "C" ml_status ml_allen_cahn(const double *Phi, const double *lambda, int6
     double *buf[2] = {U, Ub.as<double>()};
     {
         ProfScope pr("allen_cahn", st);
-        k_ac_init<<<(int)std::min<int64_t>((n * m + 255) / 256, 152 * 16), 256, 0, st>>>(labels, n, m, buf[0]);
+        k_ac_init<<<(int)std::min<int64_t>((n * m + 255) / 256, sm_count() * 16), 256, 0, st>>>(labels, n, m, buf[0]);
     }
     ML_CUDA(cudaGetLastError());
     AcArgs a;
@@ -433,7 +433,7 @@ extern "C" ml_status ml_allen_cahn(const double *Phi, const double *lambda, int6
         ML_CUDA(cudaMemcpyAsync(U, buf[1], (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (pred) {
         ProfScope pr("allen_cahn", st);
-        k_ac_predict<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(U, n, m, pred);
+        k_ac_predict<<<(int)std::min<int64_t>((n + 255) / 256, sm_count() * 16), 256, 0, st>>>(U, n, m, pred);
     }
     ML_CUDA(cudaGetLastError());
     ML_CUDA(cudaStreamSynchronize(st));

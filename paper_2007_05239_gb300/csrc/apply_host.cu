@@ -181,7 +181,7 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             double *Yt = per_layer ? Y + (int64_t)t * n : Y;
             const double alpha = per_layer ? 1.0 : 1.0 / T;
             const int acc = (!per_layer && t > 0) ? 1 : 0;
-            const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+            const int blocks = (int)std::min<int64_t>((n + 255) / 256, sm_count() * 16);
             ProfScope pr("degree_out", st);
             k_degree_out<<<blocks, 256, 0, st>>>(layers[t]->deg.as<double>(), layers[t]->perm.as<int>(), n, alpha,
                                                  acc, Yt);
@@ -248,7 +248,7 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
             ML_CUDA(cudaStreamWaitEvent(st, ls->join[t], 0));
         }
         ProfScope pr("vector", st);
-        k_sum_layers<<<(int)std::min<int64_t>((n * b + 255) / 256, 152 * 16), 256, 0, st>>>(parts, T, n, b, Y, b);
+        k_sum_layers<<<(int)std::min<int64_t>((n * b + 255) / 256, sm_count() * 16), 256, 0, st>>>(parts, T, n, b, Y, b);
         ML_CUDA(cudaGetLastError());
         return ML_OK;
     }

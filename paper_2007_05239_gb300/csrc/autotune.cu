@@ -128,7 +128,7 @@ extern "C" ml_status ml_fastsum_plan_autotune(ml_plan_t *out, const double *poin
     DevBuf X, Y;
     ML_TRY(X.ensure((size_t)n * nv * sizeof(double)));
     ML_TRY(Y.ensure((size_t)n * nv * sizeof(double)));
-    k_tune_fill<<<(int)std::min<int64_t>((n * nv + 255) / 256, 152 * 16), 256, 0, st>>>(X.as<double>(), n * nv);
+    k_tune_fill<<<(int)std::min<int64_t>((n * nv + 255) / 256, sm_count() * 16), 256, 0, st>>>(X.as<double>(), n * nv);
     ML_CUDA(cudaGetLastError());
     float best_ms = 0.0f;
     ml_status s = time_plan(base, X.as<double>(), Y.as<double>(), nv, st, &best_ms);

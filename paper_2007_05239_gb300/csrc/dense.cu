@@ -135,13 +135,13 @@ __global__ void k_iota(int64_t n, int *perm)
         perm[i] = (int)i;
 }
 
-int blocks_for(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16)); }
+int blocks_for(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, sm_count() * 16)); }
 
 template <typename T, int NV>
 ml_status launch_dense(const DenseArgs &a, cudaStream_t st)
 {
     const int rows_per_cta = 8;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + rows_per_cta - 1) / rows_per_cta, 152 * 32));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + rows_per_cta - 1) / rows_per_cta, sm_count() * 32));
     ProfScope pr("dense", st);
     k_dense_apply<T, NV><<<grid, 256, 0, st>>>(a);
     ML_CUDA(cudaGetLastError());

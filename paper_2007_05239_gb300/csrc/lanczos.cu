@@ -267,7 +267,7 @@ __global__ void k_scale_cols(double *V, int64_t ldv, int64_t n, int k, const dou
         for (int c = 0; c < k; ++c) V[(int64_t)c * ldv + r] *= f[c];
 }
 
-static int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+static int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8)); }
 
 struct Workspace {
     cudaStream_t st = nullptr;
@@ -951,7 +951,11 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
             }
             ML_CUDA(cudaStreamSynchronize(st));
             if (nconv_out) *nconv_out = std::min(nconv, k);
-            return nconv >= k ? ML_OK : ML_WARN_NOT_CONVERGED;
+            if (nconv >= k) return ML_OK;
+            set_error("Lanczos stopped after " + std::to_string(matvecs) + " operator applications (maxit " +
+                      std::to_string(maxit) + ") with " + std::to_string(nconv) + " of " + std::to_string(k) +
+                      " pairs converged");
+            return ML_WARN_NOT_CONVERGED;
         }
         // thick restart: Q[:, 0:kk] = Ritz vectors, Q[:, kk] = last residual direction
         kk = keep;

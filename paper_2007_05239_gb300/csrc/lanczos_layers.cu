@@ -328,7 +328,7 @@ struct Solver {
         nslots = (int)lay.size();
         ML_CUDA(cudaMemcpyAsync(layd.p, lay.data(), lay.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         ML_CUDA(cudaStreamSynchronize(st));   // lay is host memory that changes later
-        nbx = (int)std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, (152 * 8 + nslots - 1) / nslots));
+        nbx = (int)std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, (sm_count() * 8 + nslots - 1) / nslots));
         return ML_OK;
     }
 
@@ -479,7 +479,7 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
     const int ldq = S.ldq;
     for (int w = 0; w < 2; ++w) ML_TRY(S.Q[w].ensure((size_t)T * n * ldq * sizeof(double)));
     ML_TRY(S.Wb.ensure((size_t)T * n * b * sizeof(double)));
-    const int64_t nbx_max = std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, 152 * 8));
+    const int64_t nbx_max = std::max<int64_t>(1, std::min<int64_t>((n + kRows - 1) / kRows, sm_count() * 8));
     ML_TRY(S.part.ensure((size_t)T * nbx_max * kGramOut * sizeof(double) + 64));
     ML_TRY(S.hcur.ensure((size_t)T * ldq * b * sizeof(double)));
     ML_TRY(S.Gs.ensure((size_t)T * b * b * sizeof(double)));
@@ -606,7 +606,7 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
                 double *out = evecs_dev + (int64_t)t * n * k;
                 {
                     ProfScope pr("vector", st);
-                    k_lcolmajor<<<(int)std::min<int64_t>((n * k + 255) / 256, 152 * 16), 256, 0, st>>>(S.q(cur ^ 1), t,
+                    k_lcolmajor<<<(int)std::min<int64_t>((n * k + 255) / 256, sm_count() * 16), 256, 0, st>>>(S.q(cur ^ 1), t,
                                                                                                       k, n, out);
                 }
                 ML_CUDA(cudaGetLastError());
@@ -644,7 +644,13 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
         if (nconv_out) nconv_out[t] = std::min(nconv[t], k);
         if (nconv[t] < k) all = 0;
     }
-    return all ? ML_OK : ML_WARN_NOT_CONVERGED;
+    if (all) return ML_OK;
+    std::string msg = "block Lanczos stopped at maxit " + std::to_string(maxit) + " with fewer than " +
+                      std::to_string(k) + " converged pairs on layer(s)";
+    for (int t = 0; t < T; ++t)
+        if (nconv[t] < k) msg += " " + std::to_string(t) + " (" + std::to_string(nconv[t]) + ")";
+    set_error(msg);
+    return ML_WARN_NOT_CONVERGED;
 }
 
 }  // namespace ml

@@ -451,7 +451,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         } else {
             // enough CTAs to fill the GPU: split the layers into groups whose
             // partial sums are added in a fixed order afterwards
-            const int G = std::max(1, std::min(T, (152 * 6 + max_nsub - 1) / max_nsub));
+            const int G = std::max(1, std::min(T, (sm_count() * 6 + max_nsub - 1) / max_nsub));
             const int LG = (T + G - 1) / G;
             const int Gu = (T + LG - 1) / LG;
             const int64_t n = p0->n;
@@ -465,7 +465,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
                                                                              T, LG, part, n);
             if (Gu > 1) {
                 ML_CUDA(cudaGetLastError());
-                const int blocks = (int)std::min<int64_t>((n * NV + 255) / 256, 152 * 16);
+                const int blocks = (int)std::min<int64_t>((n * NV + 255) / 256, sm_count() * 16);
                 k_sum_parts<NV><<<blocks, 256, 0, st>>>(part, Gu, n, v.Y, v.ldy);
             }
         }

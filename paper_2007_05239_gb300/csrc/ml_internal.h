@@ -37,6 +37,10 @@ constexpr int kSubPoints = 1024; // points per subproblem (bounds per-cell count
 constexpr int kBatchPtsTotal = 1024; // points per CTA of the batched interpolation (4 per thread)
 constexpr int kGroupSubs = 64;   // most subproblem tiles summed per group before the fold
 
+// Streaming multiprocessors of the current device (queried once per device and
+// cached): grid-stride launches size their grids as a multiple of it.
+int sm_count();
+
 // ------------------------------------------------------------ device buffer
 // Owns one device allocation (freed on destruction; movable, not copyable).
 struct DevBuf {

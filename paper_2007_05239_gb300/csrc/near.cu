@@ -127,7 +127,7 @@ __global__ void k_cos_axis(const double *__restrict__ in, double *__restrict__ o
     }
 }
 
-static int blocks_for(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 32)); }
+static int blocks_for(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, sm_count() * 32)); }
 
 ml_status laplace_fourier(ml_plan_s *p, const LaplaceReg &g, cudaStream_t st)
 {

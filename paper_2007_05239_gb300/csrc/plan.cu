@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,27 @@ ml_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
              cudaGetErrorString(e), what, file, line);
     g_err = buf;
     return e == cudaErrorMemoryAllocation ? ML_ERR_OOM : ML_ERR_CUDA;
+}
+
+int sm_count()
+{
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;
+    }
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (c <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            return 1;
+        }
+        cached[dev].store(v, std::memory_order_relaxed);   // every writer stores the same value
+        c = v;
+    }
+    return c;
 }
 
 ml_status DevBuf::ensure(size_t nbytes)
@@ -387,7 +409,7 @@ ml_status bounding_box(const double *points, int64_t n, int d, cudaStream_t st, 
 static int grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 16));
 }
 
 // ---------------------------------------------------------- parameters
