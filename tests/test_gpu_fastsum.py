@@ -30,6 +30,20 @@ def rel2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+def check_errors(got, ref, v, tol, what=""):
+    """The relative 2-norm error E2 and two element-wise measures, each within
+    the form's target: E_inf = ||y - y*||_inf / (K(0) ||v||_1) (the usual
+    fast-summation measure, K(0) = 1) and the largest entry error relative to
+    the largest entry, max |y - y*| / max |y*|.  A localised error on a few
+    entries that the 2-norm averages away fails the element-wise gates."""
+    got, ref, v = np.asarray(got), np.asarray(ref), np.asarray(v)
+    e2 = rel2(got, ref)
+    err = np.abs(got - ref)
+    einf = float(err.max() / np.abs(v).sum())
+    emax = float(err.max() / np.abs(ref).max())
+    assert e2 <= tol and einf <= tol and emax <= tol, f"{what}: E2 {e2:.3e} E_inf {einf:.3e} Emax {emax:.3e}"
+
+
 def clustered(n, d, seed, k=5, spread=0.02):
     rng = np.random.default_rng(seed)
     mu = rng.uniform(0, 1, size=(k, d))
@@ -62,8 +76,7 @@ def test_raw_W_matches_direct_sum(name, gen, sigma, prec):
     for v in (np.ones(X.shape[0]), rng.uniform(0, 1, X.shape[0])):
         got, plan = W_gpu(X, sigma, v, prec)
         ref = graph.W_apply(X, sigma, v)
-        e = rel2(got, ref)
-        assert e <= TOL[prec], f"{name} {prec}: E2={e:.3e} info={plan.info}"
+        check_errors(got, ref, v, TOL[prec], f"{name} {prec} {plan.info}")
 
 
 @pytest.mark.parametrize("d", [1, 2, 3])
@@ -119,11 +132,11 @@ def test_degrees_and_normalised_multilayer(prec):
     Y = torch.empty(n, 1, dtype=torch.float64, device="cuda")
     ml.ml_fastsum_apply(plans, dev(v[:, None]), Y, mode="normalized")
     ref = graph.multilayer_A_apply(layers, sig, v)
-    assert rel2(Y.cpu().numpy()[:, 0], ref) <= TOL[prec]
+    check_errors(Y.cpu().numpy()[:, 0], ref, v, TOL[prec], "normalised")
     # degree mode = mean degree
     ml.ml_fastsum_apply(plans, None, Y, mode="degree")
     ref = sum(graph.degrees(L, s) for L, s in zip(layers, sig)) / 3
-    assert rel2(Y.cpu().numpy()[:, 0], ref) <= TOL[prec]
+    check_errors(Y.cpu().numpy()[:, 0], ref, np.ones(n), TOL[prec], "degrees")
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

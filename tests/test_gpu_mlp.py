@@ -120,3 +120,21 @@ def test_per_factor_margins_exclude_cut_bandwidths():
     assert chosen[0] in (0.0, 1.0)
     with pytest.raises(ml.MLError):
         m.set_margins([1.0, 2.0])
+
+
+def test_learned_choice_gains_over_fixed_rule():
+    # what the trained network gains: trained on the method's own error and
+    # time measurements of 200 clouds (10 candidates each, 10 % of the clouds
+    # held out to calibrate one error margin per bandwidth factor), then on 24
+    # unseen clouds every learned choice must meet the 1e-4 target (judged by
+    # the direct sum on sampled rows) and the products must be faster than
+    # with the fixed rule (geometric mean of the time ratios below 1)
+    X, Y, ids = paramnet.make_dataset(0, 200, 10, "f32", 1e-4)
+    fit = ids < 180
+    model, losses, _ = paramnet.train(X[fit], Y[fit], epochs=3000)
+    margins = paramnet.calibrate_margins(model, X[~fit], Y[~fit], 0.995)
+    model.set_margins(margins)
+    ev = paramnet.evaluate(model, 6000, 24, "f32", 1e-4, margin=max(margins))
+    assert ev["success_fixed"] == 1.0
+    assert ev["success_learned"] == 1.0, [c["learned"] for c in ev["clouds"] if c["learned"]["E2"] > 1e-4]
+    assert ev["time_ratio_geomean"] < 1.0, ev["time_ratio_geomean"]

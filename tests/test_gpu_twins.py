@@ -1,0 +1,189 @@
+"""Reduced-size twins of the three large workloads: the same generators
+(image with Voronoi regions, 12-component mixture in 52 two-band layers,
+image with discs) at n = 2000-4000, each with its workload's eigenproblem
+(power mean p, k, block), on the GPU through the C ABI against the oracle's
+dense eigensolves.
+
+Bars: in the FP64 form at a product target of 1e-12, eigenvalues within 1e-8
+and eigenvector (or near-degenerate subspace) angles within 1e-6.  At the
+forms' own product targets (FP64 form 1e-6, FP32 form 1e-4), an operator
+error ||E||_2 moves each eigenvalue of the symmetric operator by at most
+||E||_2 (Weyl), and a relative product error eps over the normalised
+operator (norm 1) gives ||E||_2 of order eps; the eigenvalues are held to
+10 eps (p = 1, per layer).  For p = -1 the eigenvalues lambda = 1/mu of
+L_{-1,delta} move by |d lambda| = lambda^2 |d mu|, mu the eigenvalue of the
+mean of inverses (||(L + delta I)^{-1}|| <= 1/delta): the bound is
+10 eps lambda^2 / delta^2.
+
+Also the solvers' failure and restart paths: the iteration limit
+(ML_WARN_NOT_CONVERGED with the best Ritz pairs) and the complete graph,
+whose Krylov spaces are invariant after two steps, forcing the single-vector
+solver's restart with fresh random directions (the block solver deflates
+instead and reports that it did not converge).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import eigen, graph
+from paper_2007_05239_gb300 import _lib as ml
+from paper_2007_05239_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def check_pairs(lam, V, lam_ref, V_ref, k, tol_val=1e-8, tol_ang=1e-6):
+    assert np.abs(lam - lam_ref[:k]).max() <= tol_val, (lam, lam_ref[:k])
+    for g in eigen.eigen_groups(lam_ref, rel_gap=1e-6):
+        if max(g) >= k:
+            continue
+        ang = eigen.subspace_angle(V[:, g], V_ref[:, g])
+        assert ang <= tol_ang, (g, ang)
+
+
+# ------------------------------------------------------------ image, p = -1
+@pytest.fixture(scope="module")
+def voronoi_twin():
+    layers = workloads.image_voronoi_layers(50, 50, 8, 0.02, seed=2)
+    sig = [0.2] * 3
+    lam_ref, V_ref = eigen.Lp_eigs(layers, sig, -1.0, 23)
+    return layers, sig, lam_ref, V_ref
+
+
+def test_image_voronoi_twin_p_minus_one_k20(voronoi_twin):
+    layers, sig, lam_ref, V_ref = voronoi_twin
+    n, k = layers[0].shape[0], 20
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    V = torch.empty(n * k, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=-1.0, tol=1e-11, seed=1, evecs=V)
+    assert st == ml.ML_OK and nconv == k
+    check_pairs(lam, V.cpu().numpy().reshape(k, n).T, lam_ref, V_ref, k)
+    assert lam[0] >= math.log(2.0) - 1e-10
+
+
+def test_image_voronoi_twin_at_the_forms_target(voronoi_twin):
+    # the bench's setting: FP64 form at 1e-6, tol 1e-8
+    layers, sig, lam_ref, _ = voronoi_twin
+    k, eps, delta = 20, 1e-6, math.log(2.0)
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=eps) for L, s in zip(layers, sig)]
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=-1.0, tol=1e-8, seed=1)
+    assert st == ml.ML_OK and nconv == k
+    bound = 10 * eps * lam_ref[:k] ** 2 / delta ** 2
+    assert (np.abs(lam - lam_ref[:k]) <= bound).all(), np.abs(lam - lam_ref[:k]) / bound
+
+
+# ------------------------------------------------------------ mixture, per layer
+CHECK_LAYERS = [0, 13, 26, 51]
+
+
+@pytest.fixture(scope="module")
+def gmm_twin():
+    layers, _ = workloads.gmm_band_layers(2000, 104, 12, seed=3)
+    sig = [0.5 * float((L.max(0) - L.min(0)).max()) for L in layers]
+    refs = {t: eigen.lsym_eigs(layers[t], sig[t], 13) for t in CHECK_LAYERS}
+    return layers, sig, refs
+
+
+def test_gmm_twin_per_layer_k10_block8_fp64(gmm_twin):
+    layers, sig, refs = gmm_twin
+    n, k, T = 2000, 10, len(layers)
+    assert T == 52
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    V = torch.empty(T * n * k, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=8, tol=1e-11, seed=5, evecs=V)
+    assert st == ml.ML_OK and (nconv == k).all()
+    V = V.cpu().numpy().reshape(T, k, n)
+    for t in CHECK_LAYERS:
+        lam_ref, V_ref = refs[t]
+        check_pairs(lam[t], V[t].T, lam_ref, V_ref, k)
+    # every layer: lambda_0 = 0 (one connected component) and the spectrum in [0, 2]
+    assert np.abs(lam[:, 0]).max() <= 1e-9 and (lam <= 2).all()
+
+
+def test_gmm_twin_per_layer_fp32_form(gmm_twin):
+    # the bench's setting: all 52 FP32 layers batched, target 1e-4
+    layers, sig, refs = gmm_twin
+    n, k, T, eps = 2000, 10, len(layers), 1e-4
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f32", target_rel_err=eps) for L, s in zip(layers, sig)]
+    V = np.empty(T * n * k)
+    lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=8, tol=1e-8, seed=5, evecs=V)
+    assert st == ml.ML_OK and (nconv == k).all()
+    for t in CHECK_LAYERS:
+        assert np.abs(lam[t] - refs[t][0][:k]).max() <= 10 * eps, (t, lam[t], refs[t][0][:k])
+    V = V.reshape(T, k, n)
+    for t in CHECK_LAYERS:
+        assert np.abs(V[t] @ V[t].T - np.eye(k)).max() <= 1e-10
+
+
+# ------------------------------------------------------------ discs, p = 1
+@pytest.fixture(scope="module")
+def discs_twin():
+    layers = workloads.image_discs_layers(50, 80, 5, 0.02, seed=4)
+    sig = [0.15] * 2
+    lam_ref, V_ref = eigen.L1_eigs(layers, sig, 13)
+    return layers, sig, lam_ref, V_ref
+
+
+def test_image_discs_twin_p1_k10_fp64(discs_twin):
+    layers, sig, lam_ref, V_ref = discs_twin
+    n, k = layers[0].shape[0], 10
+    assert n == 4000
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, sig)]
+    V = torch.empty(n * k, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=1.0, tol=1e-11, seed=1, evecs=V)
+    assert st == ml.ML_OK and nconv == k
+    check_pairs(lam, V.cpu().numpy().reshape(k, n).T, lam_ref, V_ref, k)
+
+
+@pytest.mark.parametrize("prec,eps", [("f32", 1e-4), ("f64", 1e-6)])
+def test_image_discs_twin_at_the_forms_targets(discs_twin, prec, eps):
+    layers, sig, lam_ref, _ = discs_twin
+    k = 10
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec=prec, target_rel_err=eps) for L, s in zip(layers, sig)]
+    lam, nconv, st = ml.ml_lanczos_eigs(plans, k, p=1.0, tol=1e-8, seed=1)
+    assert st == ml.ML_OK and nconv == k
+    assert np.abs(lam - lam_ref[:k]).max() <= 10 * eps, (lam, lam_ref[:k])
+
+
+# ------------------------------------------------------------ failure and restart paths
+def test_iteration_limit_reports_not_converged():
+    X = workloads.uniform_cube(3000, 3, seed=400)
+    plan = ml.ml_fastsum_plan(dev(X), 0.1, prec="f64", target_rel_err=1e-10)
+    with pytest.warns(UserWarning, match="NOT_CONVERGED"):
+        lam, nconv, st = ml.ml_lanczos_eigs([plan], 10, p=1.0, tol=1e-12, maxit=25, seed=1)
+    assert st == ml.ML_WARN_NOT_CONVERGED and 0 <= nconv < 10
+    assert np.isfinite(lam).all() and (lam >= -1e-6).all() and (lam <= 2 + 1e-6).all()
+    plan2 = ml.ml_fastsum_plan(dev(X), 0.12, prec="f64", target_rel_err=1e-10)
+    with pytest.warns(UserWarning, match="NOT_CONVERGED"):
+        lam2, nconv2, st2 = ml.ml_lanczos_eigs_layers([plan, plan2], 10, block=4, tol=1e-12, maxit=24, seed=1)
+    assert st2 == ml.ML_WARN_NOT_CONVERGED and (nconv2 < 10).all()
+    assert np.isfinite(lam2).all()
+
+
+def test_complete_graph_invariant_subspaces():
+    # W = 11^T - I: D^{-1/2} W D^{-1/2} = (11^T - I)/(n-1) has two distinct
+    # eigenvalues, so every Krylov space closes after at most two steps and the
+    # solver continues from fresh random directions.  L_sym has the simple
+    # eigenvalue 0 and n/(n-1) with multiplicity n-1.
+    n, k = 40, 4
+    W = dev(np.ones((n, n)) - np.eye(n))
+    plan = ml.ml_dense_plan_matrix(W, prec="f64")
+    V = torch.empty(n * k, dtype=torch.float64, device="cuda")
+    lam, nconv, st = ml.ml_lanczos_eigs([plan], k, p=1.0, tol=1e-12, seed=3, evecs=V)
+    assert st == ml.ML_OK and nconv == k
+    assert np.allclose(lam, [0.0] + [n / (n - 1)] * (k - 1), atol=1e-12)
+    Vn = V.cpu().numpy().reshape(k, n)
+    assert np.abs(Vn @ Vn.T - np.eye(k)).max() <= 1e-12
+    assert np.abs(np.abs(Vn[0]) - 1 / math.sqrt(n)).max() <= 1e-12
+    # the block solver drops dependent directions (its block deflates) but does
+    # not refill them: once the block Krylov space closes with fewer than k
+    # directions it must report that it did not converge, not claim pairs
+    with pytest.warns(UserWarning, match="NOT_CONVERGED"):
+        lam2, nconv2, st2 = ml.ml_lanczos_eigs_layers([plan], k, block=2, tol=1e-12, maxit=200, seed=3)
+    assert st2 == ml.ML_WARN_NOT_CONVERGED and nconv2[0] < k

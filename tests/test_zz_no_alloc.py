@@ -5,7 +5,8 @@ allocator that owns the device, latency-bound loops, builds that forbid
 allocation after start-up).  This entry point takes all its scratch from a
 fixed 32 MiB device array inside the library; these tests check, through the
 C ABI, that its output equals the allocating entry point's on two calls in a
-row, and that oversized requests and host buffers are rejected.  The file is
+row, that on fresh plans it runs first without changing the plans' or the
+device's memory, and that oversized requests and host buffers are rejected.  The file is
 named so that pytest collects it last.
 """
 import numpy as np
@@ -39,6 +40,43 @@ def test_noalloc_matches_apply_two_calls(prec):
         assert np.isfinite(g).all()
         # the same kernels on the same inputs: equal up to FP64 rounding
         assert np.abs(g - r).max() <= 1e-13 * np.abs(r).max(), f"call {call}"
+
+
+def test_noalloc_first_on_fresh_plans_allocates_nothing():
+    # Fresh plans whose workspace was never grown: the no-alloc product runs
+    # first, and neither the plans' device memory nor the device's free memory
+    # changes across the call (with the device synchronised on both sides).
+    # The allocating product afterwards gives the same values.
+    n = 5000
+    rng = np.random.default_rng(8)
+    X = dev(rng.uniform(0, 1, (n, 3)))
+    got = torch.full_like(X, np.nan)
+    ref = torch.empty_like(X)
+    # one call on other plans of the same shapes first: the CUDA runtime loads
+    # kernels (and the library's static array) lazily, on first use, and that
+    # loading takes device memory once per process
+    warm = [ml.ml_fastsum_plan(dev(workloads.uniform_cube(n, dd, seed=230 + dd)), s, prec="f64")
+            for dd, s in ((3, 0.1), (2, 0.12))]
+    ml.ml_fastsum_apply_noalloc(warm, X, got, mode="normalized")
+    for pl in warm:
+        pl.destroy()
+    layers = [workloads.uniform_cube(n, 3, seed=220), workloads.uniform_cube(n, 2, seed=221)]
+    plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64") for L, s in zip(layers, [0.1, 0.12])]
+    got.fill_(np.nan)
+    torch.cuda.synchronize()
+    owned = [pl.info["device_bytes"] for pl in plans]
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        ml.ml_fastsum_apply_noalloc(plans, X, got, mode="normalized")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert [pl.info["device_bytes"] for pl in plans] == owned
+    assert free1 == free0
+    ml.ml_fastsum_apply(plans, X, ref, mode="normalized")
+    torch.cuda.synchronize()
+    r, g = ref.cpu().numpy(), got.cpu().numpy()
+    assert np.isfinite(g).all()
+    assert np.abs(g - r).max() <= 1e-13 * np.abs(r).max()
 
 
 def test_noalloc_per_layer_and_raw():
