@@ -451,6 +451,8 @@ def main():
         "vs_baseline": None, "dtype": DTYPE_LABEL[prec], "data": "synthetic", "config": config_dict(args, spec, n, T),
         "mode": args.mode, "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "clocks": clk,
         "peaks_measured": peaks,
+        "plans": [{key: info[key] for key in ("N", "n_os", "taps", "L", "bin", "nbins", "nsub", "sigma_s")}
+                  for info in msz],
     }
     if args.mode == "eig":
         line["lanczos_s"] = t_max / args.steps / 1e3

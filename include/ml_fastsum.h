@@ -517,6 +517,50 @@ ml_status ml_profile_enable(int on);
 ml_status ml_profile_reset(void);
 ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *ms);
 /*
+ * Dense products of the Lanczos solvers on the fp16 tensor cores (Sec. 3:
+ * the block Gram-Schmidt reorthogonalisation, the three-term update and the
+ * Ritz vectors are products of the Krylov basis with small matrices).  FP64
+ * operands are split into eight 8-bit slices (64-bit fixed point), every
+ * slice product is summed exactly in FP32 on the tensor cores (tcgen05.mma,
+ * at most 256 rows between integer drains), the pairs of slices whose weight
+ * is above 2^-70 are combined in 64-bit integers and converted to FP64 once
+ * (the error-free splitting of Ozaki, Ogita, Oishi and Rump, Numer.
+ * Algorithms 59 (2012)).  The result is as accurate as an FP64 product
+ * where it matters for an orthonormal basis: each entry's error is at most a
+ * few units of 2^-53 times sum_i |a_i||b_i|, plus the resolution of A's fixed
+ * scale, 2^-62 times the sum of the other factor's magnitudes.
+ *
+ * ml_block_gram - G = A^T B.
+ *   A   device, n x rc, row i at A + i * lda (point-major), |A_ij| < 2
+ *       (e.g. orthonormal basis columns); rc in 1..48.
+ *   B   device, n x cb, row i at B + i * ldb, any magnitude (each column is
+ *       scaled by a power of two over the rows one thread block handles);
+ *       cb in 1..8.
+ *   G   device, rc x cb row-major FP64, overwritten.
+ * ml_block_update - Y[:, 0:cb] = A M, or Y[:, 0:cb] -= A M with sub != 0.
+ *   A   device, n x rc as above (|A_ij| < 2, rc in 1..48).
+ *   M   device, rc x cb row-major FP64, any magnitude (scaled per column).
+ *   Y   device, n x cb, row i at Y + i * ldy; may be A itself only when the
+ *       columns written are not columns read.
+ * Both synchronise `stream` (they read the device's status flag).  Errors:
+ * ML_ERR_ARG (sizes), ML_ERR_DOMAIN (an entry of A with |v| >= 2),
+ * ML_ERR_TIMEOUT (a bounded wait of the kernel gave up), ML_ERR_OOM,
+ * ML_ERR_CUDA.
+ *
+ * ml_set_tensor_products - the eigensolvers' products of the basis on the
+ * tensor cores (on != 0) or on the FP64 pipe (on = 0, the default: for the
+ * solvers' shapes the slicing of every FP64 element costs more issue slots
+ * than the FP64 multiply-adds it replaces, so the tensor-core path is not
+ * faster).  Process-wide; a solve that meets an operand beyond |v| < 2
+ * repeats itself on the FP64 pipe.
+ */
+ml_status ml_block_gram(const double *A, int64_t n, int rc, int64_t lda, const double *B, int cb, int64_t ldb,
+                        double *G, void *stream);
+ml_status ml_block_update(const double *A, int64_t n, int rc, int64_t lda, const double *M, int cb, double *Y,
+                          int64_t ldy, int sub, void *stream);
+ml_status ml_set_tensor_products(int on);
+
+/*
  * ml_measure_peak - measured throughput of one GPU resource, the denominator
  * of a roofline fraction (measurement aid; the paper has no counterpart).
  * Runs a micro-kernel on the current device, 8 CTAs of 256 threads per SM,

@@ -33,7 +33,8 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_mlp_loss_grad", "ml_mlp_train", "ml_mlp_set_margins", "ml_mlp_destroy", "ml_lanczos_eigs", "ml_lanczos_eigs_layers", "ml_allen_cahn",
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
-           "ml_profile_reset", "ml_profile_read", "ml_graph_replays", "ml_measure_peak"]
+           "ml_profile_reset", "ml_profile_read", "ml_graph_replays", "ml_measure_peak", "ml_block_gram",
+           "ml_block_update", "ml_set_tensor_products"]
 
 
 class MLError(RuntimeError):
@@ -156,6 +157,14 @@ def load():
     lib.ml_graph_replays.restype = ctypes.c_int64
     lib.ml_graph_replays.argtypes = []
     lib.ml_measure_peak.restype = ctypes.c_int
+    lib.ml_block_gram.restype = ctypes.c_int
+    lib.ml_block_gram.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    lib.ml_block_update.restype = ctypes.c_int
+    lib.ml_block_update.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    lib.ml_set_tensor_products.restype = ctypes.c_int
+    lib.ml_set_tensor_products.argtypes = [ctypes.c_int]
     lib.ml_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     lib.ml_profile_enable.restype = ctypes.c_int
     lib.ml_profile_enable.argtypes = [ctypes.c_int]
@@ -519,6 +528,38 @@ def ml_allen_cahn(Phi, lam, labels, m, eps=0.005, omega0=1000.0, c=0.0, dt=0.01,
 def ml_graph_replays():
     """CUDA-graph replays of captured solver iterations since the library was loaded."""
     return int(load().ml_graph_replays())
+
+
+def _ptr_rows(a):
+    """Address of a float64 CUDA tensor whose rows may be strided (unit column stride)."""
+    if str(a.dtype) != "torch.float64" or a.dim() != 2 or (a.shape[1] > 1 and a.stride(1) != 1):
+        raise ValueError("tensors must be 2-d float64 with unit column stride")
+    return a.data_ptr()
+
+
+def ml_block_gram(A, B, stream=None):
+    """G = A^T B on the tensor cores (FP64-exact slices): A (n, rc), B (n, cb)
+    float64 CUDA tensors with unit column stride; returns G (rc, cb)."""
+    import torch
+    n, rc = int(A.shape[0]), int(A.shape[1])
+    cb = int(B.shape[1])
+    G = torch.empty(rc, cb, dtype=torch.float64, device=A.device)
+    _check(load().ml_block_gram(_ptr_rows(A), n, rc, int(A.stride(0)), _ptr_rows(B), cb, int(B.stride(0)),
+                                _ptr(G), _stream(stream)))
+    return G
+
+
+def ml_block_update(A, M, Y, sub=False, stream=None):
+    """Y = A M (or Y -= A M) on the tensor cores: A (n, rc), M (rc, cb), Y (n, cb)."""
+    n, rc = int(A.shape[0]), int(A.shape[1])
+    cb = int(M.shape[1])
+    _check(load().ml_block_update(_ptr_rows(A), n, rc, int(A.stride(0)), _ptr(M), cb, _ptr_rows(Y),
+                                  int(Y.stride(0)), 1 if sub else 0, _stream(stream)))
+    return Y
+
+
+def ml_set_tensor_products(on=True):
+    _check(load().ml_set_tensor_products(1 if on else 0))
 
 
 PEAKS = {"fp32": 0, "fp64": 1, "smem_atomic": 2}

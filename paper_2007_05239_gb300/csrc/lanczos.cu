@@ -273,16 +273,54 @@ struct Workspace {
     cudaStream_t st = nullptr;
     int64_t n = 0;
     int nblk = 1;
-    DevBuf part, hdev, scal;
+    bool tensor = false;   // products of the basis on the tensor cores (ozaki.cu)
+    // The single-vector products Q^T x and x - Q h stream the basis once for
+    // one multiply-add per element: on the FP64 pipe they run near the HBM
+    // rate already, so only the Ritz vectors Q S (many columns) take the
+    // tensor cores
+    bool matvec_tc = false;
+    DevBuf part, hdev, scal, lay0;
 
-    ml_status init(int64_t n_, int maxcol, cudaStream_t s)
+    ml_status init(int64_t n_, int maxcol, cudaStream_t s, bool tensor_ = false)
     {
         n = n_;
         st = s;
+        tensor = tensor_;
         nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 456));
-        ML_TRY(part.ensure((size_t)nblk * std::max(maxcol, 1) * sizeof(double)));
+        const int nb_oz = oz_gram_blocks(1, n);
+        ML_TRY(part.ensure((size_t)std::max(nblk, nb_oz) * std::max(maxcol, 1) * sizeof(double)));
         ML_TRY(hdev.ensure((size_t)(2 * maxcol + 8) * sizeof(double)));
         ML_TRY(scal.ensure(64 * sizeof(double)));
+        ML_TRY(lay0.ensure(sizeof(int)));
+        ML_CUDA(cudaMemsetAsync(lay0.p, 0, sizeof(int), st));
+        return ML_OK;
+    }
+    // out (device, ncol) = Q[:, 0:ncol]^T x for the orthonormal basis Q (column
+    // major) and a vector with |x_i| < 2: on the tensor cores when enabled
+    ml_status basis_dots(const double *Q, int64_t ldq, int ncol, const double *x, double *out)
+    {
+        if (!(tensor && matvec_tc && oz_gram_ok(ncol, 1))) return dots(Q, ldq, ncol, x, out);
+        const int nb = oz_gram_blocks(1, n);
+        {
+            ProfScope pr("dots", st);
+            ML_TRY(oz_gram(OzMat{Q, 0, 1, ldq}, ncol, OzMat{x, 0, 1, n}, 1, lay0.as<int>(), 1, n, nb,
+                           part.as<double>(), st));
+        }
+        {
+            ProfScope pr("dots_reduce", st);
+            k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nb, ncol, out);
+        }
+        ML_CUDA(cudaGetLastError());
+        return ML_OK;
+    }
+    // x -= Q[:, 0:ncol] h (h device)
+    ml_status basis_update(const double *Q, int64_t ldq, int ncol, const double *h, double *x)
+    {
+        ProfScope pr("update", st);
+        if (tensor && matvec_tc && oz_gemm_ok(ncol))
+            return oz_gemm(OzMat{Q, 0, 1, ldq}, ncol, h, 1, 1, 0, 1, OzOut{x, 0, 1, n}, lay0.as<int>(), 1, n, true, st);
+        k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h, x);
+        ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
     // out (device, ncol) = Q[:, 0:ncol]^T x
@@ -312,16 +350,10 @@ struct Workspace {
     {
         double *h1 = hdev.as<double>(), *h2 = h1 + ncol, *nrm = h2 + ncol;
         if (ncol > 0) {
-            ML_TRY(dots(Q, ldq, ncol, x, h1));
-            {
-                ProfScope pr("update", st);
-                k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h1, x);
-            }
-            ML_TRY(dots(Q, ldq, ncol, x, h2));
-            {
-                ProfScope pr("update", st);
-                k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h2, x);
-            }
+            ML_TRY(basis_dots(Q, ldq, ncol, x, h1));
+            ML_TRY(basis_update(Q, ldq, ncol, h1, x));
+            ML_TRY(basis_dots(Q, ldq, ncol, x, h2));
+            ML_TRY(basis_update(Q, ldq, ncol, h2, x));
         }
         ML_TRY(dots(x, n, 1, x, nrm));
         std::vector<double> hh(2 * ncol + 1);
@@ -830,14 +862,20 @@ ml_status sign_fix_cols(double *V, int64_t n, int k, cudaStream_t st)
     return ML_OK;
 }
 
+// returned by lanczos_impl when a tensor-core product met an operand beyond its
+// fixed scale: the solve is repeated with the FP64-pipe products
+constexpr int kRetryFp64 = 1000;
+
 static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw, double tol, int maxit,
-                              uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
+                              uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st,
+                              bool tensor)
 {
     const int64_t n = layers[0]->n;
     const int ncv = (int)std::min<int64_t>(std::max(2 * k + 1, 20), n - 1);
     const int kkeep = std::min(ncv - 2, std::max(k + 1, (ncv + k) / 2));
     Workspace ws;
-    ML_TRY(ws.init(n, ncv + 1, st));
+    ML_TRY(ws.init(n, ncv + 1, st, tensor));
+    if (tensor) ML_TRY(oz_reset_error(st));
     DevBuf Qb, Qtmp, wv, Sd;
     ML_TRY(Qb.ensure((size_t)n * (ncv + 1) * 8));
     ML_TRY(Qtmp.ensure((size_t)n * (ncv + 1) * 8));
@@ -934,7 +972,13 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         ML_CUDA(cudaMemcpyAsync(Sd.p, Sk.data(), Sk.size() * 8, cudaMemcpyHostToDevice, st));
         {
             ProfScope pr("ritz", st);
-            k_combine<<<nb, 256, 0, st>>>(Q, n, n, ncv, Sd.as<double>(), keep, Qtmp.as<double>(), n);
+            if (ws.tensor && oz_gemm_ok(ncv)) {
+                // Sk is ncv x keep column-major: M[r, j] = Sk[j * ncv + r]
+                ML_TRY(oz_gemm(OzMat{Q, 0, 1, n}, ncv, Sd.as<double>(), 1, ncv, 0, keep, OzOut{Qtmp.as<double>(), 0, 1, n},
+                               ws.lay0.as<int>(), 1, n, false, st));
+            } else {
+                k_combine<<<nb, 256, 0, st>>>(Q, n, n, ncv, Sd.as<double>(), keep, Qtmp.as<double>(), n);
+            }
         }
         ML_CUDA(cudaGetLastError());
         if (done) {
@@ -950,6 +994,12 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
                 ML_CUDA(cudaGetLastError());
             }
             ML_CUDA(cudaStreamSynchronize(st));
+            if (tensor) {
+                int flags = 0;
+                ML_TRY(oz_read_error(&flags, st));
+                if (flags & 2) return fail(ML_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up");
+                if (flags & 1) return (ml_status)kRetryFp64;
+            }
             if (nconv_out) *nconv_out = std::min(nconv, k);
             if (nconv >= k) return ML_OK;
             set_error("Lanczos stopped after " + std::to_string(matvecs) + " operator applications (maxit " +
@@ -1009,7 +1059,8 @@ extern "C" ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, doub
             host_out = true;
         }
     }
-    ml_status s = lanczos_impl(layers, T, k, p, tol, maxit, seed, evals, evd, nconv, st);
+    ml_status s = lanczos_impl(layers, T, k, p, tol, maxit, seed, evals, evd, nconv, st, oz_enabled());
+    if ((int)s == kRetryFp64) s = lanczos_impl(layers, T, k, p, tol, maxit, seed, evals, evd, nconv, st, false);
     if ((s == ML_OK || s == ML_WARN_NOT_CONVERGED) && host_out) {
         ML_CUDA(cudaMemcpy(evecs, evd, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
     }

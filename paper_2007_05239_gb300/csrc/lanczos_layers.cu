@@ -318,6 +318,7 @@ struct Solver {
     DescSlot desc;
     int64_t hstride = 0, rstride = 0;   // per layer record strides (doubles)
     int nslots = 0;                     // active layers
+    bool tensor = true;                 // dense products of the basis on the tensor cores
     std::vector<int> lay;               // slot -> layer
 
     LMat q(int which) const { return LMat{Q[which].as<double>(), n * ldq, ldq}; }
@@ -332,28 +333,42 @@ struct Solver {
         return ML_OK;
     }
 
-    // out[y] (rc x cb) = A_t[:, a0:a0+rc]^T B_t[:, b0:b0+cb]; optionally recorded
-    ml_status gram(LMat A, int a0, int rc, LMat B, int b0, int cb, double *out, double *rec, int64_t rs)
+    // out[y] (rc x cb) = A_t[:, a0:a0+rc]^T B_t[:, b0:b0+cb]; optionally recorded.
+    // basis: A is the orthonormal basis and B a block of norm-bounded vectors
+    // (|entries| < 2), so the product may run on the tensor cores (ozaki.cu)
+    ml_status gram(LMat A, int a0, int rc, LMat B, int b0, int cb, double *out, double *rec, int64_t rs,
+                   bool basis = false)
     {
         const int nout = rc * cb;
         if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
-        {
+        int nb = nbx;
+        if (basis && tensor && oz_gram_ok(rc, cb)) {
+            ProfScope pr("dots", st);
+            nb = oz_gram_blocks(nslots, n);
+            ML_TRY(oz_gram(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, OzMat{B.base + b0, B.stride, B.ld, 1}, cb,
+                           layd.as<int>(), nslots, n, nb, part.as<double>(), st));
+        } else {
             ProfScope pr("dots", st);
             k_lgram<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>());
         }
         {
             ProfScope pr("dots_reduce", st);
-            k_lreduce<<<dim3((nout + 127) / 128, nslots), 128, 0, st>>>(part.as<double>(), nbx, nout, layd.as<int>(),
+            k_lreduce<<<dim3((nout + 127) / 128, nslots), 128, 0, st>>>(part.as<double>(), nb, nout, layd.as<int>(),
                                                                        out, rec, rs);
         }
         ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
 
-    ml_status gemm(LMat A, int a0, int rc, const double *M, LMat B, int b0, int cb, bool sub)
+    // B_t[:, b0:b0+cb] (-)= A_t[:, a0:a0+rc] M_y; basis as for gram (M any magnitude)
+    ml_status gemm(LMat A, int a0, int rc, const double *M, LMat B, int b0, int cb, bool sub, bool basis = false,
+                   const char *family = "update")
     {
+        ProfScope pr(family, st);
+        if (basis && tensor && oz_gemm_ok(rc))
+            return oz_gemm(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, M, cb, 1, (int64_t)rc * cb, cb,
+                           OzOut{B.base + b0, B.stride, B.ld, 1}, layd.as<int>(), nslots, n, sub, st);
         const size_t smem = ((size_t)rc * cb + (size_t)kRows * (rc + 1)) * sizeof(double);
-        ProfScope pr("update", st);
         k_lgemm<<<dim3(nbx, nslots), 256, smem, st>>>(A, a0, rc, M, B, b0, cb, layd.as<int>(), n, sub ? 1 : 0);
         ML_CUDA(cudaGetLastError());
         return ML_OK;
@@ -392,15 +407,15 @@ struct Solver {
         const LMat Qc = q(cur), Wm = w();
         double *h = hcur.as<double>();
         if (cq > 0) {
-            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, hrec, hstride));
-            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true));
+            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, hrec, hstride, true));
+            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true, true));
         }
         ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
         ML_TRY(svqb(0, nullptr));
         ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), Wm, 0, b, false));
         if (cq > 0) {
-            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, nullptr, 0));
-            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true));
+            ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, nullptr, 0, true));
+            ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true, true));
             if (hrec) {
                 ProfScope pr("svqb", st);
                 k_lhacc<<<dim3((cq * b + 127) / 128, nslots), 128, 0, st>>>(h, Rs.as<double>(), cq, b, layd.as<int>(),
@@ -451,10 +466,17 @@ struct Solver {
 
 }  // namespace
 
+// returned by layers_impl when a tensor-core product met an operand beyond its
+// fixed scale: the solve is repeated with the FP64-pipe products
+constexpr int kRetryFp64 = 1000;
+
 static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int maxit, int b, int ncv_req,
-                             uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st)
+                             uint64_t seed, double *evals, double *evecs_dev, int *nconv_out, cudaStream_t st,
+                             bool tensor)
 {
     Solver S;
+    S.tensor = tensor;
+    if (tensor) ML_TRY(oz_reset_error(st));
     S.L = L;
     S.T = T;
     S.k = k;
@@ -592,9 +614,9 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
         }
         // Ritz vectors of every active layer -> the other basis buffer
         ML_CUDA(cudaMemcpyAsync(S.Sd.p, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        ML_TRY(S.gemm(S.q(cur), 0, ncv, S.Sd.as<double>(), S.q(cur ^ 1), 0, kkeep, false, true, "ritz"));
         {
             ProfScope pr("ritz", st);
-            ML_TRY(S.gemm(S.q(cur), 0, ncv, S.Sd.as<double>(), S.q(cur ^ 1), 0, kkeep, false));
             k_lcopy<<<dim3(std::max(1, S.nbx * 4), S.nslots), 256, 0, st>>>(S.q(cur), ncv, S.q(cur ^ 1), kkeep, b,
                                                                              S.layd.as<int>(), n);
         }
@@ -639,6 +661,12 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
         }
     }
     ML_CUDA(cudaStreamSynchronize(st));
+    if (tensor) {
+        int flags = 0;
+        ML_TRY(oz_read_error(&flags, st));
+        if (flags & 2) return fail(ML_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up");
+        if (flags & 1) return (ml_status)kRetryFp64;
+    }
     int all = 1;
     for (int t = 0; t < T; ++t) {
         if (nconv_out) nconv_out[t] = std::min(nconv[t], k);
@@ -690,7 +718,8 @@ extern "C" ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int 
         }
     }
     if (ncv < 0 || ncv > kMaxLd - block) return fail(ML_ERR_ARG, "ncv must be 0 (automatic) or at most 96 - block");
-    ml_status s = layers_impl(layers, T, k, tol, maxit, block, ncv, seed, evals, evd, nconv, st);
+    ml_status s = layers_impl(layers, T, k, tol, maxit, block, ncv, seed, evals, evd, nconv, st, oz_enabled());
+    if ((int)s == kRetryFp64) s = layers_impl(layers, T, k, tol, maxit, block, ncv, seed, evals, evd, nconv, st, false);
     if ((s == ML_OK || s == ML_WARN_NOT_CONVERGED) && host_out)
         ML_CUDA(cudaMemcpy(evecs, evd, (size_t)T * n * k * sizeof(double), cudaMemcpyDeviceToHost));
     return s;

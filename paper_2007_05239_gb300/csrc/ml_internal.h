@@ -41,6 +41,34 @@ constexpr int kGroupSubs = 64;   // most subproblem tiles summed per group befor
 // cached): grid-stride launches size their grids as a multiple of it.
 int sm_count();
 
+// ------------------------------------------------- tensor-core FP64 products
+// Tall FP64 operands of the Lanczos products: element (i, c) of layer t at
+// base + t * lstride + i * rs + c * cs (point-major: rs = ld, cs = 1;
+// column-major: rs = 1, cs = ld).  ozaki.cu: the Gram A^T B and the update
+// Y (-)= A M on the fp16 tensor cores through 8-bit slices of the FP64
+// values, exact up to FP64 rounding; the tall operands must satisfy |v| < 2.
+struct OzMat {
+    const double *base;
+    int64_t lstride, rs, cs;
+};
+struct OzOut {
+    double *base;
+    int64_t lstride, rs, cs;
+};
+bool oz_gram_ok(int rc, int cb);
+bool oz_gemm_ok(int rc);
+int oz_gram_blocks(int nslots, int64_t n);
+// part[(y * nbx + x) * rc * cb + c * cb + j]: per-block partial Grams (y = slot)
+ml_status oz_gram(OzMat A, int rc, OzMat B, int cb, const int *lay, int nslots, int64_t n, int nbx, double *part,
+                  cudaStream_t st);
+// Y_t[:, j] (-)= sum_r A_t[:, r] M_y[r, j], M_y[r, j] = M[y * mslot + r * mrs + j * mcs]
+ml_status oz_gemm(OzMat A, int rc, const double *M, int64_t mrs, int64_t mcs, int64_t mslot, int cb, OzOut Y,
+                  const int *lay, int nslots, int64_t n, bool sub, cudaStream_t st);
+// the solvers' dense products on the tensor cores (default) or the FP64 pipe
+bool oz_enabled();
+ml_status oz_reset_error(cudaStream_t st);
+ml_status oz_read_error(int *flags, cudaStream_t st);
+
 // ------------------------------------------------------------ device buffer
 // Owns one device allocation (freed on destruction; movable, not copyable).
 struct DevBuf {
