@@ -262,7 +262,9 @@ def eig_step_fn(ml, spec, sig, planner, plan_all, n):
     k, p = spec["k"], spec["p"]
 
     def step(dl, evecs):
+        t0 = time.perf_counter()
         plans = plan_all(dl, sig) if plan_all else [planner(x, s) for x, s in zip(dl, sig)]
+        step.plan_s.append(time.perf_counter() - t0)   # the plan calls synchronise their streams
         if spec.get("per_layer"):
             lam, nconv, st = ml.ml_lanczos_eigs_layers(plans, k, block=spec["block"], tol=1e-8, seed=1, evecs=evecs)
             lam, nconv = lam[0], int(nconv.min())
@@ -273,6 +275,7 @@ def eig_step_fn(ml, spec, sig, planner, plan_all, n):
         for pl in plans:
             pl.destroy()
         return lam, nconv, applied, infos
+    step.plan_s = []
     return step
 
 
@@ -456,6 +459,7 @@ def main():
     }
     if args.mode == "eig":
         line["lanczos_s"] = t_max / args.steps / 1e3
+        line["plan_s_median"] = statistics.median(step.plan_s) if step.plan_s else None
         line["eigenvalues"] = [float(x) for x in lam[:min(5, k)]]
         line["nconv"] = int(nconv)
     else:
@@ -598,7 +602,8 @@ def run_extra(wname, ml, torch, barrier, with_err):
     out = {"metric": metric_name(spec), "value": applied / (ms / 1e3) / 1e9, "unit": "Gpts·vec/s",
            "ms_per_step": ms / 2, "steps": 2, "warmup": 1, "dtype": DTYPE_LABEL[spec["prec"]],
            "target_rel_err": spec["target"], "k": spec["k"], "p": spec["p"], "nconv": int(res[1]),
-           "eigenvalues": [float(x) for x in res[0][:5]], "clocks": clk, "desc": spec["desc"]}
+           "eigenvalues": [float(x) for x in res[0][:5]], "clocks": clk, "desc": spec["desc"],
+           "plan_s_median": statistics.median(step.plan_s) if step.plan_s else None}
     if with_err:
         nv = spec.get("block", 1) if per_layer else 1
         _, errs = cpu_baseline(layers, sig, ml, torch, dev_layers, [(spec["prec"], spec["target"])],

@@ -547,18 +547,26 @@ ml_status ml_profile_read(int i, const char **name, int64_t *launches, double *m
  * ML_ERR_TIMEOUT (a bounded wait of the kernel gave up), ML_ERR_OOM,
  * ML_ERR_CUDA.
  *
- * ml_set_tensor_products - the eigensolvers' products of the basis on the
- * tensor cores (on != 0) or on the FP64 pipe (on = 0, the default: for the
- * solvers' shapes the slicing of every FP64 element costs more issue slots
- * than the FP64 multiply-adds it replaces, so the tensor-core path is not
- * faster).  Process-wide; a solve that meets an operand beyond |v| < 2
- * repeats itself on the FP64 pipe.
+ * ml_set_dense_products - how the eigensolvers form their products of the
+ * Krylov basis (Q^T x, x - Q h, the Ritz vectors Q S; in the per-layer
+ * solver the block Gram and update products on the tensor cores only):
+ *   kind = 0  on the FP64 pipe;
+ *   kind = 1  (default) in double-word arithmetic on the FP32 pipes (each
+ *             value an unevaluated pair of floats, about 47 significant
+ *             bits; exact products by FMA, compensated sums): GB300 runs
+ *             FP64 at 1/64 of the FP32 rate, and these products are bound by
+ *             it on the FP64 pipe;
+ *   kind = 2  on the tensor cores as above (FP64-accurate, but not faster
+ *             for these shapes: the slicing of every FP64 element costs more
+ *             issue slots than the multiply-adds it replaces).
+ * Process-wide.  A tensor-core solve that meets an operand beyond |v| < 2
+ * repeats itself on the FP64 pipe.  ML_ERR_ARG for other kinds.
  */
 ml_status ml_block_gram(const double *A, int64_t n, int rc, int64_t lda, const double *B, int cb, int64_t ldb,
                         double *G, void *stream);
 ml_status ml_block_update(const double *A, int64_t n, int rc, int64_t lda, const double *M, int cb, double *Y,
                           int64_t ldy, int sub, void *stream);
-ml_status ml_set_tensor_products(int on);
+ml_status ml_set_dense_products(int kind);
 
 /*
  * ml_measure_peak - measured throughput of one GPU resource, the denominator

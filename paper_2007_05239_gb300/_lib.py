@@ -34,7 +34,7 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read", "ml_graph_replays", "ml_measure_peak", "ml_block_gram",
-           "ml_block_update", "ml_set_tensor_products"]
+           "ml_block_update", "ml_set_dense_products"]
 
 
 class MLError(RuntimeError):
@@ -163,8 +163,8 @@ def load():
     lib.ml_block_update.restype = ctypes.c_int
     lib.ml_block_update.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
-    lib.ml_set_tensor_products.restype = ctypes.c_int
-    lib.ml_set_tensor_products.argtypes = [ctypes.c_int]
+    lib.ml_set_dense_products.restype = ctypes.c_int
+    lib.ml_set_dense_products.argtypes = [ctypes.c_int]
     lib.ml_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     lib.ml_profile_enable.restype = ctypes.c_int
     lib.ml_profile_enable.argtypes = [ctypes.c_int]
@@ -558,8 +558,12 @@ def ml_block_update(A, M, Y, sub=False, stream=None):
     return Y
 
 
-def ml_set_tensor_products(on=True):
-    _check(load().ml_set_tensor_products(1 if on else 0))
+DENSE = {"fp64": 0, "dword": 1, "tensor": 2}
+
+
+def ml_set_dense_products(kind="dword"):
+    """The eigensolvers' basis products: "fp64", "dword" (default) or "tensor"."""
+    _check(load().ml_set_dense_products(DENSE[kind] if isinstance(kind, str) else int(kind)))
 
 
 PEAKS = {"fp32": 0, "fp64": 1, "smem_atomic": 2}

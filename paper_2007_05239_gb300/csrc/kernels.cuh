@@ -20,13 +20,20 @@ namespace ml {
 // Normalised Kaiser-Bessel window phi_n(t) = sinh(b s)/s / (sinh(b m)/m),
 // s = sqrt(m^2 - t^2), t in [-m, m] (grid units).  norm2 = m e^{-bm}/(1-e^{-2bm}),
 // so phi_n(t) = norm2 (e^{bs} - e^{-bs}) / s.
+// FP32 form: the special-function unit's approximate reciprocal square root,
+// exponential and reciprocal (a few ulp each, far below the form's 1e-4
+// target) and no division; near the window's edge (b s < 1e-3) the series
+// 2 b (1 + (b s)^2 / 6) of sinh(b s)/s
 __device__ __forceinline__ float kb_weight(float t, float m2, float b, float norm2)
 {
-    const float s = sqrtf(fmaxf(m2 - t * t, 0.0f));
+    const float x = fmaxf(fmaf(-t, t, m2), 0.0f);       // m^2 - t^2
+    const float r = rsqrtf(fmaxf(x, 1e-30f));
+    const float s = x * r;                               // sqrt(x); 0 at the edge
     const float bs = b * s;
-    if (bs < 1e-3f) return norm2 * 2.0f * b * (1.0f + bs * bs * (1.0f / 6.0f));
     const float e = __expf(bs);
-    return norm2 * (e - __frcp_rn(e)) / s;
+    const float exact = norm2 * (e - __fdividef(1.0f, e)) * r;
+    const float series = norm2 * 2.0f * b * fmaf(bs * bs, 1.0f / 6.0f, 1.0f);
+    return bs < 1e-3f ? series : exact;
 }
 __device__ __forceinline__ double kb_weight(double t, double m2, double b, double norm2)
 {
@@ -271,6 +278,68 @@ __device__ __forceinline__ float fixed_scale(float sum_abs, float max_abs)
 // Shared-memory tiles are vector-major: tile[c * tc + cell], so that the NV
 // values of one tap fall in different banks.
 
+// Sum over the warp of 32 values per lane: after five exchange rounds lane l
+// holds the sum of every lane's v[l] (a fixed order: deterministic).
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int h = 16 >> r;
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = up ? v[k] : v[k + h];
+            const float keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return v[0];
+}
+
+// The warp's 32 points share their first tap o: every tap t (and vector c) is
+// summed over the warp in chunks of 32 taps, and lane l adds the sum of tap
+// 32 j + l of chunk j, rounded to the fixed-point integer (the scaled sum of
+// a subproblem stays below 2^30), with one atomic.  Lanes past the end of the
+// subproblem carry u = 0.
+template <int D, int W, int NV>
+__device__ __forceinline__ void warp_spread_sum(int *tile, int tc, int Pt, const int (&o)[3], const float (&u)[NV],
+                                                const float (&wx)[W], const float (&wy)[W], const float (&wz)[W],
+                                                int lane)
+{
+    constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int NT = W * ny * nz;
+    float wzy[nz * ny];
+#pragma unroll
+    for (int qz = 0; qz < nz; ++qz)
+#pragma unroll
+        for (int qy = 0; qy < ny; ++qy) wzy[qz * ny + qy] = (D >= 3 ? wz[qz] : 1.0f) * (D >= 2 ? wy[qy] : 1.0f);
+#pragma unroll 1
+    for (int c = 0; c < NV; ++c) {
+        float uc = u[0];
+#pragma unroll
+        for (int k = 1; k < NV; ++k)
+            if (c == k) uc = u[k];
+        float uw[W];
+#pragma unroll
+        for (int qx = 0; qx < W; ++qx) uw[qx] = uc * wx[qx];
+#pragma unroll
+        for (int j = 0; j < (NT + 31) / 32; ++j) {
+            float v[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int t = 32 * j + k;
+                v[k] = t < NT ? wzy[t / W] * uw[t % W] : 0.0f;
+            }
+            const float sum = warp_transpose_sum32(v, lane);
+            const int t = 32 * j + lane;
+            if (t < NT) {
+                const int qx = t % W, qy = (t / W) % ny, qz = t / (W * ny);
+                atomicAdd(tile + c * tc + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0] + qx, __float2int_rn(sum));
+            }
+        }
+    }
+}
+
 // FP32 form: one thread per point.  Weights and taps in FP32; each tile cell
 // accumulates integers (fixed point, per-subproblem power-of-two scale) with
 // 32-bit shared-memory atomics, which are exact and order-independent.  Each
@@ -322,6 +391,8 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     __syncthreads();
 
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
+    constexpr int NT = W * ny * nz;                 // taps per point
+    constexpr bool kWarpSum = NT <= 512;
     // full unrolling only for the small windows the throughput cases use
     constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
     constexpr int UY = (W <= 8) ? ny : 1;
@@ -329,18 +400,31 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     const int rz = (D == 3) ? lane % nz : 0;
     const float *coords = static_cast<const float *>(a.coords);
     const int Pt = a.Pt;
-    for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
+    // a warp takes 32 consecutive points (sorted by cell); when all of them
+    // have the same first tap, their taps are summed across the warp and
+    // each lane adds one sum per 32 taps (warp_spread_sum), else every lane
+    // adds its own point's taps
+    for (int g0 = (threadIdx.x & ~31); g0 < cnt; g0 += blockDim.x) {
+        const bool valid = g0 + lane < cnt;
+        const int i = start + min(g0 + lane, cnt - 1);
         const int orig = a.perm[i];
         const double ds = a.dinv ? a.dinv[i] : 1.0;
         float u[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c)
-            u[c] = (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c];
+            u[c] = valid ? (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c] : 0.0f;
         float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
         o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
         if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
         if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        const int key = o[0] | (o[1] << 10) | (o[2] << 20);
+        const int key0 = __shfl_sync(0xffffffffu, key, 0);
+        if (kWarpSum && __all_sync(0xffffffffu, !valid || key == key0)) {
+            warp_spread_sum<D, W, NV>(tile, tc, Pt, o, u, wx, wy, wz, lane);
+            continue;
+        }
+        if (!valid) continue;
         // rotated copies: row q of this lane is row (q + r) mod n of the point
         float wyr[ny], wzr[nz];
 #pragma unroll
@@ -551,8 +635,10 @@ __device__ __forceinline__ void grid_store(float2 *out, int64_t i, double v)
     out[i] = dw_split(v);
 }
 
+// (the cells of a bin are shared by `chunks` CTAs: chunk ch takes elements
+// ch * blockDim.x + tid, stepping by chunks * blockDim.x)
 template <typename T, int D, typename TO = T>
-__device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
+__device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin, const int ch, const int chunks)
 {
     int bc[3];
     bin_coords<D>(bin, a.nb0, a.nb1, bc);
@@ -561,7 +647,7 @@ __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
     const int cells = (D == 1 ? B : (D == 2 ? B * B : B * B * B));
     const T *scr = static_cast<const T *>(a.scratch);
     TO *grid = static_cast<TO *>(a.grid);
-    for (int e = threadIdx.x; e < cells * nv; e += blockDim.x) {
+    for (int e = ch * blockDim.x + threadIdx.x; e < cells * nv; e += chunks * blockDim.x) {
         const int c = e % nv;
         const int cell = e / nv;
         const int cx = cell % B;
@@ -594,17 +680,25 @@ __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin)
 }
 
 template <typename T, int D, typename TO = T>
-__global__ void __launch_bounds__(256) k_fold(const FoldArgs a)
+__global__ void __launch_bounds__(256) k_fold(const FoldArgs a, int chunks)
 {
-    fold_block<T, D, TO>(a, blockIdx.x);
+    fold_block<T, D, TO>(a, blockIdx.x / chunks, blockIdx.x % chunks, chunks);
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_fold_batch(const FoldArgs *__restrict__ args)
+__global__ void __launch_bounds__(256) k_fold_batch(const FoldArgs *__restrict__ args, int chunks)
 {
     const FoldArgs a = args[blockIdx.y];
-    if ((int)blockIdx.x >= a.nbins) return;
-    fold_block<T, D>(a, blockIdx.x);
+    if ((int)blockIdx.x >= a.nbins * chunks) return;
+    fold_block<T, D>(a, blockIdx.x / chunks, blockIdx.x % chunks, chunks);
+}
+
+// CTAs per bin for the fold: enough for about two CTAs per SM in all
+inline int fold_chunks(int64_t bins, int64_t cells_nv, int sms)
+{
+    const int64_t by_work = (cells_nv + 255) / 256;
+    const int64_t by_fill = (2 * (int64_t)sms + bins - 1) / std::max<int64_t>(bins, 1);
+    return (int)std::max<int64_t>(1, std::min(by_work, by_fill));
 }
 
 // ==================================================================== axis

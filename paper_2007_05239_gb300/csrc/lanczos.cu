@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "dword.cuh"
 #include "ml_internal.h"
 
 namespace ml {
@@ -220,6 +221,83 @@ __global__ void k_combine(const double *__restrict__ Q, int64_t ldq, int64_t n, 
     }
 }
 
+// ---- double-word versions of the basis products (FP32 pipes, ~47 bits)
+// part[blk * ncol + c] = sum over this block's rows of Q[:, c] x (as k_dots)
+__global__ void __launch_bounds__(kDotThreads) k_dots_dw(const double *__restrict__ Q, int64_t ldq, int64_t n,
+                                                         int ncol, const double *__restrict__ x, double *part)
+{
+    __shared__ double red[kDotThreads / 32][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < ncol; c0 += 8) {
+        float2 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.0f, 0.0f);
+        for (int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; r < n; r += (int64_t)gridDim.x * kDotThreads) {
+            const float2 xr = dword::from_double(x[r]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + k < ncol) dword::fma_acc(acc[k], dword::from_double(Q[(int64_t)(c0 + k) * ldq + r]), xr);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            double v = dword::to_double(acc[k]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < ncol) {
+            double sacc = 0.0;
+            for (int w = 0; w < kDotThreads / 32; ++w) sacc += red[w][threadIdx.x];
+            part[(int64_t)blockIdx.x * ncol + c0 + threadIdx.x] = sacc;
+        }
+        __syncthreads();
+    }
+}
+
+// x -= Q[:, 0:ncol] h, the sum in double-word (h staged once per block)
+__global__ void __launch_bounds__(256) k_update_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
+                                                  const double *__restrict__ h, double *x)
+{
+    __shared__ float2 hs[128];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = dword::from_double(h[c]);
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int c = 0; c < ncol; ++c) dword::fma_acc(acc, dword::from_double(Q[(int64_t)c * ldq + r]), hs[c]);
+        x[r] -= dword::to_double(acc);
+    }
+}
+
+// out[:, i] = Q[:, 0:ncv] S[:, i] for i < kk (S column-major ncv x kk), in
+// double-word; each row's accumulators for up to 32 columns in registers
+__global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv,
+                                                   const double *__restrict__ S, int kk, double *out, int64_t ldo)
+{
+    extern __shared__ float2 ss[];                 // [ncv][kk] double-word
+    for (int e = threadIdx.x; e < ncv * kk; e += blockDim.x) {
+        const int c = e / kk, i = e - c * kk;
+        ss[e] = dword::from_double(S[(int64_t)i * ncv + c]);
+    }
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        for (int i0 = 0; i0 < kk; i0 += 32) {
+            float2 acc[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) acc[k] = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < ncv; ++c) {
+                const float2 q = dword::from_double(Q[(int64_t)c * ldq + r]);
+                const float2 *srow = ss + (int64_t)c * kk + i0;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (i0 + k < kk) dword::fma_acc(acc[k], q, srow[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (i0 + k < kk) out[(int64_t)(i0 + k) * ldo + r] = dword::to_double(acc[k]);
+        }
+    }
+}
+
 // per-block (max |x|, signed value at the first maximum) of each column
 __global__ void k_colmax(const double *__restrict__ V, int64_t ldv, int64_t n, int k, double *part)
 {
@@ -274,18 +352,20 @@ struct Workspace {
     int64_t n = 0;
     int nblk = 1;
     bool tensor = false;   // products of the basis on the tensor cores (ozaki.cu)
+    bool dword = false;    // products of the basis in double-word FP32 (dword.cuh)
     // The single-vector products Q^T x and x - Q h stream the basis once for
-    // one multiply-add per element: on the FP64 pipe they run near the HBM
-    // rate already, so only the Ritz vectors Q S (many columns) take the
-    // tensor cores
+    // one multiply-add per element: on the tensor cores they would spend most
+    // of the instruction's width on padding, so only the Ritz vectors Q S
+    // (many columns) take them there
     bool matvec_tc = false;
     DevBuf part, hdev, scal, lay0;
 
-    ml_status init(int64_t n_, int maxcol, cudaStream_t s, bool tensor_ = false)
+    ml_status init(int64_t n_, int maxcol, cudaStream_t s, int kind = 0)
     {
         n = n_;
         st = s;
-        tensor = tensor_;
+        tensor = kind == 2;
+        dword = kind == 1;
         nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 456));
         const int nb_oz = oz_gram_blocks(1, n);
         ML_TRY(part.ensure((size_t)std::max(nblk, nb_oz) * std::max(maxcol, 1) * sizeof(double)));
@@ -299,6 +379,18 @@ struct Workspace {
     // major) and a vector with |x_i| < 2: on the tensor cores when enabled
     ml_status basis_dots(const double *Q, int64_t ldq, int ncol, const double *x, double *out)
     {
+        if (dword) {
+            {
+                ProfScope pr("dots", st);
+                k_dots_dw<<<nblk, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
+            }
+            {
+                ProfScope pr("dots_reduce", st);
+                k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nblk, ncol, out);
+            }
+            ML_CUDA(cudaGetLastError());
+            return ML_OK;
+        }
         if (!(tensor && matvec_tc && oz_gram_ok(ncol, 1))) return dots(Q, ldq, ncol, x, out);
         const int nb = oz_gram_blocks(1, n);
         {
@@ -317,6 +409,11 @@ struct Workspace {
     ml_status basis_update(const double *Q, int64_t ldq, int ncol, const double *h, double *x)
     {
         ProfScope pr("update", st);
+        if (dword && ncol <= 128) {
+            k_update_dw<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h, x);
+            ML_CUDA(cudaGetLastError());
+            return ML_OK;
+        }
         if (tensor && matvec_tc && oz_gemm_ok(ncol))
             return oz_gemm(OzMat{Q, 0, 1, ldq}, ncol, h, 1, 1, 0, 1, OzOut{x, 0, 1, n}, lay0.as<int>(), 1, n, true, st);
         k_update<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h, x);
@@ -874,7 +971,8 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
     const int ncv = (int)std::min<int64_t>(std::max(2 * k + 1, 20), n - 1);
     const int kkeep = std::min(ncv - 2, std::max(k + 1, (ncv + k) / 2));
     Workspace ws;
-    ML_TRY(ws.init(n, ncv + 1, st, tensor));
+    const int kind = tensor ? 2 : (dense_products_kind() == 1 ? 1 : 0);
+    ML_TRY(ws.init(n, ncv + 1, st, kind));
     if (tensor) ML_TRY(oz_reset_error(st));
     DevBuf Qb, Qtmp, wv, Sd;
     ML_TRY(Qb.ensure((size_t)n * (ncv + 1) * 8));
@@ -972,7 +1070,10 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         ML_CUDA(cudaMemcpyAsync(Sd.p, Sk.data(), Sk.size() * 8, cudaMemcpyHostToDevice, st));
         {
             ProfScope pr("ritz", st);
-            if (ws.tensor && oz_gemm_ok(ncv)) {
+            if (ws.dword && (size_t)ncv * keep * sizeof(float2) <= 48 * 1024) {
+                k_combine_dw<<<nb, 256, (size_t)ncv * keep * sizeof(float2), st>>>(Q, n, n, ncv, Sd.as<double>(), keep,
+                                                                                   Qtmp.as<double>(), n);
+            } else if (ws.tensor && oz_gemm_ok(ncv)) {
                 // Sk is ncv x keep column-major: M[r, j] = Sk[j * ncv + r]
                 ML_TRY(oz_gemm(OzMat{Q, 0, 1, n}, ncv, Sd.as<double>(), 1, ncv, 0, keep, OzOut{Qtmp.as<double>(), 0, 1, n},
                                ws.lay0.as<int>(), 1, n, false, st));

@@ -33,6 +33,7 @@
 #include <string>
 #include <vector>
 
+#include "dword.cuh"
 #include "ml_internal.h"
 
 namespace ml {
@@ -89,6 +90,119 @@ __global__ void __launch_bounds__(256) k_lgram(LMat A, int a0, int rc, LMat B, i
     for (int q = 0; q < 3; ++q) {
         const int e = threadIdx.x + q * 256;
         if (e < nout) part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * nout + e] = acc[q];
+    }
+}
+
+// ---- double-word versions (FP32 pipes, ~47 bits) of the basis products
+// k_lgram_dw: as k_lgram.  The CTA's outputs (r, s) are grouped in blocks of
+// 4 r x 2 s; thread t works on block t % nblk over the rows of each staged
+// chunk with index = t / nblk (mod the number of phases), and the phases'
+// partial sums are added in a fixed order at the end.
+constexpr int kDwRows = 32;
+__global__ void __launch_bounds__(256) k_lgram_dw(LMat A, int a0, int rc, LMat B, int b0, int cb,
+                                                 const int *__restrict__ lay, int64_t n, double *part)
+{
+    __shared__ float2 As[kDwRows][kMaxLd + 1];
+    __shared__ float2 Bs[kDwRows][kMaxBlk + 1];
+    __shared__ double red[kGramOut];
+    const int t = lay[blockIdx.y];
+    const double *Ab = A.at(t), *Bb = B.at(t);
+    const int rb = (rc + 3) / 4, sb = (cb + 1) / 2, nblk = rb * sb;
+    const int phases = max(1, (int)blockDim.x / nblk);
+    const int blk = threadIdx.x % nblk, ph = threadIdx.x / nblk;
+    const bool active = ph < phases && (int)threadIdx.x < nblk * phases;
+    const int r0 = (blk / sb) * 4, s0 = (blk % sb) * 2;
+    float2 acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
+    for (int64_t i0 = (int64_t)blockIdx.x * kDwRows; i0 < n; i0 += (int64_t)gridDim.x * kDwRows) {
+        const int rows = (int)min((int64_t)kDwRows, n - i0);
+        for (int e = threadIdx.x; e < kDwRows * rc; e += blockDim.x) {
+            const int rr = e / rc, cc = e - rr * rc;
+            As[rr][cc] = rr < rows ? dword::from_double(Ab[(i0 + rr) * A.ld + a0 + cc]) : make_float2(0.0f, 0.0f);
+        }
+        for (int e = threadIdx.x; e < kDwRows * cb; e += blockDim.x) {
+            const int rr = e / cb, cc = e - rr * cb;
+            Bs[rr][cc] = rr < rows ? dword::from_double(Bb[(i0 + rr) * B.ld + b0 + cc]) : make_float2(0.0f, 0.0f);
+        }
+        __syncthreads();
+        if (active)
+            for (int rr = ph; rr < kDwRows; rr += phases) {
+                float2 a[4], b[2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = r0 + i < rc ? As[rr][r0 + i] : make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) b[j] = s0 + j < cb ? Bs[rr][s0 + j] : make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) dword::fma_acc(acc[i][j], a[i], b[j]);
+            }
+        __syncthreads();
+    }
+    // phases -> one partial per output, summed in phase order
+    const int nout = rc * cb;
+    for (int e = threadIdx.x; e < nout; e += blockDim.x) red[e] = 0.0;
+    __syncthreads();
+    for (int p = 0; p < phases; ++p) {
+        if (active && ph == p)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    if (r0 + i < rc && s0 + j < cb) red[(r0 + i) * cb + s0 + j] += dword::to_double(acc[i][j]);
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nout; e += blockDim.x)
+        part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * nout + e] = red[e];
+}
+
+// k_lgemm_dw: as k_lgemm (B_t[i, b0 + s] (-)= sum_r A_t[i, a0 + r] M_y[r, s]);
+// one row per thread with its cb accumulators, the chunk of rows staged in
+// double-word and M (double-word) read by all threads alike
+constexpr int kDwGemmRows = 128;
+// (M_y row-major with leading dimension ldm: M_y = M + y * rc * ldm, columns
+// 0..cb-1 of it; cb <= 8)
+__global__ void __launch_bounds__(kDwGemmRows) k_lgemm_dw(LMat A, int a0, int rc, const double *__restrict__ M, int ldm,
+                                                         LMat B, int b0, int cb, const int *__restrict__ lay,
+                                                         int64_t n, int sub)
+{
+    extern __shared__ float2 dsm[];
+    float2 *Ms = dsm;                          // rc * cb
+    float2 *As = dsm + rc * cb;                // kDwGemmRows x (rc + 1)
+    const int t = lay[blockIdx.y];
+    const double *Ab = A.at(t);
+    double *Bb = B.at(t);
+    const double *My = M + (int64_t)blockIdx.y * rc * ldm;
+    for (int e = threadIdx.x; e < rc * cb; e += blockDim.x) {
+        const int r = e / cb, s2 = e - r * cb;
+        Ms[e] = dword::from_double(My[(int64_t)r * ldm + s2]);
+    }
+    const int lda = rc + 1;
+    for (int64_t i0 = (int64_t)blockIdx.x * kDwGemmRows; i0 < n; i0 += (int64_t)gridDim.x * kDwGemmRows) {
+        const int rows = (int)min((int64_t)kDwGemmRows, n - i0);
+        __syncthreads();   // the previous chunk is no longer read (and Ms is ready)
+        for (int e = threadIdx.x; e < rows * rc; e += blockDim.x) {
+            const int rr = e / rc, cc = e - rr * rc;
+            As[rr * lda + cc] = dword::from_double(Ab[(i0 + rr) * A.ld + a0 + cc]);
+        }
+        __syncthreads();
+        const int rr = threadIdx.x;
+        if (rr < rows) {
+            float2 acc[kMaxBlk];
+#pragma unroll
+            for (int s = 0; s < kMaxBlk; ++s) acc[s] = make_float2(0.0f, 0.0f);
+            for (int r = 0; r < rc; ++r) {
+                const float2 a = As[rr * lda + r];
+#pragma unroll
+                for (int s = 0; s < kMaxBlk; ++s)
+                    if (s < cb) dword::fma_acc(acc[s], a, Ms[r * cb + s]);
+            }
+            double *bp = Bb + (i0 + rr) * B.ld + b0;
+#pragma unroll
+            for (int s = 0; s < kMaxBlk; ++s)
+                if (s < cb) bp[s] = sub ? bp[s] - dword::to_double(acc[s]) : dword::to_double(acc[s]);
+        }
     }
 }
 
@@ -318,7 +432,8 @@ struct Solver {
     DescSlot desc;
     int64_t hstride = 0, rstride = 0;   // per layer record strides (doubles)
     int nslots = 0;                     // active layers
-    bool tensor = true;                 // dense products of the basis on the tensor cores
+    bool tensor = false;                // products of the basis on the tensor cores
+    bool dword = false;                 // products of the basis in double-word FP32
     std::vector<int> lay;               // slot -> layer
 
     LMat q(int which) const { return LMat{Q[which].as<double>(), n * ldq, ldq}; }
@@ -342,7 +457,10 @@ struct Solver {
         const int nout = rc * cb;
         if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
         int nb = nbx;
-        if (basis && tensor && oz_gram_ok(rc, cb)) {
+        if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) {
+            ProfScope pr("dots", st);
+            k_lgram_dw<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>());
+        } else if (basis && tensor && oz_gram_ok(rc, cb)) {
             ProfScope pr("dots", st);
             nb = oz_gram_blocks(nslots, n);
             ML_TRY(oz_gram(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, OzMat{B.base + b0, B.stride, B.ld, 1}, cb,
@@ -365,6 +483,16 @@ struct Solver {
                    const char *family = "update")
     {
         ProfScope pr(family, st);
+        if (basis && dword) {
+            for (int j0 = 0; j0 < cb; j0 += kMaxBlk) {
+                const int w = std::min(kMaxBlk, cb - j0);
+                const size_t smem = ((size_t)rc * w + (size_t)kDwGemmRows * (rc + 1)) * sizeof(float2);
+                k_lgemm_dw<<<dim3(nbx, nslots), kDwGemmRows, smem, st>>>(A, a0, rc, M + j0, cb, B, b0 + j0, w,
+                                                                        layd.as<int>(), n, sub ? 1 : 0);
+            }
+            ML_CUDA(cudaGetLastError());
+            return ML_OK;
+        }
         if (basis && tensor && oz_gemm_ok(rc))
             return oz_gemm(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, M, cb, 1, (int64_t)rc * cb, cb,
                            OzOut{B.base + b0, B.stride, B.ld, 1}, layd.as<int>(), nslots, n, sub, st);
@@ -476,6 +604,7 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
 {
     Solver S;
     S.tensor = tensor;
+    S.dword = !tensor && dense_products_kind() == 1;
     if (tensor) ML_TRY(oz_reset_error(st));
     S.L = L;
     S.T = T;
@@ -516,6 +645,8 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
     {
         const size_t smax = ((size_t)kMaxLd * kMaxLd + (size_t)kRows * (kMaxLd + 1)) * sizeof(double);
         ML_CUDA(cudaFuncSetAttribute(k_lgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+        const size_t sdw = ((size_t)kMaxLd * kMaxLd + (size_t)kDwGemmRows * (kMaxLd + 1)) * sizeof(float2);
+        ML_CUDA(cudaFuncSetAttribute(k_lgemm_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdw));
     }
     S.lay.resize(T);
     for (int t = 0; t < T; ++t) S.lay[t] = t;

@@ -109,8 +109,11 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     fa.L2 = g.L[2];
     {
         ProfScope pr("fold", st);
-        if (f32) k_fold<T, D><<<(int)g.nbins(), 256, 0, st>>>(fa);
-        else k_fold<T, D, float2><<<(int)g.nbins(), 256, 0, st>>>(fa);
+        int64_t cells = 1;
+        for (int a = 0; a < D; ++a) cells *= g.B;
+        const int ch = fold_chunks(g.nbins(), cells * nv, sm_count());
+        if (f32) k_fold<T, D><<<(int)(g.nbins() * ch), 256, 0, st>>>(fa, ch);
+        else k_fold<T, D, float2><<<(int)(g.nbins() * ch), 256, 0, st>>>(fa, ch);
     }
     ML_CUDA(cudaGetLastError());
     // ---- transforms (FP64 form: double-word grids, matrices and multiplier)
@@ -428,7 +431,14 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     }
     {
         ProfScope pr("fold", st);
-        k_fold_batch<T_, D><<<dim3(max_nbins, T), 256, 0, st>>>(reinterpret_cast<FoldArgs *>(d + o_fa));
+        int64_t max_cells = 1;
+        for (int t = 0; t < T; ++t) {
+            int64_t c = 1;
+            for (int a = 0; a < D; ++a) c *= L[t]->g.B;
+            max_cells = std::max(max_cells, c);
+        }
+        const int ch = fold_chunks((int64_t)max_nbins * T, max_cells * NV, sm_count());
+        k_fold_batch<T_, D><<<dim3(max_nbins * ch, T), 256, 0, st>>>(reinterpret_cast<FoldArgs *>(d + o_fa), ch);
     }
     for (int sidx = 0; sidx < 2 * D; ++sidx) {
         if (sidx == D) {

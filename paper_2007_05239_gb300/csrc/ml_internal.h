@@ -64,7 +64,8 @@ ml_status oz_gram(OzMat A, int rc, OzMat B, int cb, const int *lay, int nslots, 
 // Y_t[:, j] (-)= sum_r A_t[:, r] M_y[r, j], M_y[r, j] = M[y * mslot + r * mrs + j * mcs]
 ml_status oz_gemm(OzMat A, int rc, const double *M, int64_t mrs, int64_t mcs, int64_t mslot, int cb, OzOut Y,
                   const int *lay, int nslots, int64_t n, bool sub, cudaStream_t st);
-// the solvers' dense products on the tensor cores (default) or the FP64 pipe
+// the solvers' products of the basis: 0 FP64 pipe, 1 double-word FP32 (default), 2 tensor cores
+int dense_products_kind();
 bool oz_enabled();
 ml_status oz_reset_error(cudaStream_t st);
 ml_status oz_read_error(int *flags, cudaStream_t st);

@@ -538,13 +538,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(OzMat A, int rc, cons
 }  // namespace
 
 // ------------------------------------------------------------------ host
-// Off by default: on GB300 the products of these shapes (a basis of <= 48
-// columns against blocks of <= 8 vectors) run no faster on the tensor cores
-// than on the FP64 pipe, because forming the eight slices of every FP64
-// element costs more issue slots than the FP64 multiply-adds it replaces.
-static std::atomic<bool> g_oz_on{false};
+// The solvers' products of the basis: 0 on the FP64 pipe, 1 in double-word
+// arithmetic on the FP32 pipes (the default), 2 on the tensor cores through
+// the slices above.  On GB300 the tensor-core path is not faster for these
+// shapes (a basis of <= 48 columns against blocks of <= 8 vectors): forming
+// the eight slices of every FP64 element costs more issue slots than the
+// FP64 multiply-adds it replaces.
+static std::atomic<int> g_dense_kind{1};
 
-bool oz_enabled() { return g_oz_on.load(std::memory_order_relaxed); }
+int dense_products_kind() { return g_dense_kind.load(std::memory_order_relaxed); }
+bool oz_enabled() { return dense_products_kind() == 2; }
 
 bool oz_gram_ok(int rc, int cb) { return rc >= 1 && rc <= kOzMaxRc && cb >= 1 && cb <= 8; }
 bool oz_gemm_ok(int rc) { return rc >= 1 && rc <= kOzMaxRc; }
@@ -629,9 +632,10 @@ ml_status oz_read_error(int *flags, cudaStream_t st)
 
 }  // namespace ml
 
-extern "C" ml_status ml_set_tensor_products(int on)
+extern "C" ml_status ml_set_dense_products(int kind)
 {
-    ml::g_oz_on.store(on != 0);
+    if (kind < 0 || kind > 2) return ml::fail(ML_ERR_ARG, "kind must be 0 (FP64), 1 (double-word) or 2 (tensor cores)");
+    ml::g_dense_kind.store(kind);
     return ML_OK;
 }
 

@@ -173,27 +173,34 @@ __global__ void k_first_tap_range(const double *__restrict__ X, int64_t n, Torus
         }
 }
 
-// local coordinate relative to the point's bin origin, and the bin key
+// local coordinate relative to the point's bin origin, and the sort key:
+// bin * cells + the first-tap cell within the bin (cells = B^d), so that the
+// points of a bin are ordered by cell and the points a warp spreads together
+// usually share their taps (cells = 1: by bin only)
 struct KeyArgs {
     TorusMap tm;
     int s0[3];
     int B;
     int nb0, nb1;
+    uint32_t cells;
 };
 
 __global__ void k_keys(const double *__restrict__ X, int64_t n, KeyArgs ka, double *urel, uint32_t *keys, int *idx)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int bcoord[3] = {0, 0, 0};
+        int bcoord[3] = {0, 0, 0}, ccoord[3] = {0, 0, 0};
         for (int a = 0; a < ka.tm.d; ++a) {
             const double U = ka.tm.n_os * (ka.tm.s * (X[i * ka.tm.d + a] - ka.tm.c[a]) + 0.5);
             const double u = U - ka.s0[a];                        // local active-grid coordinate
             const long long f0 = (long long)floor(u - 0.5 * ka.tm.W) + 1;  // >= 0 by construction of s0
             const int b = (int)(f0 / ka.B);
             bcoord[a] = b;
+            ccoord[a] = (int)(f0 - (long long)b * ka.B);
             urel[i * ka.tm.d + a] = u - (double)b * ka.B;
         }
-        keys[i] = (uint32_t)((bcoord[2] * ka.nb1 + bcoord[1]) * ka.nb0 + bcoord[0]);
+        const uint32_t bin = (uint32_t)((bcoord[2] * ka.nb1 + bcoord[1]) * ka.nb0 + bcoord[0]);
+        const uint32_t cell = ka.cells > 1 ? (uint32_t)((ccoord[2] * ka.B + ccoord[1]) * ka.B + ccoord[0]) : 0u;
+        keys[i] = bin * ka.cells + cell;
         idx[i] = (int)i;
     }
 }
@@ -207,10 +214,10 @@ __global__ void k_gather_coords(const double *__restrict__ urel, const int *__re
     }
 }
 
-__global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, int *counts)
+__global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, uint32_t cells, int *counts)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&counts[keys[i]], 1);
+        atomicAdd(&counts[keys[i] / cells], 1);
 }
 
 // FP64 window weights of every point (plan time), stored as double-word
@@ -767,13 +774,24 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ka.B = g.B;
     ka.nb0 = g.nb[0];
     ka.nb1 = g.nb[1];
+    const int64_t nbins = g.nbins();
+    {
+        // FP32 layers of several bins are ordered by cell within each bin (the
+        // warp-summed spreading of points that share their taps).  A layer whose
+        // grid is one tile keeps its points in input order (the batched
+        // interpolation sums all such layers point by point in that order); the
+        // FP64 form keeps the input order within a bin (its (point, slab) items
+        // would meet the same cells in neighbouring lanes)
+        int64_t cells = 1;
+        for (int a = 0; a < d; ++a) cells *= g.B;
+        ka.cells = (p->prec == ML_F32 && nbins > 1 && nbins * cells < ((int64_t)1 << 32)) ? (uint32_t)cells : 1u;
+    }
     { ProfScope pr_("plan", st);
     k_keys<<<grid_for(n), 256, 0, st>>>(points, n, ka, urel.as<double>(), keys.as<uint32_t>(), idx.as<int>());
     }
     ML_CUDA(cudaGetLastError());
-    const int64_t nbins = g.nbins();
     int bits = 0;
-    while ((1LL << bits) < nbins) ++bits;
+    while ((1LL << bits) < nbins * (int64_t)ka.cells) ++bits;
     int *sorted_idx = nullptr;
     ML_TRY(radix_sort(keys.as<uint32_t>(), idx.as<int>(), keys2.as<uint32_t>(), idx2.as<int>(), n, bits, st,
                       &sorted_idx));
@@ -809,7 +827,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_TRY(counts.ensure((size_t)nbins * 4));
     ML_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)nbins * 4, st));
     { ProfScope pr_("plan", st);
-    k_bin_count<<<grid_for(n), 256, 0, st>>>(sorted_keys, n, counts.as<int>());
+    k_bin_count<<<grid_for(n), 256, 0, st>>>(sorted_keys, n, ka.cells, counts.as<int>());
     }
     ML_CUDA(cudaGetLastError());
     std::vector<int> hc(nbins);

@@ -124,15 +124,16 @@ def test_per_factor_margins_exclude_cut_bandwidths():
 
 def test_learned_choice_gains_over_fixed_rule():
     # what the trained network gains: trained on the method's own error and
-    # time measurements of 200 clouds (10 candidates each, 10 % of the clouds
-    # held out to calibrate one error margin per bandwidth factor), then on 24
-    # unseen clouds every learned choice must meet the 1e-4 target (judged by
-    # the direct sum on sampled rows) and the products must be faster than
-    # with the fixed rule (geometric mean of the time ratios below 1)
-    X, Y, ids = paramnet.make_dataset(0, 200, 10, "f32", 1e-4)
-    fit = ids < 180
+    # time measurements of 300 clouds (10 candidates each, 10 % of the clouds
+    # held out to calibrate one error margin per bandwidth factor at the 0.999
+    # quantile of the held-out residuals), then on 24 unseen clouds every
+    # learned choice must meet the 1e-4 target (judged by the direct sum on
+    # sampled rows) and the products must be faster than with the fixed rule
+    # (geometric mean of the time ratios below 1)
+    X, Y, ids = paramnet.make_dataset(0, 300, 10, "f32", 1e-4)
+    fit = ids < 270
     model, losses, _ = paramnet.train(X[fit], Y[fit], epochs=3000)
-    margins = paramnet.calibrate_margins(model, X[~fit], Y[~fit], 0.995)
+    margins = paramnet.calibrate_margins(model, X[~fit], Y[~fit], 0.999)
     model.set_margins(margins)
     ev = paramnet.evaluate(model, 6000, 24, "f32", 1e-4, margin=max(margins))
     assert ev["success_fixed"] == 1.0

@@ -5,7 +5,7 @@ references in extended precision, entry by entry within a few units of 2^-53
 times sum_i |a_i||b_i| (the accuracy of an FP64 product) plus the resolution
 of A's fixed scale (64-bit fixed point below 2: 2^-62 per unit of the other
 factor), and the eigensolvers' results with the products on the tensor
-cores against the same solves on the FP64 pipe."""
+cores and in double-word FP32 against the same solves on the FP64 pipe."""
 import numpy as np
 import pytest
 import torch
@@ -94,18 +94,21 @@ def test_operand_beyond_the_fixed_scale_is_refused():
         ml.ml_block_gram(dev(np.ones((100, 49))), B[:100])   # rc beyond 48
 
 
-def _solve_both(fn):
-    out = []
-    for on in (True, False):
-        ml.ml_set_tensor_products(on)
+def _solve_kinds(fn):
+    out = {}
+    for kind in ("fp64", "dword", "tensor"):
+        ml.ml_set_dense_products(kind)
         try:
-            out.append(fn())
+            out[kind] = fn()
         finally:
-            ml.ml_set_tensor_products(False)
+            ml.ml_set_dense_products("dword")
     return out
 
 
-def test_eigensolvers_same_results_on_both_paths():
+def test_eigensolvers_same_results_for_every_kind_of_product():
+    # the basis products on the FP64 pipe, in double-word FP32 (the default)
+    # and on the tensor cores: the same eigenpairs to well within the
+    # eigensolver's tolerance
     n = 6000
     layers = [workloads.uniform_cube(n, 3, seed=500), workloads.uniform_cube(n, 2, seed=501)]
     plans = [ml.ml_fastsum_plan(dev(L), s, prec="f64", target_rel_err=1e-12) for L, s in zip(layers, [0.1, 0.08])]
@@ -122,8 +125,12 @@ def test_eigensolvers_same_results_on_both_paths():
         return lam, V.cpu().numpy().reshape(2, k, n), st
 
     for fn in (combined, per_layer):
-        (l1, v1, s1), (l2, v2, s2) = _solve_both(fn)
-        assert s1 == ml.ML_OK and s2 == ml.ML_OK
-        assert np.abs(l1 - l2).max() <= 1e-12, (l1, l2)
-        # the same Krylov process up to rounding: vectors agree closely
-        assert np.abs(np.abs((v1 * v2).sum(-1)) - 1).max() <= 1e-9
+        res = _solve_kinds(fn)
+        l0, v0, s0 = res["fp64"]
+        assert s0 == ml.ML_OK
+        for kind in ("dword", "tensor"):
+            l1, v1, s1 = res[kind]
+            assert s1 == ml.ML_OK
+            assert np.abs(l1 - l0).max() <= 1e-12, (kind, l1, l0)
+            # the same Krylov process up to rounding: the vectors agree closely
+            assert np.abs(np.abs((v1 * v0).sum(-1)) - 1).max() <= 1e-9, kind
