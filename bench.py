@@ -565,7 +565,7 @@ def run_params_extra():
     """The learned NFFT-parameter workload: the MLP trained on 5000 (cloud,
     candidate) -> (error, time) samples the method generates (500 clouds, 10
     candidates each, 10 % of the clouds held out for the per-factor error
-    margins), then the learned choice against the fixed rule on 200 unseen
+    margins at the 0.999 quantile), then the learned choice against the fixed rule on 200 unseen
     clouds at target 1e-4 (errors judged by the direct sum on sampled rows)."""
     from paper_2007_05239_gb300 import paramnet
     t0 = time.perf_counter()
@@ -573,7 +573,7 @@ def run_params_extra():
     t1 = time.perf_counter()
     fit = ids < 450
     model, losses, _ = paramnet.train(X[fit], Y[fit], epochs=4000)
-    margins = paramnet.calibrate_margins(model, X[~fit], Y[~fit], 0.995)
+    margins = paramnet.calibrate_margins(model, X[~fit], Y[~fit], 0.999)
     model.set_margins(margins)
     t2 = time.perf_counter()
     ev = paramnet.evaluate(model, 5000, 200, "f32", 1e-4, margin=max(margins))

@@ -143,6 +143,7 @@ __device__ __forceinline__ int window_row(double x, double m2, double b, double 
 struct SpreadArgs {
     const int *sub_bin, *sub_start, *sub_count;
     const int *perm;
+    const int *sidx;         // null, or the spreading order of the sorted positions (one-tile FP32 layers)
     const void *coords;      // T [n][D]
     const float2 *wts;       // FP64 form: window weights [n][D][W] as double-word pairs
     const int *offs;         // FP64 form: first tap per dim, packed o0 | o1 << 10 | o2 << 20
@@ -360,7 +361,8 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     float lsum[NV], lmax[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) lsum[c] = lmax[c] = 0.0f;
-    for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
+    for (int ip = start + threadIdx.x; ip < start + cnt; ip += blockDim.x) {
+        const int i = a.sidx ? a.sidx[ip] : ip;
         const int orig = a.perm[i];
         const double ds = a.dinv ? a.dinv[i] : 1.0;
 #pragma unroll
@@ -406,7 +408,8 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     // adds its own point's taps
     for (int g0 = (threadIdx.x & ~31); g0 < cnt; g0 += blockDim.x) {
         const bool valid = g0 + lane < cnt;
-        const int i = start + min(g0 + lane, cnt - 1);
+        const int ip = start + min(g0 + lane, cnt - 1);
+        const int i = a.sidx ? a.sidx[ip] : ip;
         const int orig = a.perm[i];
         const double ds = a.dinv ? a.dinv[i] : 1.0;
         float u[NV];

@@ -232,7 +232,26 @@ __global__ void __launch_bounds__(kDotThreads) k_dots_dw(const double *__restric
         float2 acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.0f, 0.0f);
-        for (int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; r < n; r += (int64_t)gridDim.x * kDotThreads) {
+        // two rows per iteration: both rows' loads are in flight together
+        const int64_t step = (int64_t)gridDim.x * kDotThreads;
+        int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x;
+        for (; r + step < n; r += 2 * step) {
+            double q0[8], q1[8];
+            const double x0 = x[r], x1 = x[r + step];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                q0[k] = c0 + k < ncol ? Q[(int64_t)(c0 + k) * ldq + r] : 0.0;
+                q1[k] = c0 + k < ncol ? Q[(int64_t)(c0 + k) * ldq + r + step] : 0.0;
+            }
+            const float2 xr0 = dword::from_double(x0), xr1 = dword::from_double(x1);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + k < ncol) {
+                    dword::fma_acc(acc[k], dword::from_double(q0[k]), xr0);
+                    dword::fma_acc(acc[k], dword::from_double(q1[k]), xr1);
+                }
+        }
+        if (r < n) {
             const float2 xr = dword::from_double(x[r]);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(256) k_update_dw(const double *__restrict__ Q,
 }
 
 // out[:, i] = Q[:, 0:ncv] S[:, i] for i < kk (S column-major ncv x kk), in
-// double-word; each row's accumulators for up to 32 columns in registers
+// double-word; each row's accumulators for 16 columns at a time in registers
 __global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv,
                                                    const double *__restrict__ S, int kk, double *out, int64_t ldo)
 {
@@ -280,19 +299,19 @@ __global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q
     }
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        for (int i0 = 0; i0 < kk; i0 += 32) {
-            float2 acc[32];
+        for (int i0 = 0; i0 < kk; i0 += 16) {
+            float2 acc[16];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) acc[k] = make_float2(0.0f, 0.0f);
+            for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.0f, 0.0f);
             for (int c = 0; c < ncv; ++c) {
                 const float2 q = dword::from_double(Q[(int64_t)c * ldq + r]);
                 const float2 *srow = ss + (int64_t)c * kk + i0;
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
+                for (int k = 0; k < 16; ++k)
                     if (i0 + k < kk) dword::fma_acc(acc[k], q, srow[k]);
             }
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
+            for (int k = 0; k < 16; ++k)
                 if (i0 + k < kk) out[(int64_t)(i0 + k) * ldo + r] = dword::to_double(acc[k]);
         }
     }
@@ -368,25 +387,31 @@ struct Workspace {
         dword = kind == 1;
         nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 456));
         const int nb_oz = oz_gram_blocks(1, n);
-        ML_TRY(part.ensure((size_t)std::max(nblk, nb_oz) * std::max(maxcol, 1) * sizeof(double)));
+        ML_TRY(part.ensure((size_t)std::max(std::max(nblk, nb_oz), dw_blocks()) * std::max(maxcol, 1) * sizeof(double)));
         ML_TRY(hdev.ensure((size_t)(2 * maxcol + 8) * sizeof(double)));
         ML_TRY(scal.ensure(64 * sizeof(double)));
         ML_TRY(lay0.ensure(sizeof(int)));
         ML_CUDA(cudaMemsetAsync(lay0.p, 0, sizeof(int), st));
         return ML_OK;
     }
+    // blocks of the double-word Gram: several per SM (its rows are latency-bound)
+    int dw_blocks() const
+    {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((n + 2 * kDotThreads - 1) / (2 * kDotThreads), sm_count() * 8));
+    }
     // out (device, ncol) = Q[:, 0:ncol]^T x for the orthonormal basis Q (column
     // major) and a vector with |x_i| < 2: on the tensor cores when enabled
     ml_status basis_dots(const double *Q, int64_t ldq, int ncol, const double *x, double *out)
     {
         if (dword) {
+            const int nb = dw_blocks();
             {
                 ProfScope pr("dots", st);
-                k_dots_dw<<<nblk, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
+                k_dots_dw<<<nb, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
             }
             {
                 ProfScope pr("dots_reduce", st);
-                k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nblk, ncol, out);
+                k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nb, ncol, out);
             }
             ML_CUDA(cudaGetLastError());
             return ML_OK;

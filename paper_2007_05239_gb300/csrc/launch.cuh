@@ -45,6 +45,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.sub_start = p->sub_start.as<int>();
     sa.sub_count = p->sub_count.as<int>();
     sa.perm = p->perm.as<int>();
+    sa.sidx = p->sidx.as<int>();
     sa.coords = p->coords.p;
     sa.wts = p->wts.as<float2>();
     sa.offs = p->offs.as<int>();
@@ -298,6 +299,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         a.sub_start = p->sub_start.as<int>();
         a.sub_count = p->sub_count.as<int>();
         a.perm = p->perm.as<int>();
+        a.sidx = p->sidx.as<int>();
         a.coords = p->coords.p;
         a.dinv = o.normalized ? p->dinv.as<double>() : nullptr;
         a.X = vt.X;

@@ -167,6 +167,8 @@ struct ml_plan_s {
     // device data (sorted order unless noted)
     ml::DevBuf perm;      // int32 n: sorted position -> input index
     ml::DevBuf coords;    // T n*d local grid coordinates
+    ml::DevBuf sidx;      // int32 n (FP32 layers of one tile): the spreading order of the
+                          // sorted positions, by first-tap cell (the others keep input order)
     ml::DevBuf wts;       // FP64 form: float2 [n][d][W] window weights (double-word pairs)
     ml::DevBuf offs;      // FP64 form: int n packed first taps o0 | o1 << 10 | o2 << 20
     ml::DevBuf deg;       // double n: degrees

@@ -833,6 +833,30 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     std::vector<int> hc(nbins);
     ML_CUDA(cudaMemcpyAsync(hc.data(), counts.p, (size_t)nbins * 4, cudaMemcpyDeviceToHost, st));
     ML_CUDA(cudaStreamSynchronize(st));
+    if (p->prec == ML_F32 && nbins == 1 && ka.cells == 1) {
+        // one tile: the points stay in input order (perm is the identity) and the
+        // spreading visits them in the order of their first-tap cells
+        int64_t cells = 1;
+        for (int a = 0; a < d; ++a) cells *= g.B;
+        if (cells < ((int64_t)1 << 32)) {
+            KeyArgs kc = ka;
+            kc.cells = (uint32_t)cells;
+            { ProfScope pr_("plan", st);
+            k_keys<<<grid_for(n), 256, 0, st>>>(points, n, kc, urel.as<double>(), keys.as<uint32_t>(), idx.as<int>());
+            }
+            ML_CUDA(cudaGetLastError());
+            int cbits = 0;
+            while ((1LL << cbits) < cells) ++cbits;
+            int *cell_idx = nullptr;
+            ML_TRY(radix_sort(keys.as<uint32_t>(), idx.as<int>(), keys2.as<uint32_t>(), idx2.as<int>(), n, cbits, st,
+                              &cell_idx));
+            ML_TRY(p->sidx.ensure((size_t)n * 4));
+            { ProfScope pr_("plan", st);
+            k_copy_int<<<grid_for(n), 256, 0, st>>>(cell_idx, p->sidx.as<int>(), n);
+            }
+            ML_CUDA(cudaGetLastError());
+        }
+    }
     std::vector<int> sb, ss, sc, bs(nbins + 1);
     int64_t pos = 0;
     for (int64_t b = 0; b < nbins; ++b) {
@@ -938,7 +962,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
 int64_t ml_plan_s::device_bytes() const
 {
     int64_t t = 0;
-    const ml::DevBuf *bufs[] = {&perm, &coords, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
+    const ml::DevBuf *bufs[] = {&perm, &coords, &sidx, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
                                 &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status, &Wd,
                                 &nf_loc, &nf_orig, &nf_sidx, &nf_start, &nf_task};
@@ -948,7 +972,7 @@ int64_t ml_plan_s::device_bytes() const
 
 static void release_all(ml_plan_s *p)
 {
-    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
+    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->sidx, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
                           &p->stage_y, &p->status, &p->batch_desc, &p->batch_part, &p->Wd, &p->sum_parts};
