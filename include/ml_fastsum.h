@@ -590,8 +590,16 @@ ml_status ml_measure_peak(int what, double *rate, void *stream);
  * was loaded (diagnostics: 0 means every iteration launched eagerly). */
 int64_t ml_graph_replays(void);
 
-/* Release the plan and all device memory it owns.  NULL is accepted. */
+/* Release the plan and all device memory it owns.  NULL is accepted.  Blocks
+ * of 1 MiB and more are kept by the library for later plans and workspaces of
+ * the same device (a per-device cache of at most 64 GiB, filled after a device
+ * synchronisation), so that plans made step after step do not pay for the
+ * driver's allocations; ml_release_cached_memory returns them to the driver. */
 ml_status ml_plan_destroy(ml_plan_t plan);
+
+/* Free the library's cached device blocks of the current device (after a
+ * device synchronisation).  Errors: ML_ERR_CUDA. */
+ml_status ml_release_cached_memory(void);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char *ml_last_error(void);

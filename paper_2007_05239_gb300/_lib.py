@@ -34,7 +34,7 @@ EXPORTS = ["ml_fastsum_plan", "ml_fastsum_plan_ex", "ml_fastsum_plan_autotune", 
            "ml_plan_get_info",
            "ml_plan_copy_table", "ml_plan_destroy", "ml_last_error", "ml_version", "ml_profile_enable",
            "ml_profile_reset", "ml_profile_read", "ml_graph_replays", "ml_measure_peak", "ml_block_gram",
-           "ml_block_update", "ml_set_dense_products"]
+           "ml_block_update", "ml_set_dense_products", "ml_release_cached_memory"]
 
 
 class MLError(RuntimeError):
@@ -163,6 +163,8 @@ def load():
     lib.ml_block_update.restype = ctypes.c_int
     lib.ml_block_update.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    lib.ml_release_cached_memory.restype = ctypes.c_int
+    lib.ml_release_cached_memory.argtypes = []
     lib.ml_set_dense_products.restype = ctypes.c_int
     lib.ml_set_dense_products.argtypes = [ctypes.c_int]
     lib.ml_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
@@ -556,6 +558,11 @@ def ml_block_update(A, M, Y, sub=False, stream=None):
     _check(load().ml_block_update(_ptr_rows(A), n, rc, int(A.stride(0)), _ptr(M), cb, _ptr_rows(Y),
                                   int(Y.stride(0)), 1 if sub else 0, _stream(stream)))
     return Y
+
+
+def ml_release_cached_memory():
+    """Return the library's cached device blocks of the current device to the driver."""
+    _check(load().ml_release_cached_memory())
 
 
 DENSE = {"fp64": 0, "dword": 1, "tensor": 2}

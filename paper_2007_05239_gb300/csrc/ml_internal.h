@@ -72,19 +72,30 @@ ml_status oz_read_error(int *flags, cudaStream_t st);
 
 // ------------------------------------------------------------ device buffer
 // Owns one device allocation (freed on destruction; movable, not copyable).
+// Blocks of 1 MiB and more go back to a per-device cache on release (after a
+// device synchronisation, as cudaFree would imply) and are handed out again
+// by ensure, so that plans made and destroyed step after step do not pay for
+// the driver's allocation and mapping of hundreds of megabytes each time
+// (ml_release_cached_memory returns the cache to the driver).
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    int dev = -1;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), dev(o.dev)
+    {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
     DevBuf &operator=(DevBuf &&o) noexcept
     {
         if (this != &o) {
             release();
             p = o.p;
             bytes = o.bytes;
+            dev = o.dev;
             o.p = nullptr;
             o.bytes = 0;
         }

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -57,11 +59,38 @@ int sm_count()
     return c;
 }
 
+namespace {
+constexpr size_t kCacheMin = (size_t)1 << 20;
+constexpr size_t kCacheCap = (size_t)64 << 30;   // per device
+std::mutex g_cache_mu;
+std::map<int, std::multimap<size_t, void *>> g_cache;
+std::map<int, size_t> g_cache_bytes;
+}  // namespace
+
 ml_status DevBuf::ensure(size_t nbytes)
 {
     if (nbytes <= bytes && p) return ML_OK;
     release();
     if (nbytes == 0) return ML_OK;
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = -1;
+    }
+    if (nbytes >= kCacheMin && d >= 0) {
+        // the smallest cached block of at least nbytes and at most 5/4 of it
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto &m = g_cache[d];
+        auto it = m.lower_bound(nbytes);
+        if (it != m.end() && it->first <= nbytes + nbytes / 4) {
+            p = it->second;
+            bytes = it->first;
+            dev = d;
+            g_cache_bytes[d] -= bytes;
+            m.erase(it);
+            return ML_OK;
+        }
+    }
     cudaError_t e = cudaMalloc(&p, nbytes);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -69,14 +98,49 @@ ml_status DevBuf::ensure(size_t nbytes)
         return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
     }
     bytes = nbytes;
+    dev = d;
     return ML_OK;
 }
 
 void DevBuf::release()
 {
-    if (p) cudaFree(p);
+    if (!p) return;
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = -1;
+    }
+    if (bytes >= kCacheMin && d >= 0 && d == dev) {
+        // no work may still use the block when it is handed out again
+        if (cudaDeviceSynchronize() == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_cache_mu);
+            if (g_cache_bytes[d] + bytes <= kCacheCap) {
+                g_cache[d].insert({bytes, p});
+                g_cache_bytes[d] += bytes;
+                p = nullptr;
+                bytes = 0;
+                return;
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
+    cudaFree(p);
     p = nullptr;
     bytes = 0;
+}
+
+// frees every cached block of the current device
+ml_status release_cached()
+{
+    int d = 0;
+    ML_CUDA(cudaGetDevice(&d));
+    ML_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto &kv : g_cache[d]) cudaFree(kv.second);
+    g_cache[d].clear();
+    g_cache_bytes[d] = 0;
+    return ML_OK;
 }
 
 // ------------------------------------------------------------- reductions
@@ -369,16 +433,36 @@ __global__ void k_copy_int(const int *src, int *dst, int64_t n)
 }
 
 // D^{-1/2} and a validity flag (degree not positive or not finite)
-__global__ void k_dinv(const double *__restrict__ deg, int64_t n, double *dinv, int *bad)
+// D^{-1/2}, the validity flag, and per-block (min, max) of the degrees in
+// range[2 * blockIdx.x] (blockDim.x = 256)
+__global__ void k_dinv(const double *__restrict__ deg, int64_t n, double *dinv, int *bad, double *range)
 {
+    __shared__ double smin[256], smax[256];
+    double lo = INFINITY, hi = -INFINITY;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = deg[i];
+        lo = fmin(lo, v);
+        hi = fmax(hi, v);
         if (!(v > 0.0) || !isfinite(v)) {
             atomicExch(bad, 1);
             dinv[i] = 0.0;
         } else {
             dinv[i] = 1.0 / sqrt(v);
         }
+    }
+    smin[threadIdx.x] = lo;
+    smax[threadIdx.x] = hi;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + k]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + k]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        range[2 * blockIdx.x] = smin[0];
+        range[2 * blockIdx.x + 1] = smax[0];
     }
 }
 
@@ -939,18 +1023,24 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     o.sorted_out = true;
     ML_TRY(apply_layer(p, v, o, st));
     ML_CUDA(cudaMemsetAsync(p->status.p, 0, 4, st));
+    const int dblk = grid_for(n);
+    DevBuf range;
+    ML_TRY(range.ensure((size_t)dblk * 2 * sizeof(double)));
     { ProfScope pr_("plan", st);
-    k_dinv<<<grid_for(n), 256, 0, st>>>(p->deg.as<double>(), n, p->dinv.as<double>(), p->status.as<int>());
+    k_dinv<<<dblk, 256, 0, st>>>(p->deg.as<double>(), n, p->dinv.as<double>(), p->status.as<int>(),
+                                 range.as<double>());
     }
     ML_CUDA(cudaGetLastError());
     int bad = 0;
+    std::vector<double> hr((size_t)dblk * 2);
     ML_CUDA(cudaMemcpyAsync(&bad, p->status.p, 4, cudaMemcpyDeviceToHost, st));
+    ML_CUDA(cudaMemcpyAsync(hr.data(), range.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     ML_CUDA(cudaStreamSynchronize(st));
-    {
-        std::vector<double> hd(n);
-        ML_CUDA(cudaMemcpy(hd.data(), p->deg.p, n * 8, cudaMemcpyDeviceToHost));
-        p->deg_min = *std::min_element(hd.begin(), hd.end());
-        p->deg_max = *std::max_element(hd.begin(), hd.end());
+    p->deg_min = INFINITY;
+    p->deg_max = -INFINITY;
+    for (int b = 0; b < dblk; ++b) {
+        p->deg_min = std::min(p->deg_min, hr[2 * b]);
+        p->deg_max = std::max(p->deg_max, hr[2 * b + 1]);
     }
     // raw products stay available; normalised ones report ML_ERR_DEGREE
     p->deg_ok = !bad;
@@ -1157,3 +1247,5 @@ ml_status ml_plan_copy_table(ml_plan_t p, int which, double *out, int64_t count)
 }
 
 }  // extern "C"
+
+extern "C" ml_status ml_release_cached_memory(void) { return ml::release_cached(); }

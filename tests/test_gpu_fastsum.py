@@ -342,3 +342,28 @@ def test_concurrent_layer_terms_equal_sequential():
         ml.ml_profile_enable(False)
         out.append(Y.cpu())
     assert torch.equal(out[0], out[1])
+
+
+def test_plans_reuse_cached_device_blocks():
+    # a plan destroyed leaves its large blocks in the library's cache; the next
+    # plan of the same size takes them (no new device memory), and releasing
+    # the cache gives the memory back to the driver
+    X = dev(workloads.uniform_cube(400_000, 3, seed=71))
+    ml.ml_release_cached_memory()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    p = ml.ml_fastsum_plan(X, 0.05, prec="f32")
+    owned = p.info["device_bytes"]
+    p.destroy()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 >= owned // 2          # the blocks stay reserved by the cache
+    q = ml.ml_fastsum_plan(X, 0.05, prec="f32")
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 >= free1 - (64 << 20)          # the new plan was served from the cache
+    q.destroy()
+    ml.ml_release_cached_memory()
+    torch.cuda.synchronize()
+    free3, _ = torch.cuda.mem_get_info()
+    assert free3 >= free0 - (64 << 20)
