@@ -752,8 +752,11 @@ EXTRA_WORKLOADS = ["image_voronoi_n1e6_T3", "gmm_n250k_T52_d2"]
 
 # what a step's largest kernel family is, where it is not the product itself
 FAMILY_NOTES = {
-    "dots": "FP64 Gram products of the Lanczos steps (reorthogonalisation), bound by the FP64 pipe or HBM",
-    "update": "FP64 basis updates of the Lanczos steps",
+    "dots": "FP64-class products Q^T x of the Lanczos steps' Gram-Schmidt pass (double-word FP32 by default), "
+            "bound by HBM",
+    "update": "FP64-class basis updates x -= Q h of the Lanczos steps",
+    "dots2": "second Gram-Schmidt pass, run only when the first removed more than half of the norm squared",
+    "update2": "second Gram-Schmidt pass, run only when the first removed more than half of the norm squared",
     "ritz": "Ritz vectors Q S at each restart",
     "plan": "plan set-up of every layer (bounding box, sort, Fourier tables, degrees): chains of small kernels "
             "and host synchronisations; the timed steps build the layers' plans concurrently, so the summed event "

@@ -221,17 +221,61 @@ __global__ void k_combine(const double *__restrict__ Q, int64_t ldq, int64_t n, 
     }
 }
 
-// ---- double-word versions of the basis products (FP32 pipes, ~47 bits)
-// part[blk * ncol + c] = sum over this block's rows of Q[:, c] x (as k_dots)
-__global__ void __launch_bounds__(kDotThreads) k_dots_dw(const double *__restrict__ Q, int64_t ldq, int64_t n,
-                                                         int ncol, const double *__restrict__ x, double *part)
+// ---- products of the basis with one vector: on the FP64 pipe (DW = false)
+// or in double-word FP32 (DW = true, ~47 bits, dword.cuh)
+template <bool DW>
+struct BasisArith;
+template <>
+struct BasisArith<false> {
+    using op_t = double;
+    using acc_t = double;
+    static __device__ __forceinline__ op_t op(double v) { return v; }
+    static __device__ __forceinline__ acc_t zero() { return 0.0; }
+    static __device__ __forceinline__ void mac(acc_t &a, op_t q, op_t x) { a = fma(q, x, a); }
+    static __device__ __forceinline__ double value(acc_t a) { return a; }
+};
+template <>
+struct BasisArith<true> {
+    using op_t = float2;
+    using acc_t = float2;
+    static __device__ __forceinline__ op_t op(double v) { return dword::from_double(v); }
+    static __device__ __forceinline__ acc_t zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ void mac(acc_t &a, op_t q, op_t x) { dword::fma_acc(a, q, x); }
+    static __device__ __forceinline__ double value(acc_t a) { return dword::to_double(a); }
+};
+
+// block sum of one double per thread into *out (all threads call it)
+__device__ __forceinline__ void block_sum_to(double v, double *out)
 {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+// part[blk * nout + c] = sum over this block's rows of col_c(r) x_r, where
+// col_c is Q[:, c] for c < ncol and x itself for c = ncol when self = 1
+// (nout = ncol + self).  When gate is non-null and *gate == 0 the pass was
+// skipped by the device and every block returns at once.
+template <bool DW>
+__global__ void __launch_bounds__(kDotThreads) k_basis_dots(const double *__restrict__ Q, int64_t ldq, int64_t n,
+                                                            int ncol, int self, const double *__restrict__ x,
+                                                            const int *__restrict__ gate, double *part)
+{
+    using A = BasisArith<DW>;
+    if (gate && *gate == 0) return;
     __shared__ double red[kDotThreads / 32][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c0 = 0; c0 < ncol; c0 += 8) {
-        float2 acc[8];
+    const int nout = ncol + self;
+    for (int c0 = 0; c0 < nout; c0 += 8) {
+        typename A::acc_t acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.0f, 0.0f);
+        for (int k = 0; k < 8; ++k) acc[k] = A::zero();
         // two rows per iteration: both rows' loads are in flight together
         const int64_t step = (int64_t)gridDim.x * kDotThreads;
         int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x;
@@ -240,50 +284,109 @@ __global__ void __launch_bounds__(kDotThreads) k_dots_dw(const double *__restric
             const double x0 = x[r], x1 = x[r + step];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                q0[k] = c0 + k < ncol ? Q[(int64_t)(c0 + k) * ldq + r] : 0.0;
-                q1[k] = c0 + k < ncol ? Q[(int64_t)(c0 + k) * ldq + r + step] : 0.0;
+                const int c = c0 + k;
+                q0[k] = c < ncol ? Q[(int64_t)c * ldq + r] : (c < nout ? x0 : 0.0);
+                q1[k] = c < ncol ? Q[(int64_t)c * ldq + r + step] : (c < nout ? x1 : 0.0);
             }
-            const float2 xr0 = dword::from_double(x0), xr1 = dword::from_double(x1);
+            const typename A::op_t xr0 = A::op(x0), xr1 = A::op(x1);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if (c0 + k < ncol) {
-                    dword::fma_acc(acc[k], dword::from_double(q0[k]), xr0);
-                    dword::fma_acc(acc[k], dword::from_double(q1[k]), xr1);
+                if (c0 + k < nout) {
+                    A::mac(acc[k], A::op(q0[k]), xr0);
+                    A::mac(acc[k], A::op(q1[k]), xr1);
                 }
         }
         if (r < n) {
-            const float2 xr = dword::from_double(x[r]);
+            const double x0 = x[r];
+            const typename A::op_t xr = A::op(x0);
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c0 + k < ncol) dword::fma_acc(acc[k], dword::from_double(Q[(int64_t)(c0 + k) * ldq + r]), xr);
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + k;
+                if (c < nout) A::mac(acc[k], A::op(c < ncol ? Q[(int64_t)c * ldq + r] : x0), xr);
+            }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            double v = dword::to_double(acc[k]);
+            double v = A::value(acc[k]);
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) red[warp][k] = v;
         }
         __syncthreads();
-        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < ncol) {
+        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nout) {
             double sacc = 0.0;
             for (int w = 0; w < kDotThreads / 32; ++w) sacc += red[w][threadIdx.x];
-            part[(int64_t)blockIdx.x * ncol + c0 + threadIdx.x] = sacc;
+            part[(int64_t)blockIdx.x * nout + c0 + threadIdx.x] = sacc;
         }
         __syncthreads();
     }
 }
 
-// x -= Q[:, 0:ncol] h, the sum in double-word (h staged once per block)
-__global__ void __launch_bounds__(256) k_update_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
-                                                  const double *__restrict__ h, double *x)
+// x -= Q[:, 0:ncol] h, h staged once per block (dynamic shared memory of
+// ncol operands); with norm_part, also the block's sum of the new x_r^2.
+// Gate as in k_basis_dots.
+template <bool DW>
+__global__ void __launch_bounds__(256) k_basis_update(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
+                                                     const double *__restrict__ h, const int *__restrict__ gate,
+                                                     double *x, double *norm_part)
 {
-    __shared__ float2 hs[128];
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = dword::from_double(h[c]);
+    using A = BasisArith<DW>;
+    if (gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char basis_smem[];
+    auto *hs = reinterpret_cast<typename A::op_t *>(basis_smem);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = A::op(h[c]);
     __syncthreads();
+    double s2 = 0.0;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        float2 acc = make_float2(0.0f, 0.0f);
-        for (int c = 0; c < ncol; ++c) dword::fma_acc(acc, dword::from_double(Q[(int64_t)c * ldq + r]), hs[c]);
-        x[r] -= dword::to_double(acc);
+        typename A::acc_t acc = A::zero();
+        for (int c = 0; c < ncol; ++c) A::mac(acc, A::op(Q[(int64_t)c * ldq + r]), hs[c]);
+        const double v = x[r] - A::value(acc);
+        x[r] = v;
+        s2 = fma(v, v, s2);
+    }
+    if (norm_part) block_sum_to(s2, norm_part + blockIdx.x);
+}
+
+// the three-term part of a Lanczos step: x -= beta qprev (qprev may be
+// null), then the block's sum of qj_r x_r (alpha's partial)
+__global__ void __launch_bounds__(256) k_three_term(const double *__restrict__ qprev, double beta,
+                                                   const double *__restrict__ qj, int64_t n, double *x, double *part)
+{
+    double s = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double v = x[r];
+        if (qprev) {
+            v = fma(-beta, qprev[r], v);
+            x[r] = v;
+        }
+        s = fma(qj[r], v, s);
+    }
+    block_sum_to(s, part + blockIdx.x);
+}
+
+// x -= alpha qj with alpha on the device
+__global__ void k_sub_scaled(const double *__restrict__ alpha, const double *__restrict__ qj, int64_t n, double *x)
+{
+    const double a = *alpha;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        x[r] = fma(-a, qj[r], x[r]);
+}
+
+// one warp: norm2 = total of the partials (fixed order); flag = 1 when the
+// pass removed more than 1 - eta2 of the norm squared it started from
+// (*before2), i.e. the second Gram-Schmidt pass is needed
+__global__ void k_dgks(const double *__restrict__ part, int nblk, const double *__restrict__ before2, double eta2,
+                       double *norm2, int *flag, double *flag_copy)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += part[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+        *norm2 = s;
+        if (flag) {
+            const int f = s < eta2 * *before2 ? 1 : 0;
+            *flag = f;
+            *flag_copy = (double)f;
+        }
     }
 }
 
@@ -377,7 +480,8 @@ struct Workspace {
     // of the instruction's width on padding, so only the Ritz vectors Q S
     // (many columns) take them there
     bool matvec_tc = false;
-    DevBuf part, hdev, scal, lay0;
+    DevBuf part, hdev, scal, lay0, npart, flag;
+    long long second_passes = 0, steps = 0;
 
     ml_status init(int64_t n_, int maxcol, cudaStream_t s, int kind = 0)
     {
@@ -387,8 +491,11 @@ struct Workspace {
         dword = kind == 1;
         nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 456));
         const int nb_oz = oz_gram_blocks(1, n);
-        ML_TRY(part.ensure((size_t)std::max(std::max(nblk, nb_oz), dw_blocks()) * std::max(maxcol, 1) * sizeof(double)));
+        ML_TRY(part.ensure((size_t)std::max(std::max(nblk, nb_oz), dw_blocks()) * (std::max(maxcol, 1) + 1) *
+                           sizeof(double)));
         ML_TRY(hdev.ensure((size_t)(2 * maxcol + 8) * sizeof(double)));
+        ML_TRY(npart.ensure((size_t)std::max(vec_blocks(n), dw_blocks()) * sizeof(double)));
+        ML_TRY(flag.ensure(sizeof(int)));
         ML_TRY(scal.ensure(64 * sizeof(double)));
         ML_TRY(lay0.ensure(sizeof(int)));
         ML_CUDA(cudaMemsetAsync(lay0.p, 0, sizeof(int), st));
@@ -407,7 +514,7 @@ struct Workspace {
             const int nb = dw_blocks();
             {
                 ProfScope pr("dots", st);
-                k_dots_dw<<<nb, kDotThreads, 0, st>>>(Q, ldq, n, ncol, x, part.as<double>());
+                k_basis_dots<true><<<nb, kDotThreads, 0, st>>>(Q, ldq, n, ncol, 0, x, nullptr, part.as<double>());
             }
             {
                 ProfScope pr("dots_reduce", st);
@@ -434,8 +541,9 @@ struct Workspace {
     ml_status basis_update(const double *Q, int64_t ldq, int ncol, const double *h, double *x)
     {
         ProfScope pr("update", st);
-        if (dword && ncol <= 128) {
-            k_update_dw<<<vec_blocks(n), 256, 0, st>>>(Q, ldq, n, ncol, h, x);
+        if (dword) {
+            k_basis_update<true><<<vec_blocks(n), 256, (size_t)ncol * sizeof(float2), st>>>(Q, ldq, n, ncol, h, nullptr,
+                                                                                          x, nullptr);
             ML_CUDA(cudaGetLastError());
             return ML_OK;
         }
@@ -484,6 +592,78 @@ struct Workspace {
         hsum.assign(ncol, 0.0);
         for (int c = 0; c < ncol; ++c) hsum[c] = hh[c] + hh[ncol + c];
         *beta = std::sqrt(std::max(hh[2 * ncol], 0.0));
+        return ML_OK;
+    }
+    // One Lanczos step for column j of the basis, x = Op q_j on entry (FP64
+    // pipe or double-word products; the tensor-core kind uses orthogonalize).
+    // The three-term part first: x -= beta_prev q_{j-1} (when use_prev),
+    // alpha = q_j . x, x -= alpha q_j.  Then one classical Gram-Schmidt pass
+    // against Q[:, 0:j+1], and a second pass only when the first removed more
+    // than half of the norm squared it started from (the criterion of Daniel,
+    // Gragg, Kaufman and Stewart 1976), decided on the device.  x is then
+    // close to orthogonal to the basis before the pass, so the second pass is
+    // rare; without the three-term part the pass would remove the large alpha
+    // component and the criterion would ask for a second pass in nearly every
+    // step.  hsum (j + 1) receives x's coefficients against the columns,
+    // alpha and beta_prev included; beta the norm of x after.
+    ml_status lanczos_step(const double *Q, int64_t ldq, int j, bool use_prev, double beta_prev, double *x,
+                           std::vector<double> &hsum, double *beta)
+    {
+        const int ncol = j + 1;
+        const double *qj = Q + (int64_t)j * ldq;
+        double *h1 = hdev.as<double>();      // ncol coefficients + |x|^2 before the pass
+        double *h2 = h1 + ncol + 1;          // second pass
+        double *sc = h2 + ncol;              // alpha, |x|^2 after pass 1, after pass 2, flag
+        const int nbv = vec_blocks(n), nbd = dw_blocks();
+        int *fl = flag.as<int>();
+        {
+            ProfScope pr("vector", st);
+            k_three_term<<<nbv, 256, 0, st>>>(use_prev ? qj - ldq : nullptr, beta_prev, qj, n, x, npart.as<double>());
+            k_reduce_cols<<<1, 32, 0, st>>>(npart.as<double>(), nbv, 1, sc);
+            k_sub_scaled<<<nbv, 256, 0, st>>>(sc, qj, n, x);
+        }
+        const size_t hsm = (size_t)ncol * (dword ? sizeof(float2) : sizeof(double));
+        for (int pass = 0; pass < 2; ++pass) {
+            double *h = pass == 0 ? h1 : h2;
+            const int *gate = pass == 0 ? nullptr : fl;
+            const int self = pass == 0 ? 1 : 0;
+            // the second pass's kernels are timed under their own names (a skipped
+            // pass costs one early-returning launch each)
+            {
+                ProfScope pr(pass == 0 ? "dots" : "dots2", st);
+                if (dword)
+                    k_basis_dots<true><<<nbd, kDotThreads, 0, st>>>(Q, ldq, n, ncol, self, x, gate, part.as<double>());
+                else
+                    k_basis_dots<false><<<nbd, kDotThreads, 0, st>>>(Q, ldq, n, ncol, self, x, gate, part.as<double>());
+            }
+            {
+                ProfScope pr("dots_reduce", st);
+                k_reduce_cols<<<1, 256, 0, st>>>(part.as<double>(), nbd, ncol + self, h);
+            }
+            {
+                ProfScope pr(pass == 0 ? "update" : "update2", st);
+                if (dword)
+                    k_basis_update<true><<<nbv, 256, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
+                else
+                    k_basis_update<false><<<nbv, 256, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
+                k_dgks<<<1, 32, 0, st>>>(npart.as<double>(), nbv, h1 + ncol, 0.5, sc + 1 + pass,
+                                         pass == 0 ? fl : nullptr, sc + 3);
+            }
+        }
+        ML_CUDA(cudaGetLastError());
+        const int nread = 2 * ncol + 1 + 4;
+        std::vector<double> hh(nread);
+        ML_CUDA(cudaMemcpyAsync(hh.data(), h1, nread * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ML_CUDA(cudaStreamSynchronize(st));
+        const double *r1 = hh.data(), *r2 = r1 + ncol + 1, *rs = r2 + ncol;
+        const bool second = rs[3] != 0.0;
+        hsum.assign(ncol, 0.0);
+        for (int c = 0; c < ncol; ++c) hsum[c] = r1[c] + (second ? r2[c] : 0.0);
+        hsum[j] += rs[0];
+        if (use_prev) hsum[j - 1] += beta_prev;
+        *beta = std::sqrt(std::max(second ? rs[2] : rs[1], 0.0));
+        ++steps;
+        second_passes += second ? 1 : 0;
         return ML_OK;
     }
 };
@@ -1044,7 +1224,10 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         for (int j = kk; j < ncv; ++j) {
             ML_TRY(op(Q + (int64_t)j * n, w));
             ++matvecs;
-            ML_TRY(ws.orthogonalize(Q, n, j + 1, w, h, &beta));
+            if (ws.tensor)
+                ML_TRY(ws.orthogonalize(Q, n, j + 1, w, h, &beta));
+            else
+                ML_TRY(ws.lanczos_step(Q, n, j, j > kk, beta, w, h, &beta));
             for (int i = 0; i <= j; ++i) {
                 if (i < kk && j >= kk && j != kk) continue;  // keep the arrow structure exact
                 Tm[(size_t)i * ncv + j] = h[i];
