@@ -16,25 +16,22 @@
 
 namespace ml {
 
+// FP32 window weights by polynomials (plan-time fit, see window_row_poly):
+// up to kPolyW taps per dimension, degree kPolyTerms - 1 in u, each tap's
+// coefficients in a row of kPolyStride floats (16-byte aligned, zero padded)
+constexpr int kPolyW = 16;
+constexpr int kPolyTerms = 10;
+constexpr int kPolyStride = 12;
+// shared memory for an FP32 spreading tile plus its row-product slots
+constexpr size_t kRowSpreadBudget = 220 * 1024;
+
+
 // ------------------------------------------------------------ window
 // Normalised Kaiser-Bessel window phi_n(t) = sinh(b s)/s / (sinh(b m)/m),
 // s = sqrt(m^2 - t^2), t in [-m, m] (grid units).  norm2 = m e^{-bm}/(1-e^{-2bm}),
 // so phi_n(t) = norm2 (e^{bs} - e^{-bs}) / s.
-// FP32 form: the special-function unit's approximate reciprocal square root,
-// exponential and reciprocal (a few ulp each, far below the form's 1e-4
-// target) and no division; near the window's edge (b s < 1e-3) the series
-// 2 b (1 + (b s)^2 / 6) of sinh(b s)/s
-__device__ __forceinline__ float kb_weight(float t, float m2, float b, float norm2)
-{
-    const float x = fmaxf(fmaf(-t, t, m2), 0.0f);       // m^2 - t^2
-    const float r = rsqrtf(fmaxf(x, 1e-30f));
-    const float s = x * r;                               // sqrt(x); 0 at the edge
-    const float bs = b * s;
-    const float e = __expf(bs);
-    const float exact = norm2 * (e - __fdividef(1.0f, e)) * r;
-    const float series = norm2 * 2.0f * b * fmaf(bs * bs, 1.0f / 6.0f, 1.0f);
-    return bs < 1e-3f ? series : exact;
-}
+// (the FP32 form evaluates it through plan-time polynomials, window_row_poly;
+// the FP64 form tabulates it at plan time with this FP64 version)
 __device__ __forceinline__ double kb_weight(double t, double m2, double b, double norm2)
 {
     const double s = sqrt(fmax(m2 - t * t, 0.0));
@@ -121,24 +118,51 @@ __device__ __forceinline__ void fixed_split(float p, float e, int &hi, int &lo)
 // (relative to its bin origin): the taps are the W cells nearest to x, the
 // first at o = floor(x - W/2) + 1, and the weight of tap q is
 // phi_n(x - o - q), |x - o - q| <= W/2.
+// The W window weights of one dimension for a point with local coordinate x
+// (relative to its bin origin): the taps are the W cells nearest to x, the
+// first at o = floor(x - W/2) + 1, and the weight of tap q is
+// phi_n(x - o - q), |x - o - q| <= W/2.  FP32 form, from polynomials fitted
+// at plan time: with
+// f = (x - W/2) - floor(x - W/2) in [0, 1) and u = f - 1/2, tap q has weight
+// phi_n(W/2 - 1 - q + f) ~ sum_k c[q][k] u^k (degree 9, Chebyshev
+// interpolation of the window on each unit interval; the fit error is below
+// 1e-7 of the window's peak for every W and oversampling the plans allow,
+// checked at plan time).  Horner in FP32: 9 FMAs per weight, in place of an
+// approximate square root, exponential and reciprocal on the special-function
+// unit, whose fast exponential alone errs by about 1e-6 for the arguments
+// near b W/2 of the window's centre.  c: kernel parameters (single-layer
+// launches) or a shared copy.
 template <int W>
-__device__ __forceinline__ int window_row(float x, float m2, float b, float norm2, float *w)
+__device__ __forceinline__ int window_row_poly(float x, const float *__restrict__ c, float *w)
 {
-    const float fl = floorf(x - 0.5f * (float)W);
-    const float t0 = x - fl - 1.0f;
+    const float xs = x - 0.5f * (float)W;
+    const float fl = floorf(xs);
+    const float u = (xs - fl) - 0.5f;
 #pragma unroll
-    for (int q = 0; q < W; ++q) w[q] = kb_weight(t0 - (float)q, m2, b, norm2);
+    for (int q = 0; q < W; ++q) {
+        const float4 *row = reinterpret_cast<const float4 *>(c + q * kPolyStride);
+        const float4 c0 = row[0], c1 = row[1], c2 = row[2];
+        float v = fmaf(c2.y, u, c2.x);
+        v = fmaf(v, u, c1.w);
+        v = fmaf(v, u, c1.z);
+        v = fmaf(v, u, c1.y);
+        v = fmaf(v, u, c1.x);
+        v = fmaf(v, u, c0.w);
+        v = fmaf(v, u, c0.z);
+        v = fmaf(v, u, c0.y);
+        w[q] = fmaf(v, u, c0.x);
+    }
     return (int)fl + 1;
 }
-template <int W>
-__device__ __forceinline__ int window_row(double x, double m2, double b, double norm2, double *w)
+static_assert(kPolyTerms == 10 && kPolyStride == 12, "window_row_poly evaluates degree 9 from 12-float rows");
+
+// coefficients of a batched launch's layer copied to shared memory (the
+// caller synchronises before they are read)
+__device__ __forceinline__ void stage_window_poly(const float *__restrict__ src, float *dst, int W)
 {
-    const double fl = floor(x - 0.5 * (double)W);
-    const double t0 = x - fl - 1.0;
-#pragma unroll
-    for (int q = 0; q < W; ++q) w[q] = kb_weight(t0 - (double)q, m2, b, norm2);
-    return (int)fl + 1;
+    for (int e = threadIdx.x; e < W * kPolyStride; e += blockDim.x) dst[e] = src[e];
 }
+
 
 struct SpreadArgs {
     const int *sub_bin, *sub_start, *sub_count;
@@ -158,6 +182,9 @@ struct SpreadArgs {
     void *scratch;           // T [nsub][Pt^D][nv]
     int sub_max;             // largest subproblem (smem staging size)
     int nsub;                // subproblems (batched launches)
+    int rows_off;            // FP32, D = 3: byte offset of the row-product slots in dynamic shared
+                             // memory (RowSpread), 0 = not used
+    alignas(16) float kbp[kPolyW * kPolyStride];   // FP32 window polynomials (window_row_poly)
 };
 
 // Sum of the tiles of each group of consecutive subproblems of one bin
@@ -235,6 +262,7 @@ struct InterpArgs {
     double alpha, shift, self;
     int normalized, accumulate, sorted_out;
     int nsub;                // subproblems (batched launches)
+    alignas(16) float kbp[kPolyW * kPolyStride];   // FP32 window polynomials (window_row_poly)
 };
 
 template <int D>
@@ -250,6 +278,17 @@ __device__ __forceinline__ int tile_cells(int Pt)
 {
     return D == 1 ? Pt : (D == 2 ? Pt * Pt : Pt * Pt * Pt);
 }
+
+// Division by a divisor that is fixed for a whole block: q = x / d by one
+// multiply-high with m = floor((2^32 - 1) / d) + 1.  Exact for d >= 2 and
+// 0 <= x < 2^32 / d: m d = 2^32 + e with 0 <= e < d, so x m / 2^32 exceeds
+// x / d by x e / (d 2^32) < 1 / d, which cannot reach the next multiple of
+// 1/d above x / d.  d = 1 returns x.
+struct FastDiv {
+    uint32_t d, m;
+    __device__ __forceinline__ explicit FastDiv(int div) : d((uint32_t)div), m(0xFFFFFFFFu / (uint32_t)div + 1u) {}
+    __device__ __forceinline__ int div(int x) const { return d == 1u ? x : (int)__umulhi((uint32_t)x, m); }
+};
 
 // ------------------------------------------------------------ block reductions
 __device__ __forceinline__ float warp_sum(float v)
@@ -341,13 +380,112 @@ __device__ __forceinline__ void warp_spread_sum(int *tile, int tc, int Pt, const
     }
 }
 
+// Row-product spreading (D = 3).  When the warp's 32 points share their first
+// tap o, the tap sums S_c[qz][qy][qx] = sum_p u_pc wz_p[qz] wy_p[qy] wx_p[qx]
+// are products of small matrices: lane l owns the rows r = l, l + 32, ...
+// (r = qz W + qy) and adds, for p = 0..31 in order, wx_p[qx] times
+// (u_pc (wy_p[qy] wz_p[qz])) to its accumulators (W per vector c).  Each lane
+// first writes its point's wx, wy, wz and u to its slot in the warp's shared
+// region: the wx and u loads are then broadcasts and the row factors W
+// distinct words.  One atomic per row, qx and vector, with the sum rounded
+// to the fixed-point integer (the scaled sum of a subproblem stays below
+// 2^30).  The arithmetic per vector does not depend on the number of vectors
+// in the pass, so passes of any width give the same bits.  About 7
+// instructions per point, row group and vector, against a transpose of the
+// 32 lanes' tap values (5 exchange rounds per 32 taps) in warp_spread_sum.
+__host__ __device__ constexpr int row_slot_floats(int W, int NV)
+{
+    // floats per point, padded to 4 (mod 8) so that the lanes' 16-byte slot
+    // stores fall on distinct bank groups
+    return ((3 * W + NV + 3) / 4 * 4) % 8 == 0 ? (3 * W + NV + 3) / 4 * 4 + 4 : (3 * W + NV + 3) / 4 * 4;
+}
+// bytes of the slots of a 256-thread block (8 warps of 32 points)
+__host__ __device__ constexpr size_t row_spread_bytes(int W, int NV)
+{
+    return (size_t)8 * 32 * row_slot_floats(W, NV) * sizeof(float);
+}
+template <int D, int W, int NV>
+struct RowSpread {
+    static constexpr bool on = (D == 3 && W <= 8);
+    static constexpr int S = row_slot_floats(W, NV);
+    static constexpr int warp_floats = 32 * S;
+    static constexpr size_t smem = on ? row_spread_bytes(W, NV) : 0;
+};
+
+template <int W, int NV>
+__device__ __forceinline__ void warp_spread_rows(int *tile, int tc, int Pt, const int (&o)[3], const float (&u)[NV],
+                                                 const float (&wx)[W], const float (&wy)[W], const float (&wz)[W],
+                                                 float *slots, int lane)
+{
+    constexpr int S = row_slot_floats(W, NV);
+    constexpr int R = W * W;
+    {
+        float v[S];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            v[q] = wx[q];
+            v[W + q] = wy[q];
+            v[2 * W + q] = wz[q];
+        }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[3 * W + c] = u[c];
+#pragma unroll
+        for (int q = 3 * W + NV; q < S; ++q) v[q] = 0.0f;
+        float4 *dst = reinterpret_cast<float4 *>(slots + lane * S);
+#pragma unroll
+        for (int k = 0; k < S / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int r0 = 0; r0 < R; r0 += 32) {
+        const int r = r0 + lane;
+        const int rr = r < R ? r : R - 1;
+        const int qz = rr / W, qy = rr - qz * W;
+        float acc[NV][W];
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+#pragma unroll
+            for (int qx = 0; qx < W; ++qx) acc[c][qx] = 0.0f;
+#pragma unroll 4
+        for (int p = 0; p < 32; ++p) {
+            const float *sp = slots + p * S;
+            float a[W];
+#pragma unroll
+            for (int k = 0; k + 4 <= W; k += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(sp + k);
+                a[k] = t.x;
+                a[k + 1] = t.y;
+                a[k + 2] = t.z;
+                a[k + 3] = t.w;
+            }
+#pragma unroll
+            for (int k = W / 4 * 4; k < W; ++k) a[k] = sp[k];
+            const float b = sp[W + qy] * sp[2 * W + qz];
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                const float ub = sp[3 * W + c] * b;
+#pragma unroll
+                for (int qx = 0; qx < W; ++qx) acc[c][qx] = fmaf(a[qx], ub, acc[c][qx]);
+            }
+        }
+        if (r < R) {
+            int *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
+#pragma unroll
+            for (int c = 0; c < NV; ++c)
+#pragma unroll
+                for (int qx = 0; qx < W; ++qx) atomicAdd(row + c * tc + qx, __float2int_rn(acc[c][qx]));
+        }
+    }
+    __syncwarp();   // the slots are rewritten by the next group
+}
+
 // FP32 form: one thread per point.  Weights and taps in FP32; each tile cell
 // accumulates integers (fixed point, per-subproblem power-of-two scale) with
 // 32-bit shared-memory atomics, which are exact and order-independent.  Each
 // lane walks its (qz, qy) rows starting at a lane-dependent offset, so lanes
 // whose points share a cell (clustered data) hit different addresses.
 template <int D, int W, int NV>
-__device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int sub)
+__device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int sub, const float *kb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int *tile = reinterpret_cast<int *>(smem_raw);
@@ -402,6 +540,11 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     const int rz = (D == 3) ? lane % nz : 0;
     const float *coords = static_cast<const float *>(a.coords);
     const int Pt = a.Pt;
+    float *slots = nullptr;
+    if constexpr (RowSpread<D, W, NV>::on) {
+        if (a.rows_off > 0)
+            slots = reinterpret_cast<float *>(smem_raw + a.rows_off) + warp * RowSpread<D, W, NV>::warp_floats;
+    }
     // a warp takes 32 consecutive points (sorted by cell); when all of them
     // have the same first tap, their taps are summed across the warp and
     // each lane adds one sum per 32 taps (warp_spread_sum), else every lane
@@ -418,12 +561,18 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
             u[c] = valid ? (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c] : 0.0f;
         float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
-        o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
-        if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
-        if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        o[0] = window_row_poly<W>(coords[(int64_t)i * D], kb, wx);
+        if (D >= 2) o[1] = window_row_poly<W>(coords[(int64_t)i * D + 1], kb, wy);
+        if (D >= 3) o[2] = window_row_poly<W>(coords[(int64_t)i * D + 2], kb, wz);
         const int key = o[0] | (o[1] << 10) | (o[2] << 20);
         const int key0 = __shfl_sync(0xffffffffu, key, 0);
         if (kWarpSum && __all_sync(0xffffffffu, !valid || key == key0)) {
+            if constexpr (RowSpread<D, W, NV>::on) {
+                if (slots) {
+                    warp_spread_rows<W, NV>(tile, tc, Pt, o, u, wx, wy, wz, slots, lane);
+                    continue;
+                }
+            }
             warp_spread_sum<D, W, NV>(tile, tc, Pt, o, u, wx, wy, wz, lane);
             continue;
         }
@@ -470,17 +619,25 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
         }
     }
     __syncthreads();
+    // the scales are powers of two: multiplying by the reciprocal is exact
+    float inv_scale[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) inv_scale[c] = 1.0f / s_scale[c];
     float *out = static_cast<float *>(a.scratch) + (int64_t)sub * tc * NV;
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
         const int c = e % NV, cell = e / NV;
-        out[e] = (float)tile[c * tc + cell] / s_scale[c];
+        float is = inv_scale[0];
+#pragma unroll
+        for (int k = 1; k < NV; ++k)
+            if (c == k) is = inv_scale[k];
+        out[e] = (float)tile[c * tc + cell] * is;
     }
 }
 
 template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_spread_f32(const SpreadArgs a)
 {
-    spread_f32_block<D, W, NV>(a, blockIdx.x);
+    spread_f32_block<D, W, NV>(a, blockIdx.x, a.kbp);
 }
 
 // all layers of a batch in one launch: blockIdx.y is the layer
@@ -489,7 +646,9 @@ __global__ void __launch_bounds__(256) k_spread_f32_batch(const SpreadArgs *__re
 {
     const SpreadArgs a = args[blockIdx.y];
     if ((int)blockIdx.x >= a.nsub) return;
-    spread_f32_block<D, W, NV>(a, blockIdx.x);
+    __shared__ __align__(16) float s_kb[kPolyW * kPolyStride];
+    stage_window_poly(args[blockIdx.y].kbp, s_kb, W);   // read after the block's first barrier
+    spread_f32_block<D, W, NV>(a, blockIdx.x, s_kb);
 }
 
 // FP64 form: one shared tile per CTA, taps in double-word arithmetic on the
@@ -650,12 +809,14 @@ __device__ __forceinline__ void fold_block(const FoldArgs &a, const int bin, con
     const int cells = (D == 1 ? B : (D == 2 ? B * B : B * B * B));
     const T *scr = static_cast<const T *>(a.scratch);
     TO *grid = static_cast<TO *>(a.grid);
+    const FastDiv dv(nv), db(B);   // e < B^3 nv, so e * nv < 2^32 and cell * B < 2^32
     for (int e = ch * blockDim.x + threadIdx.x; e < cells * nv; e += chunks * blockDim.x) {
-        const int c = e % nv;
-        const int cell = e / nv;
-        const int cx = cell % B;
-        const int cy = (D >= 2) ? (cell / B) % B : 0;
-        const int cz = (D >= 3) ? cell / (B * B) : 0;
+        const int cell = dv.div(e);
+        const int c = e - cell * nv;
+        const int q1 = db.div(cell);
+        const int cx = cell - q1 * B;
+        const int cz = (D >= 3) ? db.div(q1) : 0;
+        const int cy = (D >= 2) ? q1 - cz * B : 0;
         const int gx = bc[0] * B + cx, gy = bc[1] * B + cy, gz = bc[2] * B + cz;
         if (gx >= a.L0 || gy >= a.L1 || gz >= a.L2) continue;
         T acc = 0;
@@ -869,12 +1030,14 @@ __device__ __forceinline__ void load_interp_tile(const InterpArgs &a, int D, con
 {
     const T *grid = static_cast<const T *>(a.grid);
     const int Pt = a.Pt;
+    const FastDiv dp(Pt);     // tile cells < Pt^3, so cell * Pt < 2^32
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
         const int c = e % NV;
         const int cell = e / NV;
-        const int lx = cell % Pt;
-        const int ly = (D >= 2) ? (cell / Pt) % Pt : 0;
-        const int lz = (D >= 3) ? cell / (Pt * Pt) : 0;
+        const int q1 = dp.div(cell);
+        const int lx = cell - q1 * Pt;
+        const int lz = (D >= 3) ? dp.div(q1) : 0;
+        const int ly = (D >= 2) ? q1 - lz * Pt : 0;
         const int gx = bc[0] * a.B + lx, gy = bc[1] * a.B + ly, gz = bc[2] * a.B + lz;
         T v{};
         if (gx < a.L0 && gy < a.L1 && gz < a.L2) v = grid[((int64_t)(gz * a.L1 + gy) * a.L0 + gx) * NV + c];
@@ -919,7 +1082,7 @@ __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int 
 
 // FP32 form: one thread per point.
 template <int D, int W, int NV>
-__device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int sub)
+__device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int sub, const float *kb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);
@@ -937,9 +1100,9 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
         float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
-        o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
-        if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
-        if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+        o[0] = window_row_poly<W>(coords[(int64_t)i * D], kb, wx);
+        if (D >= 2) o[1] = window_row_poly<W>(coords[(int64_t)i * D + 1], kb, wy);
+        if (D >= 3) o[2] = window_row_poly<W>(coords[(int64_t)i * D + 2], kb, wz);
         float acc[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
@@ -974,7 +1137,7 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
 template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 {
-    interp_f32_block<D, W, NV>(a, blockIdx.x);
+    interp_f32_block<D, W, NV>(a, blockIdx.x, a.kbp);
 }
 
 // all layers of a batch in one launch, each writing its own output block:
@@ -984,7 +1147,9 @@ __global__ void __launch_bounds__(256) k_interp_f32_batch(const InterpArgs *__re
 {
     const InterpArgs a = args[blockIdx.y];
     if ((int)blockIdx.x >= a.nsub) return;
-    interp_f32_block<D, W, NV>(a, blockIdx.x);
+    __shared__ __align__(16) float s_kb[kPolyW * kPolyStride];
+    stage_window_poly(args[blockIdx.y].kbp, s_kb, W);   // read after the block's first barrier
+    interp_f32_block<D, W, NV>(a, blockIdx.x, s_kb);
 }
 
 // FP64 form: one thread per point, on the FP32 pipes.  The grid arrives as
@@ -1072,6 +1237,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__rest
                                                         float *__restrict__ part, int64_t n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) float s_kb[kPolyW * kPolyStride];
     float *tile = reinterpret_cast<float *>(smem_raw);
     const int sub = blockIdx.x;
     const int g = blockIdx.y;
@@ -1093,6 +1259,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__rest
         const int bc[3] = {0, 0, 0};
         __syncthreads();                       // previous layer's tile no longer read
         load_interp_tile<float, NV>(a, D, bc, tc, tile);
+        stage_window_poly(args[t].kbp, s_kb, W);
         __syncthreads();
         const float *coords = static_cast<const float *>(a.coords);
 #pragma unroll
@@ -1102,9 +1269,9 @@ __global__ void __launch_bounds__(256) k_interp_f32_sum(const InterpArgs *__rest
             const int i = start + li;
             float wx[W], wy[W], wz[W];
             int o[3] = {0, 0, 0};
-            o[0] = window_row<W>(coords[(int64_t)i * D], a.m2f, a.bf, a.normf, wx);
-            if (D >= 2) o[1] = window_row<W>(coords[(int64_t)i * D + 1], a.m2f, a.bf, a.normf, wy);
-            if (D >= 3) o[2] = window_row<W>(coords[(int64_t)i * D + 2], a.m2f, a.bf, a.normf, wz);
+            o[0] = window_row_poly<W>(coords[(int64_t)i * D], s_kb, wx);
+            if (D >= 2) o[1] = window_row_poly<W>(coords[(int64_t)i * D + 1], s_kb, wy);
+            if (D >= 3) o[2] = window_row_poly<W>(coords[(int64_t)i * D + 2], s_kb, wz);
             float acc[NV];
 #pragma unroll
             for (int c = 0; c < NV; ++c) acc[c] = 0.0f;

@@ -31,6 +31,18 @@ static ml_status set_smem(K kernel, size_t bytes)
     return ML_OK;
 }
 
+// Offset of the row-product slots of the FP32 spreading after a tile of
+// tile_bytes (16-byte aligned), or 0 when the path does not apply or the
+// slots would not fit next to the tile (the plan limits its vectors per pass
+// so that, where the slots fit for one vector, they fit for every pass width)
+template <int D, int W, int NV>
+static size_t row_spread_offset(size_t tile_bytes)
+{
+    if (!RowSpread<D, W, NV>::on) return 0;
+    const size_t off = (tile_bytes + 15) & ~(size_t)15;
+    return off + RowSpread<D, W, NV>::smem <= kRowSpreadBudget ? off : 0;
+}
+
 template <typename T, int D, int W, int NV>
 static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                               cudaStream_t st)
@@ -40,7 +52,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     const int tc = (int)g.tile_cells();
     const bool f32 = sizeof(T) == 4;
     // ---- spread
-    SpreadArgs sa;
+    SpreadArgs sa{};
     sa.sub_bin = p->sub_bin.as<int>();
     sa.sub_start = p->sub_start.as<int>();
     sa.sub_count = p->sub_count.as<int>();
@@ -64,11 +76,18 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     sa.m2f = (float)sa.m2d;
     sa.bf = (float)sa.bd;
     sa.normf = (float)sa.normd;
+    static_assert(sizeof(sa.kbp) == sizeof(p->kbp), "window polynomial table sizes");
+    memcpy(sa.kbp, p->kbp, sizeof(sa.kbp));
     sa.scratch = w.scratch;
     if (p->nsub > 0) {
         ProfScope pr("spread", st);
         if (f32) {
-            const size_t smem = (size_t)tc * nv * sizeof(int);
+            size_t smem = (size_t)tc * nv * sizeof(int);
+            const size_t roff = row_spread_offset<D, W, NV>(smem);
+            if (roff) {
+                sa.rows_off = (int)roff;
+                smem = roff + RowSpread<D, W, NV>::smem;
+            }
             ML_TRY(set_smem(k_spread_f32<D, W, NV>, smem));
             k_spread_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
@@ -170,7 +189,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     }
     ML_CUDA(cudaGetLastError());
     // ---- interpolation + epilogue
-    InterpArgs ia;
+    InterpArgs ia{};
     ia.sub_bin = sa.sub_bin;
     ia.sub_start = sa.sub_start;
     ia.sub_count = sa.sub_count;
@@ -194,6 +213,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.m2f = sa.m2f;
     ia.bf = sa.bf;
     ia.normf = sa.normf;
+    memcpy(ia.kbp, p->kbp, sizeof(ia.kbp));
     ia.m2d = sa.m2d;
     ia.bd = sa.bd;
     ia.normd = sa.normd;
@@ -315,6 +335,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         a.m2f = (float)a.m2d;
         a.bf = (float)a.bd;
         a.normf = (float)a.normd;
+        memcpy(a.kbp, p->kbp, sizeof(a.kbp));
         a.scratch = scratch;
         a.nsub = p->nsub;
         ga[t] = GroupArgs{scratch, p->grp_sub.as<int>(), tile_elems, gtile, p->ngroups};
@@ -360,6 +381,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         }
         InterpArgs &ip = ia[t];
         ip = InterpArgs{};
+        memcpy(ip.kbp, p->kbp, sizeof(ip.kbp));
         ip.sub_bin = a.sub_bin;
         ip.sub_start = a.sub_start;
         ip.sub_count = a.sub_count;
@@ -397,6 +419,15 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         max_tile = std::max(max_tile, (int64_t)tc);
     }
     // pack and upload
+    // the row-product slots follow the largest tile (one offset for all layers)
+    size_t spread_batch_smem = (size_t)max_tile * NV * sizeof(int);
+    {
+        const size_t roff = row_spread_offset<D, W, NV>(spread_batch_smem);
+        if (roff) {
+            for (int t = 0; t < T; ++t) sa[t].rows_off = (int)roff;
+            spread_batch_smem = roff + RowSpread<D, W, NV>::smem;
+        }
+    }
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_sa = 0, o_ga = align(o_sa + sizeof(SpreadArgs) * T), o_fa = align(o_ga + sizeof(GroupArgs) * T),
                  o_ax = align(o_fa + sizeof(FoldArgs) * T), o_ma = align(o_ax + sizeof(AxisArgs) * ax.size()),
@@ -420,7 +451,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     unsigned char *d = ddev.as<unsigned char>();
     {
         ProfScope pr("spread", st);
-        const size_t smem = (size_t)max_tile * NV * sizeof(int);
+        const size_t smem = spread_batch_smem;
         ML_TRY(set_smem(k_spread_f32_batch<D, W, NV>, smem));
         k_spread_f32_batch<D, W, NV><<<dim3(max_nsub, T), 256, smem, st>>>(reinterpret_cast<SpreadArgs *>(d + o_sa));
         ML_CUDA(cudaGetLastError());

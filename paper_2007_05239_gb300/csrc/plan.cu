@@ -503,6 +503,73 @@ static int grid_for(int64_t n, int threads)
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 16));
 }
 
+// ---------------------------------------------------------- window polynomials
+// phi_n(t) = norm (e^{bs} - e^{-bs}) / s, s = sqrt(h^2 - t^2), in FP64
+static double kb_phi(double t, double h, double b, double norm)
+{
+    const double s = std::sqrt(std::max(h * h - t * t, 0.0)), bs = b * s;
+    if (bs < 1e-4) return norm * 2.0 * b * (1.0 + bs * bs / 6.0);
+    return norm * 2.0 * std::sinh(bs) / s;
+}
+
+// FP32 form: for every tap q < W the polynomial of degree 9 in u = f - 1/2
+// that interpolates phi_n(W/2 - 1 - q + f), f in [0, 1), at the 10 Chebyshev
+// points of the unit interval (monomial coefficients from the Vandermonde
+// system, Gaussian elimination with partial pivoting in FP64).  The window is
+// a function of s^2 = h^2 - t^2 whose series has only positive terms (an
+// entire function of t), so the interpolant converges fast: the check on 2001
+// points, with the coefficients rounded to FP32, must stay below 1e-7 of the
+// window's peak.
+static ml_status fit_window_poly(ml_plan_s *p)
+{
+    constexpr int K = kPolyTerms;
+    static_assert(sizeof(p->kbp) == sizeof(float) * kPolyW * kPolyStride, "window polynomial table size");
+    const int W = p->W;
+    if (W > 16) return fail(ML_ERR_ARG, "FP32 window wider than 16 taps");
+    const double h = 0.5 * W, b = p->kb_shape, nm = p->kb_norm;
+    const double peak = kb_phi(0.0, h, b, nm);
+    double worst = 0.0;
+    for (int q = 0; q < W; ++q) {
+        double V[K][K + 1];
+        for (int j = 0; j < K; ++j) {
+            const double u = 0.5 * std::cos((2 * j + 1) * M_PI / (2.0 * K));
+            double pw = 1.0;
+            for (int k = 0; k < K; ++k) {
+                V[j][k] = pw;
+                pw *= u;
+            }
+            V[j][K] = kb_phi(h - 1.0 - q + 0.5 + u, h, b, nm);
+        }
+        for (int c = 0; c < K; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < K; ++r)
+                if (std::fabs(V[r][c]) > std::fabs(V[piv][c])) piv = r;
+            for (int k = 0; k <= K; ++k) std::swap(V[c][k], V[piv][k]);
+            for (int r = c + 1; r < K; ++r) {
+                const double f = V[r][c] / V[c][c];
+                for (int k = c; k <= K; ++k) V[r][k] -= f * V[c][k];
+            }
+        }
+        double coef[K];
+        for (int c = K - 1; c >= 0; --c) {
+            double v = V[c][K];
+            for (int k = c + 1; k < K; ++k) v -= V[c][k] * coef[k];
+            coef[c] = v / V[c][c];
+        }
+        float *row = p->kbp + q * kPolyStride;
+        for (int k = 0; k < kPolyStride; ++k) row[k] = k < K ? (float)coef[k] : 0.0f;
+        for (int e = 0; e <= 2000; ++e) {
+            const double u = -0.5 + e / 2000.0;
+            double v = row[K - 1];
+            for (int k = K - 2; k >= 0; --k) v = v * u + row[k];
+            worst = std::max(worst, std::fabs(v - kb_phi(h - 1.0 - q + 0.5 + u, h, b, nm)));
+        }
+    }
+    if (!(worst <= 1e-7 * peak))
+        return fail(ML_ERR_DOMAIN, "window polynomial fit error " + std::to_string(worst / peak) + " of the peak");
+    return ML_OK;
+}
+
 // ---------------------------------------------------------- parameters
 // Window width W and oversampling sigma_os for a target error.  The
 // Kaiser-Bessel window's error falls like exp(-pi W sqrt(1 - 1/sigma_os));
@@ -771,6 +838,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         const double b = p->kb_shape, h = 0.5 * p->W;
         p->kb_norm = h * std::exp(-b * h) / (1.0 - std::exp(-2.0 * b * h));
     }
+    if (p->prec == ML_F32) ML_TRY(fit_window_poly(p));
     // ---- active grid
     TorusMap tm;
     for (int a = 0; a < 3; ++a) tm.c[a] = p->center[a];
@@ -835,6 +903,14 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
             return fail(ML_ERR_ARG, "bin edge " + std::to_string(g.B) + " gives a tile beyond the shared-memory budget");
         if (p->prec == ML_F32) {
             p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * 4)));
+            // d = 3, W <= 8: when the row-product slots of the spreading fit
+            // next to the tile for one vector, keep every pass width within
+            // that budget, so that all passes take the same arithmetic
+            auto fits = [&](int v) {
+                return (((size_t)tc * 4 * v + 15) & ~(size_t)15) + row_spread_bytes(p->W, v) <= kRowSpreadBudget;
+            };
+            if (d == 3 && p->W <= 8 && fits(1))
+                while (p->vp > 1 && !fits(p->vp)) --p->vp;
         } else {
             int vp = 1;
             for (int v = kMaxVec; v >= 1; --v)
