@@ -440,7 +440,12 @@ ml_status ml_lanczos_eigs(const ml_plan_t *layers, int T, int k, double p, doubl
  * reached maxit with fewer than k converged pairs; ML_ERR_ARG for k or block
  * out of range; ML_ERR_DEGREE for a layer with a degree <= 0.  When a block
  * becomes numerically rank-deficient its dependent directions are dropped
- * (the block deflates) instead of failing.
+ * (the block deflates) instead of failing; dropped directions take no part
+ * in the Rayleigh-Ritz step, so a layer whose basis holds fewer than k
+ * directions reports ML_WARN_NOT_CONVERGED with NaN in the evals entries
+ * that have no Ritz pair.  Each block step removes the three-term terms
+ * first and runs its second Gram-Schmidt pass only where the first removed
+ * more than half of some column's norm squared.
  */
 ml_status ml_lanczos_eigs_layers(const ml_plan_t *layers, int T, int k, double tol, int maxit, int block,
                                  int ncv, uint64_t seed, double *evals, double *evecs, int *nconv, void *stream);

@@ -184,6 +184,8 @@ struct SpreadArgs {
     int nsub;                // subproblems (batched launches)
     int rows_off;            // FP32, D = 3: byte offset of the row-product slots in dynamic shared
                              // memory (RowSpread), 0 = not used
+    int stage_off;           // FP32: byte offset of the staged points (sub_max x nv values u, then,
+                             // with sidx, sub_max sorted indices) in dynamic shared memory, 0 = not staged
     alignas(16) float kbp[kPolyW * kPolyStride];   // FP32 window polynomials (window_row_poly)
 };
 
@@ -385,19 +387,24 @@ __device__ __forceinline__ void warp_spread_sum(int *tile, int tc, int Pt, const
 // are products of small matrices: lane l owns the rows r = l, l + 32, ...
 // (r = qz W + qy) and adds, for p = 0..31 in order, wx_p[qx] times
 // (u_pc (wy_p[qy] wz_p[qz])) to its accumulators (W per vector c).  Each lane
-// first writes its point's wx, wy, wz and u to its slot in the warp's shared
-// region: the wx and u loads are then broadcasts and the row factors W
-// distinct words.  One atomic per row, qx and vector, with the sum rounded
-// to the fixed-point integer (the scaled sum of a subproblem stays below
-// 2^30).  The arithmetic per vector does not depend on the number of vectors
-// in the pass, so passes of any width give the same bits.  About 7
-// instructions per point, row group and vector, against a transpose of the
-// 32 lanes' tap values (5 exchange rounds per 32 taps) in warp_spread_sum.
+// first writes its point's slot in the warp's shared region: wx and u (read
+// by all lanes alike: broadcasts, 16 bytes at a time), then wy and wz (W
+// distinct words each).  One atomic per row, qx and vector, with the sum
+// rounded to the fixed-point integer (the scaled sum of a subproblem stays
+// below 2^30).  The arithmetic per vector does not depend on the number of
+// vectors in the pass, so passes of any width give the same bits.  About 11
+// instructions per point and row group for one vector, against a transpose
+// of the 32 lanes' tap values (5 exchange rounds per 32 taps) in
+// warp_spread_sum.  (Storing the W^2 products wy wz instead would save one
+// load and one multiply per point but nearly double the slots, which then
+// cost a resident block per SM.)
+__host__ __device__ constexpr int row_slot_head(int W, int NV) { return (W + NV + 3) / 4 * 4; }
 __host__ __device__ constexpr int row_slot_floats(int W, int NV)
 {
     // floats per point, padded to 4 (mod 8) so that the lanes' 16-byte slot
     // stores fall on distinct bank groups
-    return ((3 * W + NV + 3) / 4 * 4) % 8 == 0 ? (3 * W + NV + 3) / 4 * 4 + 4 : (3 * W + NV + 3) / 4 * 4;
+    return ((row_slot_head(W, NV) + 2 * W + 3) / 4 * 4) % 8 == 0 ? (row_slot_head(W, NV) + 2 * W + 3) / 4 * 4 + 4
+                                                                 : (row_slot_head(W, NV) + 2 * W + 3) / 4 * 4;
 }
 // bytes of the slots of a 256-thread block (8 warps of 32 points)
 __host__ __device__ constexpr size_t row_spread_bytes(int W, int NV)
@@ -418,19 +425,23 @@ __device__ __forceinline__ void warp_spread_rows(int *tile, int tc, int Pt, cons
                                                  float *slots, int lane)
 {
     constexpr int S = row_slot_floats(W, NV);
+    constexpr int H = row_slot_head(W, NV);     // wx, u, padding; then wy, wz
     constexpr int R = W * W;
     {
         float v[S];
 #pragma unroll
+        for (int q = 0; q < W; ++q) v[q] = wx[q];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[W + c] = u[c];
+#pragma unroll
+        for (int q = W + NV; q < H; ++q) v[q] = 0.0f;
+#pragma unroll
         for (int q = 0; q < W; ++q) {
-            v[q] = wx[q];
-            v[W + q] = wy[q];
-            v[2 * W + q] = wz[q];
+            v[H + q] = wy[q];
+            v[H + W + q] = wz[q];
         }
 #pragma unroll
-        for (int c = 0; c < NV; ++c) v[3 * W + c] = u[c];
-#pragma unroll
-        for (int q = 3 * W + NV; q < S; ++q) v[q] = 0.0f;
+        for (int q = H + 2 * W; q < S; ++q) v[q] = 0.0f;
         float4 *dst = reinterpret_cast<float4 *>(slots + lane * S);
 #pragma unroll
         for (int k = 0; k < S / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
@@ -449,23 +460,21 @@ __device__ __forceinline__ void warp_spread_rows(int *tile, int tc, int Pt, cons
 #pragma unroll 4
         for (int p = 0; p < 32; ++p) {
             const float *sp = slots + p * S;
-            float a[W];
+            float h[H];
 #pragma unroll
-            for (int k = 0; k + 4 <= W; k += 4) {
+            for (int k = 0; k < H; k += 4) {
                 const float4 t = *reinterpret_cast<const float4 *>(sp + k);
-                a[k] = t.x;
-                a[k + 1] = t.y;
-                a[k + 2] = t.z;
-                a[k + 3] = t.w;
+                h[k] = t.x;
+                h[k + 1] = t.y;
+                h[k + 2] = t.z;
+                h[k + 3] = t.w;
             }
-#pragma unroll
-            for (int k = W / 4 * 4; k < W; ++k) a[k] = sp[k];
-            const float b = sp[W + qy] * sp[2 * W + qz];
+            const float b = sp[H + qy] * sp[H + W + qz];
 #pragma unroll
             for (int c = 0; c < NV; ++c) {
-                const float ub = sp[3 * W + c] * b;
+                const float ub = h[W + c] * b;
 #pragma unroll
-                for (int qx = 0; qx < W; ++qx) acc[c][qx] = fmaf(a[qx], ub, acc[c][qx]);
+                for (int qx = 0; qx < W; ++qx) acc[c][qx] = fmaf(h[qx], ub, acc[c][qx]);
             }
         }
         if (r < R) {
@@ -495,19 +504,47 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     const int tc = tile_cells<D>(a.Pt);
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) tile[e] = 0;
 
-    // per-vector sum and max of |u| over this subproblem's points
+    // per-vector sum and max of |u| over this subproblem's points, u =
+    // D^{-1/2} x in FP32; with staging, each point's sorted index and u go to
+    // shared memory for the spreading pass.  Four points per thread are in
+    // flight at once (the index, permutation and input loads form a chain).
+    float *st_u = a.stage_off > 0 ? reinterpret_cast<float *>(smem_raw + a.stage_off) : nullptr;
+    int *st_i = (st_u && a.sidx) ? reinterpret_cast<int *>(st_u + a.sub_max * NV) : nullptr;
     float lsum[NV], lmax[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) lsum[c] = lmax[c] = 0.0f;
-    for (int ip = start + threadIdx.x; ip < start + cnt; ip += blockDim.x) {
-        const int i = a.sidx ? a.sidx[ip] : ip;
-        const int orig = a.perm[i];
-        const double ds = a.dinv ? a.dinv[i] : 1.0;
+    for (int l0 = threadIdx.x; l0 < cnt; l0 += 4 * blockDim.x) {
+        int ii[4], orig[4];
+        double ds[4];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) {
-            const float u = fabsf((float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds));
-            lsum[c] += u;
-            lmax[c] = fmaxf(lmax[c], u);
+        for (int k = 0; k < 4; ++k) {
+            const int l = min(l0 + k * (int)blockDim.x, cnt - 1);
+            ii[k] = a.sidx ? a.sidx[start + l] : start + l;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            orig[k] = a.perm[ii[k]];
+            ds[k] = a.dinv ? a.dinv[ii[k]] : 1.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * (int)blockDim.x;
+            float uk[NV];
+#pragma unroll
+            for (int c = 0; c < NV; ++c) uk[c] = (float)((a.X ? a.X[(int64_t)orig[k] * a.ldx + c] : 1.0) * ds[k]);
+            if (l < cnt) {
+#pragma unroll
+                for (int c = 0; c < NV; ++c) {
+                    const float au = fabsf(uk[c]);
+                    lsum[c] += au;
+                    lmax[c] = fmaxf(lmax[c], au);
+                }
+                if (st_u) {
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) st_u[l * NV + c] = uk[c];
+                    if (st_i) st_i[l] = ii[k];
+                }
+            }
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -551,14 +588,21 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     // adds its own point's taps
     for (int g0 = (threadIdx.x & ~31); g0 < cnt; g0 += blockDim.x) {
         const bool valid = g0 + lane < cnt;
-        const int ip = start + min(g0 + lane, cnt - 1);
-        const int i = a.sidx ? a.sidx[ip] : ip;
-        const int orig = a.perm[i];
-        const double ds = a.dinv ? a.dinv[i] : 1.0;
+        const int l = min(g0 + lane, cnt - 1);
+        int i;
         float u[NV];
+        if (st_u) {
+            i = st_i ? st_i[l] : start + l;
 #pragma unroll
-        for (int c = 0; c < NV; ++c)
-            u[c] = valid ? (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c] : 0.0f;
+            for (int c = 0; c < NV; ++c) u[c] = valid ? st_u[l * NV + c] * s_scale[c] : 0.0f;
+        } else {
+            i = a.sidx ? a.sidx[start + l] : start + l;
+            const int orig = a.perm[i];
+            const double ds = a.dinv ? a.dinv[i] : 1.0;
+#pragma unroll
+            for (int c = 0; c < NV; ++c)
+                u[c] = valid ? (float)((a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0) * ds) * s_scale[c] : 0.0f;
+        }
         float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
         o[0] = window_row_poly<W>(coords[(int64_t)i * D], kb, wx);
@@ -1064,6 +1108,36 @@ __device__ __forceinline__ void interp_epilogue_f32(const InterpArgs &a, int i, 
     }
 }
 
+// interp_epilogue_f32 split into its loads and its arithmetic (same results)
+template <int NV>
+struct EpilogueIn {
+    int orig;
+    float ds;
+    double x[NV], yold[NV];
+    __device__ __forceinline__ void load(const InterpArgs &a, int i)
+    {
+        orig = a.perm[i];
+        ds = a.dinv ? (float)a.dinv[i] : 1.0f;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            x[c] = a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0;
+            yold[c] = (!a.sorted_out && a.accumulate) ? a.Y[(int64_t)orig * a.ldy + c] : 0.0;
+        }
+    }
+    __device__ __forceinline__ void finish(const InterpArgs &a, int i, int c, float acc) const
+    {
+        const float r = acc - (float)a.self * ((float)x[c] * ds);
+        if (a.sorted_out) {
+            a.Y[(int64_t)i * a.ldy + c] = (double)r;
+        } else {
+            double outv = (double)((float)a.alpha * ds * r);
+            if (a.shift != 0.0) outv += a.shift * x[c];
+            if (a.accumulate) outv += yold[c];
+            a.Y[(int64_t)orig * a.ldy + c] = outv;
+        }
+    }
+};
+
 __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int c, double acc)
 {
     const int orig = a.perm[i];
@@ -1097,7 +1171,13 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
     constexpr int UY = (W <= 8) ? ny : 1;       // unroll the rows of small windows
     constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
+    // one or two vectors: the epilogue's loads (permutation, D^{-1/2}, input,
+    // the previous output when accumulating) are issued before the taps, so
+    // that their latency hides behind the tap sums
+    constexpr bool kPrefetch = NV <= 2;
     for (int i = start + threadIdx.x; i < start + cnt; i += blockDim.x) {
+        EpilogueIn<NV> ein;
+        if constexpr (kPrefetch) ein.load(a, i);
         float wx[W], wy[W], wz[W];
         int o[3] = {0, 0, 0};
         o[0] = window_row_poly<W>(coords[(int64_t)i * D], kb, wx);
@@ -1129,8 +1209,13 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
 #pragma unroll
             for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
         }
+        if constexpr (kPrefetch) {
 #pragma unroll
-        for (int c = 0; c < NV; ++c) interp_epilogue_f32(a, i, c, acc[c]);
+            for (int c = 0; c < NV; ++c) ein.finish(a, i, c, acc[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) interp_epilogue_f32(a, i, c, acc[c]);
+        }
     }
 }
 

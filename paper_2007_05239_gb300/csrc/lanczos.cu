@@ -7,9 +7,11 @@
 //           delta = log(1 + |p|): for p = -1 each term by conjugate gradients,
 //           otherwise by the Lanczos approximation of the matrix power (PowerOp)
 // for its k largest eigenvalues.  The Krylov basis Q (n x (ncv+1), column
-// major, FP64) lives on the device; every new vector is orthogonalised
-// against all columns twice (classical Gram-Schmidt, CGS2) with
-// deterministic block reductions.  The projected (ncv x ncv) matrix and its
+// major, FP64) lives on the device; every new vector has the three-term
+// recurrence's terms removed and is then orthogonalised against all columns
+// by classical Gram-Schmidt, a second time where the first pass removed
+// most of its norm (Workspace::lanczos_step), with deterministic block
+// reductions.  The projected (ncv x ncv) matrix and its
 // eigendecomposition are on the host in FP64.  For p = -1 each term
 // (L_sym^(t) + delta I)^{-1} x is a conjugate-gradient solve whose matvec is
 // the fast summation of layer t (the polynomial Krylov approach of Sec. 3

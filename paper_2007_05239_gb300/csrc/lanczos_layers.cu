@@ -11,14 +11,18 @@
 //   Q_t  n x ldq, ldq = ncv + b: columns 0..ncv-1 the basis of the cycle,
 //        ncv..ncv+b-1 the next (residual) block;
 //   W_t  n x b, the product block.
-// One block step for the block Q[:, c:c+b] (cq = c + b):
-//   W = A_t Q[:, c:c+b]
+// One block step for the block Q_j = Q[:, c:c+b] (cq = c + b):
+//   W = A_t Q_j
+//   W -= Q_{j-1} R_{j-1}^T, A_j = Q_j^T W, W -= Q_j A_j   (three-term part, j >= 1)
 //   H1 = Q[:, 0:cq]^T W,  W -= Q[:, 0:cq] H1          (classical Gram-Schmidt)
 //   W = V1 R1                                         (SVQB)
-//   H2 = Q[:, 0:cq]^T V1, V1 -= Q[:, 0:cq] H2         (second Gram-Schmidt pass)
+//   H2 = Q[:, 0:cq]^T V1, V1 -= Q[:, 0:cq] H2         (second pass, only when
+//                                                      the first removed over
+//                                                      half of a column's norm^2)
 //   V1 = V2 R2, Q[:, cq:cq+b] = V2                    (SVQB)
-// so that A Q[:, c:c+b] = Q[:, 0:cq] (H1 + H2 R1) + Q[:, cq:cq+b] (R2 R1): the
-// columns c..c+b-1 of the projected matrix T = Q^T A Q.
+// so that A Q_j = Q[:, 0:cq] (H1 + three-term part + H2 R1) + Q[:, cq:cq+b] (R2 R1):
+// the columns c..c+b-1 of the projected matrix T = Q^T A Q.  The tensor-core
+// kind of products keeps both passes in every step (orthonormalise).
 // SVQB (Stathopoulos & Wu, SIAM J. Sci. Comput. 23 (2002)): G = W^T W,
 // S = diag(G)^{-1/2}, S G S = U L U^T, V = W S U L^{-1/2}, R = L^{1/2} U^T S^{-1};
 // directions with L_i <= 1e-20 max L are dropped (zero columns: the block
@@ -54,8 +58,10 @@ struct LMat {
 // part[(y * gridDim.x + x) * rc * cb + r * cb + s] = sum over this CTA's rows i
 // of A_t[i, a0 + r] * B_t[i, b0 + s], t = lay[y]   (rc * cb <= kGramOut)
 __global__ void __launch_bounds__(256) k_lgram(LMat A, int a0, int rc, LMat B, int b0, int cb,
-                                              const int *__restrict__ lay, int64_t n, double *part)
+                                              const int *__restrict__ lay, int64_t n, double *part,
+                                              const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;   // a pass the device decided to skip
     __shared__ double As[kRows][kMaxLd + 1];
     __shared__ double Bs[kRows][kMaxBlk + 1];
     const int t = lay[blockIdx.y];
@@ -100,8 +106,10 @@ __global__ void __launch_bounds__(256) k_lgram(LMat A, int a0, int rc, LMat B, i
 // partial sums are added in a fixed order at the end.
 constexpr int kDwRows = 32;
 __global__ void __launch_bounds__(256) k_lgram_dw(LMat A, int a0, int rc, LMat B, int b0, int cb,
-                                                 const int *__restrict__ lay, int64_t n, double *part)
+                                                 const int *__restrict__ lay, int64_t n, double *part,
+                                                 const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     __shared__ float2 As[kDwRows][kMaxLd + 1];
     __shared__ float2 Bs[kDwRows][kMaxBlk + 1];
     __shared__ double red[kGramOut];
@@ -165,8 +173,9 @@ constexpr int kDwGemmRows = 128;
 // 0..cb-1 of it; cb <= 8)
 __global__ void __launch_bounds__(kDwGemmRows) k_lgemm_dw(LMat A, int a0, int rc, const double *__restrict__ M, int ldm,
                                                          LMat B, int b0, int cb, const int *__restrict__ lay,
-                                                         int64_t n, int sub)
+                                                         int64_t n, int sub, const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     extern __shared__ float2 dsm[];
     float2 *Ms = dsm;                          // rc * cb
     float2 *As = dsm + rc * cb;                // kDwGemmRows x (rc + 1)
@@ -209,8 +218,9 @@ __global__ void __launch_bounds__(kDwGemmRows) k_lgemm_dw(LMat A, int a0, int rc
 // out[y][e] = sum over the nbx partial blocks in a fixed order; with rec,
 // also rec[lay[y] * rstride + e] = out[y][e]
 __global__ void k_lreduce(const double *__restrict__ part, int nbx, int nout, const int *__restrict__ lay,
-                          double *out, double *rec, int64_t rstride)
+                          double *out, double *rec, int64_t rstride, const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     const int y = blockIdx.y;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nout; e += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -224,8 +234,10 @@ __global__ void k_lreduce(const double *__restrict__ part, int nbx, int nout, co
 // (M_y = M + y * rc * cb, row-major rc x cb).  Rows are staged per chunk, so
 // B may be A (in place on the same columns).
 __global__ void __launch_bounds__(256) k_lgemm(LMat A, int a0, int rc, const double *__restrict__ M, LMat B, int b0,
-                                              int cb, const int *__restrict__ lay, int64_t n, int sub)
+                                              int cb, const int *__restrict__ lay, int64_t n, int sub,
+                                              const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     extern __shared__ double lsm[];
     double *Ms = lsm;                 // rc * cb
     double *As = lsm + rc * cb;       // kRows x (rc + 1)
@@ -357,8 +369,9 @@ __global__ void k_lsvqb(const double *__restrict__ G, int nslots, const int *__r
 // rec_t[r, s] += sum_q H2_y[r, q] Rs_y[q, s]   (r < rc): the second pass's
 // coefficients mapped back to the product block
 __global__ void k_lhacc(const double *__restrict__ H2, const double *__restrict__ Rs, int rc, int b,
-                        const int *__restrict__ lay, double *rec, int64_t rstride)
+                        const int *__restrict__ lay, double *rec, int64_t rstride, const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     const int y = blockIdx.y;
     const double *H = H2 + (int64_t)y * rc * b, *R = Rs + (int64_t)y * b * b;
     double *out = rec + (int64_t)lay[y] * rstride;
@@ -367,6 +380,50 @@ __global__ void k_lhacc(const double *__restrict__ H2, const double *__restrict_
         double x = 0.0;
         for (int q = 0; q < b; ++q) x = fma(H[r * b + q], R[q * b + s], x);
         out[e] += x;
+    }
+}
+
+// Three-term part of a block step: M_y[s, q] = R_t[q, s] for the record R_t
+// (b x b, row-major) of the previous step, t = lay[y]: A Q_{j-1} has the
+// component Q_j R, so A Q_j has the component Q_{j-1} R^T
+__global__ void k_lthree(const double *__restrict__ rprev, int64_t rstride, const int *__restrict__ lay, int nslots,
+                         int b, double *M)
+{
+    const int y = blockIdx.x;
+    if (y >= nslots) return;
+    const double *R = rprev + (int64_t)lay[y] * rstride;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int s = e / b, q = e - s * b;
+        M[(int64_t)y * b * b + e] = R[q * b + s];
+    }
+}
+
+// the coefficients the three-term part removed, added to this step's record
+// (rows c - b .. c - 1: M_y = R^T when given; rows c .. c + b - 1: A_y)
+__global__ void k_lrec_add(double *rec, int64_t rstride, const int *__restrict__ lay, int nslots, const double *M,
+                           const double *__restrict__ A, int c, int b)
+{
+    const int y = blockIdx.x;
+    if (y >= nslots) return;
+    double *R = rec + (int64_t)lay[y] * rstride;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int s = e / b, q = e - s * b;
+        if (M) R[(int64_t)(c - b + s) * b + q] += M[(int64_t)y * b * b + e];
+        R[(int64_t)(c + s) * b + q] += A[(int64_t)y * b * b + e];
+    }
+}
+
+// Second-pass criterion over all active layers: *flag = 1 when some column
+// of some layer kept less than eta2 of its norm squared through the first
+// Gram-Schmidt pass (G0: the block's Gram matrix before it, G after);
+// *flag is cleared by the caller before
+__global__ void k_ldgks(const double *__restrict__ G0, const double *__restrict__ G, int nslots, int b, double eta2,
+                        int *flag)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nslots * b; e += gridDim.x * blockDim.x) {
+        const int y = e / b, s = e - y * b;
+        const double before = G0[(int64_t)y * b * b + s * b + s], after = G[(int64_t)y * b * b + s * b + s];
+        if (after < eta2 * before) atomicOr(flag, 1);
     }
 }
 
@@ -429,6 +486,7 @@ struct Solver {
     int nbx = 1;
     cudaStream_t st;
     DevBuf Q[2], Wb, part, hcur, Gs, Ms, Rs, Hrec, Rrec, Sd, layd, flags;
+    DevBuf G0s, Mt, Ajs, dflag;         // block_step: Gram before the pass, R^T, A_j, second-pass flag
     DescSlot desc;
     int64_t hstride = 0, rstride = 0;   // per layer record strides (doubles)
     int nslots = 0;                     // active layers
@@ -452,27 +510,29 @@ struct Solver {
     // basis: A is the orthonormal basis and B a block of norm-bounded vectors
     // (|entries| < 2), so the product may run on the tensor cores (ozaki.cu)
     ml_status gram(LMat A, int a0, int rc, LMat B, int b0, int cb, double *out, double *rec, int64_t rs,
-                   bool basis = false)
+                   bool basis = false, const int *gate = nullptr, const char *family = "dots")
     {
         const int nout = rc * cb;
         if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
         int nb = nbx;
         if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) {
-            ProfScope pr("dots", st);
-            k_lgram_dw<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>());
+            ProfScope pr(family, st);
+            k_lgram_dw<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>(),
+                                                         gate);
         } else if (basis && tensor && oz_gram_ok(rc, cb)) {
             ProfScope pr("dots", st);
             nb = oz_gram_blocks(nslots, n);
             ML_TRY(oz_gram(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, OzMat{B.base + b0, B.stride, B.ld, 1}, cb,
                            layd.as<int>(), nslots, n, nb, part.as<double>(), st));
         } else {
-            ProfScope pr("dots", st);
-            k_lgram<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>());
+            ProfScope pr(family, st);
+            k_lgram<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>(),
+                                                      gate);
         }
         {
             ProfScope pr("dots_reduce", st);
             k_lreduce<<<dim3((nout + 127) / 128, nslots), 128, 0, st>>>(part.as<double>(), nb, nout, layd.as<int>(),
-                                                                       out, rec, rs);
+                                                                       out, rec, rs, gate);
         }
         ML_CUDA(cudaGetLastError());
         return ML_OK;
@@ -480,7 +540,7 @@ struct Solver {
 
     // B_t[:, b0:b0+cb] (-)= A_t[:, a0:a0+rc] M_y; basis as for gram (M any magnitude)
     ml_status gemm(LMat A, int a0, int rc, const double *M, LMat B, int b0, int cb, bool sub, bool basis = false,
-                   const char *family = "update")
+                   const char *family = "update", const int *gate = nullptr)
     {
         ProfScope pr(family, st);
         if (basis && dword) {
@@ -488,7 +548,7 @@ struct Solver {
                 const int w = std::min(kMaxBlk, cb - j0);
                 const size_t smem = ((size_t)rc * w + (size_t)kDwGemmRows * (rc + 1)) * sizeof(float2);
                 k_lgemm_dw<<<dim3(nbx, nslots), kDwGemmRows, smem, st>>>(A, a0, rc, M + j0, cb, B, b0 + j0, w,
-                                                                        layd.as<int>(), n, sub ? 1 : 0);
+                                                                        layd.as<int>(), n, sub ? 1 : 0, gate);
             }
             ML_CUDA(cudaGetLastError());
             return ML_OK;
@@ -497,7 +557,7 @@ struct Solver {
             return oz_gemm(OzMat{A.base + a0, A.stride, A.ld, 1}, rc, M, cb, 1, (int64_t)rc * cb, cb,
                            OzOut{B.base + b0, B.stride, B.ld, 1}, layd.as<int>(), nslots, n, sub, st);
         const size_t smem = ((size_t)rc * cb + (size_t)kRows * (rc + 1)) * sizeof(double);
-        k_lgemm<<<dim3(nbx, nslots), 256, smem, st>>>(A, a0, rc, M, B, b0, cb, layd.as<int>(), n, sub ? 1 : 0);
+        k_lgemm<<<dim3(nbx, nslots), 256, smem, st>>>(A, a0, rc, M, B, b0, cb, layd.as<int>(), n, sub ? 1 : 0, gate);
         ML_CUDA(cudaGetLastError());
         return ML_OK;
     }
@@ -547,13 +607,70 @@ struct Solver {
             if (hrec) {
                 ProfScope pr("svqb", st);
                 k_lhacc<<<dim3((cq * b + 127) / 128, nslots), 128, 0, st>>>(h, Rs.as<double>(), cq, b, layd.as<int>(),
-                                                                           hrec, hstride);
+                                                                           hrec, hstride, nullptr);
                 ML_CUDA(cudaGetLastError());
             }
         }
         ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
         ML_TRY(svqb(1, rrec));
         ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), dst, d0, b, false));
+        return ML_OK;
+    }
+
+    // One block step for the block Q[:, c:c+b] (step j of the cycle), W = A Q_j
+    // on entry; FP64-pipe or double-word products (the tensor-core kind uses
+    // orthonormalise).  The three-term part first: W -= Q_{j-1} R^T (R the
+    // previous step's record, j >= 1), A_j = Q_j^T W, W -= Q_j A_j.  Then one
+    // Gram-Schmidt pass against Q[:, 0:c+b] and SVQB, and a second pass only
+    // when some column of some layer lost more than half of its norm squared
+    // in the first (the criterion of Daniel, Gragg, Kaufman and Stewart
+    // 1976, decided on the device; the second pass's kernels return at once
+    // otherwise), then SVQB into Q[:, c+b:c+2b].  The record holds the same
+    // coefficients as orthonormalise's: the three-term part's are added back.
+    ml_status block_step(int cur, int c, int j, double *hrec, double *rrec)
+    {
+        const LMat Qc = q(cur), Wm = w();
+        const int cq = c + b;
+        double *h = hcur.as<double>();
+        int *fl = dflag.as<int>();
+        const double *rprev = j >= 1 ? Rrec.as<double>() + (int64_t)(j - 1) * b * b : nullptr;
+        if (rprev) {
+            {
+                ProfScope pr("vector", st);
+                k_lthree<<<nslots, 64, 0, st>>>(rprev, rstride, layd.as<int>(), nslots, b, Mt.as<double>());
+            }
+            ML_TRY(gemm(Qc, c - b, b, Mt.as<double>(), Wm, 0, b, true, true));
+        }
+        ML_TRY(gram(Qc, c, b, Wm, 0, b, Ajs.as<double>(), nullptr, 0, true));
+        ML_TRY(gemm(Qc, c, b, Ajs.as<double>(), Wm, 0, b, true, true));
+        ML_TRY(gram(Wm, 0, b, Wm, 0, b, G0s.as<double>(), nullptr, 0));
+        ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, hrec, hstride, true));
+        ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true, true));
+        {
+            ProfScope pr("svqb", st);
+            k_lrec_add<<<nslots, 64, 0, st>>>(hrec, hstride, layd.as<int>(), nslots, rprev ? Mt.as<double>() : nullptr,
+                                             Ajs.as<double>(), c, b);
+        }
+        ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
+        ML_TRY(svqb(0, nullptr));
+        {
+            ProfScope pr("svqb", st);
+            ML_CUDA(cudaMemsetAsync(fl, 0, sizeof(int), st));
+            k_ldgks<<<std::max(1, (nslots * b + 127) / 128), 128, 0, st>>>(G0s.as<double>(), Gs.as<double>(), nslots, b,
+                                                                          0.5, fl);
+        }
+        ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), Wm, 0, b, false));
+        ML_TRY(gram(Qc, 0, cq, Wm, 0, b, h, nullptr, 0, true, fl, "dots2"));
+        ML_TRY(gemm(Qc, 0, cq, h, Wm, 0, b, true, true, "update2", fl));
+        if (hrec) {
+            ProfScope pr("svqb", st);
+            k_lhacc<<<dim3((cq * b + 127) / 128, nslots), 128, 0, st>>>(h, Rs.as<double>(), cq, b, layd.as<int>(), hrec,
+                                                                       hstride, fl);
+        }
+        ML_CUDA(cudaGetLastError());
+        ML_TRY(gram(Wm, 0, b, Wm, 0, b, Gs.as<double>(), nullptr, 0));
+        ML_TRY(svqb(1, rrec));
+        ML_TRY(gemm(Wm, 0, b, Ms.as<double>(), q(cur), cq, b, false));
         return ML_OK;
     }
 
@@ -641,6 +758,10 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
     ML_TRY(S.Sd.ensure((size_t)T * ncv * kkeep * sizeof(double)));
     ML_TRY(S.layd.ensure((size_t)T * sizeof(int)));
     ML_TRY(S.flags.ensure((size_t)T * sizeof(int)));
+    ML_TRY(S.G0s.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.Mt.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.Ajs.ensure((size_t)T * b * b * sizeof(double)));
+    ML_TRY(S.dflag.ensure(sizeof(int)));
     ML_CUDA(cudaMemsetAsync(S.flags.p, 0, (size_t)T * sizeof(int), st));
     {
         const size_t smax = ((size_t)kMaxLd * kMaxLd + (size_t)kRows * (kMaxLd + 1)) * sizeof(double);
@@ -662,6 +783,11 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
     ML_TRY(S.orthonormalise(cur, 0, S.q(cur), 0, nullptr, nullptr));
 
     std::vector<std::vector<double>> Tm(T, std::vector<double>((size_t)ncv * ncv, 0.0));
+    // per layer, the basis columns (0..ncv+b-1, the last b the residual block)
+    // that are zero because SVQB dropped their direction (a deflated block,
+    // recognised by a zero row of the step's R): the Rayleigh-Ritz step
+    // leaves them out, so that they give no spurious Ritz pairs
+    std::vector<std::vector<char>> dead(T, std::vector<char>((size_t)ncv + b, 0));
     std::vector<int> nconv(T, 0), matvecs(T, 0);
     std::vector<char> done(T, 0);
     std::vector<double> hrec_h, rrec_h, theta, Sv;
@@ -673,7 +799,10 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
             ML_TRY(S.apply(cur, c));
             double *hr = S.Hrec.as<double>() + (int64_t)j * ldq * b;
             double *rr = S.Rrec.as<double>() + (int64_t)j * b * b;
-            ML_TRY(S.orthonormalise(cur, c + b, S.q(cur), c + b, hr, rr));
+            if (tensor)
+                ML_TRY(S.orthonormalise(cur, c + b, S.q(cur), c + b, hr, rr));
+            else
+                ML_TRY(S.block_step(cur, c, j, hr, rr));
         }
         for (int y = 0; y < S.nslots; ++y) matvecs[S.lay[y]] += nsteps * b;
         // records of the cycle to the host
@@ -709,10 +838,34 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
                 }
             }
             const double *Rl = R + (int64_t)(nsteps - 1) * b * b;
-            std::vector<double> a = Tt;
-            sym_eig(ncv, a, theta, Sv);
+            std::vector<char> &dd = dead[t];
+            for (int j = 0; j < nsteps; ++j)
+                for (int qq = 0; qq < b; ++qq) {
+                    bool zero = true;
+                    for (int s2 = 0; s2 < b; ++s2) zero = zero && R[(int64_t)j * b * b + qq * b + s2] == 0.0;
+                    dd[(size_t)kk + (j + 1) * b + qq] = zero ? 1 : 0;
+                }
+            std::vector<int> live;
+            for (int i = 0; i < ncv; ++i)
+                if (!dd[i]) live.push_back(i);
+            const int m = (int)live.size(), nd = ncv - m;   // theta[0..nd-1]: no Ritz pair
+            if (m == ncv) {
+                std::vector<double> a = Tt;
+                sym_eig(ncv, a, theta, Sv);
+            } else {
+                std::vector<double> a((size_t)m * m), thc, Sc;
+                for (int r = 0; r < m; ++r)
+                    for (int c2 = 0; c2 < m; ++c2) a[(size_t)r * m + c2] = Tt[(size_t)live[r] * ncv + live[c2]];
+                if (m > 0) sym_eig(m, a, thc, Sc);
+                theta.assign(ncv, 0.0);
+                Sv.assign((size_t)ncv * ncv, 0.0);
+                for (int e = 0; e < m; ++e) {
+                    theta[nd + e] = thc[e];
+                    for (int r = 0; r < m; ++r) Sv[(size_t)live[r] * ncv + nd + e] = Sc[(size_t)r * m + e];
+                }
+            }
             double tmax = 0.0;
-            for (double x : theta) tmax = std::max(tmax, std::fabs(x));
+            for (int i = nd; i < ncv; ++i) tmax = std::max(tmax, std::fabs(theta[i]));
             // coupling of each Ritz vector to the residual block: Rl * S[last block, i]
             auto coupling = [&](int col, int qq) {
                 double x = 0.0;
@@ -720,7 +873,7 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
                 return x;
             };
             int nc = 0;
-            for (int i = ncv - 1; i >= ncv - k; --i) {
+            for (int i = ncv - 1; i >= ncv - k && i >= nd; --i) {
                 double r2 = 0.0;
                 for (int qq = 0; qq < b; ++qq) {
                     const double x = coupling(i, qq);
@@ -734,14 +887,19 @@ static ml_status layers_impl(ml_plan_s *const *L, int T, int k, double tol, int 
             if (fin) finishing.push_back(y);
             th_keep[y].resize(kkeep);
             coup[y].assign((size_t)b * kkeep, 0.0);
+            std::vector<char> nextdead((size_t)ncv + b, 0);
             for (int i = 0; i < kkeep; ++i) {
                 const int col = ncv - 1 - i;   // descending theta
-                th_keep[y][i] = theta[col];
+                nextdead[i] = col < nd ? 1 : 0;   // no Ritz pair: a zero column after the restart
+                th_keep[y][i] = col < nd ? 0.0 : theta[col];
                 for (int c2 = 0; c2 < ncv; ++c2) Sh[((size_t)y * ncv + c2) * kkeep + i] = Sv[(size_t)c2 * ncv + col];
                 for (int qq = 0; qq < b; ++qq) coup[y][(size_t)qq * kkeep + i] = coupling(col, qq);
             }
+            for (int qq = 0; qq < b; ++qq) nextdead[(size_t)kkeep + qq] = dd[(size_t)ncv + qq];
+            dd.swap(nextdead);
             if (fin)
-                for (int i = 0; i < k; ++i) evals[(size_t)t * k + i] = 1.0 - th_keep[y][i];
+                for (int i = 0; i < k; ++i)
+                    evals[(size_t)t * k + i] = ncv - 1 - i < nd ? std::nan("") : 1.0 - th_keep[y][i];
         }
         // Ritz vectors of every active layer -> the other basis buffer
         ML_CUDA(cudaMemcpyAsync(S.Sd.p, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -43,6 +43,23 @@ static size_t row_spread_offset(size_t tile_bytes)
     return off + RowSpread<D, W, NV>::smem <= kRowSpreadBudget ? off : 0;
 }
 
+// Shared memory for the FP32 spreading's staged points (the nv inputs u of
+// each of at most sub_max points, and their sorted indices when the layer
+// has a spreading order) after `bytes`, when it fits the budget: returns the
+// new total and sets *off (0: not staged; the kernel then reads the inputs
+// twice).  Staging changes no result.
+static size_t add_spread_staging(size_t bytes, int sub_max, int nv, bool with_index, int *off)
+{
+    const size_t o = (bytes + 15) & ~(size_t)15;
+    const size_t need = (size_t)sub_max * sizeof(float) * (nv + (with_index ? 1 : 0));
+    if (sub_max > 0 && o + need <= kRowSpreadBudget) {
+        *off = (int)o;
+        return o + need;
+    }
+    *off = 0;
+    return bytes;
+}
+
 template <typename T, int D, int W, int NV>
 static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &o, const LayerWork &w,
                               cudaStream_t st)
@@ -88,6 +105,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
                 sa.rows_off = (int)roff;
                 smem = roff + RowSpread<D, W, NV>::smem;
             }
+            smem = add_spread_staging(smem, p->sub_max, NV, sa.sidx != nullptr, &sa.stage_off);
             ML_TRY(set_smem(k_spread_f32<D, W, NV>, smem));
             k_spread_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(sa);
         } else {
@@ -338,6 +356,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
         memcpy(a.kbp, p->kbp, sizeof(a.kbp));
         a.scratch = scratch;
         a.nsub = p->nsub;
+        a.sub_max = p->sub_max;
         ga[t] = GroupArgs{scratch, p->grp_sub.as<int>(), tile_elems, gtile, p->ngroups};
         FoldArgs &f = fa[t];
         f.nbins = (int)g.nbins();
@@ -427,6 +446,14 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
             for (int t = 0; t < T; ++t) sa[t].rows_off = (int)roff;
             spread_batch_smem = roff + RowSpread<D, W, NV>::smem;
         }
+        int max_sub = 0, soff = 0;
+        bool any_sidx = false;
+        for (int t = 0; t < T; ++t) {
+            max_sub = std::max(max_sub, L[t]->sub_max);
+            any_sidx = any_sidx || sa[t].sidx != nullptr;
+        }
+        spread_batch_smem = add_spread_staging(spread_batch_smem, max_sub, NV, any_sidx, &soff);
+        for (int t = 0; t < T; ++t) sa[t].stage_off = soff;
     }
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_sa = 0, o_ga = align(o_sa + sizeof(SpreadArgs) * T), o_fa = align(o_ga + sizeof(GroupArgs) * T),

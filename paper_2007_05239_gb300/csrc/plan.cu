@@ -278,10 +278,18 @@ __global__ void k_gather_coords(const double *__restrict__ urel, const int *__re
     }
 }
 
-__global__ void k_bin_count(const uint32_t *__restrict__ keys, int64_t n, uint32_t cells, int *counts)
+// First sorted position of every bin (bin = key / cells, keys ascending):
+// starts[b] for b in 0..nbins, starts[nbins] = n.  Position i writes the
+// starts of the bins from just after its predecessor's bin up to its own, so
+// every entry (empty bins included) is written exactly once: no atomics
+// (a global atomic count on a few dozen bins serialised on their addresses).
+__global__ void k_bin_starts(const uint32_t *__restrict__ keys, int64_t n, uint32_t cells, int nbins, int *starts)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&counts[keys[i] / cells], 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = i < n ? (int)(keys[i] / cells) : nbins;
+        const int bp = i > 0 ? (int)(keys[i - 1] / cells) : -1;
+        for (int bb = bp + 1; bb <= b; ++bb) starts[bb] = (int)i;
+    }
 }
 
 // FP64 window weights of every point (plan time), stored as double-word
@@ -330,31 +338,95 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restri
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of `total` entries in place, one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *a, int64_t total)
+// Exclusive scan of `total` entries in place, in three launches: per-chunk
+// sums (one CTA per chunk of `chunk` entries, coalesced), a scan of the chunk
+// sums in one CTA, and the chunks' own scans from their offsets (tiles of
+// 1024 entries, Hillis-Steele in shared memory).  Integer sums: exact.
+constexpr int RS_SCAN_THREADS = 1024;
+
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v)
 {
-    __shared__ uint32_t sums[1024];
-    const int64_t chunk = (total + 1023) / 1024;
-    const int64_t lo = threadIdx.x * chunk, hi = min(total, lo + chunk);
-    uint32_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += a[i];
-    sums[threadIdx.x] = s;
+    __shared__ uint32_t red[RS_SCAN_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int t = 0; t < 1024; ++t) {
-            const uint32_t v = sums[t];
-            sums[t] = run;
-            run += v;
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// inclusive scan of one value per thread over the block (blockDim.x = 1024)
+__device__ __forceinline__ uint32_t block_incl_scan_u32(uint32_t v)
+{
+    __shared__ uint32_t wsum[RS_SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
         }
+        if (lane < (int)(blockDim.x >> 5)) wsum[lane] = w;
     }
     __syncthreads();
-    uint32_t run = sums[threadIdx.x];
-    for (int64_t i = lo; i < hi; ++i) {
-        const uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    const uint32_t r = v + (warp > 0 ? wsum[warp - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(RS_SCAN_THREADS) k_scan_sums(const uint32_t *__restrict__ a, int64_t total,
+                                                               int64_t chunk, uint32_t *sums)
+{
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(total, lo + chunk);
+    uint32_t s = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += a[i];
+    s = block_sum_u32(s);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+}
+
+// exclusive scan of the g <= 1024 chunk sums, in place
+__global__ void __launch_bounds__(RS_SCAN_THREADS) k_scan_top(uint32_t *sums, int g)
+{
+    const uint32_t v = (int)threadIdx.x < g ? sums[threadIdx.x] : 0u;
+    const uint32_t incl = block_incl_scan_u32(v);
+    if ((int)threadIdx.x < g) sums[threadIdx.x] = incl - v;
+}
+
+__global__ void __launch_bounds__(RS_SCAN_THREADS) k_scan_apply(uint32_t *a, int64_t total, int64_t chunk,
+                                                                const uint32_t *__restrict__ sums)
+{
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(total, lo + chunk);
+    uint32_t run = sums[blockIdx.x];
+    for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int64_t i = t0 + threadIdx.x;
+        const uint32_t v = i < hi ? a[i] : 0u;
+        const uint32_t incl = block_incl_scan_u32(v);
+        if (i < hi) a[i] = run + incl - v;
+        // the tile's total, from the last thread's inclusive value
+        __shared__ uint32_t tile_total;
+        if (threadIdx.x == blockDim.x - 1) tile_total = incl;
+        __syncthreads();
+        run += tile_total;
+        __syncthreads();
     }
+}
+
+static ml_status exclusive_scan(uint32_t *a, int64_t total, DevBuf &sums, cudaStream_t st)
+{
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(RS_SCAN_THREADS, (total + 4095) / 4096));
+    const int64_t chunk = (total + g - 1) / g;
+    ML_TRY(sums.ensure((size_t)g * sizeof(uint32_t)));
+    k_scan_sums<<<g, RS_SCAN_THREADS, 0, st>>>(a, total, chunk, sums.as<uint32_t>());
+    k_scan_top<<<1, RS_SCAN_THREADS, 0, st>>>(sums.as<uint32_t>(), g);
+    k_scan_apply<<<g, RS_SCAN_THREADS, 0, st>>>(a, total, chunk, sums.as<uint32_t>());
+    return ML_OK;
 }
 
 // Stable scatter: items of a block are ranked in input order, 256 per round;
@@ -402,7 +474,7 @@ ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int
                      cudaStream_t st, int **result_vals)
 {
     const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
-    DevBuf hist;
+    DevBuf hist, sums;
     ML_TRY(hist.ensure((size_t)256 * nblk * sizeof(uint32_t)));
     uint32_t *ka = keys, *kb = keys2;
     int *va = vals, *vb = vals2;
@@ -411,7 +483,7 @@ ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int
         k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist.as<uint32_t>(), nblk);
         }
         { ProfScope pr_("plan", st);
-        k_rs_scan<<<1, 1024, 0, st>>>(hist.as<uint32_t>(), (int64_t)256 * nblk);
+        ML_TRY(exclusive_scan(hist.as<uint32_t>(), (int64_t)256 * nblk, sums, st));
         }
         { ProfScope pr_("plan", st);
         k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist.as<uint32_t>(), nblk);
@@ -984,15 +1056,15 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     }
     // ---- bins -> subproblems
     DevBuf counts;
-    ML_TRY(counts.ensure((size_t)nbins * 4));
-    ML_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)nbins * 4, st));
+    ML_TRY(counts.ensure((size_t)(nbins + 1) * 4));
     { ProfScope pr_("plan", st);
-    k_bin_count<<<grid_for(n), 256, 0, st>>>(sorted_keys, n, ka.cells, counts.as<int>());
+    k_bin_starts<<<grid_for(n + 1), 256, 0, st>>>(sorted_keys, n, ka.cells, (int)nbins, counts.as<int>());
     }
     ML_CUDA(cudaGetLastError());
-    std::vector<int> hc(nbins);
-    ML_CUDA(cudaMemcpyAsync(hc.data(), counts.p, (size_t)nbins * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<int> hc(nbins), hstart(nbins + 1);
+    ML_CUDA(cudaMemcpyAsync(hstart.data(), counts.p, (size_t)(nbins + 1) * 4, cudaMemcpyDeviceToHost, st));
     ML_CUDA(cudaStreamSynchronize(st));
+    for (int64_t b = 0; b < nbins; ++b) hc[b] = hstart[b + 1] - hstart[b];
     if (p->prec == ML_F32 && nbins == 1 && ka.cells == 1) {
         // one tile: the points stay in input order (perm is the identity) and the
         // spreading visits them in the order of their first-tap cells
