@@ -603,7 +603,8 @@ int64_t ml_graph_replays(void);
 ml_status ml_plan_destroy(ml_plan_t plan);
 
 /* Free the library's cached device blocks of the current device (after a
- * device synchronisation).  Errors: ML_ERR_CUDA. */
+ * device synchronisation), and return the memory its stream-ordered pool for
+ * plan-time temporaries keeps.  Errors: ML_ERR_CUDA. */
 ml_status ml_release_cached_memory(void);
 
 /* Thread-local description of the last failure on this thread ("" if none). */

@@ -107,6 +107,26 @@ struct DevBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Temporaries of one call on one stream, from a per-device stream-ordered
+// pool (cudaMallocFromPoolAsync / cudaFreeAsync) that keeps its memory
+// between calls: allocation and release are ordered with the stream's own
+// work and never wait for the device, so calls on other streams (the layers'
+// plans built concurrently) do not serialise on each other's frees.  Falls
+// back to cudaMalloc / cudaFree where the device has no memory pools.
+struct StreamBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    bool pooled = false;
+    explicit StreamBuf(cudaStream_t s) : st(s) {}
+    StreamBuf(const StreamBuf &) = delete;
+    StreamBuf &operator=(const StreamBuf &) = delete;
+    ~StreamBuf() { release(); }
+    ml_status ensure(size_t nbytes);   // grow (contents not kept)
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
 // ------------------------------------------------------------------ plan
 struct GridGeom {
     int d = 1;

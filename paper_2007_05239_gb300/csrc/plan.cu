@@ -130,6 +130,69 @@ void DevBuf::release()
     bytes = 0;
 }
 
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;   // null entry: the device has no pools
+
+cudaMemPool_t scratch_pool(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPool_t pool = nullptr;
+    int ok = 0;
+    if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess && ok) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;   // keep freed memory in the pool
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            pool = nullptr;
+        }
+    }
+    cudaGetLastError();
+    g_pools[dev] = pool;
+    return pool;
+}
+}  // namespace
+
+ml_status StreamBuf::ensure(size_t nbytes)
+{
+    if (nbytes <= bytes && p) return ML_OK;
+    release();
+    if (nbytes == 0) return ML_OK;
+    int d = 0;
+    ML_CUDA(cudaGetDevice(&d));
+    cudaMemPool_t pool = scratch_pool(d);
+    cudaError_t e;
+    if (pool) {
+        e = cudaMallocFromPoolAsync(&p, nbytes, pool, st);
+        pooled = true;
+    } else {
+        e = cudaMalloc(&p, nbytes);
+        pooled = false;
+    }
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        return cuda_fail(e, "scratch allocation", __FILE__, __LINE__);
+    }
+    bytes = nbytes;
+    return ML_OK;
+}
+
+void StreamBuf::release()
+{
+    if (!p) return;
+    if (pooled) cudaFreeAsync(p, st);
+    else cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
 // frees every cached block of the current device
 ml_status release_cached()
 {
@@ -140,6 +203,7 @@ ml_status release_cached()
     for (auto &kv : g_cache[d]) cudaFree(kv.second);
     g_cache[d].clear();
     g_cache_bytes[d] = 0;
+    if (cudaMemPool_t pool = scratch_pool(d)) ML_CUDA(cudaMemPoolTrimTo(pool, 0));
     return ML_OK;
 }
 
@@ -418,7 +482,7 @@ __global__ void __launch_bounds__(RS_SCAN_THREADS) k_scan_apply(uint32_t *a, int
     }
 }
 
-static ml_status exclusive_scan(uint32_t *a, int64_t total, DevBuf &sums, cudaStream_t st)
+static ml_status exclusive_scan(uint32_t *a, int64_t total, StreamBuf &sums, cudaStream_t st)
 {
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(RS_SCAN_THREADS, (total + 4095) / 4096));
     const int64_t chunk = (total + g - 1) / g;
@@ -474,7 +538,7 @@ ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int
                      cudaStream_t st, int **result_vals)
 {
     const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
-    DevBuf hist, sums;
+    StreamBuf hist(st), sums(st);
     ML_TRY(hist.ensure((size_t)256 * nblk * sizeof(uint32_t)));
     uint32_t *ka = keys, *kb = keys2;
     int *va = vals, *vb = vals2;
@@ -544,7 +608,7 @@ static int grid_for(int64_t n, int threads = 256);
 ml_status bounding_box(const double *points, int64_t n, int d, cudaStream_t st, double lo[3], double hi[3])
 {
     const int nblk = grid_for(n);
-    DevBuf part;
+    StreamBuf part(st);
     ML_TRY(part.ensure((size_t)nblk * 6 * sizeof(double)));
     {
         ProfScope pr_("plan", st);
@@ -785,7 +849,7 @@ ml_status ensure_workspace(ml_plan_s *p, int nv)
 // scaling; b_l of K_R; and the measured max |K_RF - K_R| on probe distances.
 // Above target/2 the automatic choices widen the inner region (c += 2, or a
 // larger N when eps_I is fixed) and try again.
-static ml_status laplace_setup(ml_plan_s *p, const double *points, int nblk, DevBuf &part, cudaStream_t st)
+static ml_status laplace_setup(ml_plan_s *p, const double *points, int nblk, StreamBuf &part, cudaStream_t st)
 {
     const int64_t n = p->n;
     const int d = p->d;
@@ -851,7 +915,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     const int d = p->d;
     // ---- bounding box
     const int nblk = grid_for(n);
-    DevBuf part;
+    StreamBuf part(st);
     ML_TRY(part.ensure((size_t)nblk * 6 * sizeof(double)));
     { ProfScope pr_("plan", st);
     k_bbox<<<nblk, 256, 0, st>>>(points, n, d, part.as<double>());
@@ -918,7 +982,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     tm.n_os = p->n_os;
     tm.W = p->W;
     tm.d = d;
-    DevBuf lpart;
+    StreamBuf lpart(st);
     ML_TRY(lpart.ensure((size_t)nblk * 6 * sizeof(long long)));
     { ProfScope pr_("plan", st);
     k_first_tap_range<<<nblk, 256, 0, st>>>(points, n, tm, lpart.as<long long>());
@@ -994,7 +1058,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         }
     }
     // ---- keys, sort
-    DevBuf urel, keys, keys2, idx, idx2;
+    StreamBuf urel(st), keys(st), keys2(st), idx(st), idx2(st);
     ML_TRY(urel.ensure((size_t)n * d * sizeof(double)));
     ML_TRY(keys.ensure((size_t)n * 4));
     ML_TRY(keys2.ensure((size_t)n * 4));
@@ -1055,7 +1119,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
         ML_CUDA(cudaGetLastError());
     }
     // ---- bins -> subproblems
-    DevBuf counts;
+    StreamBuf counts(st);
     ML_TRY(counts.ensure((size_t)(nbins + 1) * 4));
     { ProfScope pr_("plan", st);
     k_bin_starts<<<grid_for(n + 1), 256, 0, st>>>(sorted_keys, n, ka.cells, (int)nbins, counts.as<int>());
@@ -1172,7 +1236,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     ML_TRY(apply_layer(p, v, o, st));
     ML_CUDA(cudaMemsetAsync(p->status.p, 0, 4, st));
     const int dblk = grid_for(n);
-    DevBuf range;
+    StreamBuf range(st);
     ML_TRY(range.ensure((size_t)dblk * 2 * sizeof(double)));
     { ProfScope pr_("plan", st);
     k_dinv<<<dblk, 256, 0, st>>>(p->deg.as<double>(), n, p->dinv.as<double>(), p->status.as<int>(),
