@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -469,6 +470,19 @@ __global__ void k_scale_cols(double *V, int64_t ldv, int64_t n, int k, const dou
         for (int c = 0; c < k; ++c) V[(int64_t)c * ldv + r] *= f[c];
 }
 
+// at most one full wave of resident CTAs of `kernel` (blocks of `threads`
+// threads with `smem` bytes of dynamic shared memory), and at most `want`
+template <typename K>
+static int one_wave(K kernel, int threads, size_t smem, int64_t want)
+{
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, threads, smem) != cudaSuccess || r <= 0) {
+        cudaGetLastError();
+        r = 1;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * r));
+}
+
 static int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8)); }
 
 struct Workspace {
@@ -504,9 +518,11 @@ struct Workspace {
         return ML_OK;
     }
     // blocks of the double-word Gram: several per SM (its rows are latency-bound)
+    // one full wave of resident CTAs (a partial last wave left SMs idle for a
+    // third of the pass: 8 CTAs per SM requested, 3 resident at 80 registers)
     int dw_blocks() const
     {
-        return (int)std::max<int64_t>(1, std::min<int64_t>((n + 2 * kDotThreads - 1) / (2 * kDotThreads), sm_count() * 8));
+        return one_wave(k_basis_dots<true>, kDotThreads, 0, (n + 2 * kDotThreads - 1) / (2 * kDotThreads));
     }
     // out (device, ncol) = Q[:, 0:ncol]^T x for the orthonormal basis Q (column
     // major) and a vector with |x_i| < 2: on the tensor cores when enabled
@@ -1281,8 +1297,9 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         {
             ProfScope pr("ritz", st);
             if (ws.dword && (size_t)ncv * keep * sizeof(float2) <= 48 * 1024) {
-                k_combine_dw<<<nb, 256, (size_t)ncv * keep * sizeof(float2), st>>>(Q, n, n, ncv, Sd.as<double>(), keep,
-                                                                                   Qtmp.as<double>(), n);
+                const size_t sm = (size_t)ncv * keep * sizeof(float2);
+                k_combine_dw<<<one_wave(k_combine_dw, 256, sm, nb), 256, sm, st>>>(Q, n, n, ncv, Sd.as<double>(), keep,
+                                                                                 Qtmp.as<double>(), n);
             } else if (ws.tensor && oz_gemm_ok(ncv)) {
                 // Sk is ncv x keep column-major: M[r, j] = Sk[j * ncv + r]
                 ML_TRY(oz_gemm(OzMat{Q, 0, 1, n}, ncv, Sd.as<double>(), 1, ncv, 0, keep, OzOut{Qtmp.as<double>(), 0, 1, n},

@@ -495,6 +495,19 @@ struct Solver {
     std::vector<int> lay;               // slot -> layer
 
     LMat q(int which) const { return LMat{Q[which].as<double>(), n * ldq, ldq}; }
+
+    // CTAs per layer so that the launch (x nslots) fills one wave of resident
+    // CTAs of `kernel` (a partial last wave leaves SMs idle), at most nbx
+    template <typename K>
+    int wave_x(K kernel, int threads, size_t smem) const
+    {
+        int r = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, threads, smem) != cudaSuccess || r <= 0) {
+            cudaGetLastError();
+            return nbx;
+        }
+        return std::max(1, std::min(nbx, sm_count() * r / std::max(1, nslots)));
+    }
     LMat w() const { return LMat{Wb.as<double>(), n * b, b}; }
 
     ml_status upload_lay()
@@ -515,9 +528,10 @@ struct Solver {
         const int nout = rc * cb;
         if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
         int nb = nbx;
+        if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) nb = wave_x(k_lgram_dw, 256, 0);
         if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) {
             ProfScope pr(family, st);
-            k_lgram_dw<<<dim3(nbx, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>(),
+            k_lgram_dw<<<dim3(nb, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>(),
                                                          gate);
         } else if (basis && tensor && oz_gram_ok(rc, cb)) {
             ProfScope pr("dots", st);
@@ -547,7 +561,8 @@ struct Solver {
             for (int j0 = 0; j0 < cb; j0 += kMaxBlk) {
                 const int w = std::min(kMaxBlk, cb - j0);
                 const size_t smem = ((size_t)rc * w + (size_t)kDwGemmRows * (rc + 1)) * sizeof(float2);
-                k_lgemm_dw<<<dim3(nbx, nslots), kDwGemmRows, smem, st>>>(A, a0, rc, M + j0, cb, B, b0 + j0, w,
+                k_lgemm_dw<<<dim3(wave_x(k_lgemm_dw, kDwGemmRows, smem), nslots), kDwGemmRows, smem, st>>>(
+                    A, a0, rc, M + j0, cb, B, b0 + j0, w,
                                                                         layd.as<int>(), n, sub ? 1 : 0, gate);
             }
             ML_CUDA(cudaGetLastError());
