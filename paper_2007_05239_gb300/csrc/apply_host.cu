@@ -105,6 +105,28 @@ int pass_width(const ml_plan_s *p, int remaining)
 
 // Y[i, c] = sum_t parts[t][i, c] in layer order (the layers' terms of a
 // multilayer product computed concurrently)
+// Layer terms written in each layer's sorted order (ApplyOpts::sorted_final),
+// gathered back to input order and summed in layer order:
+// Y[i, c] = sum_t parts_t[iperm_t[i], c].  The interpolation then writes
+// its output coalesced instead of read-modify-writing 32-byte sectors at
+// random input positions; one random read per layer remains, here.
+constexpr int kGatherLayers = 8;
+struct LayerPerms {
+    const int *iperm[kGatherLayers];
+};
+__global__ void k_gather_layers(const double *__restrict__ parts, LayerPerms lp, int T, int64_t n, int b, double *Y,
+                                int ldy)
+{
+    const int64_t nb = n * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / b;
+        const int c = (int)(e - i * b);
+        double s = parts[(int64_t)lp.iperm[0][i] * b + c];
+        for (int t = 1; t < T; ++t) s += parts[(int64_t)t * nb + (int64_t)lp.iperm[t][i] * b + c];
+        Y[i * ldy + c] = s;
+    }
+}
+
 __global__ void k_sum_layers(const double *__restrict__ parts, int T, int64_t n, int b, double *Y, int ldy)
 {
     const int64_t nb = n * b;
@@ -232,6 +254,10 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
         ml_plan_s *p0 = layers[0];
         ML_TRY(p0->sum_parts.ensure((size_t)T * n * b * sizeof(double)));
         double *parts = p0->sum_parts.as<double>();
+        // Gaussian fast-summation layers: terms in sorted order, gathered after
+        bool gather = T <= kGatherLayers;
+        for (int t = 0; t < T; ++t)
+            gather = gather && !layers[t]->dense && layers[t]->kernel == ML_KERNEL_GAUSS && layers[t]->iperm.p;
         ML_CUDA(cudaEventRecord(ls->fork, st));
         for (int t = 0; t < T; ++t) {
             cudaStream_t s = ls->s[t];
@@ -242,13 +268,21 @@ ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, 
                 ApplyOpts o;
                 o.normalized = base == ML_NORMALIZED_A;
                 o.alpha = 1.0 / T;
+                o.sorted_final = gather;
                 ML_TRY(apply_layer(layers[t], v, o, s));
             }
             ML_CUDA(cudaEventRecord(ls->join[t], s));
             ML_CUDA(cudaStreamWaitEvent(st, ls->join[t], 0));
         }
         ProfScope pr("vector", st);
-        k_sum_layers<<<(int)std::min<int64_t>((n * b + 255) / 256, sm_count() * 16), 256, 0, st>>>(parts, T, n, b, Y, b);
+        const int blocks = (int)std::min<int64_t>((n * b + 255) / 256, sm_count() * 16);
+        if (gather) {
+            LayerPerms lp{};
+            for (int t = 0; t < T; ++t) lp.iperm[t] = layers[t]->iperm.as<int>();
+            k_gather_layers<<<blocks, 256, 0, st>>>(parts, lp, T, n, b, Y, b);
+        } else {
+            k_sum_layers<<<blocks, 256, 0, st>>>(parts, T, n, b, Y, b);
+        }
         ML_CUDA(cudaGetLastError());
         return ML_OK;
     }

@@ -263,6 +263,7 @@ struct InterpArgs {
     const void *grid;        // T [L2][L1][L0][nv]
     double alpha, shift, self;
     int normalized, accumulate, sorted_out;
+    int sorted_final;        // the finished value at the sorted position (no accumulation)
     int nsub;                // subproblems (batched launches)
     alignas(16) float kbp[kPolyW * kPolyStride];   // FP32 window polynomials (window_row_poly)
 };
@@ -913,29 +914,33 @@ inline int fold_chunks(int64_t bins, int64_t cells_nv, int sms)
 // out[(a*Ko + k)*C + c] = sum_j M[k*J + j] * in[(a*J + j)*C + c]
 // (one real trigonometric transform along the middle index).  Tiles of
 // 32 k x 64 flattened (a, c) pairs; 256 threads, 8 outputs each.
-template <typename T>
+template <typename T, int KT = 32, int PT = 64>
 __device__ __forceinline__ void axis_block(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ M,
                                            int A, int J, int Ko, int C, int bx, int by)
 {
-    __shared__ T Ms[32][33];
-    __shared__ T Is[32][65];
+    // tiles of KT k x PT flattened (a, c) pairs; 16 threads along p and KT/2
+    // along k, each thread 2 k x PT/16 p outputs (KT * 8 threads)
+    constexpr int NQ = PT / 16;
+    __shared__ T Ms[32][KT + 1];
+    __shared__ T Is[32][PT + 1];
     const int64_t P = (int64_t)A * C;
-    const int64_t p0 = (int64_t)bx * 64;
-    const int k0 = by * 32;
+    const int64_t p0 = (int64_t)bx * PT;
+    const int k0 = by * KT;
+    const int nthr = KT * 8;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    T acc[2][4];
+    T acc[2][NQ];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = 0;
+        for (int q = 0; q < NQ; ++q) acc[i][q] = 0;
     for (int j0 = 0; j0 < J; j0 += 32) {
-        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        for (int e = threadIdx.x; e < 32 * KT; e += nthr) {
             const int kk = e >> 5, jj = e & 31;
             Ms[jj][kk] = (k0 + kk < Ko && j0 + jj < J) ? M[(int64_t)(k0 + kk) * J + j0 + jj] : (T)0;
         }
-        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+        for (int e = threadIdx.x; e < 32 * PT; e += nthr) {
             int jj, pp;
-            if (C >= 16) { jj = e >> 6; pp = e & 63; }
+            if (C >= 16) { jj = e / PT; pp = e % PT; }
             else { pp = e >> 5; jj = e & 31; }
             const int64_t p = p0 + pp;
             T v = 0;
@@ -951,7 +956,7 @@ __device__ __forceinline__ void axis_block(const T *__restrict__ in, T *__restri
         for (int jj = 0; jj < 32; ++jj) {
             const T m0 = Ms[jj][ty * 2], m1 = Ms[jj][ty * 2 + 1];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 const T x = Is[jj][tx + 16 * q];
                 acc[0][q] += m0 * x;
                 acc[1][q] += m1 * x;
@@ -964,7 +969,7 @@ __device__ __forceinline__ void axis_block(const T *__restrict__ in, T *__restri
         const int k = k0 + ty * 2 + i;
         if (k >= Ko) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int64_t p = p0 + tx + 16 * q;
             if (p >= P) continue;
             const int64_t aa = p / C;
@@ -979,6 +984,15 @@ __global__ void __launch_bounds__(256) k_axis(const T *__restrict__ in, T *__res
                                               const T *__restrict__ M, int A, int J, int Ko, int C)
 {
     axis_block<T>(in, out, M, A, J, Ko, C, blockIdx.x, blockIdx.y);
+}
+
+// the same with tiles of 16 k x 32 p (128 threads), for transforms whose
+// 32 x 64 tiles would occupy only a few SMs
+template <typename T>
+__global__ void __launch_bounds__(128) k_axis_small(const T *__restrict__ in, T *__restrict__ out,
+                                                    const T *__restrict__ M, int A, int J, int Ko, int C)
+{
+    axis_block<T, 16, 32>(in, out, M, A, J, Ko, C, blockIdx.x, blockIdx.y);
 }
 
 // FP64 form: the same transform in double-word arithmetic (grid, matrix and
@@ -1102,8 +1116,8 @@ __device__ __forceinline__ void interp_epilogue_f32(const InterpArgs &a, int i, 
     } else {
         double outv = (double)((float)a.alpha * ds * r);
         if (a.shift != 0.0) outv += a.shift * (a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0);
-        double *yp = a.Y + (int64_t)orig * a.ldy + c;
-        if (a.accumulate) outv += *yp;
+        double *yp = a.Y + (int64_t)(a.sorted_final ? i : orig) * a.ldy + c;
+        if (a.accumulate && !a.sorted_final) outv += *yp;
         *yp = outv;
     }
 }
@@ -1121,7 +1135,7 @@ struct EpilogueIn {
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
             x[c] = a.X ? a.X[(int64_t)orig * a.ldx + c] : 1.0;
-            yold[c] = (!a.sorted_out && a.accumulate) ? a.Y[(int64_t)orig * a.ldy + c] : 0.0;
+            yold[c] = (!a.sorted_out && !a.sorted_final && a.accumulate) ? a.Y[(int64_t)orig * a.ldy + c] : 0.0;
         }
     }
     __device__ __forceinline__ void finish(const InterpArgs &a, int i, int c, float acc) const
@@ -1132,8 +1146,8 @@ struct EpilogueIn {
         } else {
             double outv = (double)((float)a.alpha * ds * r);
             if (a.shift != 0.0) outv += a.shift * x[c];
-            if (a.accumulate) outv += yold[c];
-            a.Y[(int64_t)orig * a.ldy + c] = outv;
+            if (a.accumulate && !a.sorted_final) outv += yold[c];
+            a.Y[(int64_t)(a.sorted_final ? i : orig) * a.ldy + c] = outv;
         }
     }
 };
@@ -1148,8 +1162,8 @@ __device__ __forceinline__ void interp_epilogue(const InterpArgs &a, int i, int 
         a.Y[(int64_t)i * a.ldy + c] = r;
     } else {
         double outv = a.alpha * ds * r + a.shift * x;
-        double *yp = a.Y + (int64_t)orig * a.ldy + c;
-        if (a.accumulate) outv += *yp;
+        double *yp = a.Y + (int64_t)(a.sorted_final ? i : orig) * a.ldy + c;
+        if (a.accumulate && !a.sorted_final) outv += *yp;
         *yp = outv;
     }
 }

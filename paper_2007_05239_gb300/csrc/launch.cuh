@@ -31,6 +31,21 @@ static ml_status set_smem(K kernel, size_t bytes)
     return ML_OK;
 }
 
+// One real trigonometric transform along an axis (k_axis): 32 x 64 tiles, or
+// 16 x 32 tiles when the large ones would leave most SMs idle
+template <typename T>
+static void launch_axis(const T *in, T *out, const T *M, int64_t A, int J, int Ko, int64_t C, cudaStream_t st)
+{
+    const int64_t big = ((A * C + 63) / 64) * ((Ko + 31) / 32);
+    if (big >= 2 * (int64_t)sm_count()) {
+        k_axis<T><<<dim3((unsigned)((A * C + 63) / 64), (unsigned)((Ko + 31) / 32)), 256, 0, st>>>(in, out, M, (int)A, J,
+                                                                                              Ko, (int)C);
+    } else {
+        k_axis_small<T><<<dim3((unsigned)((A * C + 31) / 32), (unsigned)((Ko + 15) / 16)), 128, 0, st>>>(
+            in, out, M, (int)A, J, Ko, (int)C);
+    }
+}
+
 // Offset of the row-product slots of the FP32 spreading after a tile of
 // tile_bytes (16-byte aligned), or 0 when the path does not apply or the
 // slots would not fit next to the tile (the plan limits its vectors per pass
@@ -164,9 +179,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         const int64_t C = Kpow * nv;
         ProfScope pr("axis", st);
         if (f32) {
-            dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.K + 31) / 32));
-            k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_f[a].as<T>(), (int)A, g.L[a], g.K,
-                                            (int)C);
+            launch_axis<T>(bufs[cur], bufs[cur ^ 1], p->trig_f[a].as<T>(), A, g.L[a], g.K, C, st);
         } else {
             const int64_t outs = A * C * g.K;
             k_axis_dw<float2><<<(unsigned)((outs + 127) / 128), 128, 0, st>>>(
@@ -194,9 +207,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         const int64_t C = Kpow * nv;
         ProfScope pr("axis", st);
         if (f32) {
-            dim3 grid((unsigned)((A * C + 63) / 64), (unsigned)((g.L[a] + 31) / 32));
-            k_axis<T><<<grid, 256, 0, st>>>(bufs[cur], bufs[cur ^ 1], p->trig_b[a].as<T>(), (int)A, g.K, g.L[a],
-                                            (int)C);
+            launch_axis<T>(bufs[cur], bufs[cur ^ 1], p->trig_b[a].as<T>(), A, g.K, g.L[a], C, st);
         } else {
             const int64_t outs = A * C * g.L[a];
             k_axis_dw<float2><<<(unsigned)((outs + 127) / 128), 128, 0, st>>>(
@@ -242,6 +253,7 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     ia.normalized = o.normalized;
     ia.accumulate = o.accumulate;
     ia.sorted_out = o.sorted_out;
+    ia.sorted_final = o.sorted_final;
     ia.nsub = p->nsub;
     if (p->nsub > 0) {
         const size_t smem = (size_t)tc * nv * sizeof(T);

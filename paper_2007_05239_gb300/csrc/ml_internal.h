@@ -198,6 +198,7 @@ struct ml_plan_s {
 
     // device data (sorted order unless noted)
     ml::DevBuf perm;      // int32 n: sorted position -> input index
+    ml::DevBuf iperm;     // int32 n: input index -> sorted position
     ml::DevBuf coords;    // T n*d local grid coordinates
     ml::DevBuf sidx;      // int32 n (FP32 layers of one tile): the spreading order of the
                           // sorted positions, by first-tap cell (the others keep input order)
@@ -298,6 +299,8 @@ struct ApplyOpts {
     bool normalized = false;   // pre- and post-scale by D^{-1/2}
     bool accumulate = false;   // Y += instead of Y =
     bool sorted_out = false;   // write Y in sorted order, no post-scale (degree set-up)
+    bool sorted_final = false; // write the finished value (post-scaled, no accumulation) at the sorted
+                               // position: the layer terms gathered back to input order later
     double alpha = 1.0;
     double shift = 0.0;        // adds shift * x (input order) to the output: used for L_sym + delta I
     double self = 1.0;         // K(0): subtracted self term coefficient

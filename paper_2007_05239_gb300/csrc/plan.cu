@@ -562,6 +562,13 @@ ml_status radix_sort(uint32_t *keys, int *vals, uint32_t *keys2, int *vals2, int
     return ML_OK;
 }
 
+// iperm[perm[s]] = s
+__global__ void k_invert_perm(const int *__restrict__ perm, int64_t n, int *iperm)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        iperm[perm[s]] = (int)s;
+}
+
 __global__ void k_copy_int(const int *src, int *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1097,6 +1104,10 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
     { ProfScope pr_("plan", st);
     k_copy_int<<<grid_for(n), 256, 0, st>>>(sorted_idx, p->perm.as<int>(), n);
     }
+    ML_TRY(p->iperm.ensure((size_t)n * 4));
+    { ProfScope pr_("plan", st);
+    k_invert_perm<<<grid_for(n), 256, 0, st>>>(p->perm.as<int>(), n, p->iperm.as<int>());
+    }
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     ML_TRY(p->coords.ensure((size_t)n * d * ts));
     if (p->prec == ML_F32)
@@ -1264,7 +1275,7 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
 int64_t ml_plan_s::device_bytes() const
 {
     int64_t t = 0;
-    const ml::DevBuf *bufs[] = {&perm, &coords, &sidx, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
+    const ml::DevBuf *bufs[] = {&perm, &iperm, &coords, &sidx, &wts, &offs, &deg, &dinv, &sub_bin, &sub_start, &sub_count, &bin_sub, &grp_sub, &bin_grp,
                                 &trig_f[0], &trig_f[1], &trig_f[2], &trig_b[0], &trig_b[1], &trig_b[2],
                                 &mult_d, &scratch, &work[0], &work[1], &stage_x, &stage_y, &status, &Wd,
                                 &nf_loc, &nf_orig, &nf_sidx, &nf_start, &nf_task};
@@ -1274,7 +1285,7 @@ int64_t ml_plan_s::device_bytes() const
 
 static void release_all(ml_plan_s *p)
 {
-    ml::DevBuf *bufs[] = {&p->perm, &p->coords, &p->sidx, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
+    ml::DevBuf *bufs[] = {&p->perm, &p->iperm, &p->coords, &p->sidx, &p->wts, &p->offs, &p->deg, &p->dinv, &p->sub_bin, &p->sub_start, &p->sub_count,
                           &p->bin_sub, &p->grp_sub, &p->bin_grp, &p->trig_f[0], &p->trig_f[1], &p->trig_f[2], &p->trig_b[0], &p->trig_b[1],
                           &p->trig_b[2], &p->mult_d, &p->scratch, &p->work[0], &p->work[1], &p->stage_x,
                           &p->stage_y, &p->status, &p->batch_desc, &p->batch_part, &p->Wd, &p->sum_parts};
