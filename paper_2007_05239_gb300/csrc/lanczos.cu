@@ -261,6 +261,15 @@ __device__ __forceinline__ void block_sum_to(double v, double *out)
     }
 }
 
+// Row tiles of the update: a block walks tiles of kDotThreads * kTileRows
+// consecutive rows (thread t owns rows r0 + t + kDotThreads k, k <
+// kTileRows: coalesced) and, within a tile, streams the basis column by
+// column, so that the memory sees long runs of one column (16 KB per tile)
+// instead of short pieces of all columns at once; each thread keeps
+// kTileRows loads in flight.  (The dots keep whole-grid strides: their
+// per-tile reductions cost more than the locality gained.)
+constexpr int kTileRows = 8;
+
 // part[blk * nout + c] = sum over this block's rows of col_c(r) x_r, where
 // col_c is Q[:, c] for c < ncol and x itself for c = ncol when self = 1
 // (nout = ncol + self).  When gate is non-null and *gate == 0 the pass was
@@ -324,13 +333,15 @@ __global__ void __launch_bounds__(kDotThreads) k_basis_dots(const double *__rest
     }
 }
 
-// x -= Q[:, 0:ncol] h, h staged once per block (dynamic shared memory of
-// ncol operands); with norm_part, also the block's sum of the new x_r^2.
-// Gate as in k_basis_dots.
+// x -= Q[:, 0:ncol] h over row tiles (each thread's
+// kTileRows rows accumulated in registers while the columns stream by), h
+// staged once per block (dynamic shared memory of ncol operands); with
+// norm_part, also the block's sum of the new x_r^2.  Gate as in k_basis_dots.
 template <bool DW>
-__global__ void __launch_bounds__(256) k_basis_update(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
-                                                     const double *__restrict__ h, const int *__restrict__ gate,
-                                                     double *x, double *norm_part)
+__global__ void __launch_bounds__(kDotThreads) k_basis_update(const double *__restrict__ Q, int64_t ldq, int64_t n,
+                                                              int ncol, const double *__restrict__ h,
+                                                              const int *__restrict__ gate, double *x,
+                                                              double *norm_part)
 {
     using A = BasisArith<DW>;
     if (gate && *gate == 0) return;
@@ -339,12 +350,31 @@ __global__ void __launch_bounds__(256) k_basis_update(const double *__restrict__
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = A::op(h[c]);
     __syncthreads();
     double s2 = 0.0;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        typename A::acc_t acc = A::zero();
-        for (int c = 0; c < ncol; ++c) A::mac(acc, A::op(Q[(int64_t)c * ldq + r]), hs[c]);
-        const double v = x[r] - A::value(acc);
-        x[r] = v;
-        s2 = fma(v, v, s2);
+    constexpr int64_t tile = (int64_t)kDotThreads * kTileRows;
+    for (int64_t r0 = (int64_t)blockIdx.x * tile; r0 < n; r0 += (int64_t)gridDim.x * tile) {
+        typename A::acc_t acc[kTileRows];
+#pragma unroll
+        for (int k = 0; k < kTileRows; ++k) acc[k] = A::zero();
+        for (int c = 0; c < ncol; ++c) {
+            double q[kTileRows];
+#pragma unroll
+            for (int k = 0; k < kTileRows; ++k) {
+                const int64_t r = r0 + threadIdx.x + (int64_t)kDotThreads * k;
+                q[k] = r < n ? Q[(int64_t)c * ldq + r] : 0.0;
+            }
+            const typename A::op_t hc = hs[c];
+#pragma unroll
+            for (int k = 0; k < kTileRows; ++k) A::mac(acc[k], A::op(q[k]), hc);
+        }
+#pragma unroll
+        for (int k = 0; k < kTileRows; ++k) {
+            const int64_t r = r0 + threadIdx.x + (int64_t)kDotThreads * k;
+            if (r < n) {
+                const double v = x[r] - A::value(acc[k]);
+                x[r] = v;
+                s2 = fma(v, v, s2);
+            }
+        }
     }
     if (norm_part) block_sum_to(s2, norm_part + blockIdx.x);
 }
@@ -517,12 +547,22 @@ struct Workspace {
         ML_CUDA(cudaMemsetAsync(lay0.p, 0, sizeof(int), st));
         return ML_OK;
     }
-    // blocks of the double-word Gram: several per SM (its rows are latency-bound)
-    // one full wave of resident CTAs (a partial last wave left SMs idle for a
-    // third of the pass: 8 CTAs per SM requested, 3 resident at 80 registers)
+    // grids of the basis products: one full wave of resident CTAs (a partial
+    // last wave leaves SMs idle); the update at most one CTA per row tile.
+    // dw_blocks() and vec_blocks() bound these grids (the partial-sum buffers
+    // are sized with them).
+    int64_t row_tiles() const { return (n + (int64_t)kDotThreads * kTileRows - 1) / ((int64_t)kDotThreads * kTileRows); }
     int dw_blocks() const
     {
-        return one_wave(k_basis_dots<true>, kDotThreads, 0, (n + 2 * kDotThreads - 1) / (2 * kDotThreads));
+        const int64_t want = (n + 2 * kDotThreads - 1) / (2 * kDotThreads);
+        return dword ? one_wave(k_basis_dots<true>, kDotThreads, 0, want)
+                     : one_wave(k_basis_dots<false>, kDotThreads, 0, want);
+    }
+    static size_t update_smem(int ncol, bool dw) { return (size_t)ncol * (dw ? sizeof(float2) : sizeof(double)); }
+    int update_blocks(int ncol) const
+    {
+        return dword ? one_wave(k_basis_update<true>, kDotThreads, update_smem(ncol, true), row_tiles())
+                     : one_wave(k_basis_update<false>, kDotThreads, update_smem(ncol, false), row_tiles());
     }
     // out (device, ncol) = Q[:, 0:ncol]^T x for the orthonormal basis Q (column
     // major) and a vector with |x_i| < 2: on the tensor cores when enabled
@@ -560,8 +600,8 @@ struct Workspace {
     {
         ProfScope pr("update", st);
         if (dword) {
-            k_basis_update<true><<<vec_blocks(n), 256, (size_t)ncol * sizeof(float2), st>>>(Q, ldq, n, ncol, h, nullptr,
-                                                                                          x, nullptr);
+            k_basis_update<true><<<update_blocks(ncol), kDotThreads, update_smem(ncol, true), st>>>(
+                Q, ldq, n, ncol, h, nullptr, x, nullptr);
             ML_CUDA(cudaGetLastError());
             return ML_OK;
         }
@@ -632,7 +672,7 @@ struct Workspace {
         double *h1 = hdev.as<double>();      // ncol coefficients + |x|^2 before the pass
         double *h2 = h1 + ncol + 1;          // second pass
         double *sc = h2 + ncol;              // alpha, |x|^2 after pass 1, after pass 2, flag
-        const int nbv = vec_blocks(n), nbd = dw_blocks();
+        const int nbv = vec_blocks(n), nbd = dw_blocks(), nbu = update_blocks(ncol);
         int *fl = flag.as<int>();
         {
             ProfScope pr("vector", st);
@@ -640,7 +680,7 @@ struct Workspace {
             k_reduce_cols<<<1, 32, 0, st>>>(npart.as<double>(), nbv, 1, sc);
             k_sub_scaled<<<nbv, 256, 0, st>>>(sc, qj, n, x);
         }
-        const size_t hsm = (size_t)ncol * (dword ? sizeof(float2) : sizeof(double));
+        const size_t hsm = update_smem(ncol, dword);
         for (int pass = 0; pass < 2; ++pass) {
             double *h = pass == 0 ? h1 : h2;
             const int *gate = pass == 0 ? nullptr : fl;
@@ -661,10 +701,10 @@ struct Workspace {
             {
                 ProfScope pr(pass == 0 ? "update" : "update2", st);
                 if (dword)
-                    k_basis_update<true><<<nbv, 256, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
+                    k_basis_update<true><<<nbu, kDotThreads, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
                 else
-                    k_basis_update<false><<<nbv, 256, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
-                k_dgks<<<1, 32, 0, st>>>(npart.as<double>(), nbv, h1 + ncol, 0.5, sc + 1 + pass,
+                    k_basis_update<false><<<nbu, kDotThreads, hsm, st>>>(Q, ldq, n, ncol, h, gate, x, npart.as<double>());
+                k_dgks<<<1, 32, 0, st>>>(npart.as<double>(), nbu, h1 + ncol, 0.5, sc + 1 + pass,
                                          pass == 0 ? fl : nullptr, sc + 3);
             }
         }
