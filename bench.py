@@ -767,7 +767,16 @@ FAMILY_NOTES = {
 # keyed by (workload, form, kernel family, window width, vectors per pass),
 # with the hash of the kernel sources at the time of the capture: a changed
 # source makes the figure stale and the line reports null
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_spread_f32<3,5,1>, both layers of the 10-megapixel image (one launch
+    # each, ncu --set full of the apply-mode run): 794.1 and 513.1 MB, mean
+    # 653.6 MB per launch
+    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (653.6e6, "1605bc3bffe0d808",
+                                                      "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
+                                                      "the two layers' launches; includes the subproblem tiles "
+                                                      "written for the fold (192 MB) and 32-byte sectors of the "
+                                                      "random input gathers"),
+}
 KERNEL_SOURCES = ["paper_2007_05239_gb300/csrc/kernels.cuh", "paper_2007_05239_gb300/csrc/launch.cuh"]
 
 
