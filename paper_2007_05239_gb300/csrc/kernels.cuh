@@ -117,10 +117,6 @@ __device__ __forceinline__ void fixed_split(float p, float e, int &hi, int &lo)
 // The W window weights of one dimension for a point with local coordinate x
 // (relative to its bin origin): the taps are the W cells nearest to x, the
 // first at o = floor(x - W/2) + 1, and the weight of tap q is
-// phi_n(x - o - q), |x - o - q| <= W/2.
-// The W window weights of one dimension for a point with local coordinate x
-// (relative to its bin origin): the taps are the W cells nearest to x, the
-// first at o = floor(x - W/2) + 1, and the weight of tap q is
 // phi_n(x - o - q), |x - o - q| <= W/2.  FP32 form, from polynomials fitted
 // at plan time: with
 // f = (x - W/2) - floor(x - W/2) in [0, 1) and u = f - 1/2, tap q has weight
