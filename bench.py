@@ -767,6 +767,8 @@ FAMILY_NOTES = {
 # keyed by (workload, form, kernel family, window width, vectors per pass),
 # with the hash of the kernel sources at the time of the capture: a changed
 # source makes the figure stale and the line reports null
+DW_OPS_PER_FMA = 10
+
 NCU_TRAFFIC = {
     # k_spread_f32<3,5,1>, both layers of the 10-megapixel image (one launch
     # each, ncu --set full of the apply-mode run): 794.1 and 513.1 MB, mean
@@ -805,7 +807,10 @@ def kernel_roofline(workload, spec, prof, infos, applied, n, T, nv, prec, prof_s
     sec = fam_ms / 1e3
     flops = applied * 2.0 * taps
     achieved = flops / sec / 1e12 if sec > 0 else 0.0
-    peak = peaks["fp32_tflops"]
+    # the FP64 form's taps are double-word multiply-adds on the FP32 pipe: an
+    # exact product by FMA (4 lane operations) and an exact two-sum (6), so its
+    # ALU roof is the measured FP32 rate / 10 in FP64-class flops
+    peak = peaks["fp32_tflops"] if prec == "f32" else peaks["fp32_tflops"] / DW_OPS_PER_FMA
     point_bytes = (8 * d * W + 4 if prec == "f64" else 4 * d) + 4 + 8
     vec_bytes = 8 if fam == "spread" else 16
     hbm_bytes = applied / nv * point_bytes + applied * vec_bytes
@@ -823,8 +828,8 @@ def kernel_roofline(workload, spec, prof, infos, applied, n, T, nv, prec, prof_s
            "frac": achieved / peak if peak else None, "traffic": traffic, "traffic_note": traffic_note,
            "algorithmic_bytes_per_launch": per_launch,
            "peak_source": "FP32 FMA pipe, measured in this run (ml_measure_peak fp32)"
-                          + ("; the FP64 form's taps are double-word operations on this pipe" if prec == "f64"
-                             else ""),
+                          + (f"; FP64 form: / {DW_OPS_PER_FMA} lane operations per double-word multiply-add"
+                             if prec == "f64" else ""),
            "work": f"2 flop per tap, W^d = {taps} taps per point-vector, W = {W}, {nv} vector(s) per pass",
            "hbm": {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": hbm_gbs / peaks["hbm_gbs"], "bytes_per_point_pass": point_bytes,
@@ -840,7 +845,11 @@ def kernel_roofline(workload, spec, prof, infos, applied, n, T, nv, prec, prof_s
         out["smem_atomics"] = {"achieved": atom, "peak": peaks["smem_atomic_per_s_1e12"], "unit": "1e12/s",
                                "frac": atom / peaks["smem_atomic_per_s_1e12"],
                                "per_tap_and_vector": per_tap,
-                               "peak_source": "conflict-free 32-bit shared atomics, measured in this run"}
+                               "peak_source": "conflict-free 32-bit shared atomics, measured in this run",
+                               "note": ("tap accumulations per second; warps whose points share their first tap "
+                                        "(the row products) issue one atomic per 32 taps, so the atomics "
+                                        "themselves are fewer" if prec == "f32" else
+                                        "two 32-bit atomics (fixed-point hi and lo) per tap")}
     largest = max(prof, key=lambda f: prof[f][1]) if prof else None
     out["largest_family"] = largest
     if largest in FAMILY_NOTES:
