@@ -261,19 +261,24 @@ __device__ __forceinline__ void block_sum_to(double v, double *out)
     }
 }
 
-// Row tiles of the update: a block walks tiles of kDotThreads * kTileRows
-// consecutive rows (thread t owns rows r0 + t + kDotThreads k, k <
-// kTileRows: coalesced) and, within a tile, streams the basis column by
+// Row tiles of the basis products: a block walks tiles of kDotThreads *
+// kTileRows consecutive rows (thread t owns rows r0 + t + kDotThreads k,
+// k < kTileRows: coalesced) and, within a tile, streams the basis column by
 // column, so that the memory sees long runs of one column (16 KB per tile)
 // instead of short pieces of all columns at once; each thread keeps
-// kTileRows loads in flight.  (The dots keep whole-grid strides: their
-// per-tile reductions cost more than the locality gained.)
+// kTileRows loads in flight.
 constexpr int kTileRows = 8;
 
 // part[blk * nout + c] = sum over this block's rows of col_c(r) x_r, where
 // col_c is Q[:, c] for c < ncol and x itself for c = ncol when self = 1
-// (nout = ncol + self).  When gate is non-null and *gate == 0 the pass was
-// skipped by the device and every block returns at once.
+// (nout = ncol + self).  Row tiles as the update (below); the columns in
+// chunks of kDotCols: for each chunk the block walks all its tiles, each
+// thread accumulating its rows' products per column in registers, and
+// reduces once at the end of the chunk (warp shuffles, then the warps in a
+// fixed order).  x is read once per chunk (the block's rows stay in L2).
+// When gate is non-null and *gate == 0 the pass was skipped by the device
+// and every block returns at once.
+constexpr int kDotCols = 4;
 template <bool DW>
 __global__ void __launch_bounds__(kDotThreads) k_basis_dots(const double *__restrict__ Q, int64_t ldq, int64_t n,
                                                             int ncol, int self, const double *__restrict__ x,
@@ -281,50 +286,46 @@ __global__ void __launch_bounds__(kDotThreads) k_basis_dots(const double *__rest
 {
     using A = BasisArith<DW>;
     if (gate && *gate == 0) return;
-    __shared__ double red[kDotThreads / 32][8];
+    __shared__ double red[kDotThreads / 32][kDotCols];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nout = ncol + self;
-    for (int c0 = 0; c0 < nout; c0 += 8) {
-        typename A::acc_t acc[8];
+    constexpr int64_t tile = (int64_t)kDotThreads * kTileRows;
+    for (int c0 = 0; c0 < nout; c0 += kDotCols) {
+        typename A::acc_t acc[kDotCols];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = A::zero();
-        // two rows per iteration: both rows' loads are in flight together
-        const int64_t step = (int64_t)gridDim.x * kDotThreads;
-        int64_t r = blockIdx.x * (int64_t)kDotThreads + threadIdx.x;
-        for (; r + step < n; r += 2 * step) {
-            double q0[8], q1[8];
-            const double x0 = x[r], x1 = x[r + step];
+        for (int k = 0; k < kDotCols; ++k) acc[k] = A::zero();
+        for (int64_t r0 = (int64_t)blockIdx.x * tile; r0 < n; r0 += (int64_t)gridDim.x * tile) {
+            double xv[kTileRows];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = c0 + k;
-                q0[k] = c < ncol ? Q[(int64_t)c * ldq + r] : (c < nout ? x0 : 0.0);
-                q1[k] = c < ncol ? Q[(int64_t)c * ldq + r + step] : (c < nout ? x1 : 0.0);
+            for (int k = 0; k < kTileRows; ++k) {
+                const int64_t r = r0 + threadIdx.x + (int64_t)kDotThreads * k;
+                xv[k] = r < n ? x[r] : 0.0;
             }
-            const typename A::op_t xr0 = A::op(x0), xr1 = A::op(x1);
+            typename A::op_t xo[kTileRows];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c0 + k < nout) {
-                    A::mac(acc[k], A::op(q0[k]), xr0);
-                    A::mac(acc[k], A::op(q1[k]), xr1);
+            for (int k = 0; k < kTileRows; ++k) xo[k] = A::op(xv[k]);
+#pragma unroll
+            for (int j = 0; j < kDotCols; ++j) {
+                const int c = c0 + j;
+                if (c >= nout) break;
+                double q[kTileRows];
+#pragma unroll
+                for (int k = 0; k < kTileRows; ++k) {
+                    const int64_t r = r0 + threadIdx.x + (int64_t)kDotThreads * k;
+                    q[k] = c < ncol ? (r < n ? Q[(int64_t)c * ldq + r] : 0.0) : xv[k];
                 }
-        }
-        if (r < n) {
-            const double x0 = x[r];
-            const typename A::op_t xr = A::op(x0);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = c0 + k;
-                if (c < nout) A::mac(acc[k], A::op(c < ncol ? Q[(int64_t)c * ldq + r] : x0), xr);
+                for (int k = 0; k < kTileRows; ++k) A::mac(acc[j], A::op(q[k]), xo[k]);
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            double v = A::value(acc[k]);
+        for (int j = 0; j < kDotCols; ++j) {
+            double v = A::value(acc[j]);
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][k] = v;
+            if (lane == 0) red[warp][j] = v;
         }
         __syncthreads();
-        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nout) {
+        if (threadIdx.x < kDotCols && c0 + (int)threadIdx.x < nout) {
             double sacc = 0.0;
             for (int w = 0; w < kDotThreads / 32; ++w) sacc += red[w][threadIdx.x];
             part[(int64_t)blockIdx.x * nout + c0 + threadIdx.x] = sacc;
@@ -554,9 +555,8 @@ struct Workspace {
     int64_t row_tiles() const { return (n + (int64_t)kDotThreads * kTileRows - 1) / ((int64_t)kDotThreads * kTileRows); }
     int dw_blocks() const
     {
-        const int64_t want = (n + 2 * kDotThreads - 1) / (2 * kDotThreads);
-        return dword ? one_wave(k_basis_dots<true>, kDotThreads, 0, want)
-                     : one_wave(k_basis_dots<false>, kDotThreads, 0, want);
+        return dword ? one_wave(k_basis_dots<true>, kDotThreads, 0, row_tiles())
+                     : one_wave(k_basis_dots<false>, kDotThreads, 0, row_tiles());
     }
     static size_t update_smem(int ncol, bool dw) { return (size_t)ncol * (dw ? sizeof(float2) : sizeof(double)); }
     int update_blocks(int ncol) const
