@@ -527,9 +527,13 @@ struct Solver {
     {
         const int nout = rc * cb;
         if (nout > kGramOut) return fail(ML_ERR_ARG, "Gram block too large");
+        // double-word products for every Gram of the double-word kind (any
+        // magnitudes: the block's own Gram W^T W as well; the FP64 kernel's
+        // 8 x 8 outputs left most of its threads idle at each chunk's barrier)
         int nb = nbx;
-        if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) nb = wave_x(k_lgram_dw, 256, 0);
-        if (basis && dword && rc <= kMaxLd && cb <= kMaxBlk) {
+        const bool dw = dword && rc <= kMaxLd && cb <= kMaxBlk;
+        if (dw) nb = wave_x(k_lgram_dw, 256, 0);
+        if (dw) {
             ProfScope pr(family, st);
             k_lgram_dw<<<dim3(nb, nslots), 256, 0, st>>>(A, a0, rc, B, b0, cb, layd.as<int>(), n, part.as<double>(),
                                                          gate);
@@ -552,18 +556,19 @@ struct Solver {
         return ML_OK;
     }
 
-    // B_t[:, b0:b0+cb] (-)= A_t[:, a0:a0+rc] M_y; basis as for gram (M any magnitude)
+    // B_t[:, b0:b0+cb] (-)= A_t[:, a0:a0+rc] M_y (M any magnitude); B may be A.
+    // Double-word kind: k_lgemm_dw for every product; basis (A the orthonormal
+    // basis, entries below 2) lets the tensor-core kind take it
     ml_status gemm(LMat A, int a0, int rc, const double *M, LMat B, int b0, int cb, bool sub, bool basis = false,
                    const char *family = "update", const int *gate = nullptr)
     {
         ProfScope pr(family, st);
-        if (basis && dword) {
+        if (dword && rc <= kMaxLd) {
             for (int j0 = 0; j0 < cb; j0 += kMaxBlk) {
                 const int w = std::min(kMaxBlk, cb - j0);
                 const size_t smem = ((size_t)rc * w + (size_t)kDwGemmRows * (rc + 1)) * sizeof(float2);
                 k_lgemm_dw<<<dim3(wave_x(k_lgemm_dw, kDwGemmRows, smem), nslots), kDwGemmRows, smem, st>>>(
-                    A, a0, rc, M + j0, cb, B, b0 + j0, w,
-                                                                        layd.as<int>(), n, sub ? 1 : 0, gate);
+                    A, a0, rc, M + j0, cb, B, b0 + j0, w, layd.as<int>(), n, sub ? 1 : 0, gate);
             }
             ML_CUDA(cudaGetLastError());
             return ML_OK;
