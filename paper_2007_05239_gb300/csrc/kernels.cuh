@@ -396,24 +396,28 @@ __device__ __forceinline__ void warp_spread_sum(int *tile, int tc, int Pt, const
 // load and one multiply per point but nearly double the slots, which then
 // cost a resident block per SM.)
 __host__ __device__ constexpr int row_slot_head(int W, int NV) { return (W + NV + 3) / 4 * 4; }
-__host__ __device__ constexpr int row_slot_floats(int W, int NV)
+// floats per point, padded to 4 (mod 8) so that the lanes' 16-byte slot
+// stores fall on distinct bank groups
+__host__ __device__ constexpr int pad_slot(int f) { return ((f + 3) / 4 * 4) % 8 == 0 ? (f + 3) / 4 * 4 + 4 : (f + 3) / 4 * 4; }
+__host__ __device__ constexpr int row_slot_floats(int W, int NV) { return pad_slot(row_slot_head(W, NV) + 2 * W); }
+// d = 2 (warp_spread_taps): wx, wy, padding, u
+__host__ __device__ constexpr int tap_slot_u0(int W) { return (2 * W + 3) / 4 * 4; }
+__host__ __device__ constexpr int tap_slot_floats(int W, int NV) { return pad_slot(tap_slot_u0(W) + NV); }
+// whether warps whose points share a first tap use the shared slots (d = 3:
+// row products, d = 2: one tap per lane), and the bytes of the slots of a
+// 256-thread block (8 warps of 32 points)
+__host__ __device__ constexpr bool warp_slots_on(int D, int W) { return (D == 3 && W <= 8) || (D == 2 && W * W <= 64); }
+__host__ __device__ constexpr size_t warp_slot_bytes(int D, int W, int NV)
 {
-    // floats per point, padded to 4 (mod 8) so that the lanes' 16-byte slot
-    // stores fall on distinct bank groups
-    return ((row_slot_head(W, NV) + 2 * W + 3) / 4 * 4) % 8 == 0 ? (row_slot_head(W, NV) + 2 * W + 3) / 4 * 4 + 4
-                                                                 : (row_slot_head(W, NV) + 2 * W + 3) / 4 * 4;
-}
-// bytes of the slots of a 256-thread block (8 warps of 32 points)
-__host__ __device__ constexpr size_t row_spread_bytes(int W, int NV)
-{
-    return (size_t)8 * 32 * row_slot_floats(W, NV) * sizeof(float);
+    return !warp_slots_on(D, W) ? 0
+                                : (size_t)8 * 32 * (D == 3 ? row_slot_floats(W, NV) : tap_slot_floats(W, NV)) * sizeof(float);
 }
 template <int D, int W, int NV>
 struct RowSpread {
-    static constexpr bool on = (D == 3 && W <= 8);
-    static constexpr int S = row_slot_floats(W, NV);
+    static constexpr bool on = warp_slots_on(D, W);
+    static constexpr int S = D == 3 ? row_slot_floats(W, NV) : tap_slot_floats(W, NV);
     static constexpr int warp_floats = 32 * S;
-    static constexpr size_t smem = on ? row_spread_bytes(W, NV) : 0;
+    static constexpr size_t smem = warp_slot_bytes(D, W, NV);
 };
 
 template <int W, int NV>
@@ -480,6 +484,71 @@ __device__ __forceinline__ void warp_spread_rows(int *tile, int tc, int Pt, cons
             for (int c = 0; c < NV; ++c)
 #pragma unroll
                 for (int qx = 0; qx < W; ++qx) atomicAdd(row + c * tc + qx, __float2int_rn(acc[c][qx]));
+        }
+    }
+    __syncwarp();   // the slots are rewritten by the next group
+}
+
+// d = 2 counterpart of warp_spread_rows: the warp's 32 points share their
+// first tap, lane l owns the taps t = l, l + 32, ... (t = qy W + qx) and
+// adds, for p = 0..31 in order, u_pc (wx_p[qx] wy_p[qy]) to its
+// accumulator of vector c.  The slots hold wx and wy (W distinct words each)
+// and u (broadcast, 16 bytes at a time).  One atomic per tap and vector;
+// the arithmetic per vector does not depend on the pass width.
+template <int W, int NV>
+__device__ __forceinline__ void warp_spread_taps(int *tile, int tc, int Pt, const int (&o)[3], const float (&u)[NV],
+                                                 const float (&wx)[W], const float (&wy)[W], float *slots, int lane)
+{
+    constexpr int S = tap_slot_floats(W, NV);
+    constexpr int U0 = tap_slot_u0(W);
+    constexpr int NT = W * W;
+    constexpr int NU = (NV + 3) / 4 * 4;
+    {
+        float v[S];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            v[q] = wx[q];
+            v[W + q] = wy[q];
+        }
+#pragma unroll
+        for (int q = 2 * W; q < U0; ++q) v[q] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[U0 + c] = u[c];
+#pragma unroll
+        for (int q = U0 + NV; q < S; ++q) v[q] = 0.0f;
+        float4 *dst = reinterpret_cast<float4 *>(slots + lane * S);
+#pragma unroll
+        for (int k = 0; k < S / 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int t0 = 0; t0 < NT; t0 += 32) {
+        const int t = t0 + lane;
+        const int tt = t < NT ? t : NT - 1;
+        const int qy = tt / W, qx = tt - qy * W;
+        float acc[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
+#pragma unroll 4
+        for (int p = 0; p < 32; ++p) {
+            const float *sp = slots + p * S;
+            const float b = sp[qx] * sp[W + qy];
+            float uu[NU];
+#pragma unroll
+            for (int k = 0; k < NU; k += 4) {
+                const float4 q4 = *reinterpret_cast<const float4 *>(sp + U0 + k);
+                uu[k] = q4.x;
+                uu[k + 1] = q4.y;
+                uu[k + 2] = q4.z;
+                uu[k + 3] = q4.w;
+            }
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc[c] = fmaf(uu[c], b, acc[c]);
+        }
+        if (t < NT) {
+            int *cell = tile + (o[1] + qy) * Pt + o[0] + qx;
+#pragma unroll
+            for (int c = 0; c < NV; ++c) atomicAdd(cell + c * tc, __float2int_rn(acc[c]));
         }
     }
     __syncwarp();   // the slots are rewritten by the next group
@@ -610,7 +679,8 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
         if (kWarpSum && __all_sync(0xffffffffu, !valid || key == key0)) {
             if constexpr (RowSpread<D, W, NV>::on) {
                 if (slots) {
-                    warp_spread_rows<W, NV>(tile, tc, Pt, o, u, wx, wy, wz, slots, lane);
+                    if constexpr (D == 3) warp_spread_rows<W, NV>(tile, tc, Pt, o, u, wx, wy, wz, slots, lane);
+                    else warp_spread_taps<W, NV>(tile, tc, Pt, o, u, wx, wy, slots, lane);
                     continue;
                 }
             }

@@ -1046,13 +1046,14 @@ static ml_status plan_impl(ml_plan_s *p, const double *points, cudaStream_t st)
             return fail(ML_ERR_ARG, "bin edge " + std::to_string(g.B) + " gives a tile beyond the shared-memory budget");
         if (p->prec == ML_F32) {
             p->vp = (int)std::min<int64_t>(kMaxVec, std::max<int64_t>(1, (200 * 1024) / (tc * 4)));
-            // d = 3, W <= 8: when the row-product slots of the spreading fit
-            // next to the tile for one vector, keep every pass width within
-            // that budget, so that all passes take the same arithmetic
+            // when the spreading's warp slots (d = 3 row products, d = 2 one tap
+            // per lane) fit next to the tile for one vector, keep every pass
+            // width within that budget, so that all passes take the same
+            // arithmetic
             auto fits = [&](int v) {
-                return (((size_t)tc * 4 * v + 15) & ~(size_t)15) + row_spread_bytes(p->W, v) <= kRowSpreadBudget;
+                return (((size_t)tc * 4 * v + 15) & ~(size_t)15) + warp_slot_bytes(d, p->W, v) <= kRowSpreadBudget;
             };
-            if (d == 3 && p->W <= 8 && fits(1))
+            if (warp_slots_on(d, p->W) && fits(1))
                 while (p->vp > 1 && !fits(p->vp)) --p->vp;
         } else {
             int vp = 1;
