@@ -771,9 +771,9 @@ DW_OPS_PER_FMA = 10
 
 NCU_TRAFFIC = {
     # k_spread_f32<3,5,1>, both layers of the 10-megapixel image (one launch
-    # each, ncu --set full of the apply-mode run): 794.1 and 513.1 MB, mean
-    # 653.6 MB per launch
-    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (653.6e6, "1c733bf61c790859",
+    # each, ncu --set full of the apply-mode run): 794.4 and 513.0 MB, mean
+    # 653.7 MB per launch
+    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (653.7e6, "daec78ce9e14685b",
                                                       "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
                                                       "the two layers' launches; includes the subproblem tiles "
                                                       "written for the fold (192 MB) and 32-byte sectors of the "
