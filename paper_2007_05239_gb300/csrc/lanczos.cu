@@ -32,6 +32,10 @@ namespace ml {
 ml_status apply_device(ml_plan_s *const *layers, int T, const double *X, int b, double *Y, int mode, cudaStream_t st);
 
 constexpr int kDotThreads = 256;
+// outputs of every 16 that the Ritz combination gives to the FP64 pipe: a
+// double-word multiply-add costs about 12 FP32 issue slots, a DFMA 1/64 of
+// the FP32 rate; two of sixteen balance the two pipes
+constexpr int kCombineFp64 = 2;
 
 // partial dot products of columns c0.. of Q (column stride n) with x
 __global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncol,
@@ -429,27 +433,41 @@ __global__ void k_dgks(const double *__restrict__ part, int nblk, const double *
 __global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv,
                                                    const double *__restrict__ S, int kk, double *out, int64_t ldo)
 {
-    extern __shared__ float2 ss[];                 // [ncv][kk] double-word
+    // the first kCombineFp64 of every 16 outputs on the FP64 pipe (its own
+    // rate, beside the FP32 pipe's double-word work), the rest double-word
+    constexpr int KF = kCombineFp64;
+    extern __shared__ float2 ss[];                 // [ncv][kk] double-word, then [ncv][kk] FP64
+    double *sd = reinterpret_cast<double *>(ss + (size_t)ncv * kk);
     for (int e = threadIdx.x; e < ncv * kk; e += blockDim.x) {
         const int c = e / kk, i = e - c * kk;
-        ss[e] = dword::from_double(S[(int64_t)i * ncv + c]);
+        const double v = S[(int64_t)i * ncv + c];
+        ss[e] = dword::from_double(v);
+        sd[e] = v;
     }
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         for (int i0 = 0; i0 < kk; i0 += 16) {
             float2 acc[16];
+            double dacc[KF];
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.0f, 0.0f);
-            for (int c = 0; c < ncv; ++c) {
-                const float2 q = dword::from_double(Q[(int64_t)c * ldq + r]);
-                const float2 *srow = ss + (int64_t)c * kk + i0;
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
+            for (int k = 0; k < KF; ++k) dacc[k] = 0.0;
+            for (int c = 0; c < ncv; ++c) {
+                const double qd = Q[(int64_t)c * ldq + r];
+                const float2 q = dword::from_double(qd);
+                const float2 *srow = ss + (int64_t)c * kk + i0;
+                const double *drow = sd + (int64_t)c * kk + i0;
+#pragma unroll
+                for (int k = 0; k < KF; ++k)
+                    if (i0 + k < kk) dacc[k] = fma(qd, drow[k], dacc[k]);
+#pragma unroll
+                for (int k = KF; k < 16; ++k)
                     if (i0 + k < kk) dword::fma_acc(acc[k], q, srow[k]);
             }
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                if (i0 + k < kk) out[(int64_t)(i0 + k) * ldo + r] = dword::to_double(acc[k]);
+                if (i0 + k < kk) out[(int64_t)(i0 + k) * ldo + r] = k < KF ? dacc[k < KF ? k : 0] : dword::to_double(acc[k]);
         }
     }
 }
@@ -1336,8 +1354,8 @@ static ml_status lanczos_impl(ml_plan_s *const *layers, int T, int k, double pw,
         ML_CUDA(cudaMemcpyAsync(Sd.p, Sk.data(), Sk.size() * 8, cudaMemcpyHostToDevice, st));
         {
             ProfScope pr("ritz", st);
-            if (ws.dword && (size_t)ncv * keep * sizeof(float2) <= 48 * 1024) {
-                const size_t sm = (size_t)ncv * keep * sizeof(float2);
+            if (ws.dword && (size_t)ncv * keep * (sizeof(float2) + sizeof(double)) <= 48 * 1024) {
+                const size_t sm = (size_t)ncv * keep * (sizeof(float2) + sizeof(double));
                 k_combine_dw<<<one_wave(k_combine_dw, 256, sm, nb), 256, sm, st>>>(Q, n, n, ncv, Sd.as<double>(), keep,
                                                                                  Qtmp.as<double>(), n);
             } else if (ws.tensor && oz_gemm_ok(ncv)) {

@@ -265,105 +265,125 @@ __global__ void __launch_bounds__(256) k_lgemm(LMat A, int a0, int rc, const dou
     }
 }
 
-// One thread per slot: SVQB of the B x B Gram G_y.  Writes the transform M_y
-// (V = W M) and R (W = V R): into Rs_y on the first pass, and R2 * Rs_y into
-// rec[lay[y] * rstride] on the second.  flags[lay[y]] |= 1 when a direction
-// was dropped.  B is a template parameter so that the matrices stay in
-// registers.
+// SVQB of the B x B Gram G_y, eight lanes per slot (four slots per warp):
+// lane k of a slot holds column k of the scaled Gram and of the eigenvector
+// matrix in registers, and the cyclic Jacobi rotations (p, q) exchange
+// columns p and q by shuffles within the slot's lanes (a thread per slot held
+// three B x B matrices and spilled them to local memory).  Writes the
+// transform M_y (V = W M) and R (W = V R): into Rs_y on the first pass, and
+// R2 * Rs_y into rec[lay[y] * rstride] on the second.  flags[lay[y]] |= 1
+// when a direction was dropped.  B is a template parameter so that the
+// columns stay in registers.
 template <int B>
-__global__ void k_lsvqb(const double *__restrict__ G, int nslots, const int *__restrict__ lay, double *M, double *Rs,
-                        double *rec, int64_t rstride, int pass, int *flags)
+__global__ void __launch_bounds__(128) k_lsvqb(const double *__restrict__ G, int nslots, const int *__restrict__ lay,
+                                               double *M, double *Rs, double *rec, int64_t rstride, int pass, int *flags)
 {
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= nslots) return;
-    const int t = lay[y];
-    double g[B][B], u[B][B], sc[B], lam[B];
-    const double *Gy = G + (int64_t)y * B * B;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = gid >> 3;          // slot
+    const int k = gid & 7;           // column of this lane
+    const bool slot_ok = y < nslots;
+    const bool col_ok = slot_ok && k < B;
+    const unsigned full = 0xffffffffu;
+    const int t = slot_ok ? lay[y] : 0;
+    const double *Gy = G + (int64_t)(slot_ok ? y : 0) * B * B;
+    double sc[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-        const double d = Gy[i * B + i];
+        const double d = slot_ok ? Gy[i * B + i] : 0.0;
         sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
     }
+    // column k of the scaled, symmetrised Gram and of U (identity)
+    double g[B], u[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i)
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            g[i][j] = 0.5 * (Gy[i * B + j] + Gy[j * B + i]) * sc[i] * sc[j];
-            u[i][j] = (i == j) ? 1.0 : 0.0;
-        }
-    // cyclic Jacobi on the scaled Gram (entries below 1e-18 of the diagonal
-    // scale are not rotated; quadratic convergence ends it in a few sweeps)
+    for (int i = 0; i < B; ++i) {
+        g[i] = col_ok ? 0.5 * (Gy[i * B + k] + Gy[k * B + i]) * sc[i] * sc[k] : 0.0;
+        u[i] = (col_ok && i == k) ? 1.0 : 0.0;
+    }
+    const int base = threadIdx.x & ~7;   // first lane of the slot within the warp
     for (int sweep = 0; sweep < 30; ++sweep) {
         bool rotated = false;
 #pragma unroll
         for (int p = 0; p < B - 1; ++p)
 #pragma unroll
             for (int q = p + 1; q < B; ++q) {
-                const double apq = g[p][q];
-                if (fabs(apq) <= 1e-18 * (fabs(g[p][p]) + fabs(g[q][q])) + 1e-300) continue;
-                rotated = true;
-                const double tau = (g[q][q] - g[p][p]) / (2.0 * apq);
-                const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
-#pragma unroll
-                for (int k = 0; k < B; ++k) {
-                    const double akp = g[k][p], akq = g[k][q];
-                    g[k][p] = c * akp - s * akq;
-                    g[k][q] = s * akp + c * akq;
+                // g[p][q] lives in lane q (its element p), g[p][p] in lane p, g[q][q] in lane q
+                const double apq = __shfl_sync(full, g[p], (base & 31) + q);
+                const double app = __shfl_sync(full, g[p], (base & 31) + p);
+                const double aqq = __shfl_sync(full, g[q], (base & 31) + q);
+                // rotate while the pair is coupled beyond rounding: 1e-15 of
+                // sqrt(app aqq) (a bound below the FP64 rounding level never
+                // holds once rounding noise remains, and every call ran all 30
+                // sweeps)
+                const bool rot = !(fabs(apq) <= 1e-15 * sqrt(fabs(app * aqq)) + 1e-300);
+                double c = 1.0, sn = 0.0;
+                if (rot) {
+                    rotated = true;
+                    const double tau = (aqq - app) / (2.0 * apq);
+                    const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + tt * tt);
+                    sn = tt * c;
                 }
-#pragma unroll
-                for (int k = 0; k < B; ++k) {
-                    const double apk = g[p][k], aqk = g[q][k];
-                    g[p][k] = c * apk - s * aqk;
-                    g[q][k] = s * apk + c * aqk;
+                // rows p and q of every column (lane-local)
+                {
+                    const double gp = g[p], gq = g[q];
+                    g[p] = c * gp - sn * gq;
+                    g[q] = sn * gp + c * gq;
                 }
+                // columns p and q: lanes p and q take each other's column
+                const int partner = (k == p) ? q : ((k == q) ? p : k);
 #pragma unroll
-                for (int k = 0; k < B; ++k) {
-                    const double ukp = u[k][p], ukq = u[k][q];
-                    u[k][p] = c * ukp - s * ukq;
-                    u[k][q] = s * ukp + c * ukq;
+                for (int i = 0; i < B; ++i) {
+                    const double og = __shfl_sync(full, g[i], (base & 31) + partner);
+                    const double ou = __shfl_sync(full, u[i], (base & 31) + partner);
+                    if (k == p) {
+                        g[i] = c * g[i] - sn * og;
+                        u[i] = c * u[i] - sn * ou;
+                    } else if (k == q) {
+                        g[i] = sn * og + c * g[i];
+                        u[i] = sn * ou + c * u[i];
+                    }
                 }
             }
-        if (!rotated) break;
+        // every lane of a slot took the same decisions; the warp continues
+        // while any of its slots rotated
+        if (!__any_sync(full, rotated)) break;
     }
-    double lmax = 0.0;
+    // eigenvalue of column k: g[k]
+    double lamk = 0.0;
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-        lam[i] = g[i][i];
-        lmax = fmax(lmax, lam[i]);
+    for (int i = 0; i < B; ++i)
+        if (i == k) lamk = g[i];
+    double lmax = col_ok ? lamk : 0.0;
+    for (int o = 4; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(full, lmax, o));
+    const bool keep = col_ok && lmax > 0.0 && lamk > 1e-20 * lmax;
+    const double il = keep ? 1.0 / sqrt(lamk) : 0.0, sl = keep ? sqrt(lamk) : 0.0;
+    if (col_ok) {
+        double *My = M + (int64_t)y * B * B;
+#pragma unroll
+        for (int r = 0; r < B; ++r) My[r * B + k] = sc[r] * u[r] * il;
     }
-    int dropped = 0;
-    double R[B][B];
-    double *My = M + (int64_t)y * B * B;
+    // row k of R: R[k][q] = sl_k u[q][k] / sc[q]
+    double Rk[B];
 #pragma unroll
-    for (int s = 0; s < B; ++s) {
-        const bool keep = lmax > 0.0 && lam[s] > 1e-20 * lmax;
-        dropped |= keep ? 0 : 1;
-        const double il = keep ? 1.0 / sqrt(lam[s]) : 0.0, sl = keep ? sqrt(lam[s]) : 0.0;
+    for (int q = 0; q < B; ++q) Rk[q] = (sc[q] > 0.0) ? sl * u[q] / sc[q] : 0.0;
+    double *Ry = Rs + (int64_t)(slot_ok ? y : 0) * B * B;
+    if (col_ok) {
+        if (pass == 0) {
 #pragma unroll
-        for (int r = 0; r < B; ++r) My[r * B + s] = sc[r] * u[r][s] * il;
-#pragma unroll
-        for (int q = 0; q < B; ++q) R[s][q] = (sc[q] > 0.0) ? sl * u[q][s] / sc[q] : 0.0;
-    }
-    double *Ry = Rs + (int64_t)y * B * B;
-    if (pass == 0) {
-#pragma unroll
-        for (int i = 0; i < B; ++i)
-#pragma unroll
-            for (int j = 0; j < B; ++j) Ry[i * B + j] = R[i][j];
-    } else if (rec) {
-        double *Rt = rec + (int64_t)t * rstride;
-#pragma unroll
-        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) Ry[k * B + j] = Rk[j];
+        } else if (rec) {
+            double *Rt = rec + (int64_t)t * rstride;
 #pragma unroll
             for (int j = 0; j < B; ++j) {
                 double x = 0.0;
 #pragma unroll
-                for (int q = 0; q < B; ++q) x = fma(R[i][q], Ry[q * B + j], x);
-                Rt[i * B + j] = x;
+                for (int q = 0; q < B; ++q) x = fma(Rk[q], Ry[q * B + j], x);
+                Rt[k * B + j] = x;
             }
+        }
     }
-    if (dropped && flags) flags[t] |= 1;
+    const bool dropped = col_ok && !keep;
+    if (dropped && flags) atomicOr(flags + t, 1);
 }
 
 // rec_t[r, s] += sum_q H2_y[r, q] Rs_y[q, s]   (r < rc): the second pass's
@@ -585,13 +605,13 @@ struct Solver {
     ml_status svqb(int pass, double *rec)
     {
         ProfScope pr("svqb", st);
-        const dim3 grid((nslots + 31) / 32);
+        const dim3 grid((nslots * 8 + 127) / 128);
         double *G = Gs.as<double>(), *Mp = Ms.as<double>(), *Rp = Rs.as<double>();
         const int *ly = layd.as<int>();
         int *fl = flags.as<int>();
         switch (b) {
 #define ML_SVQB_CASE(BB) \
-    case BB: k_lsvqb<BB><<<grid, 32, 0, st>>>(G, nslots, ly, Mp, Rp, rec, rstride, pass, fl); break;
+    case BB: k_lsvqb<BB><<<grid, 128, 0, st>>>(G, nslots, ly, Mp, Rp, rec, rstride, pass, fl); break;
             ML_SVQB_CASE(1)
             ML_SVQB_CASE(2)
             ML_SVQB_CASE(3)
