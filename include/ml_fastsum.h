@@ -359,7 +359,8 @@ ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int 
  *   - X and Y must be device memory (host buffers would need staging copies);
  *     ML_ERR_ARG otherwise.
  *   - ML_ERR_ARG, with the required size in ml_last_error(), when the layers'
- *     scratch (tiles + two transform buffers at the widest vector pass)
+ *     scratch (tiles and their boxes + two transform buffers at the widest
+ *     vector pass)
  *     exceeds 32 MiB.
  *   - kernel timing (ml_profile_enable) is not recorded for these calls.
  * Set-up: the first call on each device looks the array's device address up
@@ -369,8 +370,9 @@ ml_status ml_fastsum_apply(const ml_plan_t *layers, int T, const double *X, int 
  * device's primary context) do not call this entry point again in that
  * process.
  * Sharing: every call uses the same array and leaves its contents behind; the
- * kernels overwrite every scratch value before reading it, so nothing needs
- * clearing, but calls whose executions overlap on the GPU (other streams,
+ * kernels read only scratch values that the same call wrote (FP32 tiles are
+ * written and read within the box of cells their points reach), so nothing
+ * needs clearing, but calls whose executions overlap on the GPU (other streams,
  * other threads) race on the array and must be serialised by the caller.
  * ML_DEGREE reads stored degrees and uses no scratch.
  */

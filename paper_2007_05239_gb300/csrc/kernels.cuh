@@ -17,8 +17,9 @@
 namespace ml {
 
 // FP32 window weights by polynomials (plan-time fit, see window_row_poly):
-// up to kPolyW taps per dimension, degree kPolyTerms - 1 in u, each tap's
-// coefficients in a row of kPolyStride floats (16-byte aligned, zero padded)
+// up to kPolyW taps per dimension, degree kPolyTerms - 1 in u, the even and
+// odd coefficients of each of the first ceil(W/2) taps in a row of
+// kPolyStride floats (16-byte aligned, zero padded; the other taps mirror them)
 constexpr int kPolyW = 16;
 constexpr int kPolyTerms = 10;
 constexpr int kPolyStride = 12;
@@ -120,33 +121,44 @@ __device__ __forceinline__ void fixed_split(float p, float e, int &hi, int &lo)
 // phi_n(x - o - q), |x - o - q| <= W/2.  FP32 form, from polynomials fitted
 // at plan time: with
 // f = (x - W/2) - floor(x - W/2) in [0, 1) and u = f - 1/2, tap q has weight
-// phi_n(W/2 - 1 - q + f) ~ sum_k c[q][k] u^k (degree 9, Chebyshev
+// phi_n(W/2 - 1 - q + f) ~ p_q(u), a polynomial of degree 9 (Chebyshev
 // interpolation of the window on each unit interval; the fit error is below
 // 1e-7 of the window's peak for every W and oversampling the plans allow,
-// checked at plan time).  Horner in FP32: 9 FMAs per weight, in place of an
-// approximate square root, exponential and reciprocal on the special-function
-// unit, whose fast exponential alone errs by about 1e-6 for the arguments
-// near b W/2 of the window's centre.  c: kernel parameters (single-layer
-// launches) or a shared copy.
+// checked at plan time).  The window is even, so tap W-1-q sees the mirror
+// image of tap q: p_{W-1-q}(u) = p_q(-u).  Writing p_q(u) = E_q(u^2) +
+// u O_q(u^2), the pair costs two Horner chains of degree 4 in u^2 and two
+// FMAs (the middle tap of an odd W is even: E only) -- 25 FMAs for W = 5 in
+// place of 45 for ten-term Horner per tap, and no exponential, square root or
+// reciprocal on the special-function unit (whose fast exponential errs by
+// about 1e-6 near the window's centre).  Row q < ceil(W/2) of c holds
+// e_0..e_4 (coefficients of u^0, u^2, .., u^8), then o_0..o_4 (u^1, u^3, ..,
+// u^9), then two zeros.  c: kernel parameters (single-layer launches) or a
+// shared copy.
 template <int W>
 __device__ __forceinline__ int window_row_poly(float x, const float *__restrict__ c, float *w)
 {
     const float xs = x - 0.5f * (float)W;
     const float fl = floorf(xs);
     const float u = (xs - fl) - 0.5f;
+    const float u2 = u * u;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
+    for (int q = 0; q < (W + 1) / 2; ++q) {
         const float4 *row = reinterpret_cast<const float4 *>(c + q * kPolyStride);
         const float4 c0 = row[0], c1 = row[1], c2 = row[2];
-        float v = fmaf(c2.y, u, c2.x);
-        v = fmaf(v, u, c1.w);
-        v = fmaf(v, u, c1.z);
-        v = fmaf(v, u, c1.y);
-        v = fmaf(v, u, c1.x);
-        v = fmaf(v, u, c0.w);
-        v = fmaf(v, u, c0.z);
-        v = fmaf(v, u, c0.y);
-        w[q] = fmaf(v, u, c0.x);
+        float e = fmaf(c1.x, u2, c0.w);
+        e = fmaf(e, u2, c0.z);
+        e = fmaf(e, u2, c0.y);
+        e = fmaf(e, u2, c0.x);
+        if (2 * q + 1 == W) {
+            w[q] = e;
+        } else {
+            float o = fmaf(c2.y, u2, c2.x);
+            o = fmaf(o, u2, c1.w);
+            o = fmaf(o, u2, c1.z);
+            o = fmaf(o, u2, c1.y);
+            w[q] = fmaf(u, o, e);
+            w[W - 1 - q] = fmaf(-u, o, e);
+        }
     }
     return (int)fl + 1;
 }
@@ -156,7 +168,7 @@ static_assert(kPolyTerms == 10 && kPolyStride == 12, "window_row_poly evaluates 
 // caller synchronises before they are read)
 __device__ __forceinline__ void stage_window_poly(const float *__restrict__ src, float *dst, int W)
 {
-    for (int e = threadIdx.x; e < W * kPolyStride; e += blockDim.x) dst[e] = src[e];
+    for (int e = threadIdx.x; e < (W + 1) / 2 * kPolyStride; e += blockDim.x) dst[e] = src[e];
 }
 
 
@@ -182,8 +194,20 @@ struct SpreadArgs {
                              // memory (RowSpread), 0 = not used
     int stage_off;           // FP32: byte offset of the staged points (sub_max x nv values u, then,
                              // with sidx, sub_max sorted indices) in dynamic shared memory, 0 = not staged
+    int4 *sub_box;           // FP32: null (whole tiles written), or per subproblem the box of tile
+                             // cells its taps reach (pack_box); only that box of its tile is written
     alignas(16) float kbp[kPolyW * kPolyStride];   // FP32 window polynomials (window_row_poly)
 };
+
+// most subproblem tiles per group of k_group_sum_box
+constexpr int kGroupSubsMax = 64;
+
+// Box of tile cells [lo_a, hi_a) per axis a, packed lo | hi << 16 per int
+// (tile edges are below 2^16); an empty box has hi = lo on an axis
+__device__ __forceinline__ int4 pack_box(const int lo[3], const int hi[3])
+{
+    return make_int4(lo[0] | (hi[0] << 16), lo[1] | (hi[1] << 16), lo[2] | (hi[2] << 16), 0);
+}
 
 // Sum of the tiles of each group of consecutive subproblems of one bin
 // (fixed order): gtile[g] = sum_{s in group g} scratch[s].  CTA b handles
@@ -566,9 +590,12 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
     int *tile = reinterpret_cast<int *>(smem_raw);
     __shared__ float s_part[2][NV][8];
     __shared__ float s_scale[NV];
+    __shared__ int s_box[6];            // min first tap per axis, then max
     const int start = a.sub_start[sub], cnt = a.sub_count[sub];
     const int tc = tile_cells<D>(a.Pt);
     for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) tile[e] = 0;
+    if (threadIdx.x < 6) s_box[threadIdx.x] = threadIdx.x < 3 ? 0x7FFFFFFF : -1;
+    int omin[3] = {0x7FFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF}, omax[3] = {-1, -1, -1};
 
     // per-vector sum and max of |u| over this subproblem's points, u =
     // D^{-1/2} x in FP32; with staging, each point's sorted index and u go to
@@ -674,6 +701,13 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
         o[0] = window_row_poly<W>(coords[(int64_t)i * D], kb, wx);
         if (D >= 2) o[1] = window_row_poly<W>(coords[(int64_t)i * D + 1], kb, wy);
         if (D >= 3) o[2] = window_row_poly<W>(coords[(int64_t)i * D + 2], kb, wz);
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                omin[k] = min(omin[k], o[k]);
+                omax[k] = max(omax[k], o[k]);
+            }
+        }
         const int key = o[0] | (o[1] << 10) | (o[2] << 20);
         const int key0 = __shfl_sync(0xffffffffu, key, 0);
         if (kWarpSum && __all_sync(0xffffffffu, !valid || key == key0)) {
@@ -729,19 +763,63 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
             }
         }
     }
+    if (a.sub_box) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            omin[k] = __reduce_min_sync(0xffffffffu, omin[k]);
+            omax[k] = __reduce_max_sync(0xffffffffu, omax[k]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                atomicMin(&s_box[k], omin[k]);
+                atomicMax(&s_box[3 + k], omax[k]);
+            }
+        }
+    }
     __syncthreads();
     // the scales are powers of two: multiplying by the reciprocal is exact
     float inv_scale[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) inv_scale[c] = 1.0f / s_scale[c];
     float *out = static_cast<float *>(a.scratch) + (int64_t)sub * tc * NV;
-    for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
-        const int c = e % NV, cell = e / NV;
+    if (!a.sub_box) {
+        for (int e = threadIdx.x; e < tc * NV; e += blockDim.x) {
+            const int c = e % NV, cell = e / NV;
+            float is = inv_scale[0];
+#pragma unroll
+            for (int k = 1; k < NV; ++k)
+                if (c == k) is = inv_scale[k];
+            out[e] = (float)tile[c * tc + cell] * is;
+        }
+        return;
+    }
+    // only the box of cells the taps reached: rows of bx cells (contiguous
+    // in the cell-major output), by x bz of them
+    int lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool used = k < D && s_box[k] <= s_box[3 + k];
+        lo[k] = used ? s_box[k] : 0;
+        hi[k] = used ? s_box[3 + k] + W : (k < D ? 0 : 1);
+    }
+    if (threadIdx.x == 0) a.sub_box[sub] = pack_box(lo, hi);
+    const int span = (hi[0] - lo[0]) * NV, by = hi[1] - lo[1];
+    const int rows = by * (hi[2] - lo[2]);
+    if (span <= 0 || rows <= 0) return;
+    const FastDiv dspan(span), dby(by);
+    for (int e = threadIdx.x; e < rows * span; e += blockDim.x) {
+        const int r = dspan.div(e);
+        const int j = e - r * span;
+        const int rz = dby.div(r);
+        const int cell0 = ((lo[2] + rz) * Pt + lo[1] + r - rz * by) * Pt + lo[0];
+        const int cj = j / NV, c = j - cj * NV;
         float is = inv_scale[0];
 #pragma unroll
         for (int k = 1; k < NV; ++k)
             if (c == k) is = inv_scale[k];
-        out[e] = (float)tile[c * tc + cell] * is;
+        const int cell = cell0 + cj;
+        out[cell * NV + c] = (float)tile[c * tc + cell] * is;
     }
 }
 
@@ -907,6 +985,68 @@ __device__ __forceinline__ void grid_store(float2 *out, int64_t i, double v)
 {
     out[i] = dw_split(v);
 }
+
+// FP32 tiles with boxes (the spreading wrote only the box of cells its
+// points reach): CTA (g, z) forms z-plane z of group g's tile (the whole tile
+// for d < 3), one element per thread, by adding the subproblem tiles of the
+// group in order (the same sums as k_group_sum, which adds the zeros outside
+// the boxes too) and reading only the tiles whose box holds the element.  One
+// warp first lists, in group order, the tiles whose box reaches plane z.
+// Every element of the group tile is written.  At most kGroupSubsMax tiles per group.
+template <int D>
+__global__ void __launch_bounds__(512) k_group_sum_box(const float *__restrict__ scratch, const int *__restrict__ grp_sub,
+                                                      const int4 *__restrict__ sub_box, int Pt, int nv, float *gtile)
+{
+    __shared__ int4 s_box[kGroupSubsMax];   // x0, x extent, y0, y extent of the listed tiles
+    __shared__ int s_off[kGroupSubsMax];    // their element offsets from the group's first tile
+    __shared__ int s_n;
+    const int g = blockIdx.x;
+    const int z = (D == 3) ? (int)blockIdx.y : 0;
+    const int s0 = grp_sub[g], ns = min(grp_sub[g + 1] - s0, kGroupSubsMax);
+    const int te = tile_cells<D>(Pt) * nv;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int cnt = 0;
+        for (int k0 = 0; k0 < ns; k0 += 32) {
+            const int k = k0 + lane;
+            int4 b = make_int4(0, 0, 0, 0);
+            bool in = false;
+            if (k < ns) {
+                b = sub_box[s0 + k];
+                in = (unsigned)(z - (b.z & 0xFFFF)) < (unsigned)((b.z >> 16) - (b.z & 0xFFFF));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                s_box[pos] = make_int4(b.x & 0xFFFF, (b.x >> 16) - (b.x & 0xFFFF), b.y & 0xFFFF,
+                                       (b.y >> 16) - (b.y & 0xFFFF));
+                s_off[pos] = k * te;
+            }
+            cnt += __popc(m);
+        }
+        if (lane == 0) s_n = cnt;
+    }
+    __syncthreads();
+    const int nk = s_n;
+    const int pc = (D == 1) ? Pt : Pt * Pt;           // cells of one plane
+    const int64_t base = (int64_t)z * pc * nv;        // first element of the plane
+    const float *src0 = scratch + (int64_t)s0 * te + base;
+    for (int e = threadIdx.x; e < pc * nv; e += blockDim.x) {
+        const int cell = e / nv;
+        const int y = (D >= 2) ? cell / Pt : 0, x = cell - y * Pt;
+        float acc = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < nk; ++j) {
+            const int4 b = s_box[j];
+            if ((unsigned)(x - b.x) < (unsigned)b.y && (unsigned)(y - b.z) < (unsigned)b.w) acc += src0[s_off[j] + e];
+        }
+        gtile[(int64_t)g * te + base + e] = acc;
+    }
+}
+
+
+
+
 
 // (the cells of a bin are shared by `chunks` CTAs: chunk ch takes elements
 // ch * blockDim.x + tid, stepping by chunks * blockDim.x)

@@ -31,6 +31,15 @@ static ml_status set_smem(K kernel, size_t bytes)
     return ML_OK;
 }
 
+// FP32 spreading: the box of cells written into each subproblem tile (int4,
+// pack_box), 16-byte aligned after the subproblem and group tiles
+static_assert(kGroupSubs <= kGroupSubsMax, "group size of the plan above the boxed group sum's limit");
+static int4 *tile_boxes(void *scratch, int nsub, int ngroups, int64_t tile_bytes)
+{
+    const size_t off = ((size_t)(nsub + ngroups) * (size_t)tile_bytes + 15) & ~(size_t)15;
+    return reinterpret_cast<int4 *>(static_cast<char *>(scratch) + off);
+}
+
 // One real trigonometric transform along an axis (k_axis): 32 x 64 tiles, or
 // 16 x 32 tiles when the large ones would leave most SMs idle
 template <typename T>
@@ -111,6 +120,14 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     static_assert(sizeof(sa.kbp) == sizeof(p->kbp), "window polynomial table sizes");
     memcpy(sa.kbp, p->kbp, sizeof(sa.kbp));
     sa.scratch = w.scratch;
+    // FP32: each subproblem tile records the box of cells it wrote (after
+    // the tiles in the scratch, tile_boxes); the group sums read only those
+    const int64_t tile_elems = (int64_t)tc * nv;
+    int4 *sub_box = nullptr;
+    if (f32 && p->ngroups > 0) {
+        sub_box = tile_boxes(w.scratch, p->nsub, p->ngroups, tile_elems * (int64_t)sizeof(T));
+        sa.sub_box = sub_box;
+    }
     if (p->nsub > 0) {
         ProfScope pr("spread", st);
         if (f32) {
@@ -137,16 +154,23 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
     }
     // ---- sum each group of subproblem tiles, then fold the group tiles into
     //      the active grid (work0)
-    const int64_t tile_elems = (int64_t)tc * nv;
     T *gtile = static_cast<T *>(w.scratch) + (int64_t)p->nsub * tile_elems;
     if (p->ngroups > 0) {
         ProfScope pr("group_sum", st);
-        const int chunks = (int)std::min<int64_t>((tile_elems + 255) / 256, 64);
-        k_group_sum<T><<<(unsigned)((int64_t)p->ngroups * chunks), 256, 0, st>>>(
-            static_cast<const T *>(w.scratch), p->grp_sub.as<int>(), tile_elems, chunks, gtile);
+        if (sub_box) {
+            const int plane = (D == 1 ? g.Pt : g.Pt * g.Pt) * nv;
+            const int threads = std::min(512, std::max(64, (plane + 31) / 32 * 32));
+            k_group_sum_box<D><<<dim3((unsigned)p->ngroups, D == 3 ? (unsigned)g.Pt : 1u), threads, 0, st>>>(
+                reinterpret_cast<const float *>(w.scratch), p->grp_sub.as<int>(), sub_box, g.Pt, nv,
+                reinterpret_cast<float *>(gtile));
+        } else {
+            const int chunks = (int)std::min<int64_t>((tile_elems + 255) / 256, 64);
+            k_group_sum<T><<<(unsigned)((int64_t)p->ngroups * chunks), 256, 0, st>>>(
+                static_cast<const T *>(w.scratch), p->grp_sub.as<int>(), tile_elems, chunks, gtile);
+        }
         ML_CUDA(cudaGetLastError());
     }
-    FoldArgs fa;
+    FoldArgs fa{};
     fa.bin_sub = p->bin_grp.as<int>();
     fa.scratch = gtile;
     fa.grid = w.work0;

@@ -169,7 +169,7 @@ struct ml_plan_s {
     double target = 0;
     double kb_shape = 0;   // b = pi (2 - 1/sigma_os)
     double kb_norm = 0;    // h e^{-b h} / (1 - e^{-2 b h}), h = W/2: phi_n(t) = norm (e^{bs} - e^{-bs})/s
-    float kbp[192] = {};   // FP32 form: window polynomials, 16 taps x 12 floats (window_row_poly)
+    float kbp[192] = {};   // FP32 form: window polynomials, rows of 12 floats for the first ceil(W/2) taps (window_row_poly)
     int s0[3] = {0, 0, 0}; // torus index of active-grid cell 0 per dim
     ml::GridGeom g;
     int vp = 1;            // vectors per pass

@@ -655,24 +655,30 @@ static double kb_phi(double t, double h, double b, double norm)
     return norm * 2.0 * std::sinh(bs) / s;
 }
 
-// FP32 form: for every tap q < W the polynomial of degree 9 in u = f - 1/2
-// that interpolates phi_n(W/2 - 1 - q + f), f in [0, 1), at the 10 Chebyshev
-// points of the unit interval (monomial coefficients from the Vandermonde
-// system, Gaussian elimination with partial pivoting in FP64).  The window is
-// a function of s^2 = h^2 - t^2 whose series has only positive terms (an
-// entire function of t), so the interpolant converges fast: the check on 2001
-// points, with the coefficients rounded to FP32, must stay below 1e-7 of the
-// window's peak.
+// FP32 form: for every tap q < ceil(W/2) the polynomial of degree 9 in
+// u = f - 1/2 that interpolates phi_n(W/2 - 1 - q + f), f in [0, 1), at the 10
+// Chebyshev points of the unit interval (monomial coefficients from the
+// Vandermonde system, Gaussian elimination with partial pivoting in FP64).
+// The window is even, so tap W-1-q is the same polynomial at -u and is not
+// fitted; the middle tap of an odd W keeps its even coefficients only (its
+// odd ones are rounding noise).  Stored per row: the even coefficients, then
+// the odd ones (window_row_poly).  The window is a function of
+// s^2 = h^2 - t^2 whose series has only positive terms (an entire function
+// of t), so the interpolant converges fast: the check on 2001 points of every
+// tap, mirrored ones included, with the coefficients rounded to FP32, must
+// stay below 1e-7 of the window's peak.
 static ml_status fit_window_poly(ml_plan_s *p)
 {
     constexpr int K = kPolyTerms;
     static_assert(sizeof(p->kbp) == sizeof(float) * kPolyW * kPolyStride, "window polynomial table size");
+    static_assert(K == 10 && kPolyStride >= K, "five even and five odd coefficients per row");
     const int W = p->W;
     if (W > 16) return fail(ML_ERR_ARG, "FP32 window wider than 16 taps");
     const double h = 0.5 * W, b = p->kb_shape, nm = p->kb_norm;
     const double peak = kb_phi(0.0, h, b, nm);
     double worst = 0.0;
-    for (int q = 0; q < W; ++q) {
+    std::fill(p->kbp, p->kbp + kPolyW * kPolyStride, 0.0f);
+    for (int q = 0; q < (W + 1) / 2; ++q) {
         double V[K][K + 1];
         for (int j = 0; j < K; ++j) {
             const double u = 0.5 * std::cos((2 * j + 1) * M_PI / (2.0 * K));
@@ -699,13 +705,22 @@ static ml_status fit_window_poly(ml_plan_s *p)
             for (int k = c + 1; k < K; ++k) v -= V[c][k] * coef[k];
             coef[c] = v / V[c][c];
         }
+        const bool middle = 2 * q + 1 == W;
         float *row = p->kbp + q * kPolyStride;
-        for (int k = 0; k < kPolyStride; ++k) row[k] = k < K ? (float)coef[k] : 0.0f;
+        for (int j = 0; j < K / 2; ++j) {
+            row[j] = (float)coef[2 * j];
+            row[K / 2 + j] = middle ? 0.0f : (float)coef[2 * j + 1];
+        }
         for (int e = 0; e <= 2000; ++e) {
-            const double u = -0.5 + e / 2000.0;
-            double v = row[K - 1];
-            for (int k = K - 2; k >= 0; --k) v = v * u + row[k];
-            worst = std::max(worst, std::fabs(v - kb_phi(h - 1.0 - q + 0.5 + u, h, b, nm)));
+            const double u = -0.5 + e / 2000.0, u2 = u * u;
+            double ev = 0.0, od = 0.0;
+            for (int j = K / 2 - 1; j >= 0; --j) {
+                ev = ev * u2 + row[j];
+                od = od * u2 + row[K / 2 + j];
+            }
+            worst = std::max(worst, std::fabs(ev + u * od - kb_phi(h - 1.0 - q + 0.5 + u, h, b, nm)));
+            const int qm = W - 1 - q;   // the mirrored tap
+            worst = std::max(worst, std::fabs(ev - u * od - kb_phi(h - 1.0 - qm + 0.5 + u, h, b, nm)));
         }
     }
     if (!(worst <= 1e-7 * peak))
@@ -828,8 +843,10 @@ void workspace_bytes(const ml_plan_s *p, int nv, size_t *scratch, size_t *work)
     }
     const size_t ts = p->prec == ML_F32 ? 4 : 8;
     const GridGeom &g = p->g;
-    // subproblem tiles, then one tile per group of subproblems
+    // subproblem tiles, then one tile per group of subproblems, then (FP32)
+    // the box of cells each subproblem tile was written in (tile_boxes)
     *scratch = (size_t)(p->nsub + p->ngroups) * g.tile_cells() * nv * ts;
+    if (p->prec == ML_F32) *scratch = ((*scratch + 15) & ~(size_t)15) + (size_t)p->nsub * 16;
     // transform stages: extents go from L to K one dim at a time and back
     int64_t mx = 1;
     for (int stage = 0; stage <= p->d; ++stage) {
