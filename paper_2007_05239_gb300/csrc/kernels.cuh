@@ -1386,11 +1386,19 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
     int bc[3];
     bin_coords<D>(bin, a.nb0, a.nb1, bc);
     load_interp_tile<float, NV>(a, D, bc, tc, tile);
+    if (threadIdx.x < 2) tile[tc * NV + threadIdx.x] = 0.0f;   // read with zero weights only
     __syncthreads();
     const float *coords = static_cast<const float *>(a.coords);
     constexpr int ny = (D >= 2) ? W : 1, nz = (D >= 3) ? W : 1;
     constexpr int UY = (W <= 8) ? ny : 1;       // unroll the rows of small windows
     constexpr int UZ = (NV == 1 && W <= 8) ? nz : 1;
+    // an even tile edge makes every row start even up to the first tap's
+    // parity: each row is then read as NP aligned float pairs from the even
+    // index at or below its first tap, with the weights shifted by that
+    // parity (one zero weight before or after the W taps; the zero-weight
+    // terms add nothing, so the sums are those of the W taps in the same order)
+    constexpr int NP = W / 2 + 1;
+    const bool paired = (Pt & 1) == 0;
     // one or two vectors: the epilogue's loads (permutation, D^{-1/2}, input,
     // the previous output when accumulating) are issued before the taps, so
     // that their latency hides behind the tap sums
@@ -1406,28 +1414,66 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
         float acc[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) acc[c] = 0.0f;
-#pragma unroll UZ
-        for (int qz = 0; qz < nz; ++qz) {
-            float pz[NV];
+        if (paired) {
+            const int odd = o[0] & 1;
+            float wp[2 * NP];
 #pragma unroll
-            for (int c = 0; c < NV; ++c) pz[c] = 0.0f;
-#pragma unroll UY
-            for (int qy = 0; qy < ny; ++qy) {
-                const float *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
-                float r[NV];
-#pragma unroll
-                for (int c = 0; c < NV; ++c) r[c] = 0.0f;
-#pragma unroll
-                for (int qx = 0; qx < W; ++qx)
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) r[c] = fmaf(wx[qx], row[c * tc + qx], r[c]);
-                const float wyq = (D >= 2) ? wy[qy] : 1.0f;
-#pragma unroll
-                for (int c = 0; c < NV; ++c) pz[c] = fmaf(wyq, r[c], pz[c]);
+            for (int k = 0; k < 2 * NP; ++k) {
+                const float we = k < W ? wx[k < W ? k : 0] : 0.0f;
+                const float wo = (k >= 1 && k <= W) ? wx[k >= 1 && k <= W ? k - 1 : 0] : 0.0f;
+                wp[k] = odd ? wo : we;
             }
-            const float wzq = (D >= 3) ? wz[qz] : 1.0f;
+#pragma unroll UZ
+            for (int qz = 0; qz < nz; ++qz) {
+                float pz[NV];
 #pragma unroll
-            for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
+                for (int c = 0; c < NV; ++c) pz[c] = 0.0f;
+#pragma unroll UY
+                for (int qy = 0; qy < ny; ++qy) {
+                    const float *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0] - odd;
+                    float r[NV];
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) r[c] = 0.0f;
+#pragma unroll
+                    for (int kk = 0; kk < NP; ++kk)
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) {
+                            const float2 v = *reinterpret_cast<const float2 *>(row + c * tc + 2 * kk);
+                            r[c] = fmaf(wp[2 * kk], v.x, r[c]);
+                            r[c] = fmaf(wp[2 * kk + 1], v.y, r[c]);
+                        }
+                    const float wyq = (D >= 2) ? wy[qy] : 1.0f;
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) pz[c] = fmaf(wyq, r[c], pz[c]);
+                }
+                const float wzq = (D >= 3) ? wz[qz] : 1.0f;
+#pragma unroll
+                for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
+            }
+        } else {
+#pragma unroll UZ
+            for (int qz = 0; qz < nz; ++qz) {
+                float pz[NV];
+#pragma unroll
+                for (int c = 0; c < NV; ++c) pz[c] = 0.0f;
+#pragma unroll UY
+                for (int qy = 0; qy < ny; ++qy) {
+                    const float *row = tile + ((o[2] + qz) * Pt + o[1] + qy) * Pt + o[0];
+                    float r[NV];
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) r[c] = 0.0f;
+#pragma unroll
+                    for (int qx = 0; qx < W; ++qx)
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) r[c] = fmaf(wx[qx], row[c * tc + qx], r[c]);
+                    const float wyq = (D >= 2) ? wy[qy] : 1.0f;
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) pz[c] = fmaf(wyq, r[c], pz[c]);
+                }
+                const float wzq = (D >= 3) ? wz[qz] : 1.0f;
+#pragma unroll
+                for (int c = 0; c < NV; ++c) acc[c] = fmaf(wzq, pz[c], acc[c]);
+            }
         }
         if constexpr (kPrefetch) {
 #pragma unroll
@@ -1443,6 +1489,14 @@ template <int D, int W, int NV>
 __global__ void __launch_bounds__(256) k_interp_f32(const InterpArgs a)
 {
     interp_f32_block<D, W, NV>(a, blockIdx.x, a.kbp);
+}
+
+// one vector and a narrow window: 32 registers (eight CTAs per SM, every warp
+// slot) without spills; the epilogue's gathers want the warps
+template <int D, int W>
+__global__ void __launch_bounds__(256, 8) k_interp_f32_1v(const InterpArgs a)
+{
+    interp_f32_block<D, W, 1>(a, blockIdx.x, a.kbp);
 }
 
 // all layers of a batch in one launch, each writing its own output block:

@@ -283,8 +283,14 @@ static ml_status run_layer_dm(ml_plan_s *p, const ApplyVec &v, const ApplyOpts &
         const size_t smem = (size_t)tc * nv * sizeof(T);
         ProfScope pr("interp", st);
         if (f32) {
-            ML_TRY(set_smem(k_interp_f32<D, W, NV>, smem));
-            k_interp_f32<D, W, NV><<<p->nsub, 256, smem, st>>>(ia);
+            // two zero floats after the FP32 tile (read by the paired row loads)
+            if constexpr (NV == 1 && W <= 5) {
+                ML_TRY(set_smem(k_interp_f32_1v<D, W>, smem + 2 * sizeof(float)));
+                k_interp_f32_1v<D, W><<<p->nsub, 256, smem + 2 * sizeof(float), st>>>(ia);
+            } else {
+                ML_TRY(set_smem(k_interp_f32<D, W, NV>, smem + 2 * sizeof(float)));
+                k_interp_f32<D, W, NV><<<p->nsub, 256, smem + 2 * sizeof(float), st>>>(ia);
+            }
         } else {
             ML_TRY(set_smem(k_interp_f64<D, W, NV>, smem));
             k_interp_f64<D, W, NV><<<p->nsub, 256, smem, st>>>(ia);
@@ -549,7 +555,7 @@ ml_status run_batch_dm(ml_plan_s *const *L, int T, const ApplyVec &v, const Appl
     ML_CUDA(cudaGetLastError());
     {
         ProfScope pr("interp", st);
-        const size_t smem = (size_t)max_tile * NV * sizeof(float);
+        const size_t smem = (size_t)max_tile * NV * sizeof(float) + 2 * sizeof(float);   // tile + 2 zeros
         if (o.layer_vecs) {
             ML_TRY(set_smem(k_interp_f32_batch<D, W, NV>, smem));
             k_interp_f32_batch<D, W, NV><<<dim3(max_nsub, T), 256, smem, st>>>(
