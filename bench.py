@@ -771,13 +771,14 @@ DW_OPS_PER_FMA = 10
 
 NCU_TRAFFIC = {
     # k_spread_f32<3,5,1>, both layers of the 10-megapixel image (one launch
-    # each, ncu --set full of the apply-mode run): 794.4 and 513.0 MB, mean
-    # 653.7 MB per launch
-    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (653.7e6, "daec78ce9e14685b",
+    # each, ncu --set full of the apply-mode run): 515.2 and 346.4 MB, mean
+    # 430.8 MB per launch
+    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (430.8e6, "0f75b0727561771e",
                                                       "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
-                                                      "the two layers' launches; includes the subproblem tiles "
-                                                      "written for the fold (192 MB) and 32-byte sectors of the "
-                                                      "random input gathers"),
+                                                      "the two layers' launches; the tiles are written only within "
+                                                      "the box of cells each subproblem's taps reach (14 MB); the "
+                                                      "rest is the point data and 32-byte sectors of the random "
+                                                      "input gathers"),
 }
 KERNEL_SOURCES = ["paper_2007_05239_gb300/csrc/kernels.cuh", "paper_2007_05239_gb300/csrc/launch.cuh"]
 
