@@ -430,7 +430,7 @@ __global__ void k_dgks(const double *__restrict__ part, int nblk, const double *
 
 // out[:, i] = Q[:, 0:ncv] S[:, i] for i < kk (S column-major ncv x kk), in
 // double-word; each row's accumulators for 16 columns at a time in registers
-__global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv,
+__global__ void __launch_bounds__(256, 3) k_combine_dw(const double *__restrict__ Q, int64_t ldq, int64_t n, int ncv,
                                                    const double *__restrict__ S, int kk, double *out, int64_t ldo)
 {
     // the first kCombineFp64 of every 16 outputs on the FP64 pipe (its own
@@ -453,8 +453,10 @@ __global__ void __launch_bounds__(256) k_combine_dw(const double *__restrict__ Q
             for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int k = 0; k < KF; ++k) dacc[k] = 0.0;
+            double qn = Q[r];                            // the next column's value, loaded a column ahead
             for (int c = 0; c < ncv; ++c) {
-                const double qd = Q[(int64_t)c * ldq + r];
+                const double qd = qn;
+                if (c + 1 < ncv) qn = Q[(int64_t)(c + 1) * ldq + r];
                 const float2 q = dword::from_double(qd);
                 const float2 *srow = ss + (int64_t)c * kk + i0;
                 const double *drow = sd + (int64_t)c * kk + i0;
