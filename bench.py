@@ -773,7 +773,7 @@ NCU_TRAFFIC = {
     # k_spread_f32<3,5,1>, both layers of the 10-megapixel image (one launch
     # each, ncu --set full of the apply-mode run): 515.2 and 346.4 MB, mean
     # 430.8 MB per launch
-    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (430.8e6, "0f75b0727561771e",
+    ("image_discs_n1e7_T2", "f32", "spread", 5, 1): (430.8e6, "a75fdb2bef51fef1",
                                                       "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
                                                       "the two layers' launches; the tiles are written only within "
                                                       "the box of cells each subproblem's taps reach (14 MB); the "

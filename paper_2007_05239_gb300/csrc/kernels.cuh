@@ -794,8 +794,8 @@ __device__ __forceinline__ void spread_f32_block(const SpreadArgs &a, const int 
         }
         return;
     }
-    // only the box of cells the taps reached: rows of bx cells (contiguous
-    // in the cell-major output), by x bz of them
+    // only the box of cells the taps reached: (hi_y - lo_y) (hi_z - lo_z) rows
+    // of hi_x - lo_x cells, each row contiguous in the cell-major output
     int lo[3], hi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -1395,8 +1395,9 @@ __device__ __forceinline__ void interp_f32_block(const InterpArgs &a, const int 
     // an even tile edge makes every row start even up to the first tap's
     // parity: each row is then read as NP aligned float pairs from the even
     // index at or below its first tap, with the weights shifted by that
-    // parity (one zero weight before or after the W taps; the zero-weight
-    // terms add nothing, so the sums are those of the W taps in the same order)
+    // parity (zero weights before or after the W taps, 2 NP - W of them; the
+    // zero-weight terms add nothing, so the sums are those of the W taps in the
+    // same order)
     constexpr int NP = W / 2 + 1;
     const bool paired = (Pt & 1) == 0;
     // one or two vectors: the epilogue's loads (permutation, D^{-1/2}, input,
